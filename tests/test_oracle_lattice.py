@@ -1,0 +1,156 @@
+"""Pins of the oracle's lattice Boltzmann part (Sec. II A) against what the
+paper and the mathematics fix: Tab. I, the moment identities of the
+equilibrium and of the Guo source, exact mass conservation, the momentum
+balance of a uniformly forced periodic box, and the Poiseuille profile."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2503_20605_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_tab1():
+    rows = []
+    for line in open(os.path.join(GOLD, "d3q19_tab1.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        g, cnt, c2, w = line.split()
+        rows.append((g, int(cnt), int(c2), Fraction(w)))
+    return rows
+
+
+def test_velocity_set_matches_table_1(orc):
+    c, w, opp = orc.d3q19()
+    c2 = (c ** 2).sum(1)
+    for group, count, speed2, weight in read_tab1():
+        sel = np.where(c2 == speed2)[0]
+        assert len(sel) == count, group
+        assert np.allclose(w[sel], float(weight), rtol=0, atol=1e-16), group
+    # the paper's index groups: 0 rest, 1-6 axis vectors, 7-18 diagonals
+    assert c2[0] == 0 and np.all(c2[1:7] == 1) and np.all(c2[7:] == 2)
+    assert len({tuple(v) for v in c}) == 19
+    for i in range(19):
+        assert np.all(c[opp[i]] == -c[i])
+
+
+def test_lattice_isotropy(orc):
+    c, w, _ = orc.d3q19()
+    cs2 = 1.0 / 3.0
+    d = np.eye(3)
+    assert math.isclose(w.sum(), 1.0, abs_tol=1e-15)
+    assert np.allclose(np.einsum("i,ia->a", w, c), 0, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), cs2 * d, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", w, c, c, c), 0, atol=1e-16)
+    four = np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c)
+    want = cs2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                       + np.einsum("ad,bc->abcd", d, d))
+    assert np.allclose(four, want, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_equilibrium_moments(orc, seed):
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + 0.1 * rng.standard_normal()
+    u = 0.05 * rng.standard_normal(3)
+    c, w, _ = orc.d3q19()
+    feq = orc.feq(rho, u)
+    assert math.isclose(feq.sum(), rho, rel_tol=1e-14)
+    assert np.allclose(feq @ c, rho * u, atol=1e-15)
+    # second moment of the second-order equilibrium: rho cs^2 I + rho u u
+    assert np.allclose(np.einsum("i,ia,ib->ab", feq, c, c), rho / 3 * np.eye(3) + rho * np.outer(u, u),
+                       atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_guo_source_moments(orc, seed):
+    rng = np.random.default_rng(seed)
+    tau = 0.6 + rng.uniform()
+    u = 0.05 * rng.standard_normal(3)
+    F = 1e-3 * rng.standard_normal(3)
+    c, _, _ = orc.d3q19()
+    S = orc.guo_source(tau, u, F)
+    k = 1.0 - 1.0 / (2.0 * tau)
+    assert abs(S.sum()) < 1e-18
+    assert np.allclose(S @ c, k * F, rtol=1e-13, atol=1e-19)
+    assert np.allclose(np.einsum("i,ia,ib->ab", S, c, c), k * (np.outer(u, F) + np.outer(F, u)), atol=1e-17)
+
+
+def test_collision_conserves_mass_and_adds_force(orc):
+    rng = np.random.default_rng(5)
+    c, w, _ = orc.d3q19()
+    f = w * (1.0 + 0.01 * rng.standard_normal(19))
+    F = 1e-3 * rng.standard_normal(3)
+    fs, rho, u = orc.collide_cell(0.8, F, f)
+    assert math.isclose(rho, f.sum(), rel_tol=1e-15)
+    assert np.allclose(u, (f @ c + F / 2) / rho, rtol=1e-13)
+    assert math.isclose(fs.sum(), f.sum(), rel_tol=1e-15)
+    # BGK keeps rho U, Guo adds (1 - 1/2tau) F and -(1/tau)(j - rho U) = F/(2 tau)
+    assert np.allclose(fs @ c, f @ c + F, atol=1e-16)
+    # at tau = 1 the collision relaxes fully: f* = feq + S
+    fs1, rho1, u1 = orc.collide_cell(1.0, F, f)
+    assert np.allclose(fs1, orc.feq(rho1, u1) + orc.guo_source(1.0, u1, F), atol=1e-17)
+
+
+@pytest.mark.parametrize("walls", [1, 0])
+def test_exact_mass_conservation(orc, walls):
+    nx, ny, nz = 10, 9, 8
+    p = orc.make_params(nx, ny, nz, walls=walls, tau_out=0.7, body_force=(1e-5, -2e-5, 3e-6))
+    s = orc.Sim(p)
+    _, w, _ = orc.d3q19()
+    s.set_populations(I.perturbed_populations(s.cells, w, seed=3, amp=1e-2))
+    m0 = math.fsum(s.populations())
+    s.step(300)
+    m1 = math.fsum(s.populations())
+    assert abs(m1 - m0) <= 1e-13 * m0
+    # the oracle's own (compensated) mass observable agrees with the exact sum
+    assert math.isclose(s.observe()["mass"], m1, rel_tol=1e-15)
+
+
+def test_uniform_force_periodic_momentum(orc):
+    """Fully periodic box with a uniform force density g: every step adds g
+    per cell to the total momentum of the post-collision state."""
+    nx = ny = nz = 6
+    g = np.array([1e-5, -3e-6, 2e-6])
+    p = orc.make_params(nx, ny, nz, walls=0, tau_out=0.9, body_force=tuple(g))
+    s = orc.Sim(p)
+    c, w, _ = orc.d3q19()
+    steps = 40
+    s.step(steps)
+    f = s.populations().reshape(19, -1)
+    mom = (c.T @ f).sum(1)
+    assert np.allclose(mom, steps * g * s.cells, rtol=1e-10)
+    rho, u = s.macros()
+    # uniform state: U = (momentum before the step + g/2) per unit mass
+    assert np.allclose(u.reshape(3, -1).mean(1), (steps - 0.5) * g, rtol=1e-10)
+
+
+def poiseuille(orc, tau, steps, nz=18):
+    g = 1e-6
+    p = orc.make_params(4, 4, nz, walls=1, tau_out=tau, body_force=(g, 0.0, 0.0))
+    s = orc.Sim(p)
+    s.step(steps)
+    rho, u = s.macros()
+    ux = u.reshape(3, nz - 2, 4, 4)[0].mean(axis=(1, 2))
+    Z = np.arange(1, nz - 1)
+    nu = (tau - 0.5) / 3.0
+    exact = g / (2.0 * nu) * (Z - 0.5) * (nz - 1.5 - Z)   # walls at Z = 1/2 and nz - 3/2
+    return ux, exact
+
+
+def test_poiseuille_exact_at_magic_tau(orc):
+    """BGK + halfway bounce-back puts the walls exactly half-way for
+    (tau - 1/2)^2 = 3/16: the steady profile is the exact parabola."""
+    tau = 0.5 + math.sqrt(3.0) / 4.0
+    ux, exact = poiseuille(orc, tau, 12000)
+    assert np.max(np.abs(ux - exact)) / exact.max() < 1e-9
+
+
+def test_poiseuille_tau1(orc):
+    ux, exact = poiseuille(orc, 1.0, 8000)
+    err = np.max(np.abs(ux - exact)) / exact.max()
+    assert err < 5e-3, err

@@ -1,0 +1,72 @@
+"""Physics pins of the oracle's full time step: Laplace pressure of a free
+droplet (App. C: Delta p = 2 sigma / R_c without Pi), the ordering of the
+equilibrium contact angle with theta_eq (Sec. II C: A sets the angle), mass
+conservation with a membrane, and the tau field for lambda != 1."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2503_20605_gb300 import inputs as I
+
+
+@pytest.mark.slow
+def test_laplace_pressure_free_droplet(orc):
+    n, R, sigma = 32, 8.0, 0.01
+    xyz, tri = I.icosphere(3, R, (16.0, 16.0, 16.0))
+    s = orc.Sim(orc.make_params(n, n, n, walls=0, tau_out=1.0, sigma=sigma))
+    s.set_membrane(xyz, tri)
+    s.step(1000)
+    rho, u = s.macros()
+    o = s.observe()
+    Z, Y, X = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((X - o["cx"]) ** 2 + (Y - o["cy"]) ** 2 + (Z - o["cz"]) ** 2).ravel()
+    dp = (rho[r < R - 3].mean() - rho[r > R + 3].mean()) / 3.0    # p = cs^2 rho
+    RV = (3 * o["volume"] / (4 * math.pi)) ** (1 / 3)
+    assert abs(dp / (2 * sigma / RV) - 1) < 0.03
+    assert np.abs(u).max() < 1e-4        # spurious currents only
+
+
+@pytest.mark.slow
+def test_equilibrium_angle_follows_theta_eq(orc):
+    """Droplets released at h = xi spread from the sphere (180 deg) towards
+    their imposed angle: the measured angles keep the order of theta_eq."""
+    got = []
+    for th in (60.0, 120.0):
+        sp = I.DropletSpec(24, 24, 18, 6.0, 3, 0.01, th, 1.5, tau=1.0)
+        xyz, tri = sp.mesh()
+        A = orc.wetting_A(sp.sigma, math.radians(th), sp.xi)
+        s = orc.Sim(orc.make_params(24, 24, 18, tau_out=1.0, sigma=sp.sigma, wetting=1, A=A, xi=sp.xi,
+                                    volume_correction=1))
+        s.set_membrane(xyz, tri)
+        s.step(1500)
+        o = s.observe()
+        assert s.clamped() == 0
+        got.append(o["theta_RV"])
+    assert got[0] < got[1] < 179.0
+    assert got[1] - got[0] > 15.0
+
+
+def test_mass_conserved_with_membrane(orc):
+    sp = I.workload_parity_32()
+    xyz, tri = sp.mesh()
+    A = orc.wetting_A(sp.sigma, math.radians(sp.theta_deg), sp.xi)
+    s = orc.Sim(orc.make_params(32, 32, 32, tau_out=1.0, sigma=sp.sigma, wetting=1, A=A, xi=sp.xi))
+    s.set_membrane(xyz, tri)
+    m0 = math.fsum(s.populations())
+    s.step(20)
+    assert abs(math.fsum(s.populations()) - m0) < 1e-13 * m0
+
+
+def test_viscosity_ratio_sets_tau_inside(orc):
+    sp = I.DropletSpec(24, 24, 24, 6.0, 3, 0.01, 90.0, 2.0, tau=0.8, lam=10.0)
+    xyz, tri = sp.mesh()
+    s = orc.Sim(orc.make_params(24, 24, 24, tau_out=sp.tau, tau_in=sp.tau_in, sigma=sp.sigma))
+    s.set_membrane(xyz, tri)
+    s.step(1)
+    tau = s.tau()
+    n_in = int((tau == sp.tau_in).sum())
+    assert math.isclose(sp.tau_in, 0.5 + 10 * 0.3)
+    assert set(np.unique(tau)) == {sp.tau, sp.tau_in}
+    # the inside cells fill the droplet volume up to the surface discretisation
+    assert abs(n_in / orc.mesh_volume(xyz, tri) - 1) < 0.1
