@@ -1,0 +1,321 @@
+"""Throughput of the IB-LB wetting time step on GB300.
+
+Workload (default): the 128^3 statics droplet -- D3Q19, tau = 1, walls at
+Z = 0 and Z = 127, L5 icosphere (10 242 nodes, 20 480 faces), R = 24,
+sigma = 0.005, xi = 2.4, theta_eq = 90 deg, volume correction on -- with
+populations stored as FP16 offsets (the headline) and, as a second line of
+numbers in the same JSON, as FP32.  One step = the whole hot path: nodal
+forces, binned spread, stream-collide, interpolation + advection, FP64 mesh
+reductions + volume correction.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Value: MLUPS = fluid cells x steps / device time of the steps (CUDA events on
+the library's stream), L2 flushed between timed steps.  Under torchrun each
+rank runs its own replica of the workload (the droplet does not shard; the
+value sums the cells of all ranks over the slowest rank's time).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and IB nodes/s at 128^3; FP16-store vs FP32 at <=1 deg contact-angle error"
+BYTES_PER_CELL = {"f32": 152, "f16": 76, "bf16": 76}
+FLUSH_BYTES = 512 << 20          # > 129 MB L2
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def lb_source_sha():
+    h = hashlib.sha1()
+    for f in ("lb.cu", "iblb_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2503_20605_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(storage):
+    """DRAM bytes per launch of the stream-collide kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"lb_kernel_{storage}_statics128.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != lb_source_sha():
+        return None
+    return float(t.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_ctx(iblb, spec, storage, stream):
+    lat = iblb.lattice_desc(spec.nx, spec.ny, spec.nz, tau_out=spec.tau, lam=spec.lam, storage=storage)
+    phys = iblb.physics_desc(sigma=spec.sigma, theta_eq_deg=spec.theta_deg, xi=spec.xi,
+                             volume_correction=int(spec.volume_correction))
+    ctx = iblb.iblb_create(lat, phys, stream)
+    xyz, tri = spec.mesh()
+    iblb.iblb_set_membrane(ctx, 0, xyz, tri)
+    return ctx, xyz, tri
+
+
+def launches_per_step(spec):
+    n = 1 + 3 + 1 + 1 + 1            # forces; scan x2 + fill; spread; stream-collide; interp/advect
+    if spec.lam != 1.0:
+        n += 3
+    if spec.volume_correction:
+        n += 3
+    return n
+
+
+def run_gpu(spec, storage, steps, warmup, torch, iblb, flush):
+    """Device-timed steps with L2 flushed before each; returns per-phase sums."""
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx, xyz, tri = make_ctx(iblb, spec, storage, stream)
+    try:
+        iblb.iblb_autotune(ctx, os.path.join(ROOT, "paper_2503_20605_gb300", "_build", "autotune.txt"))
+        iblb.iblb_set_option(ctx, iblb.IBLB_OPT_PROFILE, 1)
+        for _ in range(warmup):
+            flush.zero_()
+            iblb.iblb_step(ctx, 1)
+        iblb.iblb_sync(ctx)
+        iblb.iblb_reset_profile(ctx)
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            iblb.iblb_step(ctx, 1)
+        iblb.iblb_sync(ctx)
+        torch.cuda.synchronize()
+        phases, step_ms, n = iblb.iblb_get_profile(ctx)
+        obs = iblb.iblb_observe(ctx, 0)
+        info = iblb.iblb_info(ctx, 0)
+    finally:
+        iblb.iblb_destroy(ctx)
+    return dict(phases=phases, step_ms=step_ms, n=n, obs=obs, cells=info["cells"], nodes=info["n_nodes"])
+
+
+def run_e2e(spec, storage, steps, warmup, torch, iblb):
+    """Through the public API with host buffers: each step uploads the node
+    positions from pinned host memory, advances one step and reads back the
+    node positions and the observables (contact angle, volume, mass)."""
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx, xyz, tri = make_ctx(iblb, spec, storage, stream)
+    try:
+        pin = torch.empty((len(xyz), 3), dtype=torch.float64, pin_memory=True)
+        host = pin.numpy()
+        host[:] = xyz
+        for _ in range(warmup):
+            iblb.iblb_set_nodes(ctx, 0, host)
+            iblb.iblb_step(ctx, 1)
+            iblb.iblb_get_nodes(ctx, 0, host)
+            iblb.iblb_observe(ctx, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            iblb.iblb_set_nodes(ctx, 0, host)
+            iblb.iblb_step(ctx, 1)
+            iblb.iblb_get_nodes(ctx, 0, host)
+            iblb.iblb_observe(ctx, 0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        cells = iblb.iblb_info(ctx, 0)["cells"]
+    finally:
+        iblb.iblb_destroy(ctx)
+    n = len(xyz)
+    return dict(value=cells * steps / dt / 1e6, unit="MLUPS", h2d_bytes_per_step=n * 3 * 8,
+                d2h_bytes_per_step=n * 3 * 8 + 8 + 8 * 15)
+
+
+def cpu_oracle(spec, budget_s, steps_cap):
+    """The FP64 oracle on the host cores: full steps of the same workload
+    until the time budget is used (at least one)."""
+    import oracle.oracle as O
+    O.build()
+    xyz, tri = spec.mesh()
+    A = O.wetting_A(spec.sigma, math.radians(spec.theta_deg), spec.xi)
+    s = O.Sim(O.make_params(spec.nx, spec.ny, spec.nz, tau_out=spec.tau, tau_in=spec.tau_in, sigma=spec.sigma,
+                            wetting=1, A=A, xi=spec.xi, volume_correction=int(spec.volume_correction)))
+    s.set_membrane(xyz, tri)
+    t0 = time.perf_counter()
+    n = 0
+    while n < steps_cap and (n == 0 or time.perf_counter() - t0 < budget_s):
+        s.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n, dt, s.cells, len(xyz)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+
+    from paper_2503_20605_gb300 import inputs as I
+    spec = I.workload_statics_128(90.0, args.storage)
+    rank, world, local = dist_env()
+    workload = "statics droplet 128^3 (D3Q19 tau=1, walls z, L5 icosphere 10242 nodes, R=24, sigma=0.005, " \
+               "xi=2.4, theta_eq=90, volume correction)"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        n, dt, cells, nodes = cpu_oracle(spec, budget_s=120.0, steps_cap=max(1, args.steps + args.warmup))
+        cores = 1
+        v = cells * n / dt / 1e6
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / n * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload, "storage": "f64 (oracle)", "cells": cells, "nodes": nodes},
+                "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                 "sample": f"{n} full oracle steps of the workload (time budget 120 s)"},
+                "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2503_20605_gb300 import iblb
+    iblb.lib()
+
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    barrier()
+    with Clocks(local) as clk:
+        main_run = run_gpu(spec, args.storage, args.steps, args.warmup, torch, iblb, flush)
+    barrier()
+    spec32 = I.workload_statics_128(90.0, "f32")
+    run32 = run_gpu(spec32, "f32", args.steps, args.warmup, torch, iblb, flush)
+    e2e = run_e2e(spec, args.storage, max(20, args.steps // 4), 3, torch, iblb)
+
+    step_ms = main_run["step_ms"]
+    if world > 1:
+        t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    K = main_run["n"]
+    cells, nodes = main_run["cells"], main_run["nodes"]
+    value = world * cells * K / (step_ms * 1e-3) / 1e6
+    ph = main_run["phases"]
+    ib_ms = ph["forces"] + ph["spread"] + ph["inout"] + ph["advect"] + ph["reduce"]
+    lb_ms = ph["lb"] / K
+    peak, src = peaks()
+    bpc = BYTES_PER_CELL[args.storage]
+    achieved = cells * bpc / (lb_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(args.storage)
+    ph32 = run32["phases"]
+    value32 = cells * run32["n"] / (run32["step_ms"] * 1e-3) / 1e6
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n, dt, c_cells, _ = cpu_oracle(spec, args.cpu_budget, 1000)
+        cpu = {"value": c_cells * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{n} full FP64 oracle steps of the same 128^3 workload on one host core"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload, "storage": args.storage, "cells": cells, "nodes": nodes,
+                       "grid": [spec.nx, spec.ny, spec.nz], "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "ib_nodes_per_s": world * nodes * K / (ib_ms * 1e-3),
+            "phase_ms_per_step": {k: v / K for k, v in ph.items()},
+            "fp32": {"value": value32, "unit": "MLUPS",
+                     "phase_ms_per_step": {k: v / run32["n"] for k, v in ph32.items()},
+                     "ib_nodes_per_s": nodes * run32["n"] / ((ph32["forces"] + ph32["spread"] + ph32["inout"]
+                                                              + ph32["advect"] + ph32["reduce"]) * 1e-3)},
+            "roofline": {"bound": "hbm", "kernel": "lb_kernel (fused stream-collide)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
+                         "algorithmic_bytes_per_cell": bpc, "traffic": traffic},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step(spec) * K,
+            "clocks": clk.summary(),
+            "theta_RV_deg_after": main_run["obs"]["theta_RV_deg"],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

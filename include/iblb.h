@@ -1,0 +1,267 @@
+/*
+ * iblb.h -- C ABI of libiblb, a single-GPU (sm_103a) implementation of the
+ * time step of the immersed boundary - lattice Boltzmann (IB-LB) method for
+ * wetting of Bellantoni et al., "Immersed boundary - lattice Boltzmann method
+ * for wetting problems" (arXiv 2503.20605).
+ *
+ * One time step (Sec. II) advances a D3Q19 BGK lattice with Guo forcing and
+ * bounce-back walls (Sec. II A, eqs. LBE, hydro_var1/2), coupled through the
+ * four-point delta kernel (eqs. force_spread, vel_interpolation) to a closed
+ * triangulated droplet membrane carrying surface-tension forces (Sec. II B)
+ * and the regularised wall interaction Pi(h) that sets the contact angle
+ * (Sec. II C, eqs. disjoin-p, A_choice); membrane nodes move by forward Euler.
+ *
+ * Conventions
+ *   - Units: lattice units, dx = dt = 1 (Sec. III).
+ *   - Box: nx * ny * nz lattice nodes, periodic in x and y.  With walls on,
+ *     layers Z = 0 and Z = nz - 1 are solid (halfway bounce-back, resting
+ *     walls) and the fluid is Z = 1 .. nz - 2; the bottom wall plane is
+ *     z = 1/2.  With walls off the box is periodic in z too.
+ *   - Lattice arrays exchanged through this API cover the FLUID cells only,
+ *     layout a[k][z'][y][x] (x fastest), z' = Z - 1 with walls, Z without.
+ *   - Populations are absolute f_i (not offsets), velocity order:
+ *       0 (0,0,0); 1 (+x) 2 (-x) 3 (+y) 4 (-y) 5 (+z) 6 (-z);
+ *       7 (+x+y) 8 (-x-y) 9 (+x-y) 10 (-x+y) 11 (+y+z) 12 (-y-z)
+ *       13 (+y-z) 14 (-y+z) 15 (+x+z) 16 (-x-z) 17 (+x-z) 18 (-x+z)
+ *     (Tab. I groups; the order inside a group is this library's choice).
+ *   - Membrane nodes are (x, y, z) triples in lattice coordinates; faces are
+ *     int32 triples of node indices, counter-clockwise seen from outside.
+ *
+ * Ownership and threading
+ *   - Every host pointer argument is owned by the caller and only read (or
+ *     written, for outputs) during the call; the library keeps no reference.
+ *     Output buffers are caller-allocated with the sizes stated per function.
+ *   - A context owns all of its device memory and one CUDA stream of its own.
+ *     Work is ordered after the work already queued on the caller's stream
+ *     given at creation, and the caller's stream is made to wait for the
+ *     context's work before each call returns (stream ordering both ways).
+ *   - Calls that return data to the host synchronise; iblb_step does not.
+ *   - A context must not be used from two host threads at once.
+ *
+ * Errors
+ *   - Every int-returning function returns IBLB_OK (0) or a negative
+ *     IBLB_E_* code and stores a message readable with iblb_last_error().
+ *   - Device-side conditions (NaN, a node moving more than half a lattice
+ *     unit in one step, a list overflow) set a status word that iblb_sync()
+ *     and the data-returning calls report as IBLB_E_UNSTABLE / IBLB_E_OVERFLOW.
+ *   - No exception or longjmp crosses the ABI.
+ */
+#ifndef IBLB_H
+#define IBLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define IBLB_OK 0
+#define IBLB_E_ARG -1       /* invalid argument (sizes, tau <= 1/2, ...)      */
+#define IBLB_E_MESH -2      /* membrane mesh not closed / not orientable / V<=0 */
+#define IBLB_E_NOMEM -3     /* device or host allocation failed               */
+#define IBLB_E_CUDA -4      /* a CUDA call failed                             */
+#define IBLB_E_UNSTABLE -5  /* NaN, non-positive density or node jump > 0.5  */
+#define IBLB_E_TIMEOUT -6   /* a bounded device wait gave up                  */
+#define IBLB_E_STATE -7     /* call not valid in the context's state          */
+#define IBLB_E_IO -8        /* checkpoint file error                          */
+#define IBLB_E_OVERFLOW -9  /* a per-tile or per-column list exceeded its cap */
+
+/* ---- population storage (the arithmetic is FP32 in every case) ---------- */
+#define IBLB_STORE_F32 0   /* offsets f_i - w_i rho0 stored as float          */
+#define IBLB_STORE_F16 1   /* offsets stored as IEEE half, round-to-nearest   */
+#define IBLB_STORE_BF16 2  /* offsets stored as bfloat16, round-to-nearest    */
+
+/* ---- wetting models ------------------------------------------------------ */
+#define IBLB_WET_OFF 0     /* no wall interaction                              */
+#define IBLB_WET_THETA 1   /* A from theta_eq by eq. A_choice                  */
+#define IBLB_WET_RAW 2     /* A given directly                                 */
+
+/* Lattice and fluid (Sec. II A, Sec. III). */
+typedef struct {
+    int nx, ny, nz;        /* full box in lattice nodes; nx, ny >= 8; nz >= 8 with walls */
+    int walls;             /* 1: bounce-back walls at Z = 0 and Z = nz-1; 0: periodic z  */
+    double tau_out;        /* BGK relaxation time outside the droplet, > 1/2            */
+    double lambda;         /* viscosity ratio mu_in/mu_out (eq. def_lambda); inside
+                              tau_in = 1/2 + lambda (tau_out - 1/2); 1 disables the
+                              in/out classification                                     */
+    double rho0;           /* initial density (Sec. III: 1)                             */
+    int storage;           /* IBLB_STORE_*; the same for every droplet of a context     */
+    double body_force[3];  /* uniform force density on every fluid cell                 */
+} iblb_lattice_desc;
+
+/* Membrane physics (Sec. II B, II C). */
+typedef struct {
+    double sigma;          /* surface tension                                           */
+    int wetting;           /* IBLB_WET_*                                                */
+    double theta_eq_deg;   /* equilibrium contact angle, degrees (IBLB_WET_THETA)       */
+    double A;              /* interaction strength (IBLB_WET_RAW)                      */
+    double xi;             /* regularising length scale xi > 0                          */
+    int n, m;              /* exponents of Pi(h), n > m > 1 (the paper uses 6, 3)      */
+    double h_min_frac;     /* near-wall guard: h_eff = max(h, h_min_frac * xi); 0 = off */
+    int volume_correction; /* 1: after each step rescale the mesh about its node
+                              centroid to the initial volume (not in the paper)       */
+} iblb_physics_desc;
+
+/* Observables of one droplet (Sec. III, App. C), FP64. */
+typedef struct {
+    double mass;           /* sum over fluid cells of sum_i f_i                         */
+    double volume;         /* enclosed mesh volume                                      */
+    double area;           /* mesh area                                                 */
+    double centroid[3];    /* mean of the node positions                                */
+    double zmin, zmax;     /* lowest / highest node                                     */
+    double theta_R0_deg;   /* angle from the half-height l = (zmax-zmin)/2, eq. angleh,
+                              with R0 = radius of the initial volume                    */
+    double theta_RV_deg;   /* same with the current volume-equivalent radius           */
+    double rc_cut;         /* contact radius, protocol (i): mesh edges crossing the
+                              plane z = 1/2 + zcut_frac*R0, mean distance from their
+                              centre                                                    */
+    double rc_flat;        /* contact radius, protocol (ii): sqrt(chi_eps / pi)         */
+    double n_cut;          /* number of edges crossing the protocol (i) plane           */
+    double chi_flat;       /* area of the flat lower-half faces, protocol (ii)          */
+    int status;            /* IBLB_OK or the pending device status                      */
+    int clamped;           /* nodes clamped by the near-wall guard in the last step     */
+} iblb_obs;
+
+/* Per-phase timing slots returned by iblb_get_profile. */
+#define IBLB_PH_FORCES 0   /* nodal forces + binning (a1)                               */
+#define IBLB_PH_SPREAD 1   /* scan, fill, deterministic gather-spread (a2)              */
+#define IBLB_PH_INOUT 2    /* in/out ray casting (a3)                                   */
+#define IBLB_PH_LB 3       /* fused stream-collide (a4)                                 */
+#define IBLB_PH_ADVECT 4   /* interpolation + advection (a5)                            */
+#define IBLB_PH_REDUCE 5   /* FP64 reductions + volume correction (a6)                  */
+#define IBLB_NPHASE 6
+
+/* Options for iblb_set_option. */
+#define IBLB_OPT_GRAPHS 0     /* 1 (default): replay captured CUDA graphs of one step    */
+#define IBLB_OPT_PROFILE 1    /* 1: record CUDA events around each phase (adds a sync
+                                 per step); 0 (default)                                  */
+#define IBLB_OPT_LB_BLOCK 2   /* threads (= cells) per block of the stream-collide
+                                 kernel (64..512, multiple of 32); 0 = default 256        */
+#define IBLB_OPT_LB_PERSISTENT 3 /* 1: stream-collide grid of SMs x resident blocks that
+                                 walks the cell blocks of all droplets; 0: one block
+                                 per cell block (default)                                */
+
+typedef struct iblb_ctx iblb_ctx;
+
+/* Library version string (static storage). */
+const char *iblb_version(void);
+
+/* Message of the last error on ctx (ctx may be NULL for creation errors);
+ * static or context-owned storage, valid until the next call on ctx. */
+const char *iblb_last_error(const iblb_ctx *ctx);
+
+/* Eq. A_choice: A = sigma (m-1)(n-1) / ((n-m) xi) (1 + cos theta_eq).
+ * Writes *A; IBLB_E_ARG if xi <= 0 or n <= m. */
+int iblb_wetting_A(double sigma, double theta_eq_deg, double xi, int n, int m, double *A);
+
+/* Create a context holding one droplet (lattice + membrane) on the current
+ * CUDA device.  stream: cudaStream_t of the caller (NULL = legacy default).
+ * The lattice starts at rest, f_i = w_i rho0 (Sec. III).  The membrane is set
+ * with iblb_set_membrane.  IBLB_E_ARG on invalid descriptors. */
+int iblb_create(const iblb_lattice_desc *lat, const iblb_physics_desc *phys, void *stream,
+                iblb_ctx **out);
+
+/* Create a context holding n independent droplets with their own boxes and
+ * parameters (arrays of n descriptors, all with the same storage).  Each
+ * phase of a step runs as one launch over all droplets; a droplet of a batch
+ * evolves bitwise as it would alone. */
+int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_desc *phys,
+                      void *stream, iblb_ctx **out);
+
+/* Free all device and host memory of ctx (NULL is ignored). */
+void iblb_destroy(iblb_ctx *ctx);
+
+/* Number of droplets, and for droplet k its fluid cells and membrane sizes. */
+int iblb_info(const iblb_ctx *ctx, int k, int *n_drops, int64_t *cells, int *n_nodes, int *n_tri);
+
+/* Set the membrane of droplet k (Sec. II A: closed triangular mesh).
+ * xyz: host, 3*n_nodes doubles; tri: host, 3*n_tri int32, CCW from outside.
+ * The mesh must be closed and orientable with Euler characteristic 2 and
+ * positive volume (IBLB_E_MESH otherwise).  Records the initial volume V0.
+ * All membranes of a batch must be set before the first step; calling it
+ * again replaces the membrane (and resets V0). */
+int iblb_set_membrane(iblb_ctx *ctx, int k, const double *xyz, int n_nodes, const int32_t *tri,
+                      int n_tri);
+
+/* Overwrite / read the node positions of droplet k (host, 3*n_nodes doubles). */
+int iblb_set_nodes(iblb_ctx *ctx, int k, const double *xyz);
+int iblb_get_nodes(iblb_ctx *ctx, int k, double *xyz);
+
+/* Overwrite / read the populations of droplet k: host, 19*cells doubles,
+ * absolute f_i, fluid-cell layout (see Conventions).  Values are rounded to
+ * the context's storage on set. */
+int iblb_set_populations(iblb_ctx *ctx, int k, const double *f);
+int iblb_get_populations(iblb_ctx *ctx, int k, double *f);
+
+/* Density and velocity of droplet k at the end of the last step, evaluated
+ * from the stored post-collision populations and that step's force density:
+ * rho = sum_i f*_i, U = (sum_i c_i f*_i - F/2) / rho (equal to eq. hydro_var2
+ * of the step).  rho: cells doubles, u: 3*cells doubles ([k][cell]). */
+int iblb_get_macros(iblb_ctx *ctx, int k, double *rho, double *u);
+
+/* Evaluate, for the current node positions and without advancing time, the
+ * nodal forces (Sec. II B, II C), the spread force density (eq. force_spread)
+ * and, with lambda != 1, the in/out classification of every cell. */
+int iblb_compute_forces(iblb_ctx *ctx);
+
+/* Results of the last force evaluation (iblb_compute_forces or a step) for
+ * droplet k: phi (3*n_nodes doubles), F (3*cells doubles, [k][cell], body
+ * force included), inside (cells bytes, 1 inside / 0 outside). */
+int iblb_get_node_forces(iblb_ctx *ctx, int k, double *phi);
+int iblb_get_force_density(iblb_ctx *ctx, int k, double *F);
+int iblb_get_inside(iblb_ctx *ctx, int k, uint8_t *inside);
+
+/* Advance every droplet by nsteps time steps (asynchronous on the context's
+ * stream; replays a captured graph per step unless IBLB_OPT_GRAPHS is 0). */
+int iblb_step(iblb_ctx *ctx, int nsteps);
+
+/* Wait for the context's work; returns the device status (IBLB_OK,
+ * IBLB_E_UNSTABLE or IBLB_E_OVERFLOW) and clears it. */
+int iblb_sync(iblb_ctx *ctx);
+
+/* Observables of droplet k (synchronises).  zcut_frac: protocol (i) plane
+ * height over R0 (the paper's optimum 0.05); eps_flat: protocol (ii)
+ * flatness parameter (the paper's optimum 0.1). */
+int iblb_observe(iblb_ctx *ctx, int k, double zcut_frac, double eps_flat, iblb_obs *out);
+
+/* IBLB_OPT_* switches; IBLB_E_ARG for unknown options or values. */
+int iblb_set_option(iblb_ctx *ctx, int option, int value);
+
+/* Accumulated per-phase device time (ms, IBLB_NPHASE doubles), whole-step
+ * device time and number of profiled steps since the last reset.  Times are
+ * taken with CUDA events on the context's stream while IBLB_OPT_PROFILE is on. */
+int iblb_get_profile(iblb_ctx *ctx, double *phase_ms, double *step_ms, int64_t *steps);
+int iblb_reset_profile(iblb_ctx *ctx);
+
+/* Time candidate launch shapes of the stream-collide kernel on this context's
+ * lattice (a few steps each, state restored afterwards), keep the fastest and
+ * append it to the text file cache_path (NULL: no cache).  A cached entry for
+ * the same shape class is used without timing.  Results are bitwise
+ * identical for every candidate. */
+int iblb_autotune(iblb_ctx *ctx, const char *cache_path);
+
+/* Checkpoint: write / read the complete dynamic state (populations, nodes,
+ * V0, step counter) of every droplet to / from a binary file.  Loading needs
+ * a context created with the same descriptors and membranes.  A resumed run
+ * is bitwise identical to an uninterrupted one. */
+int iblb_save(iblb_ctx *ctx, const char *path);
+int iblb_load(iblb_ctx *ctx, const char *path);
+
+/* Stateless mesh observables on DEVICE arrays (same definitions as
+ * iblb_observe without the mass): d_xyz 3*n_nodes doubles (xyz triples),
+ * d_tri 3*n_tri int32 (node indices), results written to the HOST array
+ * out[13] in the order of iblb_obs from volume to chi_flat (volume, area,
+ * centroid[3], zmin, zmax, theta_R0_deg, theta_RV_deg, rc_cut, rc_flat,
+ * n_cut, chi_flat).  R0 > 0 is the reference radius of eq. angleh.
+ * Allocates its scratch with cudaMallocAsync on `stream` (NULL = legacy
+ * default stream), frees it the same way and synchronises the stream. */
+int iblb_mesh_observe_dev(const double *d_xyz, int n_nodes, const int32_t *d_tri, int n_tri,
+                          double R0, double zcut_frac, double eps_flat, void *stream,
+                          double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

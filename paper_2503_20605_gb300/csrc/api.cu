@@ -1,0 +1,1278 @@
+// api.cu -- host side of libiblb: the C ABI declared in include/iblb.h.
+//
+// A context owns pooled device buffers for all of its droplets, a CUDA
+// stream of its own, and (by default) two captured CUDA graphs of one time
+// step (one per population buffer parity).  The step enqueues, in order:
+//   (a1) nodal forces + binning, (a2) bin scan, fill, deterministic gather-
+//   spread, (a3) in/out ray casting when some droplet has lambda != 1,
+//   (a4) fused stream-collide, (a5) interpolation + advection, (a6) FP64 mesh
+//   reductions + volume correction when requested.
+#include <math.h>
+#include <stdio.h>
+
+#include <cmath>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/iblb.h"
+#include "iblb_internal.h"
+
+using namespace iblb;
+
+namespace {
+
+const char *kVersion = "iblb 0.1 (sm_103a)";
+thread_local std::string g_create_error;
+
+const double kWh[Q] = {1.0 / 3.0,  1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
+                       1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
+                       1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+size_t storage_bytes(int storage) { return storage == IBLB_STORE_F32 ? 4 : 2; }
+
+struct Membrane {
+    std::vector<double> xyz;   // current positions (host copy, refreshed on rebuild)
+    std::vector<int> tri;      // local node indices
+    bool set = false;
+    double V0 = 0.0;
+};
+
+}  // namespace
+
+struct iblb_ctx {
+    int ndrops = 0;
+    int storage = 0;
+    std::vector<iblb_lattice_desc> lat;
+    std::vector<iblb_physics_desc> phys;
+    std::vector<Drop> drops;
+    std::vector<Membrane> mem;
+    bool mem_dirty = false;
+    bool any_vartau = false, any_volcorr = false;
+    Arrays A{};
+    Drop *d_drops = nullptr;
+    void *fbuf[2] = {nullptr, nullptr};
+    int cur = 0;
+    int *d_tri = nullptr, *d_adj_start = nullptr, *d_adj = nullptr;
+    int n_red_chunks = 0, mass_blocks = 0;
+    double *d_mass = nullptr;
+    cudaStream_t user = nullptr, stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ph[IBLB_NPHASE + 1] = {};
+    bool graphs = true, profile = false;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool gvalid[2] = {false, false};
+    double ph_ms[IBLB_NPHASE] = {};
+    double step_ms = 0.0;
+    int64_t prof_steps = 0;
+    int64_t step_count = 0;
+    LaunchCfg cfg{256, 0, 148};
+    int *h_status = nullptr;     // pinned, 4 per droplet
+    std::string err;
+};
+
+namespace {
+
+int fail(iblb_ctx *c, int code, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(c, IBLB_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0)
+        n = 1;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+void dfree(void *p)
+{
+    if (p)
+        cudaFree(p);
+}
+
+// order the context's stream after the caller's, and the caller's after ours
+void enter(iblb_ctx *c)
+{
+    cudaEventRecord(c->ev_in, c->user);
+    cudaStreamWaitEvent(c->stream, c->ev_in, 0);
+}
+void leave(iblb_ctx *c)
+{
+    cudaEventRecord(c->ev_out, c->stream);
+    cudaStreamWaitEvent(c->user, c->ev_out, 0);
+}
+
+void invalidate_graphs(iblb_ctx *c)
+{
+    for (int p = 0; p < 2; ++p) {
+        if (c->gexec[p])
+            cudaGraphExecDestroy(c->gexec[p]);
+        c->gexec[p] = nullptr;
+        c->gvalid[p] = false;
+    }
+}
+
+int check_desc(const iblb_lattice_desc &l, const iblb_physics_desc &p, std::string &why)
+{
+    if (l.nx < 8 || l.ny < 8 || l.nz < 8) {
+        why = "box sides must be >= 8";
+        return 0;
+    }
+    if ((int64_t)l.nx * l.ny * l.nz > ((int64_t)1 << 31) / 2) {
+        why = "box too large (cells must stay below 2^30)";
+        return 0;
+    }
+    if (!(l.tau_out > 0.5)) {
+        why = "tau_out must exceed 1/2";
+        return 0;
+    }
+    if (!(l.lambda > 0.0)) {
+        why = "lambda must be positive";
+        return 0;
+    }
+    if (!(l.rho0 > 0.0)) {
+        why = "rho0 must be positive";
+        return 0;
+    }
+    if (l.storage < 0 || l.storage > 2) {
+        why = "unknown storage";
+        return 0;
+    }
+    if (l.walls != 0 && l.walls != 1) {
+        why = "walls must be 0 or 1";
+        return 0;
+    }
+    if (p.sigma < 0.0) {
+        why = "sigma must be >= 0";
+        return 0;
+    }
+    if (p.wetting < 0 || p.wetting > 2) {
+        why = "unknown wetting model";
+        return 0;
+    }
+    if (p.wetting) {
+        if (!(p.xi > 0.0) || p.n <= p.m || p.m < 1 || p.n > 32) {
+            why = "wetting needs xi > 0 and 32 >= n > m >= 1";
+            return 0;
+        }
+        if (!l.walls) {
+            why = "wetting needs walls";
+            return 0;
+        }
+        if (p.h_min_frac < 0.0) {
+            why = "h_min_frac must be >= 0";
+            return 0;
+        }
+    }
+    return 1;
+}
+
+// Closed, orientable, Euler characteristic 2 and positive volume.
+int validate_mesh(const double *xyz, int n, const int32_t *tri, int nt, std::string &why, double *V)
+{
+    if (n < 4 || nt < 4) {
+        why = "a closed mesh needs at least 4 nodes and 4 faces";
+        return 0;
+    }
+    std::map<std::pair<int, int>, int> directed;
+    std::vector<int> used(n, 0);
+    for (int t = 0; t < nt; ++t) {
+        const int a = tri[3 * t], b = tri[3 * t + 1], cc = tri[3 * t + 2];
+        if (a < 0 || b < 0 || cc < 0 || a >= n || b >= n || cc >= n) {
+            why = "face index out of range";
+            return 0;
+        }
+        if (a == b || b == cc || a == cc) {
+            why = "degenerate face";
+            return 0;
+        }
+        const int v[3] = {a, b, cc};
+        for (int k = 0; k < 3; ++k) {
+            used[v[k]] = 1;
+            if (++directed[{v[k], v[(k + 1) % 3]}] > 1) {
+                why = "edge used twice in the same direction (non-manifold or inconsistent orientation)";
+                return 0;
+            }
+        }
+    }
+    for (auto &kv : directed)
+        if (!directed.count({kv.first.second, kv.first.first})) {
+            why = "open mesh: an edge has one face only";
+            return 0;
+        }
+    for (int j = 0; j < n; ++j)
+        if (!used[j]) {
+            why = "node not used by any face";
+            return 0;
+        }
+    const int64_t E = (int64_t)directed.size() / 2;
+    if ((int64_t)n - E + nt != 2) {
+        why = "Euler characteristic is not 2";
+        return 0;
+    }
+    double vol = 0.0;
+    for (int t = 0; t < nt; ++t) {
+        const double *a = xyz + 3 * tri[3 * t], *b = xyz + 3 * tri[3 * t + 1], *cc = xyz + 3 * tri[3 * t + 2];
+        vol += a[0] * (b[1] * cc[2] - b[2] * cc[1]) + a[1] * (b[2] * cc[0] - b[0] * cc[2]) +
+               a[2] * (b[0] * cc[1] - b[1] * cc[0]);
+    }
+    vol /= 6.0;
+    if (!(vol > 0.0)) {
+        why = "mesh volume not positive (faces must be counter-clockwise seen from outside)";
+        return 0;
+    }
+    for (int k = 0; k < 3 * n; ++k)
+        if (!std::isfinite(xyz[k])) {
+            why = "non-finite node position";
+            return 0;
+        }
+    *V = vol;
+    return 1;
+}
+
+void fill_drop_params(Drop &D, const iblb_lattice_desc &l, const iblb_physics_desc &p)
+{
+    D.nx = l.nx;
+    D.ny = l.ny;
+    D.nz = l.nz;
+    D.walls = l.walls;
+    D.nzf = l.walls ? l.nz - 2 : l.nz;
+    D.tx = (l.nx + 3) / 4;
+    D.ty = (l.ny + 3) / 4;
+    D.tz = (D.nzf + 3) / 4;
+    D.ntiles = D.tx * D.ty * D.tz;
+    D.cells = (int64_t)l.nx * l.ny * D.nzf;
+    const double tin = 0.5 + l.lambda * (l.tau_out - 0.5);
+    D.tau_out = (float)l.tau_out;
+    D.tau_in = (float)tin;
+    D.omega_out = (float)(1.0 / l.tau_out);
+    D.omega_in = (float)(1.0 / tin);
+    D.vartau = l.lambda != 1.0;
+    D.rho0 = (float)l.rho0;
+    for (int k = 0; k < 3; ++k)
+        D.bf[k] = (float)l.body_force[k];
+    D.sigma = (float)p.sigma;
+    D.wetting = p.wetting != IBLB_WET_OFF;
+    double A = 0.0;
+    if (p.wetting == IBLB_WET_THETA)
+        A = p.sigma * (double)((p.m - 1) * (p.n - 1)) / ((double)(p.n - p.m) * p.xi) *
+            (1.0 + cos(p.theta_eq_deg * M_PI / 180.0));
+    else if (p.wetting == IBLB_WET_RAW)
+        A = p.A;
+    D.A = (float)A;
+    D.xi = (float)(p.xi > 0 ? p.xi : 1.0);
+    D.hmin = (float)(p.h_min_frac * (p.xi > 0 ? p.xi : 1.0));
+    D.n = p.n;
+    D.m = p.m;
+    D.volcorr = p.volume_correction != 0;
+}
+
+// Offsets of cells, tiles, columns, launch blocks for the current launch shape.
+void layout(iblb_ctx *c)
+{
+    int64_t cell0 = 0, tile0 = 0, col0 = 0;
+    int lb0 = 0, mb0 = 0;
+    for (auto &D : c->drops) {
+        D.cell0 = cell0;
+        D.tile0 = tile0;
+        D.col0 = col0;
+        D.lb_block0 = lb0;
+        D.lb_nblocks = (int)((D.cells + c->cfg.lb_block - 1) / c->cfg.lb_block);
+        D.mass_block0 = mb0;
+        D.mass_nblocks = (int)((D.cells + 255) / 256);
+        cell0 += D.cells;
+        tile0 += D.ntiles;
+        col0 += (int64_t)D.nx * D.ny;
+        lb0 += D.lb_nblocks;
+        mb0 += D.mass_nblocks;
+    }
+    c->A.total_cells = cell0;
+    c->A.total_tiles = tile0;
+    c->A.total_cols = col0;
+    c->A.lb_blocks_total = lb0;
+    c->A.lb_cpb = c->cfg.lb_block;
+    c->mass_blocks = mb0;
+}
+
+int upload_drops(iblb_ctx *c)
+{
+    CK(cudaMemcpyAsync(c->d_drops, c->drops.data(), sizeof(Drop) * c->ndrops, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IBLB_OK;
+}
+
+// Pull the current device node positions into the host copies.
+int download_nodes(iblb_ctx *c)
+{
+    if (!c->A.total_nodes)
+        return IBLB_OK;
+    const int N = c->A.total_nodes;
+    std::vector<double> x(N), y(N), z(N);
+    CK(cudaMemcpyAsync(x.data(), c->A.qx, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(y.data(), c->A.qy, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(z.data(), c->A.qz, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int d = 0; d < c->ndrops; ++d) {
+        const Drop &D = c->drops[d];
+        for (int j = 0; j < D.nnodes; ++j) {
+            c->mem[d].xyz[3 * j] = x[D.node0 + j];
+            c->mem[d].xyz[3 * j + 1] = y[D.node0 + j];
+            c->mem[d].xyz[3 * j + 2] = z[D.node0 + j];
+        }
+    }
+    return IBLB_OK;
+}
+
+void free_membrane_arrays(iblb_ctx *c)
+{
+    dfree(c->A.qx);
+    dfree(c->A.qy);
+    dfree(c->A.qz);
+    dfree(c->A.node_drop);
+    dfree(c->d_tri);
+    dfree(c->A.face_drop);
+    dfree(c->d_adj_start);
+    dfree(c->d_adj);
+    dfree(c->A.rec);
+    dfree(c->A.bin_list);
+    dfree(c->A.red_part);
+    dfree(c->A.red_out);
+    c->A.qx = c->A.qy = c->A.qz = nullptr;
+    c->A.node_drop = c->A.face_drop = nullptr;
+    c->d_tri = c->d_adj_start = c->d_adj = nullptr;
+    c->A.tri = c->A.adj_start = c->A.adj = nullptr;
+    c->A.rec = nullptr;
+    c->A.bin_list = nullptr;
+    c->A.red_part = c->A.red_out = nullptr;
+}
+
+// (Re)build the pooled node / face / adjacency arrays from the host copies.
+int rebuild_membranes(iblb_ctx *c)
+{
+    if (!c->mem_dirty)
+        return IBLB_OK;
+    free_membrane_arrays(c);
+    int N = 0, NT = 0, chunks = 0;
+    for (int d = 0; d < c->ndrops; ++d) {
+        Drop &D = c->drops[d];
+        const Membrane &M = c->mem[d];
+        D.node0 = N;
+        D.tri0 = NT;
+        D.nnodes = M.set ? (int)(M.xyz.size() / 3) : 0;
+        D.ntri = M.set ? (int)(M.tri.size() / 3) : 0;
+        D.red_chunk0 = chunks;
+        int nc = 0;
+        if (D.nnodes) {
+            nc = std::max((D.ntri + RED_FACES - 1) / RED_FACES, (D.nnodes + RED_NODES - 1) / RED_NODES);
+            nc = std::max(nc, 1);
+        }
+        D.red_nchunks = nc;
+        D.V0 = M.V0;
+        D.R0 = cbrt(3.0 * M.V0 / (4.0 * M_PI));
+        N += D.nnodes;
+        NT += D.ntri;
+        chunks += nc;
+    }
+    c->A.total_nodes = N;
+    c->A.total_tri = NT;
+    c->n_red_chunks = chunks;
+    std::vector<double> x(N), y(N), z(N);
+    std::vector<int> nd(N), tri(3 * (size_t)NT), fd(NT), start(N + 1, 0), adj;
+    for (int d = 0; d < c->ndrops; ++d) {
+        const Drop &D = c->drops[d];
+        const Membrane &M = c->mem[d];
+        for (int j = 0; j < D.nnodes; ++j) {
+            x[D.node0 + j] = M.xyz[3 * j];
+            y[D.node0 + j] = M.xyz[3 * j + 1];
+            z[D.node0 + j] = M.xyz[3 * j + 2];
+            nd[D.node0 + j] = d;
+        }
+        for (int t = 0; t < D.ntri; ++t) {
+            for (int k = 0; k < 3; ++k) {
+                tri[3 * (size_t)(D.tri0 + t) + k] = D.node0 + M.tri[3 * t + k];
+                start[D.node0 + M.tri[3 * t + k] + 1]++;
+            }
+            fd[D.tri0 + t] = d;
+        }
+    }
+    for (int j = 0; j < N; ++j)
+        start[j + 1] += start[j];
+    adj.resize(start[N] > 0 ? start[N] : 1);
+    {
+        std::vector<int> pos(start.begin(), start.end() - 1);
+        for (int t = 0; t < NT; ++t)       // faces in increasing order per node
+            for (int k = 0; k < 3; ++k)
+                adj[pos[tri[3 * (size_t)t + k]]++] = (t << 2) | k;
+    }
+    if (NT >= (1 << 29))
+        return fail(c, IBLB_E_ARG, "too many faces");
+    CK(dalloc(&c->A.qx, N));
+    CK(dalloc(&c->A.qy, N));
+    CK(dalloc(&c->A.qz, N));
+    CK(dalloc(&c->A.node_drop, N));
+    CK(dalloc(&c->d_tri, 3 * (size_t)NT));
+    CK(dalloc(&c->A.face_drop, NT));
+    CK(dalloc(&c->d_adj_start, N + 1));
+    CK(dalloc(&c->d_adj, adj.size()));
+    CK(dalloc(&c->A.rec, N));
+    CK(dalloc(&c->A.bin_list, N));
+    CK(dalloc(&c->A.red_part, (size_t)NRED * std::max(chunks, 1)));
+    CK(dalloc(&c->A.red_out, (size_t)NRED * c->ndrops));
+    c->A.tri = c->d_tri;
+    c->A.adj_start = c->d_adj_start;
+    c->A.adj = c->d_adj;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream) : cudaSuccess;
+    };
+    CK(up(c->A.qx, x.data(), sizeof(double) * N));
+    CK(up(c->A.qy, y.data(), sizeof(double) * N));
+    CK(up(c->A.qz, z.data(), sizeof(double) * N));
+    CK(up(c->A.node_drop, nd.data(), sizeof(int) * N));
+    CK(up(c->d_tri, tri.data(), sizeof(int) * tri.size()));
+    CK(up(c->A.face_drop, fd.data(), sizeof(int) * NT));
+    CK(up(c->d_adj_start, start.data(), sizeof(int) * (N + 1)));
+    CK(up(c->d_adj, adj.data(), sizeof(int) * adj.size()));
+    CK(cudaMemsetAsync(c->A.bin_cnt, 0, sizeof(int) * (c->A.total_tiles + 1), c->stream));
+    c->mem_dirty = false;
+    int r = upload_drops(c);
+    invalidate_graphs(c);
+    return r;
+}
+
+int ensure_ready(iblb_ctx *c)
+{
+    return rebuild_membranes(c);
+}
+
+// One time step on c->stream with population buffers (src = fbuf[par]).
+int enqueue_step(iblb_ctx *c, int par, bool forces_only)
+{
+    cudaStream_t s = c->stream;
+    const Arrays &a = c->A;
+    const bool nodes = a.total_nodes > 0;
+    const bool prof = c->profile;
+    // phase boundaries; "external" so that, under stream capture, they become
+    // event-record nodes of the graph that the host can time after a replay
+    auto mark = [&](int k) {
+        return prof ? cudaEventRecordWithFlags(c->ph[k], s, cudaEventRecordExternal) : cudaSuccess;
+    };
+    CK(mark(0));
+    if (nodes) {
+        CK(cudaMemsetAsync(a.clamped, 0, sizeof(int) * c->ndrops, s));
+        CK(launch_node_force(a, s));
+    }
+    CK(mark(1));
+    if (nodes)
+        CK(launch_spread(a, s));
+    CK(mark(2));
+    if (nodes && c->any_vartau)
+        CK(launch_inout(a, s));
+    CK(mark(3));
+    if (forces_only)
+        return IBLB_OK;
+    CK(launch_lb(a, c->storage, c->fbuf[par], c->fbuf[par ^ 1], nodes && c->any_vartau, c->cfg, s));
+    CK(mark(4));
+    if (nodes)
+        CK(launch_interp_advect(a, s));
+    CK(mark(5));
+    if (nodes && c->any_volcorr) {
+        CK(launch_mesh_reduce(a, c->n_red_chunks, s));
+        CK(launch_volume_correct(a, s));
+    }
+    CK(mark(6));
+    return IBLB_OK;
+}
+
+int capture_step(iblb_ctx *c, int par)
+{
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int r = enqueue_step(c, par, false);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (r != IBLB_OK) {
+        if (g)
+            cudaGraphDestroy(g);
+        return r;
+    }
+    if (e != cudaSuccess)
+        return fail(c, IBLB_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec[par], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess)
+        return fail(c, IBLB_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    c->gvalid[par] = true;
+    return IBLB_OK;
+}
+
+int accumulate_profile(iblb_ctx *c)
+{
+    CK(cudaEventSynchronize(c->ph[IBLB_NPHASE]));
+    for (int k = 0; k < IBLB_NPHASE; ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ph[k], c->ph[k + 1]));
+        c->ph_ms[k] += ms;
+    }
+    float tot = 0.f;
+    CK(cudaEventElapsedTime(&tot, c->ph[0], c->ph[IBLB_NPHASE]));
+    c->step_ms += tot;
+    c->prof_steps++;
+    return IBLB_OK;
+}
+
+int status_code(int flags)
+{
+    if (flags & (ST_SPREAD_OVF | ST_COL_OVF))
+        return IBLB_E_OVERFLOW;
+    if (flags & (ST_NAN | ST_JUMP | ST_ESCAPE))
+        return IBLB_E_UNSTABLE;
+    return IBLB_OK;
+}
+
+std::string status_text(int flags)
+{
+    std::string s;
+    if (flags & ST_NAN) s += " non-finite node velocity;";
+    if (flags & ST_JUMP) s += " a node moved more than 1/2 in one step;";
+    if (flags & ST_ESCAPE) s += " a node left the fluid layers;";
+    if (flags & ST_SPREAD_OVF) s += " more nodes overlap a band tile than the spread holds;";
+    if (flags & ST_COL_OVF) s += " more ray crossings in a column than kept;";
+    return s;
+}
+
+// read (and optionally clear) the device status of every droplet
+int read_status(iblb_ctx *c, bool clear, int *flags_or)
+{
+    CK(cudaMemcpyAsync(c->h_status, c->A.status, sizeof(int) * 4 * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int f = 0;
+    for (int d = 0; d < c->ndrops; ++d)
+        f |= c->h_status[4 * d];
+    if (clear && f) {
+        for (int d = 0; d < c->ndrops; ++d)
+            CK(cudaMemsetAsync(c->A.status + 4 * d, 0, sizeof(int), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    *flags_or = f;
+    return IBLB_OK;
+}
+
+int check_k(iblb_ctx *c, int k)
+{
+    if (!c)
+        return fail(nullptr, IBLB_E_ARG, "null context");
+    if (k < 0 || k >= c->ndrops)
+        return fail(c, IBLB_E_ARG, "droplet index out of range");
+    return IBLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *iblb_version(void) { return kVersion; }
+
+const char *iblb_last_error(const iblb_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int iblb_wetting_A(double sigma, double theta_eq_deg, double xi, int n, int m, double *A)
+{
+    if (!A || !(xi > 0.0) || n <= m)
+        return fail(nullptr, IBLB_E_ARG, "iblb_wetting_A: need xi > 0, n > m and an output pointer");
+    // eq. A_choice
+    *A = sigma * (double)((m - 1) * (n - 1)) / ((double)(n - m) * xi) * (1.0 + cos(theta_eq_deg * M_PI / 180.0));
+    return IBLB_OK;
+}
+
+int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_desc *phys, void *stream,
+                      iblb_ctx **out)
+{
+    iblb_ctx *c = nullptr;
+    if (!out || !lat || !phys || n < 1)
+        return fail(nullptr, IBLB_E_ARG, "iblb_batch_create: bad arguments");
+    *out = nullptr;
+    for (int d = 0; d < n; ++d) {
+        std::string why;
+        if (!check_desc(lat[d], phys[d], why))
+            return fail(nullptr, IBLB_E_ARG, "droplet " + std::to_string(d) + ": " + why);
+        if (lat[d].storage != lat[0].storage)
+            return fail(nullptr, IBLB_E_ARG, "all droplets of a context need the same storage");
+    }
+    c = new iblb_ctx();
+    c->ndrops = n;
+    c->storage = lat[0].storage;
+    c->lat.assign(lat, lat + n);
+    c->phys.assign(phys, phys + n);
+    c->drops.resize(n);
+    c->mem.resize(n);
+    for (int d = 0; d < n; ++d) {
+        memset(&c->drops[d], 0, sizeof(Drop));
+        fill_drop_params(c->drops[d], lat[d], phys[d]);
+        c->any_vartau |= c->drops[d].vartau != 0;
+        c->any_volcorr |= c->drops[d].volcorr != 0;
+    }
+    c->user = (cudaStream_t)stream;
+    int dev = 0;
+    auto bad = [&](cudaError_t e, const char *what) {
+        std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+        iblb_destroy(c);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? IBLB_E_NOMEM : IBLB_E_CUDA, msg);
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess)
+        return bad(e, "cudaGetDevice");
+    cudaDeviceGetAttribute(&c->cfg.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bad(e, "cudaStreamCreate");
+    if ((e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+        return bad(e, "cudaEventCreate");
+    for (int k = 0; k <= IBLB_NPHASE; ++k)
+        if ((e = cudaEventCreate(&c->ph[k])) != cudaSuccess)
+            return bad(e, "cudaEventCreate");
+    layout(c);
+    Arrays &A = c->A;
+    A.ndrops = n;
+    const size_t sb = storage_bytes(c->storage);
+    const int64_t T = A.total_tiles;
+    A.n_scan_blocks = (int)((T + 1 + SCAN_ITEMS - 1) / SCAN_ITEMS);
+    A.active_cap = (int)T;
+    if ((e = cudaMalloc(&c->fbuf[0], sb * Q * A.total_cells)) != cudaSuccess ||
+        (e = cudaMalloc(&c->fbuf[1], sb * Q * A.total_cells)) != cudaSuccess ||
+        (e = dalloc(&A.F, 3 * (size_t)A.total_cells)) != cudaSuccess ||
+        (e = dalloc(&A.U, 3 * (size_t)A.total_cells)) != cudaSuccess ||
+        (e = dalloc(&A.tile_gen, (size_t)T)) != cudaSuccess || (e = dalloc(&A.gen, 1)) != cudaSuccess ||
+        (e = dalloc(&A.n_active, 1)) != cudaSuccess || (e = dalloc(&A.active, (size_t)T)) != cudaSuccess ||
+        (e = dalloc(&A.bin_cnt, (size_t)T + 1)) != cudaSuccess ||
+        (e = dalloc(&A.bin_off, (size_t)T + 1)) != cudaSuccess ||
+        (e = dalloc(&A.blk_sum, (size_t)A.n_scan_blocks)) != cudaSuccess ||
+        (e = dalloc(&A.blk_off, (size_t)A.n_scan_blocks)) != cudaSuccess ||
+        (e = dalloc(&A.col_cnt, (size_t)A.total_cols)) != cudaSuccess ||
+        (e = dalloc(&A.col_z, (size_t)A.total_cols * MAXC)) != cudaSuccess ||
+        (e = dalloc(&A.mass_part, (size_t)c->mass_blocks)) != cudaSuccess ||
+        (e = dalloc(&A.status, 4 * (size_t)n)) != cudaSuccess || (e = dalloc(&A.clamped, (size_t)n)) != cudaSuccess ||
+        (e = dalloc(&c->d_mass, (size_t)n)) != cudaSuccess || (e = dalloc(&c->d_drops, (size_t)n)) != cudaSuccess)
+        return bad(e, "cudaMalloc");
+    if ((e = cudaMallocHost(&c->h_status, sizeof(int) * 4 * n)) != cudaSuccess)
+        return bad(e, "cudaMallocHost");
+    A.drops = c->d_drops;
+    cudaStream_t s = c->stream;
+    const uint32_t one = 1;
+    if ((e = cudaMemsetAsync(A.tile_gen, 0, sizeof(uint32_t) * T, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(A.gen, &one, sizeof(one), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.n_active, 0, sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.bin_cnt, 0, sizeof(int) * (T + 1), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.col_cnt, 0, sizeof(int) * A.total_cols, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.status, 0, sizeof(int) * 4 * n, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.clamped, 0, sizeof(int) * n, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.F, 0, sizeof(float) * 3 * A.total_cells, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.U, 0, sizeof(float) * 3 * A.total_cells, s)) != cudaSuccess ||
+        (e = launch_init_populations(A, c->storage, c->fbuf[0], s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->d_drops, c->drops.data(), sizeof(Drop) * n, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return bad(e, "initialisation");
+    *out = c;
+    return IBLB_OK;
+}
+
+int iblb_create(const iblb_lattice_desc *lat, const iblb_physics_desc *phys, void *stream, iblb_ctx **out)
+{
+    return iblb_batch_create(1, lat, phys, stream, out);
+}
+
+void iblb_destroy(iblb_ctx *c)
+{
+    if (!c)
+        return;
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    invalidate_graphs(c);
+    free_membrane_arrays(c);
+    Arrays &A = c->A;
+    dfree(c->fbuf[0]);
+    dfree(c->fbuf[1]);
+    dfree(A.F);
+    dfree(A.U);
+    dfree(A.tile_gen);
+    dfree(A.gen);
+    dfree(A.n_active);
+    dfree(A.active);
+    dfree(A.bin_cnt);
+    dfree(A.bin_off);
+    dfree(A.blk_sum);
+    dfree(A.blk_off);
+    dfree(A.col_cnt);
+    dfree(A.col_z);
+    dfree(A.mass_part);
+    dfree(A.status);
+    dfree(A.clamped);
+    dfree(c->d_mass);
+    dfree(c->d_drops);
+    if (c->h_status)
+        cudaFreeHost(c->h_status);
+    for (int k = 0; k <= IBLB_NPHASE; ++k)
+        if (c->ph[k])
+            cudaEventDestroy(c->ph[k]);
+    if (c->ev_in)
+        cudaEventDestroy(c->ev_in);
+    if (c->ev_out)
+        cudaEventDestroy(c->ev_out);
+    if (c->stream)
+        cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int iblb_info(const iblb_ctx *ctx, int k, int *n_drops, int64_t *cells, int *n_nodes, int *n_tri)
+{
+    iblb_ctx *c = const_cast<iblb_ctx *>(ctx);
+    int r = check_k(c, k);
+    if (r)
+        return r;
+    if (n_drops)
+        *n_drops = c->ndrops;
+    if (cells)
+        *cells = c->drops[k].cells;
+    if (n_nodes)
+        *n_nodes = c->mem[k].set ? (int)(c->mem[k].xyz.size() / 3) : 0;
+    if (n_tri)
+        *n_tri = c->mem[k].set ? (int)(c->mem[k].tri.size() / 3) : 0;
+    return IBLB_OK;
+}
+
+int iblb_set_membrane(iblb_ctx *c, int k, const double *xyz, int n_nodes, const int32_t *tri, int n_tri)
+{
+    int r = check_k(c, k);
+    if (r)
+        return r;
+    if (!xyz || !tri)
+        return fail(c, IBLB_E_ARG, "null mesh arrays");
+    std::string why;
+    double V = 0.0;
+    if (!validate_mesh(xyz, n_nodes, tri, n_tri, why, &V))
+        return fail(c, IBLB_E_MESH, why);
+    if (c->A.total_nodes && (r = download_nodes(c)))   // keep the other droplets' current state
+        return r;
+    Membrane &M = c->mem[k];
+    M.xyz.assign(xyz, xyz + 3 * (size_t)n_nodes);
+    M.tri.assign(tri, tri + 3 * (size_t)n_tri);
+    M.set = true;
+    M.V0 = V;
+    c->mem_dirty = true;
+    return rebuild_membranes(c);
+}
+
+int iblb_set_nodes(iblb_ctx *c, int k, const double *xyz)
+{
+    int r = check_k(c, k);
+    if (r || (r = ensure_ready(c)))
+        return r;
+    const Drop &D = c->drops[k];
+    if (!D.nnodes)
+        return fail(c, IBLB_E_STATE, "droplet has no membrane");
+    std::vector<double> x(D.nnodes), y(D.nnodes), z(D.nnodes);
+    for (int j = 0; j < D.nnodes; ++j) {
+        x[j] = xyz[3 * j];
+        y[j] = xyz[3 * j + 1];
+        z[j] = xyz[3 * j + 2];
+    }
+    enter(c);
+    CK(cudaMemcpyAsync(c->A.qx + D.node0, x.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->A.qy + D.node0, y.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->A.qz + D.node0, z.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));   // the host vectors die here
+    leave(c);
+    return IBLB_OK;
+}
+
+int iblb_get_nodes(iblb_ctx *c, int k, double *xyz)
+{
+    int r = check_k(c, k);
+    if (r || (r = ensure_ready(c)))
+        return r;
+    const Drop &D = c->drops[k];
+    if (!D.nnodes)
+        return fail(c, IBLB_E_STATE, "droplet has no membrane");
+    std::vector<double> x(D.nnodes), y(D.nnodes), z(D.nnodes);
+    enter(c);
+    CK(cudaMemcpyAsync(x.data(), c->A.qx + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(y.data(), c->A.qy + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(z.data(), c->A.qz + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    leave(c);
+    for (int j = 0; j < D.nnodes; ++j) {
+        xyz[3 * j] = x[j];
+        xyz[3 * j + 1] = y[j];
+        xyz[3 * j + 2] = z[j];
+    }
+    return IBLB_OK;
+}
+
+// temporary device buffer for one transfer
+struct Tmp {
+    void *p = nullptr;
+    ~Tmp() { dfree(p); }
+};
+
+int iblb_set_populations(iblb_ctx *c, int k, const double *f)
+{
+    int r = check_k(c, k);
+    if (r)
+        return r;
+    const Drop &D = c->drops[k];
+    Tmp t;
+    CK(cudaMalloc(&t.p, sizeof(double) * Q * D.cells));
+    enter(c);
+    CK(cudaMemcpyAsync(t.p, f, sizeof(double) * Q * D.cells, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_import_populations(c->A, k, c->storage, c->fbuf[c->cur], (const double *)t.p, D.cells, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    leave(c);
+    return IBLB_OK;
+}
+
+int iblb_get_populations(iblb_ctx *c, int k, double *f)
+{
+    int r = check_k(c, k);
+    if (r)
+        return r;
+    const Drop &D = c->drops[k];
+    Tmp t;
+    CK(cudaMalloc(&t.p, sizeof(double) * Q * D.cells));
+    enter(c);
+    CK(launch_export_populations(c->A, k, c->storage, c->fbuf[c->cur], (double *)t.p, D.cells, c->stream));
+    CK(cudaMemcpyAsync(f, t.p, sizeof(double) * Q * D.cells, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    leave(c);
+    return IBLB_OK;
+}
+
+int iblb_get_macros(iblb_ctx *c, int k, double *rho, double *u)
+{
+    int r = check_k(c, k);
+    if (r)
+        return r;
+    const Drop &D = c->drops[k];
+    Tmp t;
+    CK(cudaMalloc(&t.p, sizeof(double) * 4 * D.cells));
+    double *dr = (double *)t.p, *du = dr + D.cells;
+    enter(c);
+    CK(launch_export_macros(c->A, k, c->storage, c->fbuf[c->cur], dr, du, D.cells, c->stream));
+    CK(cudaMemcpyAsync(rho, dr, sizeof(double) * D.cells, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(u, du, sizeof(double) * 3 * D.cells, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    leave(c);
+    return IBLB_OK;
+}
+
+int iblb_compute_forces(iblb_ctx *c)
+{
+    if (!c)
+        return fail(nullptr, IBLB_E_ARG, "null context");
+    int r = ensure_ready(c);
+    if (r)
+        return r;
+    const bool prof = c->profile;
+    c->profile = false;
+    enter(c);
+    r = enqueue_step(c, c->cur, true);
+    c->profile = prof;
+    if (r)
+        return r;
+    CK(cudaStreamSynchronize(c->stream));
+    leave(c);
+    int flags = 0;
+    if ((r = read_status(c, false, &flags)))
+        return r;
+    if (status_code(flags))
+        return fail(c, status_code(flags), "device status:" + status_text(flags));
+    return IBLB_OK;
+}
+
+int iblb_get_node_forces(iblb_ctx *c, int k, double *phi)
+{
+    int r = check_k(c, k);
+    if (r || (r = ensure_ready(c)))
+        return r;
+    const Drop &D = c->drops[k];
+    if (!D.nnodes)
+        return fail(c, IBLB_E_STATE, "droplet has no membrane");
+    std::vector<NodeRec> rec(D.nnodes);
+    enter(c);
+    CK(cudaMemcpyAsync(rec.data(), c->A.rec + D.node0, sizeof(NodeRec) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    leave(c);
+    for (int j = 0; j < D.nnodes; ++j)
+        for (int e = 0; e < 3; ++e)
+            phi[3 * j + e] = rec[j].phi[e];
+    return IBLB_OK;
+}
+
+int iblb_get_force_density(iblb_ctx *c, int k, double *F)
+{
+    int r = check_k(c, k);
+    if (r)
+        return r;
+    const Drop &D = c->drops[k];
+    Tmp t;
+    CK(cudaMalloc(&t.p, sizeof(double) * 3 * D.cells));
+    enter(c);
+    CK(launch_export_force(c->A, k, (double *)t.p, D.cells, c->stream));
+    CK(cudaMemcpyAsync(F, t.p, sizeof(double) * 3 * D.cells, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    leave(c);
+    return IBLB_OK;
+}
+
+int iblb_get_inside(iblb_ctx *c, int k, uint8_t *inside)
+{
+    int r = check_k(c, k);
+    if (r)
+        return r;
+    const Drop &D = c->drops[k];
+    Tmp t;
+    CK(cudaMalloc(&t.p, D.cells));
+    enter(c);
+    CK(launch_export_inside(c->A, k, (uint8_t *)t.p, D.cells, c->stream));
+    CK(cudaMemcpyAsync(inside, t.p, D.cells, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    leave(c);
+    return IBLB_OK;
+}
+
+int iblb_step(iblb_ctx *c, int nsteps)
+{
+    if (!c)
+        return fail(nullptr, IBLB_E_ARG, "null context");
+    if (nsteps < 0)
+        return fail(c, IBLB_E_ARG, "nsteps < 0");
+    int r = ensure_ready(c);
+    if (r)
+        return r;
+    enter(c);
+    for (int i = 0; i < nsteps; ++i) {
+        const int par = c->cur;
+        if (c->graphs) {
+            if (!c->gvalid[par] && (r = capture_step(c, par)))
+                return r;
+            CK(cudaGraphLaunch(c->gexec[par], c->stream));
+        } else if ((r = enqueue_step(c, par, false))) {
+            return r;
+        }
+        c->cur ^= 1;
+        c->step_count++;
+        if (c->profile && (r = accumulate_profile(c)))
+            return r;
+    }
+    leave(c);
+    return IBLB_OK;
+}
+
+int iblb_sync(iblb_ctx *c)
+{
+    if (!c)
+        return fail(nullptr, IBLB_E_ARG, "null context");
+    CK(cudaStreamSynchronize(c->stream));
+    int flags = 0, r = read_status(c, true, &flags);
+    if (r)
+        return r;
+    if (status_code(flags))
+        return fail(c, status_code(flags), "device status:" + status_text(flags));
+    return IBLB_OK;
+}
+
+int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs *out)
+{
+    int r = check_k(c, k);
+    if (r || (r = ensure_ready(c)))
+        return r;
+    if (!out)
+        return fail(c, IBLB_E_ARG, "null output");
+    memset(out, 0, sizeof(*out));
+    const Drop &D = c->drops[k];
+    enter(c);
+    CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
+    CK(cudaMemcpyAsync(&out->mass, c->d_mass + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (D.nnodes) {
+        Tmp t;
+        CK(cudaMalloc(&t.p, sizeof(double) * observe_scratch_doubles(D.nnodes, D.ntri)));
+        double h[13];
+        CK(launch_observe_view(c->A.qx, c->A.qy, c->A.qz, 1, c->A.tri + 3 * (int64_t)D.tri0, D.ntri, D.node0,
+                               D.nnodes, D.R0, zcut_frac, eps_flat, (double *)t.p, h, c->stream));
+        out->volume = h[0];
+        out->area = h[1];
+        out->centroid[0] = h[2];
+        out->centroid[1] = h[3];
+        out->centroid[2] = h[4];
+        out->zmin = h[5];
+        out->zmax = h[6];
+        out->theta_R0_deg = h[7];
+        out->theta_RV_deg = h[8];
+        out->rc_cut = h[9];
+        out->rc_flat = h[10];
+        out->n_cut = h[11];
+        out->chi_flat = h[12];
+    }
+    int flags = 0;
+    if ((r = read_status(c, false, &flags)))
+        return r;
+    out->status = status_code(flags);
+    CK(cudaMemcpy(&out->clamped, c->A.clamped + k, sizeof(int), cudaMemcpyDeviceToHost));
+    leave(c);
+    return IBLB_OK;
+}
+
+int iblb_set_option(iblb_ctx *c, int option, int value)
+{
+    if (!c)
+        return fail(nullptr, IBLB_E_ARG, "null context");
+    switch (option) {
+    case IBLB_OPT_GRAPHS:
+        c->graphs = value != 0;
+        return IBLB_OK;
+    case IBLB_OPT_PROFILE:
+        if (c->profile != (value != 0))
+            invalidate_graphs(c);
+        c->profile = value != 0;
+        return IBLB_OK;
+    case IBLB_OPT_LB_BLOCK: {
+        if (value == 0)
+            value = 256;
+        if (value < 64 || value > 512 || value % 32)
+            return fail(c, IBLB_E_ARG, "block size must be a multiple of 32 in [64, 512]");
+        int r = ensure_ready(c);
+        if (r)
+            return r;
+        c->cfg.lb_block = value;
+        layout(c);
+        invalidate_graphs(c);
+        return upload_drops(c);
+    }
+    case IBLB_OPT_LB_PERSISTENT:
+        if (value < 0 || value > 1)
+            return fail(c, IBLB_E_ARG, "persistent flag must be 0 or 1");
+        c->cfg.lb_persistent = value;
+        invalidate_graphs(c);
+        return IBLB_OK;
+    }
+    return fail(c, IBLB_E_ARG, "unknown option");
+}
+
+int iblb_get_profile(iblb_ctx *c, double *phase_ms, double *step_ms, int64_t *steps)
+{
+    if (!c)
+        return fail(nullptr, IBLB_E_ARG, "null context");
+    if (phase_ms)
+        for (int k = 0; k < IBLB_NPHASE; ++k)
+            phase_ms[k] = c->ph_ms[k];
+    if (step_ms)
+        *step_ms = c->step_ms;
+    if (steps)
+        *steps = c->prof_steps;
+    return IBLB_OK;
+}
+
+int iblb_reset_profile(iblb_ctx *c)
+{
+    if (!c)
+        return fail(nullptr, IBLB_E_ARG, "null context");
+    for (int k = 0; k < IBLB_NPHASE; ++k)
+        c->ph_ms[k] = 0.0;
+    c->step_ms = 0.0;
+    c->prof_steps = 0;
+    return IBLB_OK;
+}
+
+int iblb_autotune(iblb_ctx *c, const char *cache_path)
+{
+    if (!c)
+        return fail(nullptr, IBLB_E_ARG, "null context");
+    int r = ensure_ready(c);
+    if (r)
+        return r;
+    char key[160];
+    snprintf(key, sizeof(key), "storage=%d cells=%lld drops=%d vartau=%d", c->storage,
+             (long long)c->A.total_cells, c->ndrops, (int)c->any_vartau);
+    if (cache_path) {
+        FILE *fp = fopen(cache_path, "r");
+        if (fp) {
+            char line[256];
+            while (fgets(line, sizeof(line), fp)) {
+                int blk = 0, pers = 0;
+                const char *bar = strchr(line, '|');
+                if (bar && (size_t)(bar - line) == strlen(key) && !strncmp(line, key, strlen(key)) &&
+                    sscanf(bar + 1, "%d %d", &blk, &pers) == 2) {
+                    fclose(fp);
+                    if ((r = iblb_set_option(c, IBLB_OPT_LB_BLOCK, blk)))
+                        return r;
+                    return iblb_set_option(c, IBLB_OPT_LB_PERSISTENT, pers);
+                }
+            }
+            fclose(fp);
+        }
+    }
+    // time the stream-collide kernel alone from the current buffer into the
+    // spare one: the current state is left untouched
+    const int blocks[4] = {128, 256, 384, 512};
+    float best = 1e30f;
+    int bb = 256, bp = 0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    enter(c);
+    for (int pers = 0; pers <= 1; ++pers)
+        for (int bi = 0; bi < 4; ++bi) {
+            c->cfg.lb_block = blocks[bi];
+            c->cfg.lb_persistent = pers;
+            layout(c);
+            if ((r = upload_drops(c)))
+                return r;
+            const bool vt = c->A.total_nodes > 0 && c->any_vartau;
+            for (int w = 0; w < 2; ++w)
+                CK(launch_lb(c->A, c->storage, c->fbuf[c->cur], c->fbuf[c->cur ^ 1], vt, c->cfg, c->stream));
+            CK(cudaEventRecord(e0, c->stream));
+            for (int w = 0; w < 5; ++w)
+                CK(launch_lb(c->A, c->storage, c->fbuf[c->cur], c->fbuf[c->cur ^ 1], vt, c->cfg, c->stream));
+            CK(cudaEventRecord(e1, c->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bb = blocks[bi];
+                bp = pers;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    leave(c);
+    c->cfg.lb_block = bb;
+    c->cfg.lb_persistent = bp;
+    layout(c);
+    invalidate_graphs(c);
+    if ((r = upload_drops(c)))
+        return r;
+    if (cache_path) {
+        FILE *fp = fopen(cache_path, "a");
+        if (fp) {
+            fprintf(fp, "%s|%d %d\n", key, bb, bp);
+            fclose(fp);
+        }
+    }
+    return IBLB_OK;
+}
+
+int iblb_save(iblb_ctx *c, const char *path)
+{
+    if (!c || !path)
+        return fail(c, IBLB_E_ARG, "null argument");
+    int r = ensure_ready(c);
+    if (r || (r = download_nodes(c)))
+        return r;
+    FILE *fp = fopen(path, "wb");
+    if (!fp)
+        return fail(c, IBLB_E_IO, std::string("cannot open ") + path);
+    const size_t sb = storage_bytes(c->storage);
+    std::vector<char> buf;
+    bool ok = true;
+    const char magic[8] = {'I', 'B', 'L', 'B', 'C', 'K', '0', '1'};
+    ok &= fwrite(magic, 8, 1, fp) == 1;
+    const int64_t hdr[4] = {c->ndrops, c->storage, c->step_count, c->A.total_cells};
+    ok &= fwrite(hdr, sizeof(hdr), 1, fp) == 1;
+    CK(cudaStreamSynchronize(c->stream));
+    for (int d = 0; d < c->ndrops && ok; ++d) {
+        const Drop &D = c->drops[d];
+        const int64_t dh[3] = {D.cells, D.nnodes, D.ntri};
+        ok &= fwrite(dh, sizeof(dh), 1, fp) == 1;
+        buf.resize(sb * Q * D.cells);
+        CK(cudaMemcpy(buf.data(), (char *)c->fbuf[c->cur] + sb * Q * D.cell0, buf.size(), cudaMemcpyDeviceToHost));
+        ok &= fwrite(buf.data(), buf.size(), 1, fp) == 1;
+        if (D.nnodes) {
+            ok &= fwrite(c->mem[d].xyz.data(), sizeof(double) * 3 * D.nnodes, 1, fp) == 1;
+            ok &= fwrite(&c->mem[d].V0, sizeof(double), 1, fp) == 1;
+        }
+    }
+    ok &= fclose(fp) == 0;
+    return ok ? IBLB_OK : fail(c, IBLB_E_IO, "write failed");
+}
+
+int iblb_load(iblb_ctx *c, const char *path)
+{
+    if (!c || !path)
+        return fail(c, IBLB_E_ARG, "null argument");
+    int r = ensure_ready(c);
+    if (r)
+        return r;
+    FILE *fp = fopen(path, "rb");
+    if (!fp)
+        return fail(c, IBLB_E_IO, std::string("cannot open ") + path);
+    const size_t sb = storage_bytes(c->storage);
+    char magic[8];
+    int64_t hdr[4];
+    bool ok = fread(magic, 8, 1, fp) == 1 && !memcmp(magic, "IBLBCK01", 8) && fread(hdr, sizeof(hdr), 1, fp) == 1 &&
+              hdr[0] == c->ndrops && hdr[1] == c->storage && hdr[3] == c->A.total_cells;
+    std::vector<char> buf;
+    CK(cudaStreamSynchronize(c->stream));
+    for (int d = 0; d < c->ndrops && ok; ++d) {
+        Drop &D = c->drops[d];
+        int64_t dh[3];
+        ok &= fread(dh, sizeof(dh), 1, fp) == 1 && dh[0] == D.cells && dh[1] == D.nnodes && dh[2] == D.ntri;
+        if (!ok)
+            break;
+        buf.resize(sb * Q * D.cells);
+        ok &= fread(buf.data(), buf.size(), 1, fp) == 1;
+        if (!ok)
+            break;
+        CK(cudaMemcpy((char *)c->fbuf[c->cur] + sb * Q * D.cell0, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+        if (D.nnodes) {
+            std::vector<double> xyz(3 * (size_t)D.nnodes);
+            double V0 = 0.0;
+            ok &= fread(xyz.data(), sizeof(double) * xyz.size(), 1, fp) == 1 && fread(&V0, sizeof(double), 1, fp) == 1;
+            if (!ok)
+                break;
+            c->mem[d].xyz = xyz;
+            c->mem[d].V0 = V0;
+        }
+    }
+    fclose(fp);
+    if (!ok)
+        return fail(c, IBLB_E_IO, "checkpoint does not match this context or is truncated");
+    c->step_count = hdr[2];
+    c->mem_dirty = true;
+    return rebuild_membranes(c);
+}
+
+int iblb_mesh_observe_dev(const double *d_xyz, int n_nodes, const int32_t *d_tri, int n_tri, double R0,
+                          double zcut_frac, double eps_flat, void *stream, double *out)
+{
+    iblb_ctx *c = nullptr;
+    if (!d_xyz || !d_tri || !out || n_nodes < 1 || n_tri < 1 || !(R0 > 0.0))
+        return fail(nullptr, IBLB_E_ARG, "iblb_mesh_observe_dev: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *scr = nullptr;
+    CK(cudaMallocAsync((void **)&scr, sizeof(double) * observe_scratch_doubles(n_nodes, n_tri), s));
+    cudaError_t e = launch_observe_view(d_xyz, d_xyz + 1, d_xyz + 2, 3, d_tri, n_tri, 0, n_nodes, R0, zcut_frac,
+                                        eps_flat, scr, out, s);
+    cudaFreeAsync(scr, s);
+    CK(e);
+    CK(cudaStreamSynchronize(s));
+    return IBLB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// iblb_internal.h -- data layout shared by the host code and the kernels of
+// libiblb.  Every kernel works over a table of droplets (a context with one
+// droplet is a table of length one), so the batched path and the single
+// path execute the same arithmetic.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace iblb {
+
+constexpr int Q = 19;
+constexpr int TILE = 4;            // band tiles are 4x4x4 fluid cells
+constexpr int TILE_CELLS = 64;
+constexpr int MAXC = 16;           // ray crossings kept per lattice column
+constexpr int SPREAD_CAP = 512;    // nodes whose stencil overlaps one tile
+constexpr int SCAN_ITEMS = 4096;   // elements per block of the tile scan
+constexpr int RED_FACES = 2048;    // faces per reduction chunk
+constexpr int RED_NODES = 1024;    // nodes per reduction chunk
+constexpr int NRED = 8;            // partial sums per chunk (see reduce.cu)
+
+// device status bits (Arrays::status[4 * d + 0])
+constexpr int ST_NAN = 1;          // NaN / Inf in a node velocity or position
+constexpr int ST_JUMP = 2;         // |qdot| > 1/2 in one step
+constexpr int ST_SPREAD_OVF = 4;   // more than SPREAD_CAP nodes overlap a tile
+constexpr int ST_COL_OVF = 8;      // more than MAXC crossings in a column
+constexpr int ST_ESCAPE = 16;      // a node left the fluid in z
+
+// Per-droplet descriptor (device resident, read-only in kernels).
+struct Drop {
+    int nx, ny, nz, nzf, walls;
+    int tx, ty, tz, ntiles;
+    int64_t cell0, cells;          // first cell in the pooled cell arrays, count
+    int64_t tile0;                 // first tile in the pooled tile arrays
+    int64_t col0;                  // first column (nx*ny per droplet)
+    int node0, nnodes, tri0, ntri;
+    int lb_block0, lb_nblocks;     // blocks of the stream-collide launch
+    int mass_block0, mass_nblocks; // blocks of the mass reduction
+    int red_chunk0, red_nchunks;   // chunks of the mesh reductions
+    float tau_out, tau_in, omega_out, omega_in;
+    float rho0;
+    float bf[3];                   // body force density
+    float sigma, A, xi, hmin;
+    int n, m, wetting, vartau, volcorr;
+    double V0, R0;
+};
+
+// Record written per node by the force kernel and read by the spread and
+// the interpolation: base cell of the 4^3 support (fluid coordinates, x and
+// y wrapped into the box), bin key, kernel weights Psi along each axis for
+// the support cells base-1 .. base+2, and the nodal force phi_j.
+struct __align__(16) NodeRec {
+    int bx, by, bz, key;
+    float wx[4], wy[4], wz[4];
+    float phi[3];
+    int spare;
+};
+
+// Every device array of a context.  Lattice fields are pooled over droplets:
+// cell c of droplet d is index Drop::cell0 + c; a 3-vector field stores
+// component k at k * total_cells + index.
+struct Arrays {
+    const Drop *drops;
+    int ndrops;
+    int64_t total_cells;
+    int64_t total_tiles;
+    int total_nodes, total_tri;
+    int lb_blocks_total;           // sum of Drop::lb_nblocks
+    int lb_cpb;                    // cells per block of the stream-collide launch
+    // lattice
+    float *F;                      // 3 * total_cells, force density (band tiles only)
+    float *U;                      // 3 * total_cells, velocity (band tiles only)
+    uint32_t *tile_gen;            // tile is in the band of this step iff == *gen
+    uint32_t *gen;                 // step generation counter (device)
+    int *n_active;                 // number of band tiles this step
+    int *active;                   // band tiles (global tile index)
+    int active_cap;
+    // bins
+    int *bin_cnt;                  // total_tiles, returns to 0 after the fill
+    int *bin_off;                  // total_tiles + 1, block-local exclusive scan
+    int *blk_sum;                  // blocks of the scan
+    int *blk_off;
+    int n_scan_blocks;
+    int *bin_list;                 // total_nodes node indices sorted by bin
+    // membrane
+    double *qx, *qy, *qz;          // node positions (FP64)
+    int *node_drop;                // droplet of each node
+    const int *tri;                // 3 * total_tri global node indices
+    const int *adj_start;          // total_nodes + 1
+    const int *adj;                // (face << 2) | corner, faces in increasing order
+    NodeRec *rec;                  // total_nodes
+    // in/out
+    int *col_cnt;                  // crossings per column
+    double *col_z;                 // MAXC crossings per column (sorted)
+    int64_t total_cols;
+    int *face_drop;                // droplet of each face
+    // reductions
+    double *red_part;              // NRED * chunks
+    double *red_out;               // NRED * ndrops: V, A, cx, cy, cz, zmin, zmax, -
+    double *mass_part;
+    int *status;                   // 4 ints per droplet: flags (ST_*), -, -, -
+    int *clamped;                  // per droplet: nodes clamped by the near-wall guard this step
+};
+
+__host__ __device__ inline int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// floor(a / b) for b > 0
+__host__ __device__ inline int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Tiles along one axis whose cells a support 4 wide, keyed by tile k, can
+// touch: k-1, k, k+1 (periodic axes wrap), plus, on a periodic axis whose
+// last tile holds a single cell, tile 0 for k = t-2 (the support of a base
+// cell n-2 wraps onto cell 0).  Returns the count written to out[0..3].
+__host__ __device__ inline int tile_neighbours(int k, int t, int ncell, bool periodic, int *out)
+{
+    int cnt = 0;
+    for (int dk = -1; dk <= 1; ++dk) {
+        int v = k + dk;
+        if (periodic)
+            v = (v % t + t) % t;
+        else if (v < 0 || v >= t)
+            continue;
+        bool dup = false;
+        for (int i = 0; i < cnt; ++i)
+            dup |= out[i] == v;
+        if (!dup)
+            out[cnt++] = v;
+    }
+    if (periodic && (ncell & 3) == 1 && t >= 2) {
+        int extra = -1;
+        if (k == t - 2)
+            extra = 0;
+        else if (k == 0)
+            extra = t - 2;
+        if (extra >= 0) {
+            bool dup = false;
+            for (int i = 0; i < cnt; ++i)
+                dup |= out[i] == extra;
+            if (!dup)
+                out[cnt++] = extra;
+        }
+    }
+    return cnt;
+}
+
+// Host-side launchers (lb.cu, ib.cu, inout.cu, reduce.cu, fields.cu).
+struct LaunchCfg {
+    int lb_block;                  // threads per block, stream-collide
+    int lb_persistent;             // 1: grid = SMs * resident blocks, block-stride loop
+    int sm_count;
+};
+
+cudaError_t launch_lb(const Arrays &a, int storage, const void *src, void *dst, bool vartau,
+                      const LaunchCfg &cfg, cudaStream_t s);
+cudaError_t launch_node_force(const Arrays &a, cudaStream_t s);
+cudaError_t launch_spread(const Arrays &a, cudaStream_t s);
+cudaError_t launch_inout(const Arrays &a, cudaStream_t s);
+cudaError_t launch_interp_advect(const Arrays &a, cudaStream_t s);
+cudaError_t launch_mesh_reduce(const Arrays &a, int n_chunks_total, cudaStream_t s);
+cudaError_t launch_volume_correct(const Arrays &a, cudaStream_t s);
+cudaError_t launch_mass(const Arrays &a, int storage, const void *f, double *d_out, int mass_blocks,
+                        cudaStream_t s);
+// Observables of one mesh: node j at q*[j * stride]; tri holds node indices
+// into q*; nodes node0 .. node0 + nnodes - 1.  Writes 13 doubles to h_out
+// (volume, area, centroid[3], zmin, zmax, theta_R0, theta_RV, rc_cut,
+// rc_flat, n_cut, chi_flat) and synchronises s.
+int64_t observe_scratch_doubles(int n_nodes, int n_tri);
+cudaError_t launch_observe_view(const double *qx, const double *qy, const double *qz, int stride,
+                                const int *tri, int ntri, int node0, int nnodes, double R0, double zcut_frac,
+                                double eps_flat, double *scratch, double *h_out, cudaStream_t s);
+
+// Conversions of droplet d (device pointers; `cells` = that droplet's cells).
+cudaError_t launch_export_populations(const Arrays &a, int d, int storage, const void *f, double *out,
+                                      int64_t cells, cudaStream_t s);
+cudaError_t launch_import_populations(const Arrays &a, int d, int storage, void *f, const double *in,
+                                      int64_t cells, cudaStream_t s);
+cudaError_t launch_export_macros(const Arrays &a, int d, int storage, const void *f, double *rho, double *u,
+                                 int64_t cells, cudaStream_t s);
+cudaError_t launch_export_force(const Arrays &a, int d, double *F, int64_t cells, cudaStream_t s);
+cudaError_t launch_export_inside(const Arrays &a, int d, uint8_t *inside, int64_t cells, cudaStream_t s);
+cudaError_t launch_init_populations(const Arrays &a, int storage, void *f, cudaStream_t s);
+
+}  // namespace iblb

@@ -1,0 +1,458 @@
+// reduce.cu -- FP64 reductions over the membrane and the lattice:
+//   * mesh volume V = (1/6) sum_t q_a . (q_b x q_c), area, node centroid,
+//     z_min and z_max (the half-height l = (z_max - z_min)/2 of App. C, eq. ell);
+//   * the volume correction q <- c + (q - c)(V0/V)^(1/3) (not in the paper);
+//   * contact-radius protocols (i) and (ii) of Sec. III B;
+//   * lattice mass sum_x sum_i f_i.
+// Every reduction uses a fixed assignment of items to threads and a fixed
+// shuffle tree, so results are bitwise reproducible and a droplet's values
+// do not depend on the other droplets of a batch.
+#include <math.h>
+
+#include "iblb_internal.h"
+
+namespace iblb {
+
+struct MeshView {
+    const double *qx, *qy, *qz;  // node j at q*[j * stride]
+    int stride;
+    const int *tri;              // this droplet's faces (node indices into q*)
+    int ntri;
+    int node0, nnodes;           // this droplet's node range
+};
+
+namespace {
+
+constexpr int RB = 256;          // threads per reduction block
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o >= 1; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+    for (int o = 16; o >= 1; o >>= 1)
+        v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o >= 1; o >>= 1)
+        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Reduce NV values per thread over a block of RB threads; kind[k]: 0 sum,
+// 1 min, 2 max.  Result valid in thread 0.
+template <int NV>
+__device__ void block_reduce(double *v, const int *kind)
+{
+    __shared__ double sh[NV][RB / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = 0; k < NV; ++k) {
+        double x = kind[k] == 0 ? warp_sum(v[k]) : (kind[k] == 1 ? warp_min(v[k]) : warp_max(v[k]));
+        if (lane == 0)
+            sh[k][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NV; ++k) {
+            double x = sh[k][0];
+            for (int i = 1; i < RB / 32; ++i)
+                x = kind[k] == 0 ? x + sh[k][i] : (kind[k] == 1 ? fmin(x, sh[k][i]) : fmax(x, sh[k][i]));
+            v[k] = x;
+        }
+    __syncthreads();
+}
+
+// chunk k of a mesh: faces [k*RED_FACES, ...) and nodes [k*RED_NODES, ...)
+// -> 6V, area, sum x, sum y, sum z, z_min, z_max
+__device__ void pass1_chunk(const MeshView &m, int k, double *out)
+{
+    const int KIND[7] = {0, 0, 0, 0, 0, 1, 2};
+    double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};
+    const int f1 = min(m.ntri, (k + 1) * RED_FACES);
+    for (int t = k * RED_FACES + threadIdx.x; t < f1; t += RB) {
+        const int ia = m.tri[3 * t] * m.stride, ib = m.tri[3 * t + 1] * m.stride, ic = m.tri[3 * t + 2] * m.stride;
+        const double ax = m.qx[ia], ay = m.qy[ia], az = m.qz[ia];
+        const double bx = m.qx[ib], by = m.qy[ib], bz = m.qz[ib];
+        const double cx = m.qx[ic], cy = m.qy[ic], cz = m.qz[ic];
+        v[0] += ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
+        const double e1x = bx - ax, e1y = by - ay, e1z = bz - az, e2x = cx - ax, e2y = cy - ay, e2z = cz - az;
+        const double Nx = e1y * e2z - e1z * e2y, Ny = e1z * e2x - e1x * e2z, Nz = e1x * e2y - e1y * e2x;
+        v[1] += 0.5 * sqrt(Nx * Nx + Ny * Ny + Nz * Nz);
+    }
+    const int n1 = min(m.nnodes, (k + 1) * RED_NODES);
+    for (int j = k * RED_NODES + threadIdx.x; j < n1; j += RB) {
+        const int ij = (m.node0 + j) * m.stride;
+        v[2] += m.qx[ij];
+        v[3] += m.qy[ij];
+        const double z = m.qz[ij];
+        v[4] += z;
+        v[5] = fmin(v[5], z);
+        v[6] = fmax(v[6], z);
+    }
+    block_reduce<7>(v, KIND);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 7; ++i)
+            out[i] = v[i];
+}
+
+__device__ __forceinline__ int find_drop_chunk(const Drop *D, int n, int c)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (D[mid].red_chunk0 <= c)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ MeshView view_of(const Arrays &a, const Drop &D)
+{
+    MeshView m;
+    m.qx = a.qx;
+    m.qy = a.qy;
+    m.qz = a.qz;
+    m.stride = 1;
+    m.tri = a.tri + 3 * (int64_t)D.tri0;
+    m.ntri = D.ntri;
+    m.node0 = D.node0;
+    m.nnodes = D.nnodes;
+    return m;
+}
+
+__global__ void __launch_bounds__(RB) pass1_batch_kernel(Arrays a)
+{
+    const int c = blockIdx.x;
+    const int d = find_drop_chunk(a.drops, a.ndrops, c);
+    const Drop &D = a.drops[d];
+    if (D.nnodes == 0)
+        return;
+    pass1_chunk(view_of(a, D), c - D.red_chunk0, a.red_part + (int64_t)NRED * c);
+}
+
+// Fold the chunks of droplet blockIdx.x (one warp; chunk i goes to lane i % 32,
+// lanes add their chunks in order, then a fixed shuffle tree).  Writes
+// V, A, cx, cy, cz, zmin, zmax.
+__device__ void fold_chunks(const double *part, int nch, int nnodes, double *out)
+{
+    const int lane = threadIdx.x;
+    double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};
+    for (int i = lane; i < nch; i += 32) {
+        const double *p = part + (int64_t)NRED * i;
+        for (int k = 0; k < 5; ++k)
+            v[k] += p[k];
+        v[5] = fmin(v[5], p[5]);
+        v[6] = fmax(v[6], p[6]);
+    }
+    for (int k = 0; k < 5; ++k)
+        v[k] = warp_sum(v[k]);
+    v[5] = warp_min(v[5]);
+    v[6] = warp_max(v[6]);
+    if (lane == 0) {
+        out[0] = v[0] / 6.0;
+        out[1] = v[1];
+        out[2] = v[2] / nnodes;
+        out[3] = v[3] / nnodes;
+        out[4] = v[4] / nnodes;
+        out[5] = v[5];
+        out[6] = v[6];
+    }
+}
+
+__global__ void fold_batch_kernel(Arrays a)
+{
+    const Drop &D = a.drops[blockIdx.x];
+    if (D.nnodes == 0)
+        return;
+    fold_chunks(a.red_part + (int64_t)NRED * D.red_chunk0, D.red_nchunks, D.nnodes,
+                a.red_out + (int64_t)NRED * blockIdx.x);
+}
+
+__global__ void volume_correct_kernel(Arrays a)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.total_nodes)
+        return;
+    const int d = a.node_drop[j];
+    const Drop &D = a.drops[d];
+    if (!D.volcorr)
+        return;
+    const double *r = a.red_out + (int64_t)NRED * d;
+    const double k = cbrt(D.V0 / r[0]);
+    a.qx[j] = r[2] + (a.qx[j] - r[2]) * k;
+    a.qy[j] = r[3] + (a.qy[j] - r[3]) * k;
+    a.qz[j] = r[4] + (a.qz[j] - r[4]) * k;
+}
+
+// --- observation of one mesh (view), used by iblb_observe and the stateless
+//     entry point.  scratch layout (doubles): [0, NRED*nch) chunk partials,
+//     then 8 result slots R: V, A, cx, cy, cz, zmin, zmax, -, then protocol
+//     partials.
+
+__global__ void __launch_bounds__(RB) pass1_view_kernel(MeshView m, double *part)
+{
+    pass1_chunk(m, blockIdx.x, part + (int64_t)NRED * blockIdx.x);
+}
+
+__global__ void fold_view_kernel(MeshView m, const double *part, int nch, double *R)
+{
+    fold_chunks(part, nch, m.nnodes, R);
+}
+
+// protocol (i): edges (a < b) crossing z = zp: sum of crossing x, y and count;
+// protocol (ii): lower-half faces with max |dz| < eps: area.
+__global__ void __launch_bounds__(RB) pass2_view_kernel(MeshView m, const double *R, double zp, double flat,
+                                                        double *part)
+{
+    const int KIND[4] = {0, 0, 0, 0};
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const double zmid = 0.5 * (R[5] + R[6]);
+    const int k = blockIdx.x;
+    const int f1 = min(m.ntri, (k + 1) * RED_FACES);
+    for (int t = k * RED_FACES + threadIdx.x; t < f1; t += RB) {
+        int idx[3] = {m.tri[3 * t], m.tri[3 * t + 1], m.tri[3 * t + 2]};
+        double zz[3];
+        for (int e = 0; e < 3; ++e)
+            zz[e] = m.qz[idx[e] * m.stride];
+        for (int e = 0; e < 3; ++e) {
+            const int ia = idx[e], ib = idx[(e + 1) % 3];
+            if (ia > ib)
+                continue;
+            const double za = zz[e], zb = zz[(e + 1) % 3];
+            if (!((za < zp && zb >= zp) || (zb < zp && za >= zp)))
+                continue;
+            const double s = (zp - za) / (zb - za);
+            const double xa = m.qx[ia * m.stride], ya = m.qy[ia * m.stride];
+            v[0] += xa + s * (m.qx[ib * m.stride] - xa);
+            v[1] += ya + s * (m.qy[ib * m.stride] - ya);
+            v[2] += 1.0;
+        }
+        if ((zz[0] + zz[1] + zz[2]) / 3.0 < zmid) {
+            const double dz = fmax(fabs(zz[0] - zz[1]), fmax(fabs(zz[1] - zz[2]), fabs(zz[0] - zz[2])));
+            if (dz < flat) {
+                const int ia = idx[0] * m.stride, ib = idx[1] * m.stride, ic = idx[2] * m.stride;
+                const double e1x = m.qx[ib] - m.qx[ia], e1y = m.qy[ib] - m.qy[ia], e1z = zz[1] - zz[0];
+                const double e2x = m.qx[ic] - m.qx[ia], e2y = m.qy[ic] - m.qy[ia], e2z = zz[2] - zz[0];
+                const double Nx = e1y * e2z - e1z * e2y, Ny = e1z * e2x - e1x * e2z, Nz = e1x * e2y - e1y * e2x;
+                v[3] += 0.5 * sqrt(Nx * Nx + Ny * Ny + Nz * Nz);
+            }
+        }
+    }
+    block_reduce<4>(v, KIND);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i)
+            part[4 * k + i] = v[i];
+}
+
+// protocol (i) second pass: sum of distances of the crossings from their centre
+__global__ void __launch_bounds__(RB) pass3_view_kernel(MeshView m, double zp, const double *C, double *part)
+{
+    const int KIND[1] = {0};
+    double v[1] = {0.0};
+    const double cx = C[0], cy = C[1];
+    const int k = blockIdx.x;
+    const int f1 = min(m.ntri, (k + 1) * RED_FACES);
+    for (int t = k * RED_FACES + threadIdx.x; t < f1; t += RB)
+        for (int e = 0; e < 3; ++e) {
+            const int ia = m.tri[3 * t + e], ib = m.tri[3 * t + (e + 1) % 3];
+            if (ia > ib)
+                continue;
+            const double za = m.qz[ia * m.stride], zb = m.qz[ib * m.stride];
+            if (!((za < zp && zb >= zp) || (zb < zp && za >= zp)))
+                continue;
+            const double s = (zp - za) / (zb - za);
+            const double xa = m.qx[ia * m.stride], ya = m.qy[ia * m.stride];
+            const double px = xa + s * (m.qx[ib * m.stride] - xa) - cx;
+            const double py = ya + s * (m.qy[ib * m.stride] - ya) - cy;
+            v[0] += sqrt(px * px + py * py);
+        }
+    block_reduce<1>(v, KIND);
+    if (threadIdx.x == 0)
+        part[k] = v[0];
+}
+
+// fold nch groups of `width` partials (one warp, fixed order) into out[width];
+// with center != NULL also writes the crossing centre (sum x / count, sum y / count)
+__global__ void fold_sums_kernel(const double *part, int nch, int width, double *out, double *center)
+{
+    const int lane = threadIdx.x;
+    for (int k = 0; k < width; ++k) {
+        double v = 0.0;
+        for (int i = lane; i < nch; i += 32)
+            v += part[(int64_t)width * i + k];
+        v = warp_sum(v);
+        if (lane == 0)
+            out[k] = v;
+    }
+    if (center && lane == 0) {
+        center[0] = out[2] > 0.0 ? out[0] / out[2] : 0.0;
+        center[1] = out[2] > 0.0 ? out[1] / out[2] : 0.0;
+    }
+}
+
+// ---- lattice mass: sum over cells of sum_i s_i (FP64), per droplet
+template <typename S>
+__device__ __forceinline__ double tod(S v);
+template <> __device__ __forceinline__ double tod<float>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double tod<__half>(__half v) { return (double)__half2float(v); }
+template <> __device__ __forceinline__ double tod<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+__device__ __forceinline__ int find_drop_mass(const Drop *D, int n, int b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (D[mid].mass_block0 <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(RB) mass_kernel(Arrays a, const S *f)
+{
+    const int KIND[1] = {0};
+    const int b = blockIdx.x;
+    const int d = find_drop_mass(a.drops, a.ndrops, b);
+    const Drop &D = a.drops[d];
+    const int64_t c = (int64_t)(b - D.mass_block0) * RB + threadIdx.x;
+    double v[1] = {0.0};
+    if (c < D.cells) {
+        const S *p = f + (int64_t)Q * D.cell0 + c;
+        for (int i = 0; i < Q; ++i)
+            v[0] += tod<S>(p[(int64_t)i * D.cells]);
+    }
+    block_reduce<1>(v, KIND);
+    if (threadIdx.x == 0)
+        a.mass_part[b] = v[0];
+}
+
+__global__ void mass_fold_kernel(Arrays a, double *out)
+{
+    const Drop &D = a.drops[blockIdx.x];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < D.mass_nblocks; i += 32)
+        v += a.mass_part[D.mass_block0 + i];
+    v = warp_sum(v);
+    if (threadIdx.x == 0)
+        out[blockIdx.x] = v + (double)D.rho0 * (double)D.cells;
+}
+
+}  // namespace
+
+cudaError_t launch_mesh_reduce(const Arrays &a, int n_chunks_total, cudaStream_t s)
+{
+    if (a.total_nodes <= 0)
+        return cudaSuccess;
+    pass1_batch_kernel<<<n_chunks_total, RB, 0, s>>>(a);
+    fold_batch_kernel<<<a.ndrops, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_volume_correct(const Arrays &a, cudaStream_t s)
+{
+    if (a.total_nodes <= 0)
+        return cudaSuccess;
+    volume_correct_kernel<<<(a.total_nodes + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// scratch: at least NRED*nch + 32 + 4*nch + nch doubles
+static cudaError_t observe_view(const MeshView &m, double R0, double zcut_frac, double eps_flat,
+                                double *scr, double *h_out, cudaStream_t s)
+{
+    const int nch = (m.ntri + RED_FACES - 1) / RED_FACES > (m.nnodes + RED_NODES - 1) / RED_NODES
+                        ? (m.ntri + RED_FACES - 1) / RED_FACES
+                        : (m.nnodes + RED_NODES - 1) / RED_NODES;
+    const int nc = nch > 0 ? nch : 1;
+    double *part1 = scr;                    // NRED * nc
+    double *R = scr + (int64_t)NRED * nc;  // 8 results
+    double *S2 = R + 8;                     // 4 protocol sums
+    double *Cc = S2 + 4;                    // crossing centre (2)
+    double *S3 = Cc + 2;                    // 1
+    double *part2 = R + 32;                 // 4 * nc
+    double *part3 = part2 + 4 * (int64_t)nc;  // nc
+    const double zp = 0.5 + zcut_frac * R0;
+    const double flat = eps_flat * R0;
+    pass1_view_kernel<<<nc, RB, 0, s>>>(m, part1);
+    fold_view_kernel<<<1, 32, 0, s>>>(m, part1, nc, R);
+    pass2_view_kernel<<<nc, RB, 0, s>>>(m, R, zp, flat, part2);
+    fold_sums_kernel<<<1, 32, 0, s>>>(part2, nc, 4, S2, Cc);
+    pass3_view_kernel<<<nc, RB, 0, s>>>(m, zp, Cc, part3);
+    fold_sums_kernel<<<1, 32, 0, s>>>(part3, nc, 1, S3, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    double hv[32];
+    e = cudaMemcpyAsync(hv, R, sizeof(double) * 32, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return e;
+    // hv: R[0..6], S2 at 8..11, Cc at 12..13, S3 at 14
+    const double V = hv[0], A = hv[1], zmin = hv[5], zmax = hv[6];
+    const double ell = 0.5 * (zmax - zmin);
+    const double RV = cbrt(3.0 * V / (4.0 * M_PI));
+    auto theta = [](double l, double Rr) {
+        const double l3 = l * l * l, R3 = Rr * Rr * Rr;
+        if (l3 >= R3)
+            return 180.0;
+        return 2.0 * atan(sqrt(3.0 * l3 / (R3 - l3))) * 180.0 / M_PI;  // eq. angleh
+    };
+    h_out[0] = V;
+    h_out[1] = A;
+    h_out[2] = hv[2];
+    h_out[3] = hv[3];
+    h_out[4] = hv[4];
+    h_out[5] = zmin;
+    h_out[6] = zmax;
+    h_out[7] = theta(ell, R0);
+    h_out[8] = theta(ell, RV);
+    h_out[9] = hv[10] > 0.0 ? hv[14] / hv[10] : 0.0;  // rc_cut
+    h_out[10] = sqrt(hv[11] / M_PI);                  // rc_flat
+    h_out[11] = hv[10];                               // n_cut
+    h_out[12] = hv[11];                               // chi_flat
+    return cudaSuccess;
+}
+
+int64_t observe_scratch_doubles(int n_nodes, int n_tri)
+{
+    int nch = (n_tri + RED_FACES - 1) / RED_FACES;
+    int nn = (n_nodes + RED_NODES - 1) / RED_NODES;
+    nch = nch > nn ? nch : nn;
+    nch = nch > 0 ? nch : 1;
+    return (int64_t)NRED * nch + 32 + 5 * (int64_t)nch + 8;
+}
+
+cudaError_t launch_observe_view(const double *qx, const double *qy, const double *qz, int stride,
+                                const int *tri, int ntri, int node0, int nnodes, double R0, double zcut_frac,
+                                double eps_flat, double *scratch, double *h_out, cudaStream_t s)
+{
+    MeshView m{qx, qy, qz, stride, tri, ntri, node0, nnodes};
+    return observe_view(m, R0, zcut_frac, eps_flat, scratch, h_out, s);
+}
+
+cudaError_t launch_mass(const Arrays &a, int storage, const void *f, double *d_out, int mass_blocks,
+                        cudaStream_t s)
+{
+    switch (storage) {
+    case 0: mass_kernel<float><<<mass_blocks, RB, 0, s>>>(a, (const float *)f); break;
+    case 1: mass_kernel<__half><<<mass_blocks, RB, 0, s>>>(a, (const __half *)f); break;
+    case 2: mass_kernel<__nv_bfloat16><<<mass_blocks, RB, 0, s>>>(a, (const __nv_bfloat16 *)f); break;
+    default: return cudaErrorInvalidValue;
+    }
+    mass_fold_kernel<<<a.ndrops, 32, 0, s>>>(a, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace iblb
