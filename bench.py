@@ -108,7 +108,7 @@ class Clocks:
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]})
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
 
@@ -132,12 +132,13 @@ def launches_per_step(spec):
     return n
 
 
-def run_gpu(spec, storage, steps, warmup, torch, iblb, flush):
+def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
     """Device-timed steps with L2 flushed before each; returns per-phase sums."""
     stream = torch.cuda.current_stream().cuda_stream
     ctx, xyz, tri = make_ctx(iblb, spec, storage, stream)
     try:
-        iblb.iblb_autotune(ctx, os.path.join(ROOT, "paper_2503_20605_gb300", "_build", "autotune.txt"))
+        if autotune:
+            iblb.iblb_autotune(ctx, os.path.join(ROOT, "paper_2503_20605_gb300", "_build", "autotune.txt"))
         iblb.iblb_set_option(ctx, iblb.IBLB_OPT_PROFILE, 1)
         for _ in range(warmup):
             flush.zero_()
@@ -218,6 +219,9 @@ def main():
     ap.add_argument("--storage", default="f16", choices=["f16", "bf16", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--only-main", action="store_true",
+                    help="time only the headline storage (no FP32 line, no e2e loop); for profiler runs")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     args = ap.parse_args()
 
     from paper_2503_20605_gb300 import inputs as I
@@ -259,11 +263,14 @@ def main():
 
     barrier()
     with Clocks(local) as clk:
-        main_run = run_gpu(spec, args.storage, args.steps, args.warmup, torch, iblb, flush)
+        main_run = run_gpu(spec, args.storage, args.steps, args.warmup, torch, iblb, flush,
+                           autotune=not args.no_autotune)
     barrier()
-    spec32 = I.workload_statics_128(90.0, "f32")
-    run32 = run_gpu(spec32, "f32", args.steps, args.warmup, torch, iblb, flush)
-    e2e = run_e2e(spec, args.storage, max(20, args.steps // 4), 3, torch, iblb)
+    run32, e2e = None, None
+    if not args.only_main:
+        spec32 = I.workload_statics_128(90.0, "f32")
+        run32 = run_gpu(spec32, "f32", args.steps, args.warmup, torch, iblb, flush, autotune=not args.no_autotune)
+        e2e = run_e2e(spec, args.storage, max(20, args.steps // 4), 3, torch, iblb)
 
     step_ms = main_run["step_ms"]
     if world > 1:
@@ -280,8 +287,16 @@ def main():
     bpc = BYTES_PER_CELL[args.storage]
     achieved = cells * bpc / (lb_ms * 1e-3) / 1e9
     traffic = ncu_traffic(args.storage)
-    ph32 = run32["phases"]
-    value32 = cells * run32["n"] / (run32["step_ms"] * 1e-3) / 1e6
+    fp32 = None
+    if run32:
+        ph32 = run32["phases"]
+        ib32 = ph32["forces"] + ph32["spread"] + ph32["inout"] + ph32["advect"] + ph32["reduce"]
+        lb32 = ph32["lb"] / run32["n"]
+        fp32 = {"value": cells * run32["n"] / (run32["step_ms"] * 1e-3) / 1e6, "unit": "MLUPS",
+                "phase_ms_per_step": {k: v / run32["n"] for k, v in ph32.items()},
+                "ib_nodes_per_s": nodes * run32["n"] / (ib32 * 1e-3),
+                "lb_kernel_gbs": cells * BYTES_PER_CELL["f32"] / (lb32 * 1e-3) / 1e9,
+                "theta_RV_deg_after": run32["obs"]["theta_RV_deg"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -299,10 +314,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "ib_nodes_per_s": world * nodes * K / (ib_ms * 1e-3),
             "phase_ms_per_step": {k: v / K for k, v in ph.items()},
-            "fp32": {"value": value32, "unit": "MLUPS",
-                     "phase_ms_per_step": {k: v / run32["n"] for k, v in ph32.items()},
-                     "ib_nodes_per_s": nodes * run32["n"] / ((ph32["forces"] + ph32["spread"] + ph32["inout"]
-                                                              + ph32["advect"] + ph32["reduce"]) * 1e-3)},
+            "fp32": fp32,
             "roofline": {"bound": "hbm", "kernel": "lb_kernel (fused stream-collide)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
                          "algorithmic_bytes_per_cell": bpc, "traffic": traffic},

@@ -137,11 +137,10 @@ typedef struct {
 #define IBLB_OPT_GRAPHS 0     /* 1 (default): replay captured CUDA graphs of one step    */
 #define IBLB_OPT_PROFILE 1    /* 1: record CUDA events around each phase (adds a sync
                                  per step); 0 (default)                                  */
-#define IBLB_OPT_LB_BLOCK 2   /* threads (= cells) per block of the stream-collide
-                                 kernel (64..512, multiple of 32); 0 = default 256        */
-#define IBLB_OPT_LB_PERSISTENT 3 /* 1: stream-collide grid of SMs x resident blocks that
-                                 walks the cell blocks of all droplets; 0: one block
-                                 per cell block (default)                                */
+#define IBLB_OPT_LB_BLOCKS_PER_SM 2 /* resident blocks per SM of the persistent
+                                 stream-collide kernel (0..8; 0 = as many as fit)       */
+#define IBLB_OPT_LB_ROW_MULT 3 /* cell rows per stream-collide group, in units of
+                                 max(1, 256 / nx) rows (1..4; 0 = 1)                     */
 
 typedef struct iblb_ctx iblb_ctx;
 

@@ -70,7 +70,7 @@ struct iblb_ctx {
     double step_ms = 0.0;
     int64_t prof_steps = 0;
     int64_t step_count = 0;
-    LaunchCfg cfg{256, 0, 148};
+    LaunchCfg cfg{0, 2, 148};
     int *h_status = nullptr;     // pinned, 4 per droplet
     std::string err;
 };
@@ -288,27 +288,42 @@ void fill_drop_params(Drop &D, const iblb_lattice_desc &l, const iblb_physics_de
 // Offsets of cells, tiles, columns, launch blocks for the current launch shape.
 void layout(iblb_ctx *c)
 {
-    int64_t cell0 = 0, tile0 = 0, col0 = 0;
-    int lb0 = 0, mb0 = 0;
+    int64_t cell0 = 0, tile0 = 0, col0 = 0, pcell0 = 0, row0 = 0;
+    int lb0 = 0, mb0 = 0, stage = 0;
+    const int sb = (int)storage_bytes(c->storage);
     for (auto &D : c->drops) {
         D.cell0 = cell0;
         D.tile0 = tile0;
         D.col0 = col0;
+        // rows padded to 16 bytes of population storage (and of the float
+        // force / velocity rows, whose pitch is the same)
+        const int align = 16 / sb;
+        D.pitch = (D.nx + align - 1) / align * align;
+        D.pcells = (int64_t)D.pitch * D.ny * D.nzf;
+        D.pcell0 = pcell0;
+        D.row0 = row0;
+        D.lb_rows = std::min(D.ny, c->cfg.lb_row_mult * lb_rows_per_group(D.nx));
+        D.lb_gpp = (D.ny + D.lb_rows - 1) / D.lb_rows;
         D.lb_block0 = lb0;
-        D.lb_nblocks = (int)((D.cells + c->cfg.lb_block - 1) / c->cfg.lb_block);
+        D.lb_nblocks = D.lb_gpp * D.nzf;
         D.mass_block0 = mb0;
         D.mass_nblocks = (int)((D.cells + 255) / 256);
+        stage = std::max(stage, lb_stage_bytes(D.lb_rows, D.pitch, sb));
         cell0 += D.cells;
+        pcell0 += D.pcells;
+        row0 += (int64_t)D.ny * D.nzf;
         tile0 += D.ntiles;
         col0 += (int64_t)D.nx * D.ny;
         lb0 += D.lb_nblocks;
         mb0 += D.mass_nblocks;
     }
     c->A.total_cells = cell0;
+    c->A.total_pcells = pcell0;
+    c->A.total_rows = row0;
     c->A.total_tiles = tile0;
     c->A.total_cols = col0;
     c->A.lb_blocks_total = lb0;
-    c->A.lb_cpb = c->cfg.lb_block;
+    c->A.lb_stage_bytes = stage;
     c->mass_blocks = mb0;
 }
 
@@ -352,15 +367,18 @@ void free_membrane_arrays(iblb_ctx *c)
     dfree(c->d_adj_start);
     dfree(c->d_adj);
     dfree(c->A.rec);
-    dfree(c->A.bin_list);
+    dfree(c->A.srec);
+    dfree(c->A.bin_rank);
     dfree(c->A.red_part);
     dfree(c->A.red_out);
+    dfree(c->A.vc_done);
+    c->A.vc_done = nullptr;
     c->A.qx = c->A.qy = c->A.qz = nullptr;
     c->A.node_drop = c->A.face_drop = nullptr;
     c->d_tri = c->d_adj_start = c->d_adj = nullptr;
     c->A.tri = c->A.adj_start = c->A.adj = nullptr;
-    c->A.rec = nullptr;
-    c->A.bin_list = nullptr;
+    c->A.rec = c->A.srec = nullptr;
+    c->A.bin_rank = nullptr;
     c->A.red_part = c->A.red_out = nullptr;
 }
 
@@ -381,7 +399,7 @@ int rebuild_membranes(iblb_ctx *c)
         D.red_chunk0 = chunks;
         int nc = 0;
         if (D.nnodes) {
-            nc = std::max((D.ntri + RED_FACES - 1) / RED_FACES, (D.nnodes + RED_NODES - 1) / RED_NODES);
+            nc = std::max((D.ntri + VC_ITEMS - 1) / VC_ITEMS, (D.nnodes + VC_ITEMS - 1) / VC_ITEMS);
             nc = std::max(nc, 1);
         }
         D.red_nchunks = nc;
@@ -433,9 +451,12 @@ int rebuild_membranes(iblb_ctx *c)
     CK(dalloc(&c->d_adj_start, N + 1));
     CK(dalloc(&c->d_adj, adj.size()));
     CK(dalloc(&c->A.rec, N));
-    CK(dalloc(&c->A.bin_list, N));
+    CK(dalloc(&c->A.srec, N));
+    CK(dalloc(&c->A.bin_rank, N));
     CK(dalloc(&c->A.red_part, (size_t)NRED * std::max(chunks, 1)));
     CK(dalloc(&c->A.red_out, (size_t)NRED * c->ndrops));
+    CK(dalloc(&c->A.vc_done, (size_t)c->ndrops));
+    CK(cudaMemsetAsync(c->A.vc_done, 0, sizeof(int) * c->ndrops, c->stream));
     c->A.tri = c->d_tri;
     c->A.adj_start = c->d_adj_start;
     c->A.adj = c->d_adj;
@@ -539,6 +560,8 @@ int accumulate_profile(iblb_ctx *c)
 
 int status_code(int flags)
 {
+    if (flags & ST_TIMEOUT)
+        return IBLB_E_TIMEOUT;
     if (flags & (ST_SPREAD_OVF | ST_COL_OVF))
         return IBLB_E_OVERFLOW;
     if (flags & (ST_NAN | ST_JUMP | ST_ESCAPE))
@@ -554,6 +577,7 @@ std::string status_text(int flags)
     if (flags & ST_ESCAPE) s += " a node left the fluid layers;";
     if (flags & ST_SPREAD_OVF) s += " more nodes overlap a band tile than the spread holds;";
     if (flags & ST_COL_OVF) s += " more ray crossings in a column than kept;";
+    if (flags & ST_TIMEOUT) s += " a bounded wait for a bulk copy gave up;";
     return s;
 }
 
@@ -653,12 +677,13 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
     const int64_t T = A.total_tiles;
     A.n_scan_blocks = (int)((T + 1 + SCAN_ITEMS - 1) / SCAN_ITEMS);
     A.active_cap = (int)T;
-    if ((e = cudaMalloc(&c->fbuf[0], sb * Q * A.total_cells)) != cudaSuccess ||
-        (e = cudaMalloc(&c->fbuf[1], sb * Q * A.total_cells)) != cudaSuccess ||
-        (e = dalloc(&A.F, 3 * (size_t)A.total_cells)) != cudaSuccess ||
-        (e = dalloc(&A.U, 3 * (size_t)A.total_cells)) != cudaSuccess ||
+    if ((e = cudaMalloc(&c->fbuf[0], sb * Q * A.total_pcells)) != cudaSuccess ||
+        (e = cudaMalloc(&c->fbuf[1], sb * Q * A.total_pcells)) != cudaSuccess ||
+        (e = dalloc(&A.F, 3 * (size_t)A.total_pcells)) != cudaSuccess ||
+        (e = dalloc(&A.U, 3 * (size_t)A.total_pcells)) != cudaSuccess ||
         (e = dalloc(&A.tile_gen, (size_t)T)) != cudaSuccess || (e = dalloc(&A.gen, 1)) != cudaSuccess ||
-        (e = dalloc(&A.n_active, 1)) != cudaSuccess || (e = dalloc(&A.active, (size_t)T)) != cudaSuccess ||
+        (e = dalloc(&A.row_gen, (size_t)A.total_rows)) != cudaSuccess ||
+        (e = dalloc(&A.n_active, 2)) != cudaSuccess || (e = dalloc(&A.active, 2 * (size_t)T)) != cudaSuccess ||
         (e = dalloc(&A.bin_cnt, (size_t)T + 1)) != cudaSuccess ||
         (e = dalloc(&A.bin_off, (size_t)T + 1)) != cudaSuccess ||
         (e = dalloc(&A.blk_sum, (size_t)A.n_scan_blocks)) != cudaSuccess ||
@@ -675,14 +700,15 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
     cudaStream_t s = c->stream;
     const uint32_t one = 1;
     if ((e = cudaMemsetAsync(A.tile_gen, 0, sizeof(uint32_t) * T, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.row_gen, 0, sizeof(uint32_t) * A.total_rows, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(A.gen, &one, sizeof(one), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(A.n_active, 0, sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.n_active, 0, 2 * sizeof(int), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.bin_cnt, 0, sizeof(int) * (T + 1), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.col_cnt, 0, sizeof(int) * A.total_cols, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.status, 0, sizeof(int) * 4 * n, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.clamped, 0, sizeof(int) * n, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(A.F, 0, sizeof(float) * 3 * A.total_cells, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(A.U, 0, sizeof(float) * 3 * A.total_cells, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.F, 0, sizeof(float) * 3 * A.total_pcells, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.U, 0, sizeof(float) * 3 * A.total_pcells, s)) != cudaSuccess ||
         (e = launch_init_populations(A, c->storage, c->fbuf[0], s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(c->d_drops, c->drops.data(), sizeof(Drop) * n, cudaMemcpyHostToDevice, s)) !=
             cudaSuccess ||
@@ -1051,25 +1077,25 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
             invalidate_graphs(c);
         c->profile = value != 0;
         return IBLB_OK;
-    case IBLB_OPT_LB_BLOCK: {
+    case IBLB_OPT_LB_BLOCKS_PER_SM:
+        if (value < 0 || value > 8)
+            return fail(c, IBLB_E_ARG, "resident blocks per SM must be in [0, 8]");
+        c->cfg.lb_blocks_per_sm = value;
+        invalidate_graphs(c);
+        return IBLB_OK;
+    case IBLB_OPT_LB_ROW_MULT: {
         if (value == 0)
-            value = 256;
-        if (value < 64 || value > 512 || value % 32)
-            return fail(c, IBLB_E_ARG, "block size must be a multiple of 32 in [64, 512]");
+            value = 1;
+        if (value < 1 || value > 4)
+            return fail(c, IBLB_E_ARG, "row multiplier must be in [1, 4]");
         int r = ensure_ready(c);
         if (r)
             return r;
-        c->cfg.lb_block = value;
+        c->cfg.lb_row_mult = value;
         layout(c);
         invalidate_graphs(c);
         return upload_drops(c);
     }
-    case IBLB_OPT_LB_PERSISTENT:
-        if (value < 0 || value > 1)
-            return fail(c, IBLB_E_ARG, "persistent flag must be 0 or 1");
-        c->cfg.lb_persistent = value;
-        invalidate_graphs(c);
-        return IBLB_OK;
     }
     return fail(c, IBLB_E_ARG, "unknown option");
 }
@@ -1114,14 +1140,14 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
         if (fp) {
             char line[256];
             while (fgets(line, sizeof(line), fp)) {
-                int blk = 0, pers = 0;
+                int bps = 0, mult = 0;
                 const char *bar = strchr(line, '|');
                 if (bar && (size_t)(bar - line) == strlen(key) && !strncmp(line, key, strlen(key)) &&
-                    sscanf(bar + 1, "%d %d", &blk, &pers) == 2) {
+                    sscanf(bar + 1, "%d %d", &bps, &mult) == 2) {
                     fclose(fp);
-                    if ((r = iblb_set_option(c, IBLB_OPT_LB_BLOCK, blk)))
+                    if ((r = iblb_set_option(c, IBLB_OPT_LB_BLOCKS_PER_SM, bps)))
                         return r;
-                    return iblb_set_option(c, IBLB_OPT_LB_PERSISTENT, pers);
+                    return iblb_set_option(c, IBLB_OPT_LB_ROW_MULT, mult);
                 }
             }
             fclose(fp);
@@ -1129,17 +1155,17 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
     }
     // time the stream-collide kernel alone from the current buffer into the
     // spare one: the current state is left untouched
-    const int blocks[4] = {128, 256, 384, 512};
+    const int bpsm[2] = {0, 1};
     float best = 1e30f;
-    int bb = 256, bp = 0;
+    int bb = 0, bm = 1;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     enter(c);
-    for (int pers = 0; pers <= 1; ++pers)
-        for (int bi = 0; bi < 4; ++bi) {
-            c->cfg.lb_block = blocks[bi];
-            c->cfg.lb_persistent = pers;
+    for (int mult = 1; mult <= 4; mult *= 2)
+        for (int bi = 0; bi < 2; ++bi) {
+            c->cfg.lb_blocks_per_sm = bpsm[bi];
+            c->cfg.lb_row_mult = mult;
             layout(c);
             if ((r = upload_drops(c)))
                 return r;
@@ -1155,15 +1181,15 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
             CK(cudaEventElapsedTime(&ms, e0, e1));
             if (ms < best) {
                 best = ms;
-                bb = blocks[bi];
-                bp = pers;
+                bb = bpsm[bi];
+                bm = mult;
             }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     leave(c);
-    c->cfg.lb_block = bb;
-    c->cfg.lb_persistent = bp;
+    c->cfg.lb_blocks_per_sm = bb;
+    c->cfg.lb_row_mult = bm;
     layout(c);
     invalidate_graphs(c);
     if ((r = upload_drops(c)))
@@ -1171,7 +1197,7 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
     if (cache_path) {
         FILE *fp = fopen(cache_path, "a");
         if (fp) {
-            fprintf(fp, "%s|%d %d\n", key, bb, bp);
+            fprintf(fp, "%s|%d %d\n", key, bb, bm);
             fclose(fp);
         }
     }
@@ -1200,8 +1226,8 @@ int iblb_save(iblb_ctx *c, const char *path)
         const Drop &D = c->drops[d];
         const int64_t dh[3] = {D.cells, D.nnodes, D.ntri};
         ok &= fwrite(dh, sizeof(dh), 1, fp) == 1;
-        buf.resize(sb * Q * D.cells);
-        CK(cudaMemcpy(buf.data(), (char *)c->fbuf[c->cur] + sb * Q * D.cell0, buf.size(), cudaMemcpyDeviceToHost));
+        buf.resize(sb * Q * D.pcells);
+        CK(cudaMemcpy(buf.data(), (char *)c->fbuf[c->cur] + sb * Q * D.pcell0, buf.size(), cudaMemcpyDeviceToHost));
         ok &= fwrite(buf.data(), buf.size(), 1, fp) == 1;
         if (D.nnodes) {
             ok &= fwrite(c->mem[d].xyz.data(), sizeof(double) * 3 * D.nnodes, 1, fp) == 1;
@@ -1235,11 +1261,11 @@ int iblb_load(iblb_ctx *c, const char *path)
         ok &= fread(dh, sizeof(dh), 1, fp) == 1 && dh[0] == D.cells && dh[1] == D.nnodes && dh[2] == D.ntri;
         if (!ok)
             break;
-        buf.resize(sb * Q * D.cells);
+        buf.resize(sb * Q * D.pcells);
         ok &= fread(buf.data(), buf.size(), 1, fp) == 1;
         if (!ok)
             break;
-        CK(cudaMemcpy((char *)c->fbuf[c->cur] + sb * Q * D.cell0, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy((char *)c->fbuf[c->cur] + sb * Q * D.pcell0, buf.data(), buf.size(), cudaMemcpyHostToDevice));
         if (D.nnodes) {
             std::vector<double> xyz(3 * (size_t)D.nnodes);
             double V0 = 0.0;

@@ -27,6 +27,13 @@ template <> __device__ __forceinline__ float from_d<float>(double v) { return (f
 template <> __device__ __forceinline__ __half from_d<__half>(double v) { return __double2half(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 
+// storage index of population k of compact cell c (rows padded to the pitch)
+__device__ __forceinline__ int64_t pop_index(const Drop &D, int k, int64_t c)
+{
+    const int64_t row = c / D.nx, x = c - row * D.nx;
+    return (int64_t)Q * D.pcell0 + (int64_t)k * D.pcells + x + (int64_t)D.pitch * row;
+}
+
 template <typename S>
 __global__ void export_pop_kernel(Arrays a, int d, const S *f, double *out)
 {
@@ -35,7 +42,7 @@ __global__ void export_pop_kernel(Arrays a, int d, const S *f, double *out)
     if (i >= Q * D.cells)
         return;
     const int k = (int)(i / D.cells);
-    out[i] = kW[k] * (double)D.rho0 + to_d<S>(f[(int64_t)Q * D.cell0 + i]);
+    out[i] = kW[k] * (double)D.rho0 + to_d<S>(f[pop_index(D, k, i - k * D.cells)]);
 }
 
 template <typename S>
@@ -46,14 +53,15 @@ __global__ void import_pop_kernel(Arrays a, int d, S *f, const double *in)
     if (i >= Q * D.cells)
         return;
     const int k = (int)(i / D.cells);
-    f[(int64_t)Q * D.cell0 + i] = from_d<S>(in[i] - kW[k] * (double)D.rho0);
+    f[pop_index(D, k, i - k * D.cells)] = from_d<S>(in[i] - kW[k] * (double)D.rho0);
 }
 
+// offsets 0 everywhere (rest state f_i = w_i rho0), padding included
 template <typename S>
 __global__ void init_pop_kernel(Arrays a, S *f)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < Q * a.total_cells)
+    if (i < Q * a.total_pcells)
         f[i] = from_d<S>(0.0);
 }
 
@@ -77,7 +85,7 @@ __global__ void macros_kernel(Arrays a, int d, const S *f, double *rho, double *
         return;
     double r = D.rho0, j[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < Q; ++k) {
-        const double s = to_d<S>(f[(int64_t)Q * D.cell0 + (int64_t)k * D.cells + c]);
+        const double s = to_d<S>(f[pop_index(D, k, c)]);
         r += s;
         for (int e = 0; e < 3; ++e)
             j[e] += kC[k][e] * s;
@@ -86,7 +94,7 @@ __global__ void macros_kernel(Arrays a, int d, const S *f, double *rho, double *
     double F[3] = {D.bf[0], D.bf[1], D.bf[2]};
     if (band_cell(a, D, c, xyz))
         for (int e = 0; e < 3; ++e)
-            F[e] += a.F[e * a.total_cells + D.cell0 + c];
+            F[e] += a.F[e * a.total_pcells + pop_index(D, 0, c) - (int64_t)Q * D.pcell0 + D.pcell0];
     rho[c] = r;
     // post-collision momentum = sum c_i f_i + F (BGK keeps rho U, Guo adds (1-1/2tau) F)
     for (int e = 0; e < 3; ++e)
@@ -101,8 +109,9 @@ __global__ void force_kernel(Arrays a, int d, double *F)
         return;
     int xyz[3];
     const bool band = band_cell(a, D, c, xyz);
+    const int64_t g = pop_index(D, 0, c) - (int64_t)Q * D.pcell0 + D.pcell0;   // padded field index
     for (int e = 0; e < 3; ++e)
-        F[e * D.cells + c] = (double)D.bf[e] + (band ? (double)a.F[e * a.total_cells + D.cell0 + c] : 0.0);
+        F[e * D.cells + c] = (double)D.bf[e] + (band ? (double)a.F[e * a.total_pcells + g] : 0.0);
 }
 
 __global__ void inside_kernel(Arrays a, int d, uint8_t *inside)
@@ -156,7 +165,7 @@ cudaError_t launch_import_populations(const Arrays &a, int d, int storage, void 
 
 cudaError_t launch_init_populations(const Arrays &a, int storage, void *f, cudaStream_t s)
 {
-    const unsigned g = blocks_for(Q * a.total_cells, 256);
+    const unsigned g = blocks_for(Q * a.total_pcells, 256);
     switch (storage) {
     case 0: init_pop_kernel<float><<<g, 256, 0, s>>>(a, (float *)f); break;
     case 1: init_pop_kernel<__half><<<g, 256, 0, s>>>(a, (__half *)f); break;

@@ -1,12 +1,14 @@
 // ib.cu -- the membrane side of the IB-LB step:
 //   * nodal forces: surface tension phi_sigma,j = -sigma dA/dq_j (Sec. II B)
-//     plus the wall interaction phi_Pi,j = -(chi_j/3) Pi(h_j) n_j (Sec. II C),
-//     one thread per node gathering over its incident faces in a fixed order;
+//     plus the wall interaction phi_Pi,j = -(chi_j/3) Pi(h_j) n_j (Sec. II C);
+//     8 lanes per node share its incident faces, partial sums meet in a fixed
+//     shuffle tree;
 //   * force spreading F(x) = sum_j phi_j Delta(q_j - x) (eq. force_spread) as
 //     a deterministic binned gather: nodes are binned by the 4^3 tile of their
-//     support's base cell, every band tile gathers the nodes overlapping it
-//     and adds their contributions in increasing node index, so the result
-//     does not depend on launch shapes or on the other droplets of a batch;
+//     support's base cell, the tiles next to a non-empty bin form the band,
+//     and every band tile gathers the nodes overlapping it and adds their
+//     contributions in increasing node index, so the result depends neither
+//     on launch shapes nor on the other droplets of a batch;
 //   * interpolation qdot_j = sum_x U(x) Delta(q_j - x) (eq. vel_interpolation)
 //     and forward-Euler advection q_j += qdot_j, 16 lanes per node.
 // Node positions are FP64 so that edge vectors and kernel offsets are exact
@@ -16,6 +18,8 @@
 namespace iblb {
 
 namespace {
+
+constexpr int FL = 8;          // lanes per node in the force kernel
 
 __device__ __forceinline__ float psi_near(float r)  // 0 <= r <= 1
 {
@@ -49,63 +53,82 @@ __device__ __forceinline__ int tile_key(const Drop &D, int bx, int by, int bz)
     return (bx >> 2) + D.tx * ((by >> 2) + D.ty * tz);
 }
 
-// One thread per node.  Thread 0 also opens the step: generation += 1 and an
-// empty band list.
-__global__ void node_force_kernel(Arrays a)
+__device__ __forceinline__ int find_drop_tile(const Drop *D, int n, int64_t t)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j == 0) {
-        *a.gen += 1u;
-        *a.n_active = 0;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (D[mid].tile0 <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
     }
-    if (j >= a.total_nodes)
+    return lo;
+}
+
+// FL lanes per node; lane l takes the node's incident faces l, l + FL, ...
+// Lane 0 of each group also opens the step for the whole grid (thread 0:
+// generation += 1, empty band list) and writes the node record.
+__global__ void __launch_bounds__(128) node_force_kernel(Arrays a)
+{
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = gid / FL, l = gid % FL;
+    if (gid == 0) {
+        const uint32_t g = *a.gen + 1u;
+        *a.gen = g;
+        a.n_active[g & 1u] = 0;    // the band list of this step; the other one holds the previous band
+    }
+    const bool valid = j < a.total_nodes;
+    float gx = 0.f, gy = 0.f, gz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, chi = 0.f;
+    if (valid) {
+        const int e1 = a.adj_start[j + 1];
+        for (int e = a.adj_start[j] + l; e < e1; e += FL) {
+            const int code = a.adj[e];
+            const int t = code >> 2, k = code & 3;
+            const int v0 = a.tri[3 * t], v1 = a.tri[3 * t + 1], v2 = a.tri[3 * t + 2];
+            const double x0 = a.qx[v0], y0 = a.qy[v0], z0 = a.qz[v0];
+            const double x1 = a.qx[v1], y1 = a.qy[v1], z1 = a.qz[v1];
+            const double x2 = a.qx[v2], y2 = a.qy[v2], z2 = a.qz[v2];
+            const float e1x = (float)(x1 - x0), e1y = (float)(y1 - y0), e1z = (float)(z1 - z0);
+            const float e2x = (float)(x2 - x0), e2y = (float)(y2 - y0), e2z = (float)(z2 - z0);
+            const float Nx = e1y * e2z - e1z * e2y;
+            const float Ny = e1z * e2x - e1x * e2z;
+            const float Nz = e1x * e2y - e1y * e2x;
+            const float len = sqrtf(Nx * Nx + Ny * Ny + Nz * Nz);
+            const float il = 1.0f / len;
+            const float hx = Nx * il, hy = Ny * il, hz = Nz * il;
+            // dA/dq_k = 1/2 n x (q_prev - q_next), corners in CCW order
+            float dx, dy, dz;
+            if (k == 0) {
+                dx = (float)(x2 - x1); dy = (float)(y2 - y1); dz = (float)(z2 - z1);
+            } else if (k == 1) {
+                dx = (float)(x0 - x2); dy = (float)(y0 - y2); dz = (float)(z0 - z2);
+            } else {
+                dx = (float)(x1 - x0); dy = (float)(y1 - y0); dz = (float)(z1 - z0);
+            }
+            gx += 0.5f * (hy * dz - hz * dy);
+            gy += 0.5f * (hz * dx - hx * dz);
+            gz += 0.5f * (hx * dy - hy * dx);
+            nx += hx;
+            ny += hy;
+            nz += hz;
+            chi += 0.5f * len;
+        }
+    }
+    for (int o = FL / 2; o >= 1; o >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        nx += __shfl_xor_sync(0xffffffffu, nx, o);
+        ny += __shfl_xor_sync(0xffffffffu, ny, o);
+        nz += __shfl_xor_sync(0xffffffffu, nz, o);
+        chi += __shfl_xor_sync(0xffffffffu, chi, o);
+    }
+    if (!valid || l != 0)
         return;
     const int d = a.node_drop[j];
     const Drop &D = a.drops[d];
     const double qx = a.qx[j], qy = a.qy[j], qz = a.qz[j];
-    float gx = 0.f, gy = 0.f, gz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, chi = 0.f;
-    for (int e = a.adj_start[j]; e < a.adj_start[j + 1]; ++e) {
-        const int code = a.adj[e];
-        const int t = code >> 2, k = code & 3;
-        const int v0 = a.tri[3 * t], v1 = a.tri[3 * t + 1], v2 = a.tri[3 * t + 2];
-        const double x0 = a.qx[v0], y0 = a.qy[v0], z0 = a.qz[v0];
-        const float e1x = (float)(a.qx[v1] - x0), e1y = (float)(a.qy[v1] - y0), e1z = (float)(a.qz[v1] - z0);
-        const float e2x = (float)(a.qx[v2] - x0), e2y = (float)(a.qy[v2] - y0), e2z = (float)(a.qz[v2] - z0);
-        const float Nx = e1y * e2z - e1z * e2y;
-        const float Ny = e1z * e2x - e1x * e2z;
-        const float Nz = e1x * e2y - e1y * e2x;
-        const float len = sqrtf(Nx * Nx + Ny * Ny + Nz * Nz);
-        const float il = 1.0f / len;
-        const float hx = Nx * il, hy = Ny * il, hz = Nz * il;
-        // dA/dq_k = 1/2 n x (q_prev - q_next), corners in CCW order
-        const int vp = k == 0 ? v2 : (k == 1 ? v0 : v1);
-        const int vn = k == 0 ? v1 : (k == 1 ? v2 : v0);
-        const float dx = (float)(a.qx[vp] - a.qx[vn]);
-        const float dy = (float)(a.qy[vp] - a.qy[vn]);
-        const float dz = (float)(a.qz[vp] - a.qz[vn]);
-        gx += 0.5f * (hy * dz - hz * dy);
-        gy += 0.5f * (hz * dx - hx * dz);
-        gz += 0.5f * (hx * dy - hy * dx);
-        nx += hx;
-        ny += hy;
-        nz += hz;
-        chi += 0.5f * len;
-    }
-    float px = -D.sigma * gx, py = -D.sigma * gy, pz = -D.sigma * gz;
-    if (D.wetting) {
-        float h = (float)(qz - 0.5);
-        if (h < D.hmin) {
-            h = D.hmin;
-            atomicAdd(&a.clamped[d], 1);
-        }
-        const float r = D.xi / h;
-        const float Pi = D.A * (ipow(r, D.n) - ipow(r, D.m));
-        const float inl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
-        const float s = -(chi * (1.0f / 3.0f)) * Pi * inl;
-        px += s * nx;
-        py += s * ny;
-        pz += s * nz;
-    }
     NodeRec r;
     if (!(fabs(qx) < 1e8 && fabs(qy) < 1e8 && fabs(qz) < 1e8)) {
         // non-finite or absurd position: no support, no bin, flagged
@@ -115,9 +138,24 @@ __global__ void node_force_kernel(Arrays a)
         for (int k = 0; k < 4; ++k)
             r.wx[k] = r.wy[k] = r.wz[k] = 0.0f;
         r.phi[0] = r.phi[1] = r.phi[2] = 0.0f;
-        r.spare = 0;
+        r.spare = d;
         a.rec[j] = r;
         return;
+    }
+    float px = -D.sigma * gx, py = -D.sigma * gy, pz = -D.sigma * gz;
+    if (D.wetting) {
+        float h = (float)(qz - 0.5);
+        if (h < D.hmin) {
+            h = D.hmin;
+            atomicAdd(&a.clamped[d], 1);
+        }
+        const float r0 = D.xi / h;
+        const float Pi = D.A * (ipow(r0, D.n) - ipow(r0, D.m));
+        const float inl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
+        const float s = -(chi * (1.0f / 3.0f)) * Pi * inl;
+        px += s * nx;
+        py += s * ny;
+        pz += s * nz;
     }
     // support of the 4-point kernel: base-1 .. base+2 on each axis
     const double fbx = floor(qx), fby = floor(qy), fbz = floor(qz);
@@ -134,25 +172,46 @@ __global__ void node_force_kernel(Arrays a)
     r.phi[0] = px;
     r.phi[1] = py;
     r.phi[2] = pz;
-    r.spare = 0;
+    r.spare = d;
     const int key = tile_key(D, r.bx, r.by, r.bz);
     r.key = key < 0 ? -1 : (int)(D.tile0 + key);
     if (key < 0)
         atomicOr(&a.status[4 * d], ST_ESCAPE);
     else
-        atomicAdd(&a.bin_cnt[r.key], 1);
+        a.bin_rank[j] = atomicAdd(&a.bin_cnt[r.key], 1);
     a.rec[j] = r;
 }
 
-// Block-level exclusive scan of the bin counts (SCAN_ITEMS per block).
-__global__ void __launch_bounds__(1024) scan_blocks_kernel(const int *__restrict__ cnt, int64_t n,
-                                                           int *__restrict__ off, int *__restrict__ blk_sum)
+// Is tile t in the band, i.e. is one of the bins around it non-empty?
+__device__ __forceinline__ bool tile_in_band(const Arrays &a, int64_t t)
+{
+    const int d = find_drop_tile(a.drops, a.ndrops, t);
+    const Drop &D = a.drops[d];
+    const int local = (int)(t - D.tile0);
+    const int kx = local % D.tx, ky = (local / D.tx) % D.ty, kz = local / (D.tx * D.ty);
+    int lx[4], ly[4], lz[4];
+    const int nxl = tile_neighbours(kx, D.tx, D.nx, true, lx);
+    const int nyl = tile_neighbours(ky, D.ty, D.ny, true, ly);
+    const int nzl = tile_neighbours(kz, D.tz, D.nzf, !D.walls, lz);
+    bool any = false;
+    for (int iz = 0; iz < nzl; ++iz)
+        for (int iy = 0; iy < nyl; ++iy)
+            for (int ix = 0; ix < nxl; ++ix)
+                any |= a.bin_cnt[D.tile0 + lx[ix] + (int64_t)D.tx * (ly[iy] + (int64_t)D.ty * lz[iz])] > 0;
+    return any;
+}
+
+// Block-level exclusive scan of the bin counts (SCAN_ITEMS per block), and
+// band marking of the same tiles: tile_gen = generation for band tiles,
+// which are appended to the band list (warp-aggregated).
+__global__ void __launch_bounds__(1024) scan_mark_kernel(Arrays a)
 {
     __shared__ int warp_tot[32];
+    const int64_t n = a.total_tiles + 1;   // the last count is a zero sentinel
     const int64_t base = (int64_t)blockIdx.x * SCAN_ITEMS + 4 * threadIdx.x;
     int v[4];
     for (int i = 0; i < 4; ++i)
-        v[i] = base + i < n ? cnt[base + i] : 0;
+        v[i] = base + i < n ? a.bin_cnt[base + i] : 0;
     const int local = v[0] + v[1] + v[2] + v[3];
     int inc = local;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -177,11 +236,65 @@ __global__ void __launch_bounds__(1024) scan_blocks_kernel(const int *__restrict
     int run = inc - local + (w ? warp_tot[w - 1] : 0);
     for (int i = 0; i < 4; ++i) {
         if (base + i < n)
-            off[base + i] = run;
+            a.bin_off[base + i] = run;
         run += v[i];
     }
     if (threadIdx.x == blockDim.x - 1)
-        blk_sum[blockIdx.x] = warp_tot[(blockDim.x >> 5) - 1];
+        a.blk_sum[blockIdx.x] = warp_tot[(blockDim.x >> 5) - 1];
+
+    const uint32_t gen = *a.gen;
+    const int cur = (int)(gen & 1u);
+    int *list = a.active + (int64_t)cur * a.active_cap;
+    for (int i = 0; i < 4; ++i) {
+        const int64_t t = base + i;
+        const bool band = t < a.total_tiles && tile_in_band(a, t);
+        if (band) {
+            a.tile_gen[t] = gen;
+            // the rows crossing this tile meet the band
+            const int d = find_drop_tile(a.drops, a.ndrops, t);
+            const Drop &D = a.drops[d];
+            const int local = (int)(t - D.tile0);
+            const int ky = (local / D.tx) % D.ty, kz = local / (D.tx * D.ty);
+            for (int z = 4 * kz; z < min(4 * kz + 4, D.nzf); ++z)
+                for (int y = 4 * ky; y < min(4 * ky + 4, D.ny); ++y)
+                    a.row_gen[D.row0 + y + (int64_t)D.ny * z] = gen;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, band);
+        if (!m)
+            continue;
+        int slot0 = 0;
+        if (lane == __ffs(m) - 1)
+            slot0 = atomicAdd(&a.n_active[cur], __popc(m));
+        slot0 = __shfl_sync(0xffffffffu, slot0, __ffs(m) - 1);
+        if (band) {
+            const int s = slot0 + __popc(m & ((1u << lane) - 1u));
+            if (s < a.active_cap)
+                list[s] = (int)t;
+        }
+    }
+
+    // zero the force density of the previous step's band tiles (the spread
+    // rewrites the tiles of this step's band), so that F vanishes outside it
+    const int prev = cur ^ 1;
+    const int64_t nprev = (int64_t)min(a.n_active[prev], a.active_cap) * TILE_CELLS;
+    const int *plist = a.active + (int64_t)prev * a.active_cap;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nprev;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = plist[idx / TILE_CELLS];
+        const int cell = (int)(idx % TILE_CELLS);
+        const int d = find_drop_tile(a.drops, a.ndrops, t);
+        const Drop &D = a.drops[d];
+        const int local = (int)(t - D.tile0);
+        const int X = 4 * (local % D.tx) + (cell & 3);
+        const int Y = 4 * ((local / D.tx) % D.ty) + ((cell >> 2) & 3);
+        const int Z = 4 * (local / (D.tx * D.ty)) + (cell >> 4);
+        if (X < D.nx && Y < D.ny && Z < D.nzf) {
+            const int64_t g = D.pcell0 + X + (int64_t)D.pitch * (Y + (int64_t)D.ny * Z);
+            a.F[g] = 0.0f;
+            a.F[a.total_pcells + g] = 0.0f;
+            a.F[2 * a.total_pcells + g] = 0.0f;
+        }
+    }
 }
 
 // Exclusive scan of the block totals by one block (serial over chunks of 1024).
@@ -226,60 +339,31 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(const int *__restrict__ 
     }
 }
 
-// start of bin t in bin_list; the scan covers total_tiles + 1 entries (the
+// start of bin t in the sorted records; the scan covers total_tiles + 1 entries (the
 // last count is always zero), so bin t ends where bin t + 1 begins
 __device__ __forceinline__ int bin_begin(const Arrays &a, int64_t t)
 {
     return a.bin_off[t] + a.blk_off[t / SCAN_ITEMS];
 }
 
-__device__ __forceinline__ int find_drop_tile(const Drop *D, int n, int64_t t)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (D[mid].tile0 <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-// Place every binned node in its bin (order inside a bin is irrelevant: the
-// gather sorts by node index).  The node that empties its bin counter marks
-// the tiles around the bin as band tiles of this step.
+// Copy every binned node's record into bin order (the order inside a bin is
+// the arrival order of the binning atomics, which is irrelevant: the gather
+// sorts by node index).  The sorted copy carries the node index in `spare`.
+// The node of rank 0 resets its bin counter for the next step.
 __global__ void fill_kernel(Arrays a)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.total_nodes)
         return;
-    const int key = a.rec[j].key;
-    if (key < 0)
+    NodeRec r = a.rec[j];
+    if (r.key < 0)
         return;
-    const int old = atomicSub(&a.bin_cnt[key], 1);
-    a.bin_list[bin_begin(a, key) + old - 1] = j;
-    if (old != 1)
-        return;
-    const uint32_t gen = *a.gen;
-    const int d = find_drop_tile(a.drops, a.ndrops, key);
-    const Drop &D = a.drops[d];
-    const int local = key - (int)D.tile0;
-    const int kx = local % D.tx, ky = (local / D.tx) % D.ty, kz = local / (D.tx * D.ty);
-    int lx[4], ly[4], lz[4];
-    const int nxl = tile_neighbours(kx, D.tx, D.nx, true, lx);
-    const int nyl = tile_neighbours(ky, D.ty, D.ny, true, ly);
-    const int nzl = tile_neighbours(kz, D.tz, D.nzf, !D.walls, lz);
-    for (int iz = 0; iz < nzl; ++iz)
-        for (int iy = 0; iy < nyl; ++iy)
-            for (int ix = 0; ix < nxl; ++ix) {
-                const int64_t t = D.tile0 + lx[ix] + (int64_t)D.tx * (ly[iy] + (int64_t)D.ty * lz[iz]);
-                if (atomicExch(&a.tile_gen[t], gen) != gen) {
-                    const int s = atomicAdd(a.n_active, 1);
-                    if (s < a.active_cap)
-                        a.active[s] = (int)t;
-                }
-            }
+    const int rank = a.bin_rank[j];
+    const int key = r.key;
+    r.spare = j;
+    a.srec[bin_begin(a, key) + rank] = r;
+    if (rank == 0)
+        a.bin_cnt[key] = 0;
 }
 
 // offset of cell X from support base b on a periodic axis of n cells,
@@ -304,20 +388,30 @@ __device__ __forceinline__ bool support_hits(int lo, int hi, int b, int n, bool 
     return false;
 }
 
-// One 64-thread block per band tile (block-stride over the band list); each
-// thread owns one cell of the tile.
-__global__ void __launch_bounds__(TILE_CELLS) spread_kernel(Arrays a)
+// One 256-thread block per band tile (block-stride over the band list).  The
+// ranges of the neighbouring bins are read in parallel, the records of the
+// nodes whose support overlaps the tile are staged in parallel and sorted by
+// node index; four threads per cell add disjoint quarters of the sorted list
+// and the quarters are summed in a fixed order, so every cell's force is the
+// same for any launch shape.
+constexpr int SPREAD_THREADS = 4 * TILE_CELLS;
+
+__global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
 {
     __shared__ int s_cnt;
+    __shared__ int s_beg[64], s_pre[65];
     __shared__ int s_node[SPREAD_CAP];
     __shared__ short s_perm[SPREAD_CAP];
     __shared__ int s_b[3][SPREAD_CAP];
     __shared__ float s_w[12][SPREAD_CAP];
     __shared__ float s_phi[3][SPREAD_CAP];
-    const int nact = min(*a.n_active, a.active_cap);
+    __shared__ float s_part[3][3][TILE_CELLS];
+    const int cur = (int)(*a.gen & 1u);
+    const int nact = min(a.n_active[cur], a.active_cap);
+    const int *list = a.active + (int64_t)cur * a.active_cap;
     const int tid = threadIdx.x;
     for (int it = blockIdx.x; it < nact; it += gridDim.x) {
-        const int64_t T = a.active[it];
+        const int64_t T = list[it];
         const int d = find_drop_tile(a.drops, a.ndrops, T);
         const Drop &D = a.drops[d];
         const int local = (int)(T - D.tile0);
@@ -328,43 +422,56 @@ __global__ void __launch_bounds__(TILE_CELLS) spread_kernel(Arrays a)
         const int nxl = tile_neighbours(kx, D.tx, D.nx, true, lx);
         const int nyl = tile_neighbours(ky, D.ty, D.ny, true, ly);
         const int nzl = tile_neighbours(kz, D.tz, D.nzf, !D.walls, lz);
-        if (tid == 0)
+        const int nb = nxl * nyl * nzl;
+        // bin ranges, one thread per neighbouring bin
+        if (tid < nb) {
+            const int ix = tid % nxl, iy = (tid / nxl) % nyl, iz = tid / (nxl * nyl);
+            const int64_t B = D.tile0 + lx[ix] + (int64_t)D.tx * (ly[iy] + (int64_t)D.ty * lz[iz]);
+            const int b0 = bin_begin(a, B);
+            s_beg[tid] = b0;
+            s_pre[tid + 1] = bin_begin(a, B + 1) - b0;
+        }
+        if (tid == 0) {
             s_cnt = 0;
+            s_pre[0] = 0;
+        }
         __syncthreads();
-        for (int iz = 0; iz < nzl; ++iz)
-            for (int iy = 0; iy < nyl; ++iy)
-                for (int ix = 0; ix < nxl; ++ix) {
-                    const int64_t B = D.tile0 + lx[ix] + (int64_t)D.tx * (ly[iy] + (int64_t)D.ty * lz[iz]);
-                    const int e0 = bin_begin(a, B), e1 = bin_begin(a, B + 1);
-                    for (int e = e0 + tid; e < e1; e += TILE_CELLS) {
-                        const int j = a.bin_list[e];
-                        const NodeRec &r = a.rec[j];
-                        if (!support_hits(X0, X1, r.bx, D.nx, true) || !support_hits(Y0, Y1, r.by, D.ny, true) ||
-                            !support_hits(Z0, Z1, r.bz, D.nzf, !D.walls))
-                            continue;
-                        const int slot = atomicAdd(&s_cnt, 1);
-                        if (slot >= SPREAD_CAP) {
-                            atomicOr(&a.status[4 * d], ST_SPREAD_OVF);
-                            continue;
-                        }
-                        s_node[slot] = j;
-                        s_b[0][slot] = r.bx;
-                        s_b[1][slot] = r.by;
-                        s_b[2][slot] = r.bz;
-                        for (int k = 0; k < 4; ++k) {
-                            s_w[k][slot] = r.wx[k];
-                            s_w[4 + k][slot] = r.wy[k];
-                            s_w[8 + k][slot] = r.wz[k];
-                        }
-                        s_phi[0][slot] = r.phi[0];
-                        s_phi[1][slot] = r.phi[1];
-                        s_phi[2][slot] = r.phi[2];
-                    }
-                }
+        if (tid == 0)
+            for (int k = 0; k < nb; ++k)
+                s_pre[k + 1] += s_pre[k];
+        __syncthreads();
+        const int total = s_pre[nb];
+        for (int e = tid; e < total; e += SPREAD_THREADS) {
+            int k = 0;
+            while (s_pre[k + 1] <= e)
+                ++k;
+            const NodeRec &r = a.srec[s_beg[k] + e - s_pre[k]];
+            const int4 hdr = *reinterpret_cast<const int4 *>(&r);
+            if (!support_hits(X0, X1, hdr.x, D.nx, true) || !support_hits(Y0, Y1, hdr.y, D.ny, true) ||
+                !support_hits(Z0, Z1, hdr.z, D.nzf, !D.walls))
+                continue;
+            const int slot = atomicAdd(&s_cnt, 1);
+            if (slot >= SPREAD_CAP) {
+                atomicOr(&a.status[4 * d], ST_SPREAD_OVF);
+                continue;
+            }
+            s_node[slot] = r.spare;
+            s_b[0][slot] = hdr.x;
+            s_b[1][slot] = hdr.y;
+            s_b[2][slot] = hdr.z;
+            for (int q = 0; q < 4; ++q) {
+                s_w[q][slot] = r.wx[q];
+                s_w[4 + q][slot] = r.wy[q];
+                s_w[8 + q][slot] = r.wz[q];
+            }
+            s_phi[0][slot] = r.phi[0];
+            s_phi[1][slot] = r.phi[1];
+            s_phi[2][slot] = r.phi[2];
+        }
         __syncthreads();
         const int cnt = min(s_cnt, SPREAD_CAP);
         // rank sort by node index: contributions are added in increasing j
-        for (int e = tid; e < cnt; e += TILE_CELLS) {
+        for (int e = tid; e < cnt; e += SPREAD_THREADS) {
             const int key = s_node[e];
             int rank = 0;
             for (int k = 0; k < cnt; ++k)
@@ -372,9 +479,11 @@ __global__ void __launch_bounds__(TILE_CELLS) spread_kernel(Arrays a)
             s_perm[rank] = (short)e;
         }
         __syncthreads();
-        const int X = X0 + (tid & 3), Y = Y0 + ((tid >> 2) & 3), Z = Z0 + (tid >> 4);
+        const int cell = tid & (TILE_CELLS - 1), part = tid >> 6;
+        const int X = X0 + (cell & 3), Y = Y0 + ((cell >> 2) & 3), Z = Z0 + (cell >> 4);
+        const int k0 = (part * cnt) >> 2, k1 = ((part + 1) * cnt) >> 2;
         float fx = 0.f, fy = 0.f, fz = 0.f;
-        for (int k = 0; k < cnt; ++k) {
+        for (int k = k0; k < k1; ++k) {
             const int e = s_perm[k];
             const int dx = per_off(X, s_b[0][e], D.nx);
             const int dy = per_off(Y, s_b[1][e], D.ny);
@@ -386,11 +495,22 @@ __global__ void __launch_bounds__(TILE_CELLS) spread_kernel(Arrays a)
             fy += s_phi[1][e] * w;
             fz += s_phi[2][e] * w;
         }
-        if (X < D.nx && Y < D.ny && Z < D.nzf) {
-            const int64_t g = D.cell0 + X + (int64_t)D.nx * (Y + (int64_t)D.ny * Z);
+        if (part > 0) {
+            s_part[part - 1][0][cell] = fx;
+            s_part[part - 1][1][cell] = fy;
+            s_part[part - 1][2][cell] = fz;
+        }
+        __syncthreads();
+        if (part == 0 && X < D.nx && Y < D.ny && Z < D.nzf) {
+            for (int p = 0; p < 3; ++p) {
+                fx += s_part[p][0][cell];
+                fy += s_part[p][1][cell];
+                fz += s_part[p][2][cell];
+            }
+            const int64_t g = D.pcell0 + X + (int64_t)D.pitch * (Y + (int64_t)D.ny * Z);
             a.F[g] = fx;
-            a.F[a.total_cells + g] = fy;
-            a.F[2 * a.total_cells + g] = fz;
+            a.F[a.total_pcells + g] = fy;
+            a.F[2 * a.total_pcells + g] = fz;
         }
         __syncthreads();
     }
@@ -398,7 +518,7 @@ __global__ void __launch_bounds__(TILE_CELLS) spread_kernel(Arrays a)
 
 // 16 lanes per node: lane l covers support row (dy, dz) = (l & 3, l >> 2)
 // and the four cells of that row; partial sums meet in a fixed shuffle tree.
-__global__ void interp_advect_kernel(Arrays a)
+__global__ void __launch_bounds__(256) interp_advect_kernel(Arrays a)
 {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = gid >> 4, l = gid & 15;
@@ -406,9 +526,9 @@ __global__ void interp_advect_kernel(Arrays a)
     float ax = 0.f, ay = 0.f, az = 0.f;
     int d = 0;
     if (valid) {
-        d = a.node_drop[j];
-        const Drop &D = a.drops[d];
         const NodeRec &r = a.rec[j];
+        d = r.spare;
+        const Drop &D = a.drops[d];
         if (r.key >= 0) {
             const int dy = l & 3, dz = l >> 2;
             int Z = r.bz - 1 + dz;
@@ -420,13 +540,13 @@ __global__ void interp_advect_kernel(Arrays a)
             if (fluid) {
                 const int Y = wrapi(r.by - 1 + dy, D.ny);
                 const float wyz = r.wy[dy] * r.wz[dz];
-                const int64_t row = D.cell0 + (int64_t)D.nx * (Y + (int64_t)D.ny * Z);
+                const int64_t row = D.pcell0 + (int64_t)D.pitch * (Y + (int64_t)D.ny * Z);
                 for (int dx = 0; dx < 4; ++dx) {
                     const int64_t g = row + wrapi(r.bx - 1 + dx, D.nx);
                     const float w = r.wx[dx] * wyz;
                     ax += a.U[g] * w;
-                    ay += a.U[a.total_cells + g] * w;
-                    az += a.U[2 * a.total_cells + g] * w;
+                    ay += a.U[a.total_pcells + g] * w;
+                    az += a.U[2 * a.total_pcells + g] * w;
                 }
             }
         }
@@ -447,13 +567,16 @@ __global__ void interp_advect_kernel(Arrays a)
     }
 }
 
+int g_sm_count = 0;
+
 }  // namespace
 
 cudaError_t launch_node_force(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    node_force_kernel<<<(a.total_nodes + 127) / 128, 128, 0, s>>>(a);
+    const int64_t threads = (int64_t)a.total_nodes * FL;
+    node_force_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -461,13 +584,15 @@ cudaError_t launch_spread(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    scan_blocks_kernel<<<a.n_scan_blocks, 1024, 0, s>>>(a.bin_cnt, a.total_tiles + 1, a.bin_off, a.blk_sum);
+    if (!g_sm_count) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    }
+    scan_mark_kernel<<<a.n_scan_blocks, 1024, 0, s>>>(a);
     scan_top_kernel<<<1, 1024, 0, s>>>(a.blk_sum, a.n_scan_blocks, a.blk_off);
-    fill_kernel<<<(a.total_nodes + 127) / 128, 128, 0, s>>>(a);
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    spread_kernel<<<sms * 16, TILE_CELLS, 0, s>>>(a);
+    fill_kernel<<<(a.total_nodes + 255) / 256, 256, 0, s>>>(a);
+    spread_kernel<<<g_sm_count * 5, SPREAD_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -17,8 +17,9 @@ constexpr int TILE_CELLS = 64;
 constexpr int MAXC = 16;           // ray crossings kept per lattice column
 constexpr int SPREAD_CAP = 512;    // nodes whose stencil overlaps one tile
 constexpr int SCAN_ITEMS = 4096;   // elements per block of the tile scan
-constexpr int RED_FACES = 2048;    // faces per reduction chunk
-constexpr int RED_NODES = 1024;    // nodes per reduction chunk
+constexpr int RED_FACES = 2048;    // faces per chunk of the observation reductions
+constexpr int RED_NODES = 1024;    // nodes per chunk of the observation reductions
+constexpr int VC_ITEMS = 256;      // faces (and nodes) per chunk of the volume correction
 constexpr int NRED = 8;            // partial sums per chunk (see reduce.cu)
 
 // device status bits (Arrays::status[4 * d + 0])
@@ -27,16 +28,22 @@ constexpr int ST_JUMP = 2;         // |qdot| > 1/2 in one step
 constexpr int ST_SPREAD_OVF = 4;   // more than SPREAD_CAP nodes overlap a tile
 constexpr int ST_COL_OVF = 8;      // more than MAXC crossings in a column
 constexpr int ST_ESCAPE = 16;      // a node left the fluid in z
+constexpr int ST_TIMEOUT = 32;     // a bounded wait for a bulk copy gave up
 
 // Per-droplet descriptor (device resident, read-only in kernels).
 struct Drop {
     int nx, ny, nz, nzf, walls;
     int tx, ty, tz, ntiles;
-    int64_t cell0, cells;          // first cell in the pooled cell arrays, count
+    int64_t cell0, cells;          // first cell in the pooled (compact) cell arrays, count
     int64_t tile0;                 // first tile in the pooled tile arrays
     int64_t col0;                  // first column (nx*ny per droplet)
+    int pitch;                     // population row pitch: nx rounded up to 16 elements
+    int64_t pcell0, pcells;        // population planes: first padded cell, pitch*ny*nzf
+    int64_t row0;                  // first row (y + ny z) in the pooled row arrays
     int node0, nnodes, tri0, ntri;
-    int lb_block0, lb_nblocks;     // blocks of the stream-collide launch
+    int lb_block0, lb_nblocks;     // row groups of the stream-collide launch
+    int lb_rows;                   // cell rows per group (consecutive y of one z-plane)
+    int lb_gpp;                    // groups per z-plane: ceil(ny / lb_rows)
     int mass_block0, mass_nblocks; // blocks of the mass reduction
     int red_chunk0, red_nchunks;   // chunks of the mesh reductions
     float tau_out, tau_in, omega_out, omega_in;
@@ -58,24 +65,28 @@ struct __align__(16) NodeRec {
     int spare;
 };
 
-// Every device array of a context.  Lattice fields are pooled over droplets:
-// cell c of droplet d is index Drop::cell0 + c; a 3-vector field stores
-// component k at k * total_cells + index.
+// Every device array of a context.  Lattice fields are pooled over droplets
+// in the padded row layout of the populations: cell (x, row = y + ny z) of
+// droplet d is index Drop::pcell0 + x + pitch * row; a 3-vector field stores
+// component k at k * total_pcells + index.
 struct Arrays {
     const Drop *drops;
     int ndrops;
     int64_t total_cells;
     int64_t total_tiles;
     int total_nodes, total_tri;
-    int lb_blocks_total;           // sum of Drop::lb_nblocks
-    int lb_cpb;                    // cells per block of the stream-collide launch
+    int lb_blocks_total;           // sum of Drop::lb_nblocks (row groups)
+    int lb_stage_bytes;            // bytes of one shared-memory stage of the stream-collide kernel
+    int64_t total_pcells;          // sum of Drop::pcells
+    int64_t total_rows;            // sum of ny * nzf
     // lattice
-    float *F;                      // 3 * total_cells, force density (band tiles only)
-    float *U;                      // 3 * total_cells, velocity (band tiles only)
+    float *F;                      // 3 * total_pcells, force density: exactly 0 outside band tiles
+    float *U;                      // 3 * total_pcells, velocity (valid on band rows only)
     uint32_t *tile_gen;            // tile is in the band of this step iff == *gen
+    uint32_t *row_gen;             // total_rows: row meets a band tile of this step iff == *gen
     uint32_t *gen;                 // step generation counter (device)
-    int *n_active;                 // number of band tiles this step
-    int *active;                   // band tiles (global tile index)
+    int *n_active;                 // 2: band tiles of this step / of the previous step
+    int *active;                   // 2 * active_cap: band tiles, indexed by generation parity
     int active_cap;
     // bins
     int *bin_cnt;                  // total_tiles, returns to 0 after the fill
@@ -83,7 +94,8 @@ struct Arrays {
     int *blk_sum;                  // blocks of the scan
     int *blk_off;
     int n_scan_blocks;
-    int *bin_list;                 // total_nodes node indices sorted by bin
+    int *bin_rank;                 // total_nodes: rank of the node inside its bin
+    NodeRec *srec;                 // total_nodes: node records in bin order (spare = node index)
     // membrane
     double *qx, *qy, *qz;          // node positions (FP64)
     int *node_drop;                // droplet of each node
@@ -97,8 +109,9 @@ struct Arrays {
     int64_t total_cols;
     int *face_drop;                // droplet of each face
     // reductions
-    double *red_part;              // NRED * chunks
-    double *red_out;               // NRED * ndrops: V, A, cx, cy, cz, zmin, zmax, -
+    double *red_part;              // NRED * chunks (volume-correction partials)
+    double *red_out;               // NRED * ndrops: (V0/V)^(1/3), cx, cy, cz, V
+    int *vc_done;                  // per droplet: finished chunks (returns to 0)
     double *mass_part;
     int *status;                   // 4 ints per droplet: flags (ST_*), -, -, -
     int *clamped;                  // per droplet: nodes clamped by the near-wall guard this step
@@ -147,10 +160,14 @@ __host__ __device__ inline int tile_neighbours(int k, int t, int ncell, bool per
 
 // Host-side launchers (lb.cu, ib.cu, inout.cu, reduce.cu, fields.cu).
 struct LaunchCfg {
-    int lb_block;                  // threads per block, stream-collide
-    int lb_persistent;             // 1: grid = SMs * resident blocks, block-stride loop
+    int lb_blocks_per_sm;          // resident stream-collide blocks per SM (0: as many as fit)
+    int lb_row_mult;               // cell rows per group = lb_row_mult * lb_rows_per_group(nx)
     int sm_count;
 };
+int lb_rows_per_group(int nx);     // 256-thread groups: max(1, 256 / nx) rows
+// bytes of one stage of the stream-collide kernel: 19 population rows and 3
+// force rows per cell row, plus one band flag per row (128-byte multiple)
+int lb_stage_bytes(int rows, int pitch, int storage_bytes);
 
 cudaError_t launch_lb(const Arrays &a, int storage, const void *src, void *dst, bool vartau,
                       const LaunchCfg &cfg, cudaStream_t s);

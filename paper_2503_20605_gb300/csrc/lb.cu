@@ -1,31 +1,92 @@
 // lb.cu -- fused pull-stream + halfway bounce-back + moments + BGK + Guo
 // source for D3Q19 (Sec. II A: eqs. LBE, hydro_var1, hydro_var2, the BGK
-// operator, the equilibrium and Guo's source term), one lattice cell per
-// thread, populations stored as offsets s_i = f_i - w_i rho0 in FP32, FP16
-// or BF16 with all arithmetic in FP32.
+// operator, the equilibrium and Guo's source term), populations stored as
+// offsets s_i = f_i - w_i rho0 in FP32, FP16 or BF16, arithmetic in FP32.
 //
-// Memory traffic per fluid cell: 19 loads and 19 stores of the storage type
-// (152 B for FP32, 76 B for 16-bit storage).  The force density is read and
-// the velocity written only on cells of the band tiles around the membrane.
+// Data movement.  Populations and the force / velocity fields live in rows
+// (y, z) of pitch P (nx rounded up to 16 elements), so every row starts on a
+// 32-byte boundary.  A group is R consecutive cell rows of one droplet.  In
+// the pull scheme population i of row (y, z) comes entirely from row
+// (y - c_iy, z - c_iz) (or, at a wall, from row (y, z) of the opposite
+// population), so one producer warp per block fetches the 19 R source rows of
+// a group -- plus the three force-density rows of every row that meets the
+// band around the membrane -- into shared memory with TMA bulk copies
+// (cp.async.bulk, completion on an mbarrier), and the eight consumer warps
+// apply the x shift and the periodic x wrap inside shared memory.  Every
+// population row is read from HBM exactly once per step; the consumers
+// touch global memory only to store results.  Blocks are persistent and
+// double-buffer: the next group is in flight while the current one is
+// computed; one block barrier per group.
+//
+// Memory traffic per fluid cell: 19 reads + 19 writes of the storage type
+// (152 B for FP32, 76 B for 16-bit storage); the force density is read and
+// the velocity written only on band rows.
 #include "iblb_internal.h"
 
 namespace iblb {
 
 namespace {
 
-__device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
-__device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-__device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
-__device__ __forceinline__ void st(__half *p, float v) { __stcs(reinterpret_cast<unsigned short *>(p), __half_as_ushort(__float2half_rn(v))); }
-__device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { __stcs(reinterpret_cast<unsigned short *>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v))); }
+constexpr int LB_THREADS = 256;                   // consumer threads per block
+constexpr int LB_BLOCK = LB_THREADS + 32;         // + one producer warp
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: bounded mbarrier wait
 
-__device__ __forceinline__ int find_drop_block(const Drop *D, int n, int b)
+__device__ __forceinline__ float cvt(float v) { return v; }
+__device__ __forceinline__ float cvt(__half v) { return __half2float(v); }
+__device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ void st(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// bounded wait on an mbarrier phase; false if the limit was reached
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES)
+            return false;
+    return true;
+}
+
+__device__ __forceinline__ int find_drop_group(const Drop *D, int n, int g)
 {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (D[mid].lb_block0 <= b)
+        if (D[mid].lb_block0 <= g)
             lo = mid;
         else
             hi = mid - 1;
@@ -33,162 +94,322 @@ __device__ __forceinline__ int find_drop_block(const Drop *D, int n, int b)
     return lo;
 }
 
+__constant__ int kCy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1, 0, 0, 0, 0};
+__constant__ int kCz[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+__constant__ int kOpp[Q] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
+
 constexpr float W0 = 1.0f / 3.0f, W1 = 1.0f / 18.0f, W2 = 1.0f / 36.0f;
 
-template <typename S, bool VARTAU>
-__global__ void __launch_bounds__(512) lb_kernel(Arrays a, const S *__restrict__ src, S *__restrict__ dst)
-{
-    const uint32_t gen = *a.gen;
-    for (int b = blockIdx.x; b < a.lb_blocks_total; b += gridDim.x) {
-        const int d = find_drop_block(a.drops, a.ndrops, b);
-        const Drop &D = a.drops[d];
-        const int nx = D.nx, ny = D.ny, nzf = D.nzf;
-        const int64_t N = D.cells;
-        const int64_t c = (int64_t)(b - D.lb_block0) * a.lb_cpb + threadIdx.x;
-        if (c >= N)
-            continue;
-        const int ci = (int)c;
-        const int x = ci % nx;
-        const int yz = ci / nx;
-        const int y = yz % ny;
-        const int z = yz / ny;
-        const int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
-        const int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
-        const bool zlo = z == 0, zhi = z == nzf - 1;
-        const bool bbm = D.walls && zlo;   // pulling from z-1 reaches the bottom wall
-        const bool bbp = D.walls && zhi;   // pulling from z+1 reaches the top wall
-        const int zm = zlo ? (D.walls ? 0 : nzf - 1) : z - 1;
-        const int zp = zhi ? (D.walls ? 0 : 0) : z + 1;
-        const int r00 = nx * (y + ny * z), rm0 = nx * (ym + ny * z), rp0 = nx * (yp + ny * z);
-        const int r0m = nx * (y + ny * zm), r0p = nx * (y + ny * zp);
-        const int rmm = nx * (ym + ny * zm), rpm = nx * (yp + ny * zm);
-        const int rmp = nx * (ym + ny * zp), rpp = nx * (yp + ny * zp);
-
-        const S *f = src + (int64_t)Q * D.cell0;
-#define P(i) (f + (int64_t)(i) * N)
-        // pull: s_i(x) = s*_i(x - c_i); halfway bounce-back at a resting wall
-        const float s0 = ld(P(0) + x + r00);
-        const float s1 = ld(P(1) + xm + r00);
-        const float s2 = ld(P(2) + xp + r00);
-        const float s3 = ld(P(3) + x + rm0);
-        const float s4 = ld(P(4) + x + rp0);
-        const float s5 = bbm ? ld(P(6) + ci) : ld(P(5) + x + r0m);
-        const float s6 = bbp ? ld(P(5) + ci) : ld(P(6) + x + r0p);
-        const float s7 = ld(P(7) + xm + rm0);
-        const float s8 = ld(P(8) + xp + rp0);
-        const float s9 = ld(P(9) + xm + rp0);
-        const float s10 = ld(P(10) + xp + rm0);
-        const float s11 = bbm ? ld(P(12) + ci) : ld(P(11) + x + rmm);
-        const float s12 = bbp ? ld(P(11) + ci) : ld(P(12) + x + rpp);
-        const float s13 = bbp ? ld(P(14) + ci) : ld(P(13) + x + rmp);
-        const float s14 = bbm ? ld(P(13) + ci) : ld(P(14) + x + rpm);
-        const float s15 = bbm ? ld(P(16) + ci) : ld(P(15) + xm + r0m);
-        const float s16 = bbp ? ld(P(15) + ci) : ld(P(16) + xp + r0p);
-        const float s17 = bbp ? ld(P(18) + ci) : ld(P(17) + xm + r0p);
-        const float s18 = bbm ? ld(P(17) + ci) : ld(P(18) + xp + r0m);
-#undef P
-
-        // force density: band tiles carry the spread IB force
-        float Fx = D.bf[0], Fy = D.bf[1], Fz = D.bf[2];
-        const int64_t gcell = D.cell0 + c;
-        const int64_t tile = D.tile0 + (x >> 2) + (int64_t)D.tx * ((y >> 2) + (int64_t)D.ty * (z >> 2));
-        const bool band = a.tile_gen[tile] == gen;
-        if (band) {
-            Fx += a.F[gcell];
-            Fy += a.F[a.total_cells + gcell];
-            Fz += a.F[2 * a.total_cells + gcell];
-        }
-
-        float omega = D.omega_out;
-        if (VARTAU && D.vartau) {
-            const int64_t col = D.col0 + x + (int64_t)nx * y;
-            const int cnt = min(a.col_cnt[col], MAXC);
-            const double Z = (double)(z + D.walls);
-            int par = 0;
-            for (int k = 0; k < cnt; ++k)
-                par ^= a.col_z[col * MAXC + k] < Z;
-            if (par)
-                omega = D.omega_in;
-        }
-
-        // moments (eqs. hydro_var1, hydro_var2) in offset form
-        const float drho = ((s0 + (s1 + s2)) + ((s3 + s4) + (s5 + s6))) +
-                           (((s7 + s8) + (s9 + s10)) + ((s11 + s12) + (s13 + s14))) +
-                           ((s15 + s16) + (s17 + s18));
-        const float jx = (s1 - s2) + (s7 - s8) + (s9 - s10) + (s15 - s16) + (s17 - s18);
-        const float jy = (s3 - s4) + (s7 - s8) - (s9 - s10) + (s11 - s12) + (s13 - s14);
-        const float jz = (s5 - s6) + (s11 - s12) - (s13 - s14) + (s15 - s16) - (s17 - s18);
-        const float rho = D.rho0 + drho;
-        const float irho = 1.0f / rho;
-        const float ux = (jx + 0.5f * Fx) * irho;
-        const float uy = (jy + 0.5f * Fy) * irho;
-        const float uz = (jz + 0.5f * Fz) * irho;
-        if (band) {
-            a.U[gcell] = ux;
-            a.U[a.total_cells + gcell] = uy;
-            a.U[2 * a.total_cells + gcell] = uz;
-        }
-
-        // BGK + Guo: s*_i = s_i + omega (s_eq_i - s_i) + S_i with
-        // s_eq_i = w_i [drho + rho (3 cu + 9/2 cu^2 - 3/2 u.u)]  (f_eq - w_i rho0)
-        // S_i    = (1 - omega/2) w_i [3 (c_i - U).F + 9 (c_i.U)(c_i.F)]
-        const float uu15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-        const float uF3 = 3.0f * (ux * Fx + uy * Fy + uz * Fz);
-        const float kS = 1.0f - 0.5f * omega;
-        S *o = dst + (int64_t)Q * D.cell0 + c;
-#define COLL(i, w, cu, cF, si)                                                              \
-    {                                                                                        \
-        const float cu_ = (cu), cF_ = (cF);                                                  \
-        const float seq = (w) * (drho + rho * (3.0f * cu_ + 4.5f * cu_ * cu_ - uu15));       \
-        const float Si = kS * (w) * (3.0f * cF_ - uF3 + 9.0f * cu_ * cF_);                   \
-        st(o + (int64_t)(i) * N, (si) + omega * (seq - (si)) + Si);                          \
+// stage layout: [19][R][P] populations | [3][R][P] force | band flag
+template <typename S>
+struct Stage {
+    S *pop;
+    float *F;
+    int *flag;
+    __device__ Stage(unsigned char *base, int R, int P)
+    {
+        pop = reinterpret_cast<S *>(base);
+        F = reinterpret_cast<float *>(base + (size_t)R * Q * P * sizeof(S));
+        flag = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(F) + (size_t)R * 3 * P * sizeof(float));
     }
-        COLL(0, W0, 0.0f, 0.0f, s0);
-        COLL(1, W1, ux, Fx, s1);
-        COLL(2, W1, -ux, -Fx, s2);
-        COLL(3, W1, uy, Fy, s3);
-        COLL(4, W1, -uy, -Fy, s4);
-        COLL(5, W1, uz, Fz, s5);
-        COLL(6, W1, -uz, -Fz, s6);
-        COLL(7, W2, ux + uy, Fx + Fy, s7);
-        COLL(8, W2, -ux - uy, -Fx - Fy, s8);
-        COLL(9, W2, ux - uy, Fx - Fy, s9);
-        COLL(10, W2, -ux + uy, -Fx + Fy, s10);
-        COLL(11, W2, uy + uz, Fy + Fz, s11);
-        COLL(12, W2, -uy - uz, -Fy - Fz, s12);
-        COLL(13, W2, uy - uz, Fy - Fz, s13);
-        COLL(14, W2, -uy + uz, -Fy + Fz, s14);
-        COLL(15, W2, ux + uz, Fx + Fz, s15);
-        COLL(16, W2, -ux - uz, -Fx - Fz, s16);
-        COLL(17, W2, ux - uz, Fx - Fz, s17);
-        COLL(18, W2, -ux + uz, -Fx + Fz, s18);
-#undef COLL
+};
+
+// rows y0 .. y0 + nr - 1 of plane z in group g of droplet D
+__device__ __forceinline__ void group_rows(const Drop &D, int g, int &y0, int &z, int &nr)
+{
+    const int lg = g - D.lb_block0;
+    z = lg / D.lb_gpp;
+    y0 = (lg - z * D.lb_gpp) * D.lb_rows;
+    nr = min(D.lb_rows, D.ny - y0);
+}
+
+// Producer warp: fetch group g into a stage.  The source rows of population i
+// for rows y0 .. y0+nr-1 of plane z are rows y0-c_iy .. of plane z-c_iz
+// (or the group's own rows of the opposite population at a wall), which are
+// contiguous in memory except across the periodic y seam: lane i < 19 issues
+// one bulk copy for population i (two at the seam).  If a row of the group
+// meets the band, lanes 19..21 copy the three force-density components of
+// the group's rows.  Every lane announces the bytes of its own copies on the
+// mbarrier (initialised for 32 arrivals) before issuing them.
+template <typename S>
+__device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t gen, int g, unsigned char *sbase,
+                                        uint64_t *bar)
+{
+    const int lane = threadIdx.x & 31;
+    const int d = find_drop_group(a.drops, a.ndrops, g);
+    const Drop &D = a.drops[d];
+    int y0, z, nr;
+    group_rows(D, g, y0, z, nr);
+    const int P = D.pitch, ny = D.ny, R = D.lb_rows;
+    Stage<S> stg(sbase, R, P);
+    const int64_t plane_row0 = (int64_t)ny * z;
+    bool band = false;
+    for (int r = lane; r < nr; r += 32)
+        band |= a.row_gen[D.row0 + plane_row0 + y0 + r] == gen;
+    band = __any_sync(0xffffffffu, band);
+    const uint32_t rowb = (uint32_t)(P * sizeof(S));
+    // copies of this lane: up to two pieces (source row, destination row, rows)
+    int src_pop = 0, src_z = 0, y_a = 0, n_a = 0, y_b = 0, n_b = 0, d_b = 0;
+    uint32_t mine = 0;
+    if (lane < Q) {
+        const int i = lane;
+        int zs = z - kCz[i], ys = y0 - kCy[i];
+        src_pop = i;
+        if (D.walls && (zs < 0 || zs >= D.nzf)) {
+            src_pop = kOpp[i];          // halfway bounce-back: own rows, opposite population
+            zs = z;
+            ys = y0;
+        } else {
+            zs = wrapi(zs, D.nzf);
+        }
+        src_z = zs;
+        if (ys < 0) {                   // first row wraps to y = ny - 1
+            y_a = ny - 1; n_a = 1;
+            y_b = 0; n_b = nr - 1; d_b = 1;
+        } else if (ys + nr > ny) {      // last row wraps to y = 0
+            y_a = ys; n_a = ny - ys;
+            y_b = 0; n_b = nr - n_a; d_b = n_a;
+        } else {
+            y_a = ys; n_a = nr;
+        }
+        mine = rowb * (uint32_t)(n_a + n_b);
+    } else if (band && lane < Q + 3) {
+        mine = (uint32_t)(nr * P * sizeof(float));
+    }
+    if (lane == 0)
+        *stg.flag = band;
+    mbar_arrive_expect_tx(bar, mine);
+    if (lane < Q) {
+        const S *plane = src + (int64_t)Q * D.pcell0 + (int64_t)src_pop * D.pcells + (int64_t)P * ny * src_z;
+        S *dst = stg.pop + (int64_t)lane * R * P;
+        if (n_a > 0)
+            bulk_g2s(dst, plane + (int64_t)P * y_a, rowb * n_a, bar);
+        if (n_b > 0)
+            bulk_g2s(dst + (int64_t)d_b * P, plane + (int64_t)P * y_b, rowb * n_b, bar);
+    } else if (band && lane < Q + 3) {
+        const int c = lane - Q;
+        bulk_g2s(stg.F + (int64_t)c * R * P, a.F + c * a.total_pcells + D.pcell0 + (int64_t)P * (plane_row0 + y0),
+                 (uint32_t)(nr * P * sizeof(float)), bar);
     }
 }
+
+// BGK + Guo for the pair (i, opp(i)), c_opp = -c_i:  with cu = c_i.U and
+// cF = c_i.F the equilibrium offsets are  A +- B  and the sources  C +- D,
+//   A = w drho + w rho (9/2 cu^2 - 3/2 U.U),   B = 3 w rho cu,
+//   C = (1 - omega/2) w (9 cu cF - 3 U.F),     D = 3 (1 - omega/2) w cF,
+// and s*_i = s_i + omega (s_eq_i - s_i) + S_i.
+#define PAIR(i, j, A0, WR45, WR3, KW, KW3, cu_e, cF_e, si, sj)                                     \
+    {                                                                                              \
+        const float cu_ = (cu_e), cF_ = (cF_e);                                                    \
+        const float Ae = fmaf(WR45 * cu_, cu_, A0);                                                \
+        const float Be = WR3 * cu_;                                                                \
+        const float Ce = KW * fmaf(9.0f * cu_, cF_, -uF3);                                         \
+        const float De = KW3 * cF_;                                                                \
+        st(o + (i) * PC, fmaf(omega, (Ae + Be) - (si), (si)) + (Ce + De));                         \
+        st(o + (j) * PC, fmaf(omega, (Ae - Be) - (sj), (sj)) + (Ce - De));                         \
+    }
+
+template <typename S, bool VARTAU>
+__global__ void __launch_bounds__(LB_BLOCK, 2) lb_kernel(Arrays a, const S *__restrict__ src, S *__restrict__ dst)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const uint32_t gen = *a.gen;
+    const int total = a.lb_blocks_total;
+    const bool producer = threadIdx.x >= LB_THREADS;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 32);
+        mbar_init(&bar[1], 32);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int g = blockIdx.x;
+    if (g < total && producer)
+        produce<S>(a, src, gen, g, smem_raw, &bar[0]);
+    int k = 0;
+    bool failed = false;
+    for (; g < total; g += gridDim.x, ++k) {
+        const int st_i = k & 1;
+        // consumers wait for this group (bounded); the barrier makes the
+        // outcome uniform and ends the previous group, so the other stage is
+        // free to be refilled
+        const bool ok = producer || mbar_wait_bounded(&bar[st_i], (uint32_t)((k >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (producer) {
+            const int gn = g + gridDim.x;
+            if (gn < total) {
+                // order the generic reads of the previous group before the
+                // asynchronous writes into the same stage
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                produce<S>(a, src, gen, gn, smem_raw + (st_i ^ 1) * a.lb_stage_bytes, &bar[st_i ^ 1]);
+            }
+            continue;
+        }
+
+        // the droplet's parameters, copied to registers once per group (the
+        // stores below could otherwise force reloads from the table)
+        const int d = find_drop_group(a.drops, a.ndrops, g);
+        const Drop &D = a.drops[d];
+        int y0, z, nr;
+        group_rows(D, g, y0, z, nr);
+        const int nx = D.nx, ny = D.ny, P = D.pitch, R = D.lb_rows;
+        const int PC = (int)D.pcells;
+        const int64_t pcell0 = D.pcell0;
+        const float bfx = D.bf[0], bfy = D.bf[1], bfz = D.bf[2], rho0 = D.rho0;
+        const float omega_out = D.omega_out, omega_in = D.omega_in;
+        const int vartau = D.vartau, walls = D.walls;
+        const int64_t col0 = D.col0;
+        const Stage<S> stg(smem_raw + st_i * a.lb_stage_bytes, R, P);
+        const bool band = *stg.flag != 0;
+        const bool bbm = walls && z == 0;              // rows pulled from z-1 bounced at the bottom
+        const bool bbp = walls && z == D.nzf - 1;      // rows pulled from z+1 bounced at the top
+        const int RP = R * P;
+        S *outb = dst + (int64_t)Q * pcell0 + (int64_t)P * ny * z;
+        const int64_t TP = a.total_pcells;
+        float *U = a.U;
+        // cell e = r * nx + x of the group, walked without divisions
+        const int step_r = LB_THREADS / nx, step_x = LB_THREADS - step_r * nx;
+        int r = threadIdx.x / nx, x = threadIdx.x - r * nx;
+        for (; r < nr; r += step_r, x += step_x) {
+            if (x >= nx) {
+                x -= nx;
+                ++r;
+                if (r >= nr)
+                    break;
+            }
+            const int y = y0 + r;
+            float Fx = bfx, Fy = bfy, Fz = bfz;
+            if (band) {     // F vanishes outside band tiles
+                const float *Fr = stg.F + r * P + x;
+                Fx += Fr[0];
+                Fy += Fr[RP];
+                Fz += Fr[2 * RP];
+            }
+            float omega = omega_out;
+            if (VARTAU && vartau) {
+                const int64_t col = col0 + x + (int64_t)nx * y;
+                const int cnt = min(a.col_cnt[col], MAXC);
+                const double Z = (double)(z + walls);
+                int par = 0;
+                for (int q = 0; q < cnt; ++q)
+                    par ^= a.col_z[col * MAXC + q] < Z;
+                if (par)
+                    omega = omega_in;
+            }
+            const int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
+            const S *Rr = stg.pop + r * P;
+#define IN(i, xx) cvt(Rr[(i) * RP + (xx)])
+            const float s0 = IN(0, x);
+            const float s1 = IN(1, xm);
+            const float s2 = IN(2, xp);
+            const float s3 = IN(3, x);
+            const float s4 = IN(4, x);
+            const float s5 = IN(5, x);
+            const float s6 = IN(6, x);
+            const float s7 = IN(7, xm);
+            const float s8 = IN(8, xp);
+            const float s9 = IN(9, xm);
+            const float s10 = IN(10, xp);
+            const float s11 = IN(11, x);
+            const float s12 = IN(12, x);
+            const float s13 = IN(13, x);
+            const float s14 = IN(14, x);
+            const float s15 = IN(15, bbm ? x : xm);
+            const float s16 = IN(16, bbp ? x : xp);
+            const float s17 = IN(17, bbp ? x : xm);
+            const float s18 = IN(18, bbm ? x : xp);
+#undef IN
+            // moments (eqs. hydro_var1, hydro_var2) in offset form, from the
+            // sums and differences of opposite pairs
+            const float p1 = s1 + s2, m1 = s1 - s2, p3 = s3 + s4, m3 = s3 - s4, p5 = s5 + s6, m5 = s5 - s6;
+            const float p7 = s7 + s8, m7 = s7 - s8, p9 = s9 + s10, m9 = s9 - s10;
+            const float p11 = s11 + s12, m11 = s11 - s12, p13 = s13 + s14, m13 = s13 - s14;
+            const float p15 = s15 + s16, m15 = s15 - s16, p17 = s17 + s18, m17 = s17 - s18;
+            const float drho = ((s0 + p1) + (p3 + p5)) + ((p7 + p9) + (p11 + p13)) + (p15 + p17);
+            const float jx = ((m1 + m7) + (m9 + m15)) + m17;
+            const float jy = ((m3 + m7) - (m9 - m11)) + m13;
+            const float jz = ((m5 + m11) - (m13 - m15)) - m17;
+            const float rho = rho0 + drho;
+            const float irho = 1.0f / rho;
+            const float ux = (jx + 0.5f * Fx) * irho;
+            const float uy = (jy + 0.5f * Fy) * irho;
+            const float uz = (jz + 0.5f * Fz) * irho;
+            const int64_t cell = (int64_t)P * (y + (int64_t)ny * z) + x;
+            if (band) {
+                const int64_t gi = pcell0 + cell;
+                U[gi] = ux;
+                U[TP + gi] = uy;
+                U[2 * TP + gi] = uz;
+            }
+            const float uu15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+            const float uF3 = 3.0f * (ux * Fx + uy * Fy + uz * Fz);
+            const float kS = 1.0f - 0.5f * omega;
+            S *o = outb + P * y + x;
+            // rest population: s_eq_0 = w0 (drho - rho 3/2 U.U), S_0 = -(1 - omega/2) w0 3 U.F
+            st(o, fmaf(omega, W0 * fmaf(-rho, uu15, drho) - s0, s0) - kS * W0 * uF3);
+            const float wr1 = 3.0f * W1 * rho, wr2 = 3.0f * W2 * rho;
+            const float a1 = fmaf(-W1 * rho, uu15, W1 * drho), a2 = fmaf(-W2 * rho, uu15, W2 * drho);
+            const float q1 = 1.5f * wr1, q2 = 1.5f * wr2;
+            const float kw1 = kS * W1, kw13 = 3.0f * kw1, kw2 = kS * W2, kw23 = 3.0f * kw2;
+            PAIR(1, 2, a1, q1, wr1, kw1, kw13, ux, Fx, s1, s2);
+            PAIR(3, 4, a1, q1, wr1, kw1, kw13, uy, Fy, s3, s4);
+            PAIR(5, 6, a1, q1, wr1, kw1, kw13, uz, Fz, s5, s6);
+            PAIR(7, 8, a2, q2, wr2, kw2, kw23, ux + uy, Fx + Fy, s7, s8);
+            PAIR(9, 10, a2, q2, wr2, kw2, kw23, ux - uy, Fx - Fy, s9, s10);
+            PAIR(11, 12, a2, q2, wr2, kw2, kw23, uy + uz, Fy + Fz, s11, s12);
+            PAIR(13, 14, a2, q2, wr2, kw2, kw23, uy - uz, Fy - Fz, s13, s14);
+            PAIR(15, 16, a2, q2, wr2, kw2, kw23, ux + uz, Fx + Fz, s15, s16);
+            PAIR(17, 18, a2, q2, wr2, kw2, kw23, ux - uz, Fx - Fz, s17, s18);
+        }
+    }
+    // a timed-out group was the only one in flight (the next one is issued
+    // after the barrier that reported the failure): flag it and leave
+    if (failed && threadIdx.x == 0)
+        atomicOr(&a.status[0], ST_TIMEOUT);
+}
+#undef PAIR
 
 template <typename S>
 cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, const LaunchCfg &cfg,
                      cudaStream_t s)
 {
-    int grid = a.lb_blocks_total;
-    if (grid <= 0)
+    const int total = a.lb_blocks_total;
+    if (total <= 0)
         return cudaSuccess;
-    if (cfg.lb_persistent) {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, vartau ? (const void *)lb_kernel<S, true> : (const void *)lb_kernel<S, false>,
-            cfg.lb_block, 0);
-        int g = cfg.sm_count * (per_sm > 0 ? per_sm : 1);
-        grid = grid < g ? grid : g;
-    }
+    const size_t smem = 2 * (size_t)a.lb_stage_bytes;
+    const void *fn = vartau ? (const void *)lb_kernel<S, true> : (const void *)lb_kernel<S, false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LB_BLOCK, smem);
+    if (e != cudaSuccess)
+        return e;
+    if (per_sm < 1)
+        return cudaErrorInvalidConfiguration;
+    if (cfg.lb_blocks_per_sm > 0 && cfg.lb_blocks_per_sm < per_sm)
+        per_sm = cfg.lb_blocks_per_sm;
+    int grid = cfg.sm_count * per_sm;
+    grid = grid < total ? grid : total;
     if (vartau)
-        lb_kernel<S, true><<<grid, cfg.lb_block, 0, s>>>(a, (const S *)src, (S *)dst);
+        lb_kernel<S, true><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst);
     else
-        lb_kernel<S, false><<<grid, cfg.lb_block, 0, s>>>(a, (const S *)src, (S *)dst);
+        lb_kernel<S, false><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+int lb_rows_per_group(int nx) { return nx >= LB_THREADS ? 1 : LB_THREADS / nx; }
+
+int lb_stage_bytes(int rows, int pitch, int sb)
+{
+    const size_t b = (size_t)rows * Q * pitch * sb + (size_t)rows * 3 * pitch * sizeof(float) + 16;
+    return (int)((b + 127) & ~(size_t)127);
+}
 
 cudaError_t launch_lb(const Arrays &a, int storage, const void *src, void *dst, bool vartau,
                       const LaunchCfg &cfg, cudaStream_t s)

@@ -113,28 +113,69 @@ __device__ __forceinline__ int find_drop_chunk(const Drop *D, int n, int c)
     return lo;
 }
 
-__device__ __forceinline__ MeshView view_of(const Arrays &a, const Drop &D)
-{
-    MeshView m;
-    m.qx = a.qx;
-    m.qy = a.qy;
-    m.qz = a.qz;
-    m.stride = 1;
-    m.tri = a.tri + 3 * (int64_t)D.tri0;
-    m.ntri = D.ntri;
-    m.node0 = D.node0;
-    m.nnodes = D.nnodes;
-    return m;
-}
 
-__global__ void __launch_bounds__(RB) pass1_batch_kernel(Arrays a)
+// Volume-correction reduction of every droplet in one launch: block c takes
+// faces and nodes [k*RB, (k+1)*RB) of its droplet (k = c - chunk0) and
+// writes 6V and the node-coordinate sums; the last block of a droplet to
+// finish folds that droplet's chunks in a fixed order and stores
+// red_out = {(V0/V)^(1/3), cx, cy, cz, V}.
+__global__ void __launch_bounds__(RB) vc_reduce_kernel(Arrays a)
 {
+    const int KIND[4] = {0, 0, 0, 0};
+    __shared__ int s_last;
     const int c = blockIdx.x;
     const int d = find_drop_chunk(a.drops, a.ndrops, c);
     const Drop &D = a.drops[d];
-    if (D.nnodes == 0)
+    if (D.nnodes == 0 || !D.volcorr)
         return;
-    pass1_chunk(view_of(a, D), c - D.red_chunk0, a.red_part + (int64_t)NRED * c);
+    const int k = c - D.red_chunk0;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const int t = k * RB + threadIdx.x;
+    if (t < D.ntri) {
+        const int *f = a.tri + 3 * ((int64_t)D.tri0 + t);
+        const int ia = f[0], ib = f[1], ic = f[2];
+        const double ax = a.qx[ia], ay = a.qy[ia], az = a.qz[ia];
+        const double bx = a.qx[ib], by = a.qy[ib], bz = a.qz[ib];
+        const double cx = a.qx[ic], cy = a.qy[ic], cz = a.qz[ic];
+        v[0] = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
+    }
+    if (t < D.nnodes) {
+        const int j = D.node0 + t;
+        v[1] = a.qx[j];
+        v[2] = a.qy[j];
+        v[3] = a.qz[j];
+    }
+    block_reduce<4>(v, KIND);
+    double *part = a.red_part + (int64_t)NRED * c;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i)
+            part[i] = v[i];
+        __threadfence();
+        s_last = atomicAdd(&a.vc_done[d], 1) == D.red_nchunks - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x >= 32)
+        return;
+    __threadfence();
+    const int lane = threadIdx.x;
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = lane; i < D.red_nchunks; i += 32) {
+        const volatile double *p = a.red_part + (int64_t)NRED * (D.red_chunk0 + i);
+        for (int q = 0; q < 4; ++q)
+            w[q] += p[q];
+    }
+    for (int q = 0; q < 4; ++q)
+        w[q] = warp_sum(w[q]);
+    if (lane == 0) {
+        const double V = w[0] / 6.0;
+        double *o = a.red_out + (int64_t)NRED * d;
+        o[0] = cbrt(D.V0 / V);
+        o[1] = w[1] / D.nnodes;
+        o[2] = w[2] / D.nnodes;
+        o[3] = w[3] / D.nnodes;
+        o[4] = V;
+        a.vc_done[d] = 0;
+    }
 }
 
 // Fold the chunks of droplet blockIdx.x (one warp; chunk i goes to lane i % 32,
@@ -166,29 +207,20 @@ __device__ void fold_chunks(const double *part, int nch, int nnodes, double *out
     }
 }
 
-__global__ void fold_batch_kernel(Arrays a)
-{
-    const Drop &D = a.drops[blockIdx.x];
-    if (D.nnodes == 0)
-        return;
-    fold_chunks(a.red_part + (int64_t)NRED * D.red_chunk0, D.red_nchunks, D.nnodes,
-                a.red_out + (int64_t)NRED * blockIdx.x);
-}
-
+// q <- c + (q - c) (V0/V)^(1/3) about the node centroid c
 __global__ void volume_correct_kernel(Arrays a)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.total_nodes)
         return;
-    const int d = a.node_drop[j];
-    const Drop &D = a.drops[d];
-    if (!D.volcorr)
+    const int d = a.rec[j].spare;
+    if (!a.drops[d].volcorr)
         return;
     const double *r = a.red_out + (int64_t)NRED * d;
-    const double k = cbrt(D.V0 / r[0]);
-    a.qx[j] = r[2] + (a.qx[j] - r[2]) * k;
-    a.qy[j] = r[3] + (a.qy[j] - r[3]) * k;
-    a.qz[j] = r[4] + (a.qz[j] - r[4]) * k;
+    const double k = r[0];
+    a.qx[j] = r[1] + (a.qx[j] - r[1]) * k;
+    a.qy[j] = r[2] + (a.qy[j] - r[2]) * k;
+    a.qz[j] = r[3] + (a.qz[j] - r[3]) * k;
 }
 
 // --- observation of one mesh (view), used by iblb_observe and the stateless
@@ -327,9 +359,10 @@ __global__ void __launch_bounds__(RB) mass_kernel(Arrays a, const S *f)
     const int64_t c = (int64_t)(b - D.mass_block0) * RB + threadIdx.x;
     double v[1] = {0.0};
     if (c < D.cells) {
-        const S *p = f + (int64_t)Q * D.cell0 + c;
+        const int64_t row = c / D.nx;
+        const S *p = f + (int64_t)Q * D.pcell0 + (c - row * D.nx) + (int64_t)D.pitch * row;
         for (int i = 0; i < Q; ++i)
-            v[0] += tod<S>(p[(int64_t)i * D.cells]);
+            v[0] += tod<S>(p[(int64_t)i * D.pcells]);
     }
     block_reduce<1>(v, KIND);
     if (threadIdx.x == 0)
@@ -353,8 +386,7 @@ cudaError_t launch_mesh_reduce(const Arrays &a, int n_chunks_total, cudaStream_t
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    pass1_batch_kernel<<<n_chunks_total, RB, 0, s>>>(a);
-    fold_batch_kernel<<<a.ndrops, 32, 0, s>>>(a);
+    vc_reduce_kernel<<<n_chunks_total, RB, 0, s>>>(a);
     return cudaGetLastError();
 }
 
