@@ -135,8 +135,9 @@ typedef struct {
 
 /* Options for iblb_set_option. */
 #define IBLB_OPT_GRAPHS 0     /* 1 (default): replay captured CUDA graphs of one step    */
-#define IBLB_OPT_PROFILE 1    /* 1: record CUDA events around each phase (adds a sync
-                                 per step); 0 (default)                                  */
+#define IBLB_OPT_PROFILE 1    /* 1: record CUDA events around each phase; 2: around the
+                                 whole step only; both add a host sync per step;
+                                 0 (default): off                                        */
 #define IBLB_OPT_LB_BLOCKS_PER_SM 2 /* resident blocks per SM of the persistent
                                  stream-collide kernel (0..8; 0 = as many as fit)       */
 #define IBLB_OPT_LB_ROW_MULT 3 /* cell rows per stream-collide group, in units of

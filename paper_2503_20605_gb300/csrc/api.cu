@@ -63,7 +63,8 @@ struct iblb_ctx {
     cudaStream_t user = nullptr, stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaEvent_t ph[IBLB_NPHASE + 1] = {};
-    bool graphs = true, profile = false;
+    bool graphs = true;
+    int profile = 0;               // 0 off, 1 every phase, 2 whole step only
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     bool gvalid[2] = {false, false};
     double ph_ms[IBLB_NPHASE] = {};
@@ -367,8 +368,8 @@ void free_membrane_arrays(iblb_ctx *c)
     dfree(c->d_adj_start);
     dfree(c->d_adj);
     dfree(c->A.rec);
-    dfree(c->A.srec);
-    dfree(c->A.bin_rank);
+    dfree(c->A.tile_list);
+    dfree(c->A.pair_rank);
     dfree(c->A.red_part);
     dfree(c->A.red_out);
     dfree(c->A.vc_done);
@@ -377,8 +378,8 @@ void free_membrane_arrays(iblb_ctx *c)
     c->A.node_drop = c->A.face_drop = nullptr;
     c->d_tri = c->d_adj_start = c->d_adj = nullptr;
     c->A.tri = c->A.adj_start = c->A.adj = nullptr;
-    c->A.rec = c->A.srec = nullptr;
-    c->A.bin_rank = nullptr;
+    c->A.rec = nullptr;
+    c->A.tile_list = c->A.pair_rank = nullptr;
     c->A.red_part = c->A.red_out = nullptr;
 }
 
@@ -451,8 +452,8 @@ int rebuild_membranes(iblb_ctx *c)
     CK(dalloc(&c->d_adj_start, N + 1));
     CK(dalloc(&c->d_adj, adj.size()));
     CK(dalloc(&c->A.rec, N));
-    CK(dalloc(&c->A.srec, N));
-    CK(dalloc(&c->A.bin_rank, N));
+    CK(dalloc(&c->A.tile_list, (size_t)MAXPAIR * N));
+    CK(dalloc(&c->A.pair_rank, (size_t)MAXPAIR * N));
     CK(dalloc(&c->A.red_part, (size_t)NRED * std::max(chunks, 1)));
     CK(dalloc(&c->A.red_out, (size_t)NRED * c->ndrops));
     CK(dalloc(&c->A.vc_done, (size_t)c->ndrops));
@@ -493,13 +494,12 @@ int enqueue_step(iblb_ctx *c, int par, bool forces_only)
     // phase boundaries; "external" so that, under stream capture, they become
     // event-record nodes of the graph that the host can time after a replay
     auto mark = [&](int k) {
-        return prof ? cudaEventRecordWithFlags(c->ph[k], s, cudaEventRecordExternal) : cudaSuccess;
+        const bool on = c->profile == 1 || (c->profile == 2 && (k == 0 || k == IBLB_NPHASE));
+        return prof && on ? cudaEventRecordWithFlags(c->ph[k], s, cudaEventRecordExternal) : cudaSuccess;
     };
     CK(mark(0));
-    if (nodes) {
-        CK(cudaMemsetAsync(a.clamped, 0, sizeof(int) * c->ndrops, s));
+    if (nodes)
         CK(launch_node_force(a, s));
-    }
     CK(mark(1));
     if (nodes)
         CK(launch_spread(a, s));
@@ -546,7 +546,7 @@ int capture_step(iblb_ctx *c, int par)
 int accumulate_profile(iblb_ctx *c)
 {
     CK(cudaEventSynchronize(c->ph[IBLB_NPHASE]));
-    for (int k = 0; k < IBLB_NPHASE; ++k) {
+    for (int k = 0; c->profile == 1 && k < IBLB_NPHASE; ++k) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ph[k], c->ph[k + 1]));
         c->ph_ms[k] += ms;
@@ -682,7 +682,6 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
         (e = dalloc(&A.F, 3 * (size_t)A.total_pcells)) != cudaSuccess ||
         (e = dalloc(&A.U, 3 * (size_t)A.total_pcells)) != cudaSuccess ||
         (e = dalloc(&A.tile_gen, (size_t)T)) != cudaSuccess || (e = dalloc(&A.gen, 1)) != cudaSuccess ||
-        (e = dalloc(&A.row_gen, (size_t)A.total_rows)) != cudaSuccess ||
         (e = dalloc(&A.n_active, 2)) != cudaSuccess || (e = dalloc(&A.active, 2 * (size_t)T)) != cudaSuccess ||
         (e = dalloc(&A.bin_cnt, (size_t)T + 1)) != cudaSuccess ||
         (e = dalloc(&A.bin_off, (size_t)T + 1)) != cudaSuccess ||
@@ -700,7 +699,6 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
     cudaStream_t s = c->stream;
     const uint32_t one = 1;
     if ((e = cudaMemsetAsync(A.tile_gen, 0, sizeof(uint32_t) * T, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(A.row_gen, 0, sizeof(uint32_t) * A.total_rows, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(A.gen, &one, sizeof(one), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.n_active, 0, 2 * sizeof(int), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.bin_cnt, 0, sizeof(int) * (T + 1), s)) != cudaSuccess ||
@@ -913,8 +911,8 @@ int iblb_compute_forces(iblb_ctx *c)
     int r = ensure_ready(c);
     if (r)
         return r;
-    const bool prof = c->profile;
-    c->profile = false;
+    const int prof = c->profile;
+    c->profile = 0;
     enter(c);
     r = enqueue_step(c, c->cur, true);
     c->profile = prof;
@@ -1073,9 +1071,11 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
         c->graphs = value != 0;
         return IBLB_OK;
     case IBLB_OPT_PROFILE:
-        if (c->profile != (value != 0))
+        if (value < 0 || value > 2)
+            return fail(c, IBLB_E_ARG, "profile mode must be 0, 1 or 2");
+        if (c->profile != value)
             invalidate_graphs(c);
-        c->profile = value != 0;
+        c->profile = value;
         return IBLB_OK;
     case IBLB_OPT_LB_BLOCKS_PER_SM:
         if (value < 0 || value > 8)

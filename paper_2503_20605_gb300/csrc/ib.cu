@@ -4,11 +4,12 @@
 //     8 lanes per node share its incident faces, partial sums meet in a fixed
 //     shuffle tree;
 //   * force spreading F(x) = sum_j phi_j Delta(q_j - x) (eq. force_spread) as
-//     a deterministic binned gather: nodes are binned by the 4^3 tile of their
-//     support's base cell, the tiles next to a non-empty bin form the band,
-//     and every band tile gathers the nodes overlapping it and adds their
-//     contributions in increasing node index, so the result depends neither
-//     on launch shapes nor on the other droplets of a batch;
+//     a deterministic binned gather: every node is listed in the 4^3 tiles its
+//     4x4x4 kernel support touches (at most 8, or 27 across a partial periodic
+//     tile); the non-empty tiles form the band; every band tile gathers its
+//     nodes, orders them by node index and each cell adds their contributions
+//     in that order, so the result depends neither on launch shapes nor on the
+//     other droplets of a batch;
 //   * interpolation qdot_j = sum_x U(x) Delta(q_j - x) (eq. vel_interpolation)
 //     and forward-Euler advection q_j += qdot_j, 16 lanes per node.
 // Node positions are FP64 so that edge vectors and kernel offsets are exact
@@ -19,7 +20,7 @@ namespace iblb {
 
 namespace {
 
-constexpr int FL = 8;          // lanes per node in the force kernel
+constexpr int FL = 8;          // lanes per node in the force and fill kernels
 
 __device__ __forceinline__ float psi_near(float r)  // 0 <= r <= 1
 {
@@ -38,21 +39,6 @@ __device__ __forceinline__ float ipow(float r, int k)
     return p;
 }
 
-__device__ __forceinline__ int tile_key(const Drop &D, int bx, int by, int bz)
-{
-    // base cell in fluid coordinates (x, y wrapped); -1 if the support misses the fluid
-    int tz;
-    if (D.walls) {
-        if (bz + 2 < 0 || bz - 1 >= D.nzf)
-            return -1;
-        tz = floordiv(bz, TILE);
-        tz = tz < 0 ? 0 : (tz >= D.tz ? D.tz - 1 : tz);
-    } else {
-        tz = bz >> 2;
-    }
-    return (bx >> 2) + D.tx * ((by >> 2) + D.ty * tz);
-}
-
 __device__ __forceinline__ int find_drop_tile(const Drop *D, int n, int64_t t)
 {
     int lo = 0, hi = n - 1;
@@ -66,18 +52,50 @@ __device__ __forceinline__ int find_drop_tile(const Drop *D, int n, int64_t t)
     return lo;
 }
 
+// Distinct tiles (in increasing cell order) holding the support cells
+// b-1 .. b+2 of one axis of n cells: wrapped on a periodic axis, clipped to
+// [0, n) otherwise.  At most 3 (a partial last tile of a periodic axis).
+__device__ __forceinline__ int support_tiles(int b, int n, bool periodic, int *out)
+{
+    int cnt = 0;
+    for (int k = -1; k <= 2; ++k) {
+        int c = b + k;
+        if (periodic)
+            c = wrapi(c, n);
+        else if (c < 0 || c >= n)
+            continue;
+        const int t = c >> 2;
+        if (cnt == 0 || out[cnt - 1] != t) {
+            bool dup = false;
+            for (int i = 0; i < cnt; ++i)
+                dup |= out[i] == t;
+            if (!dup)
+                out[cnt++] = t;
+        }
+    }
+    return cnt;
+}
+
+// Opens a step: generation += 1, an empty band list for this generation (the
+// other list keeps the previous band), clamped-node counters reset.
+__global__ void begin_step_kernel(Arrays a)
+{
+    if (threadIdx.x == 0) {
+        const uint32_t g = *a.gen + 1u;
+        *a.gen = g;
+        a.n_active[g & 1u] = 0;
+    }
+    for (int d = threadIdx.x; d < a.ndrops; d += blockDim.x)
+        a.clamped[d] = 0;
+}
+
 // FL lanes per node; lane l takes the node's incident faces l, l + FL, ...
-// Lane 0 of each group also opens the step for the whole grid (thread 0:
-// generation += 1, empty band list) and writes the node record.
+// Lane 0 writes the node record; the lanes then list the node in the tiles
+// its kernel support touches (rank in each tile's list from the counter).
 __global__ void __launch_bounds__(128) node_force_kernel(Arrays a)
 {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = gid / FL, l = gid % FL;
-    if (gid == 0) {
-        const uint32_t g = *a.gen + 1u;
-        *a.gen = g;
-        a.n_active[g & 1u] = 0;    // the band list of this step; the other one holds the previous band
-    }
     const bool valid = j < a.total_nodes;
     float gx = 0.f, gy = 0.f, gz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, chi = 0.f;
     if (valid) {
@@ -124,86 +142,84 @@ __global__ void __launch_bounds__(128) node_force_kernel(Arrays a)
         nz += __shfl_xor_sync(0xffffffffu, nz, o);
         chi += __shfl_xor_sync(0xffffffffu, chi, o);
     }
-    if (!valid || l != 0)
+    if (!valid)
         return;
     const int d = a.node_drop[j];
     const Drop &D = a.drops[d];
     const double qx = a.qx[j], qy = a.qy[j], qz = a.qz[j];
-    NodeRec r;
-    if (!(fabs(qx) < 1e8 && fabs(qy) < 1e8 && fabs(qz) < 1e8)) {
-        // non-finite or absurd position: no support, no bin, flagged
-        atomicOr(&a.status[4 * d], ST_NAN);
-        r.bx = r.by = r.bz = 0;
-        r.key = -1;
-        for (int k = 0; k < 4; ++k)
-            r.wx[k] = r.wy[k] = r.wz[k] = 0.0f;
-        r.phi[0] = r.phi[1] = r.phi[2] = 0.0f;
+    const bool sane = fabs(qx) < 1e8 && fabs(qy) < 1e8 && fabs(qz) < 1e8;
+    int bx = 0, by = 0, bz = 0;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (sane) {
+        // support of the 4-point kernel: base-1 .. base+2 on each axis
+        const double fbx = floor(qx), fby = floor(qy), fbz = floor(qz);
+        fx = (float)(qx - fbx);
+        fy = (float)(qy - fby);
+        fz = (float)(qz - fbz);
+        bx = wrapi((int)fbx % D.nx, D.nx);
+        by = wrapi((int)fby % D.ny, D.ny);
+        bz = (int)fbz - D.walls;
+        if (!D.walls)
+            bz = wrapi(bz % D.nz, D.nz);
+    }
+    // tiles touched by the support (fluid cells only)
+    int txs[3], tys[3], tzs[3];
+    int ntx = 0, nty = 0, ntz = 0;
+    if (sane) {
+        ntx = support_tiles(bx, D.nx, true, txs);
+        nty = support_tiles(by, D.ny, true, tys);
+        ntz = support_tiles(bz, D.nzf, !D.walls, tzs);
+    }
+    const int ncombo = ntx * nty * ntz;
+    if (l == 0) {
+        NodeRec r;
+        r.bx = bx;
+        r.by = by;
+        r.bz = bz;
+        r.key = ncombo;
         r.spare = d;
-        a.rec[j] = r;
-        return;
-    }
-    float px = -D.sigma * gx, py = -D.sigma * gy, pz = -D.sigma * gz;
-    if (D.wetting) {
-        float h = (float)(qz - 0.5);
-        if (h < D.hmin) {
-            h = D.hmin;
-            atomicAdd(&a.clamped[d], 1);
+        if (!sane) {
+            atomicOr(&a.status[4 * d], ST_NAN);
+            for (int k = 0; k < 4; ++k)
+                r.wx[k] = r.wy[k] = r.wz[k] = 0.0f;
+            r.phi[0] = r.phi[1] = r.phi[2] = 0.0f;
+        } else {
+            float px = -D.sigma * gx, py = -D.sigma * gy, pz = -D.sigma * gz;
+            if (D.wetting) {
+                float h = (float)(qz - 0.5);
+                if (h < D.hmin) {
+                    h = D.hmin;
+                    atomicAdd(&a.clamped[d], 1);
+                }
+                const float r0 = D.xi / h;
+                const float Pi = D.A * (ipow(r0, D.n) - ipow(r0, D.m));
+                const float inl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
+                const float s = -(chi * (1.0f / 3.0f)) * Pi * inl;
+                px += s * nx;
+                py += s * ny;
+                pz += s * nz;
+            }
+            r.wx[0] = psi_far(1.0f + fx); r.wx[1] = psi_near(fx); r.wx[2] = psi_near(1.0f - fx); r.wx[3] = psi_far(2.0f - fx);
+            r.wy[0] = psi_far(1.0f + fy); r.wy[1] = psi_near(fy); r.wy[2] = psi_near(1.0f - fy); r.wy[3] = psi_far(2.0f - fy);
+            r.wz[0] = psi_far(1.0f + fz); r.wz[1] = psi_near(fz); r.wz[2] = psi_near(1.0f - fz); r.wz[3] = psi_far(2.0f - fz);
+            r.phi[0] = px;
+            r.phi[1] = py;
+            r.phi[2] = pz;
+            if (ncombo == 0)
+                atomicOr(&a.status[4 * d], ST_ESCAPE);
         }
-        const float r0 = D.xi / h;
-        const float Pi = D.A * (ipow(r0, D.n) - ipow(r0, D.m));
-        const float inl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
-        const float s = -(chi * (1.0f / 3.0f)) * Pi * inl;
-        px += s * nx;
-        py += s * ny;
-        pz += s * nz;
+        a.rec[j] = r;
     }
-    // support of the 4-point kernel: base-1 .. base+2 on each axis
-    const double fbx = floor(qx), fby = floor(qy), fbz = floor(qz);
-    const float fx = (float)(qx - fbx), fy = (float)(qy - fby), fz = (float)(qz - fbz);
-    r.bx = wrapi((int)fbx % D.nx, D.nx);
-    r.by = wrapi((int)fby % D.ny, D.ny);
-    int bz = (int)fbz - D.walls;
-    if (!D.walls)
-        bz = wrapi(bz % D.nz, D.nz);
-    r.bz = bz;
-    r.wx[0] = psi_far(1.0f + fx); r.wx[1] = psi_near(fx); r.wx[2] = psi_near(1.0f - fx); r.wx[3] = psi_far(2.0f - fx);
-    r.wy[0] = psi_far(1.0f + fy); r.wy[1] = psi_near(fy); r.wy[2] = psi_near(1.0f - fy); r.wy[3] = psi_far(2.0f - fy);
-    r.wz[0] = psi_far(1.0f + fz); r.wz[1] = psi_near(fz); r.wz[2] = psi_near(1.0f - fz); r.wz[3] = psi_far(2.0f - fz);
-    r.phi[0] = px;
-    r.phi[1] = py;
-    r.phi[2] = pz;
-    r.spare = d;
-    const int key = tile_key(D, r.bx, r.by, r.bz);
-    r.key = key < 0 ? -1 : (int)(D.tile0 + key);
-    if (key < 0)
-        atomicOr(&a.status[4 * d], ST_ESCAPE);
-    else
-        a.bin_rank[j] = atomicAdd(&a.bin_cnt[r.key], 1);
-    a.rec[j] = r;
+    for (int c = l; c < ncombo; c += FL) {
+        const int ix = c % ntx, iy = (c / ntx) % nty, iz = c / (ntx * nty);
+        const int64_t t = D.tile0 + txs[ix] + (int64_t)D.tx * (tys[iy] + (int64_t)D.ty * tzs[iz]);
+        a.pair_rank[(int64_t)j * MAXPAIR + c] = atomicAdd(&a.bin_cnt[t], 1);
+    }
 }
 
-// Is tile t in the band, i.e. is one of the bins around it non-empty?
-__device__ __forceinline__ bool tile_in_band(const Arrays &a, int64_t t)
-{
-    const int d = find_drop_tile(a.drops, a.ndrops, t);
-    const Drop &D = a.drops[d];
-    const int local = (int)(t - D.tile0);
-    const int kx = local % D.tx, ky = (local / D.tx) % D.ty, kz = local / (D.tx * D.ty);
-    int lx[4], ly[4], lz[4];
-    const int nxl = tile_neighbours(kx, D.tx, D.nx, true, lx);
-    const int nyl = tile_neighbours(ky, D.ty, D.ny, true, ly);
-    const int nzl = tile_neighbours(kz, D.tz, D.nzf, !D.walls, lz);
-    bool any = false;
-    for (int iz = 0; iz < nzl; ++iz)
-        for (int iy = 0; iy < nyl; ++iy)
-            for (int ix = 0; ix < nxl; ++ix)
-                any |= a.bin_cnt[D.tile0 + lx[ix] + (int64_t)D.tx * (ly[iy] + (int64_t)D.ty * lz[iz])] > 0;
-    return any;
-}
-
-// Block-level exclusive scan of the bin counts (SCAN_ITEMS per block), and
-// band marking of the same tiles: tile_gen = generation for band tiles,
-// which are appended to the band list (warp-aggregated).
+// Block-level exclusive scan of the per-tile list lengths (SCAN_ITEMS per
+// block); the non-empty tiles are the band of this step: stamped with the
+// generation and appended to this step's band list (warp-aggregated).
 __global__ void __launch_bounds__(1024) scan_mark_kernel(Arrays a)
 {
     __shared__ int warp_tot[32];
@@ -247,18 +263,9 @@ __global__ void __launch_bounds__(1024) scan_mark_kernel(Arrays a)
     int *list = a.active + (int64_t)cur * a.active_cap;
     for (int i = 0; i < 4; ++i) {
         const int64_t t = base + i;
-        const bool band = t < a.total_tiles && tile_in_band(a, t);
-        if (band) {
+        const bool band = t < a.total_tiles && v[i] > 0;
+        if (band)
             a.tile_gen[t] = gen;
-            // the rows crossing this tile meet the band
-            const int d = find_drop_tile(a.drops, a.ndrops, t);
-            const Drop &D = a.drops[d];
-            const int local = (int)(t - D.tile0);
-            const int ky = (local / D.tx) % D.ty, kz = local / (D.tx * D.ty);
-            for (int z = 4 * kz; z < min(4 * kz + 4, D.nzf); ++z)
-                for (int y = 4 * ky; y < min(4 * ky + 4, D.ny); ++y)
-                    a.row_gen[D.row0 + y + (int64_t)D.ny * z] = gen;
-        }
         const unsigned m = __ballot_sync(0xffffffffu, band);
         if (!m)
             continue;
@@ -270,29 +277,6 @@ __global__ void __launch_bounds__(1024) scan_mark_kernel(Arrays a)
             const int s = slot0 + __popc(m & ((1u << lane) - 1u));
             if (s < a.active_cap)
                 list[s] = (int)t;
-        }
-    }
-
-    // zero the force density of the previous step's band tiles (the spread
-    // rewrites the tiles of this step's band), so that F vanishes outside it
-    const int prev = cur ^ 1;
-    const int64_t nprev = (int64_t)min(a.n_active[prev], a.active_cap) * TILE_CELLS;
-    const int *plist = a.active + (int64_t)prev * a.active_cap;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nprev;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = plist[idx / TILE_CELLS];
-        const int cell = (int)(idx % TILE_CELLS);
-        const int d = find_drop_tile(a.drops, a.ndrops, t);
-        const Drop &D = a.drops[d];
-        const int local = (int)(t - D.tile0);
-        const int X = 4 * (local % D.tx) + (cell & 3);
-        const int Y = 4 * ((local / D.tx) % D.ty) + ((cell >> 2) & 3);
-        const int Z = 4 * (local / (D.tx * D.ty)) + (cell >> 4);
-        if (X < D.nx && Y < D.ny && Z < D.nzf) {
-            const int64_t g = D.pcell0 + X + (int64_t)D.pitch * (Y + (int64_t)D.ny * Z);
-            a.F[g] = 0.0f;
-            a.F[a.total_pcells + g] = 0.0f;
-            a.F[2 * a.total_pcells + g] = 0.0f;
         }
     }
 }
@@ -339,31 +323,41 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(const int *__restrict__ 
     }
 }
 
-// start of bin t in the sorted records; the scan covers total_tiles + 1 entries (the
-// last count is always zero), so bin t ends where bin t + 1 begins
-__device__ __forceinline__ int bin_begin(const Arrays &a, int64_t t)
+// start of tile t's node list; the scan covers total_tiles + 1 entries (the
+// last count is always zero), so list t ends where list t + 1 begins
+__device__ __forceinline__ int list_begin(const Arrays &a, int64_t t)
 {
     return a.bin_off[t] + a.blk_off[t / SCAN_ITEMS];
 }
 
-// Copy every binned node's record into bin order (the order inside a bin is
-// the arrival order of the binning atomics, which is irrelevant: the gather
-// sorts by node index).  The sorted copy carries the node index in `spare`.
-// The node of rank 0 resets its bin counter for the next step.
-__global__ void fill_kernel(Arrays a)
+// Write every node into the lists of the tiles its support touches (same
+// enumeration as the force kernel, position = list start + rank).  The order
+// inside a list is the arrival order of the counting atomics, which does not
+// matter: the gather sorts by node index.  The entry of rank 0 resets the
+// tile's counter for the next step.
+__global__ void __launch_bounds__(128) fill_kernel(Arrays a)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = gid / FL, l = gid % FL;
     if (j >= a.total_nodes)
         return;
-    NodeRec r = a.rec[j];
-    if (r.key < 0)
+    const NodeRec &r = a.rec[j];
+    const int ncombo = r.key;
+    if (l >= ncombo)
         return;
-    const int rank = a.bin_rank[j];
-    const int key = r.key;
-    r.spare = j;
-    a.srec[bin_begin(a, key) + rank] = r;
-    if (rank == 0)
-        a.bin_cnt[key] = 0;
+    const Drop &D = a.drops[r.spare];
+    int txs[3], tys[3], tzs[3];
+    const int ntx = support_tiles(r.bx, D.nx, true, txs);
+    const int nty = support_tiles(r.by, D.ny, true, tys);
+    support_tiles(r.bz, D.nzf, !D.walls, tzs);
+    for (int c = l; c < ncombo; c += FL) {
+        const int ix = c % ntx, iy = (c / ntx) % nty, iz = c / (ntx * nty);
+        const int64_t t = D.tile0 + txs[ix] + (int64_t)D.tx * (tys[iy] + (int64_t)D.ty * tzs[iz]);
+        const int rank = a.pair_rank[(int64_t)j * MAXPAIR + c];
+        a.tile_list[list_begin(a, t) + rank] = j;
+        if (rank == 0)
+            a.bin_cnt[t] = 0;
+    }
 }
 
 // offset of cell X from support base b on a periodic axis of n cells,
@@ -378,98 +372,78 @@ __device__ __forceinline__ int per_off(int X, int b, int n)
     return d;
 }
 
-__device__ __forceinline__ bool support_hits(int lo, int hi, int b, int n, bool periodic)
-{
-    for (int X = lo; X <= hi; ++X) {
-        const int d = periodic ? per_off(X, b, n) : X - b;
-        if (d >= -1 && d <= 2)
-            return true;
-    }
-    return false;
-}
-
-// One 256-thread block per band tile (block-stride over the band list).  The
-// ranges of the neighbouring bins are read in parallel, the records of the
-// nodes whose support overlaps the tile are staged in parallel and sorted by
-// node index; four threads per cell add disjoint quarters of the sorted list
-// and the quarters are summed in a fixed order, so every cell's force is the
-// same for any launch shape.
-constexpr int SPREAD_THREADS = 4 * TILE_CELLS;
+// One 128-thread block per band tile (block-stride over the band list).  The
+// tile's nodes are staged in parallel and sorted by node index; two threads
+// per cell add the two halves of the sorted list and the halves are summed
+// in a fixed order, so every cell's force is the same for any launch shape.
+constexpr int SPREAD_THREADS = 2 * TILE_CELLS;
 
 __global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
 {
-    __shared__ int s_cnt;
-    __shared__ int s_beg[64], s_pre[65];
     __shared__ int s_node[SPREAD_CAP];
     __shared__ short s_perm[SPREAD_CAP];
     __shared__ int s_b[3][SPREAD_CAP];
     __shared__ float s_w[12][SPREAD_CAP];
     __shared__ float s_phi[3][SPREAD_CAP];
-    __shared__ float s_part[3][3][TILE_CELLS];
-    const int cur = (int)(*a.gen & 1u);
+    __shared__ float s_part[3][TILE_CELLS];
+    const uint32_t gen = *a.gen;
+    const int cur = (int)(gen & 1u);
     const int nact = min(a.n_active[cur], a.active_cap);
     const int *list = a.active + (int64_t)cur * a.active_cap;
     const int tid = threadIdx.x;
+    // tiles that left the band since the previous step: zero their force, so
+    // F vanishes outside this step's band (band tiles are rewritten below)
+    {
+        const int nprev = min(a.n_active[cur ^ 1], a.active_cap);
+        const int *plist = a.active + (int64_t)(cur ^ 1) * a.active_cap;
+        for (int it = blockIdx.x * 2 + (tid >> 6); it < nprev; it += gridDim.x * 2) {
+            const int64_t T = plist[it];
+            if (a.tile_gen[T] == gen)
+                continue;
+            const int d = find_drop_tile(a.drops, a.ndrops, T);
+            const Drop &D = a.drops[d];
+            const int local = (int)(T - D.tile0), cell = tid & 63;
+            const int X = 4 * (local % D.tx) + (cell & 3);
+            const int Y = 4 * ((local / D.tx) % D.ty) + ((cell >> 2) & 3);
+            const int Z = 4 * (local / (D.tx * D.ty)) + (cell >> 4);
+            if (X < D.nx && Y < D.ny && Z < D.nzf) {
+                const int64_t g = D.pcell0 + X + (int64_t)D.pitch * (Y + (int64_t)D.ny * Z);
+                a.F[g] = 0.0f;
+                a.F[a.total_pcells + g] = 0.0f;
+                a.F[2 * a.total_pcells + g] = 0.0f;
+            }
+        }
+    }
     for (int it = blockIdx.x; it < nact; it += gridDim.x) {
         const int64_t T = list[it];
         const int d = find_drop_tile(a.drops, a.ndrops, T);
         const Drop &D = a.drops[d];
         const int local = (int)(T - D.tile0);
-        const int kx = local % D.tx, ky = (local / D.tx) % D.ty, kz = local / (D.tx * D.ty);
-        const int X0 = 4 * kx, Y0 = 4 * ky, Z0 = 4 * kz;
-        const int X1 = min(X0 + 3, D.nx - 1), Y1 = min(Y0 + 3, D.ny - 1), Z1 = min(Z0 + 3, D.nzf - 1);
-        int lx[4], ly[4], lz[4];
-        const int nxl = tile_neighbours(kx, D.tx, D.nx, true, lx);
-        const int nyl = tile_neighbours(ky, D.ty, D.ny, true, ly);
-        const int nzl = tile_neighbours(kz, D.tz, D.nzf, !D.walls, lz);
-        const int nb = nxl * nyl * nzl;
-        // bin ranges, one thread per neighbouring bin
-        if (tid < nb) {
-            const int ix = tid % nxl, iy = (tid / nxl) % nyl, iz = tid / (nxl * nyl);
-            const int64_t B = D.tile0 + lx[ix] + (int64_t)D.tx * (ly[iy] + (int64_t)D.ty * lz[iz]);
-            const int b0 = bin_begin(a, B);
-            s_beg[tid] = b0;
-            s_pre[tid + 1] = bin_begin(a, B + 1) - b0;
-        }
-        if (tid == 0) {
-            s_cnt = 0;
-            s_pre[0] = 0;
-        }
-        __syncthreads();
-        if (tid == 0)
-            for (int k = 0; k < nb; ++k)
-                s_pre[k + 1] += s_pre[k];
-        __syncthreads();
-        const int total = s_pre[nb];
-        for (int e = tid; e < total; e += SPREAD_THREADS) {
-            int k = 0;
-            while (s_pre[k + 1] <= e)
-                ++k;
-            const NodeRec &r = a.srec[s_beg[k] + e - s_pre[k]];
-            const int4 hdr = *reinterpret_cast<const int4 *>(&r);
-            if (!support_hits(X0, X1, hdr.x, D.nx, true) || !support_hits(Y0, Y1, hdr.y, D.ny, true) ||
-                !support_hits(Z0, Z1, hdr.z, D.nzf, !D.walls))
-                continue;
-            const int slot = atomicAdd(&s_cnt, 1);
-            if (slot >= SPREAD_CAP) {
+        const int X0 = 4 * (local % D.tx), Y0 = 4 * ((local / D.tx) % D.ty), Z0 = 4 * (local / (D.tx * D.ty));
+        const int e0 = list_begin(a, T);
+        int cnt = list_begin(a, T + 1) - e0;
+        if (cnt > SPREAD_CAP) {
+            if (tid == 0)
                 atomicOr(&a.status[4 * d], ST_SPREAD_OVF);
-                continue;
-            }
-            s_node[slot] = r.spare;
-            s_b[0][slot] = hdr.x;
-            s_b[1][slot] = hdr.y;
-            s_b[2][slot] = hdr.z;
+            cnt = SPREAD_CAP;
+        }
+        for (int e = tid; e < cnt; e += SPREAD_THREADS) {
+            const int j = a.tile_list[e0 + e];
+            const NodeRec &r = a.rec[j];
+            s_node[e] = j;
+            s_b[0][e] = r.bx;
+            s_b[1][e] = r.by;
+            s_b[2][e] = r.bz;
             for (int q = 0; q < 4; ++q) {
-                s_w[q][slot] = r.wx[q];
-                s_w[4 + q][slot] = r.wy[q];
-                s_w[8 + q][slot] = r.wz[q];
+                s_w[q][e] = r.wx[q];
+                s_w[4 + q][e] = r.wy[q];
+                s_w[8 + q][e] = r.wz[q];
             }
-            s_phi[0][slot] = r.phi[0];
-            s_phi[1][slot] = r.phi[1];
-            s_phi[2][slot] = r.phi[2];
+            s_phi[0][e] = r.phi[0];
+            s_phi[1][e] = r.phi[1];
+            s_phi[2][e] = r.phi[2];
         }
         __syncthreads();
-        const int cnt = min(s_cnt, SPREAD_CAP);
         // rank sort by node index: contributions are added in increasing j
         for (int e = tid; e < cnt; e += SPREAD_THREADS) {
             const int key = s_node[e];
@@ -481,7 +455,7 @@ __global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
         __syncthreads();
         const int cell = tid & (TILE_CELLS - 1), part = tid >> 6;
         const int X = X0 + (cell & 3), Y = Y0 + ((cell >> 2) & 3), Z = Z0 + (cell >> 4);
-        const int k0 = (part * cnt) >> 2, k1 = ((part + 1) * cnt) >> 2;
+        const int k0 = part ? (cnt >> 1) : 0, k1 = part ? cnt : (cnt >> 1);
         float fx = 0.f, fy = 0.f, fz = 0.f;
         for (int k = k0; k < k1; ++k) {
             const int e = s_perm[k];
@@ -495,18 +469,16 @@ __global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
             fy += s_phi[1][e] * w;
             fz += s_phi[2][e] * w;
         }
-        if (part > 0) {
-            s_part[part - 1][0][cell] = fx;
-            s_part[part - 1][1][cell] = fy;
-            s_part[part - 1][2][cell] = fz;
+        if (part) {
+            s_part[0][cell] = fx;
+            s_part[1][cell] = fy;
+            s_part[2][cell] = fz;
         }
         __syncthreads();
-        if (part == 0 && X < D.nx && Y < D.ny && Z < D.nzf) {
-            for (int p = 0; p < 3; ++p) {
-                fx += s_part[p][0][cell];
-                fy += s_part[p][1][cell];
-                fz += s_part[p][2][cell];
-            }
+        if (!part && X < D.nx && Y < D.ny && Z < D.nzf) {
+            fx += s_part[0][cell];
+            fy += s_part[1][cell];
+            fz += s_part[2][cell];
             const int64_t g = D.pcell0 + X + (int64_t)D.pitch * (Y + (int64_t)D.ny * Z);
             a.F[g] = fx;
             a.F[a.total_pcells + g] = fy;
@@ -529,7 +501,7 @@ __global__ void __launch_bounds__(256) interp_advect_kernel(Arrays a)
         const NodeRec &r = a.rec[j];
         d = r.spare;
         const Drop &D = a.drops[d];
-        if (r.key >= 0) {
+        if (r.key > 0) {
             const int dy = l & 3, dz = l >> 2;
             int Z = r.bz - 1 + dz;
             bool fluid = true;
@@ -575,6 +547,7 @@ cudaError_t launch_node_force(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
+    begin_step_kernel<<<1, 64, 0, s>>>(a);
     const int64_t threads = (int64_t)a.total_nodes * FL;
     node_force_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
@@ -591,7 +564,8 @@ cudaError_t launch_spread(const Arrays &a, cudaStream_t s)
     }
     scan_mark_kernel<<<a.n_scan_blocks, 1024, 0, s>>>(a);
     scan_top_kernel<<<1, 1024, 0, s>>>(a.blk_sum, a.n_scan_blocks, a.blk_off);
-    fill_kernel<<<(a.total_nodes + 255) / 256, 256, 0, s>>>(a);
+    const int64_t threads = (int64_t)a.total_nodes * FL;
+    fill_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a);
     spread_kernel<<<g_sm_count * 5, SPREAD_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }

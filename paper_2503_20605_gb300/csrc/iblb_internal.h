@@ -16,6 +16,7 @@ constexpr int TILE = 4;            // band tiles are 4x4x4 fluid cells
 constexpr int TILE_CELLS = 64;
 constexpr int MAXC = 16;           // ray crossings kept per lattice column
 constexpr int SPREAD_CAP = 512;    // nodes whose stencil overlaps one tile
+constexpr int MAXPAIR = 27;        // tiles one node's 4x4x4 support can touch
 constexpr int SCAN_ITEMS = 4096;   // elements per block of the tile scan
 constexpr int RED_FACES = 2048;    // faces per chunk of the observation reductions
 constexpr int RED_NODES = 1024;    // nodes per chunk of the observation reductions
@@ -56,8 +57,9 @@ struct Drop {
 
 // Record written per node by the force kernel and read by the spread and
 // the interpolation: base cell of the 4^3 support (fluid coordinates, x and
-// y wrapped into the box), bin key, kernel weights Psi along each axis for
-// the support cells base-1 .. base+2, and the nodal force phi_j.
+// y wrapped into the box), number of tiles the support touches (0: none in
+// the fluid), kernel weights Psi along each axis for the support cells
+// base-1 .. base+2, the nodal force phi_j and the node's droplet.
 struct __align__(16) NodeRec {
     int bx, by, bz, key;
     float wx[4], wy[4], wz[4];
@@ -83,7 +85,6 @@ struct Arrays {
     float *F;                      // 3 * total_pcells, force density: exactly 0 outside band tiles
     float *U;                      // 3 * total_pcells, velocity (valid on band rows only)
     uint32_t *tile_gen;            // tile is in the band of this step iff == *gen
-    uint32_t *row_gen;             // total_rows: row meets a band tile of this step iff == *gen
     uint32_t *gen;                 // step generation counter (device)
     int *n_active;                 // 2: band tiles of this step / of the previous step
     int *active;                   // 2 * active_cap: band tiles, indexed by generation parity
@@ -94,8 +95,8 @@ struct Arrays {
     int *blk_sum;                  // blocks of the scan
     int *blk_off;
     int n_scan_blocks;
-    int *bin_rank;                 // total_nodes: rank of the node inside its bin
-    NodeRec *srec;                 // total_nodes: node records in bin order (spare = node index)
+    int *pair_rank;                // MAXPAIR per node: rank of the node in each touched tile's list
+    int *tile_list;                // MAXPAIR * total_nodes: node indices listed per tile
     // membrane
     double *qx, *qy, *qz;          // node positions (FP64)
     int *node_drop;                // droplet of each node

@@ -143,9 +143,13 @@ __device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t 
     const int P = D.pitch, ny = D.ny, R = D.lb_rows;
     Stage<S> stg(sbase, R, P);
     const int64_t plane_row0 = (int64_t)ny * z;
+    // the group carries force iff one of the tiles its rows cross is in this
+    // step's band (F vanishes elsewhere)
+    const int ky0 = y0 >> 2, nty = ((y0 + nr - 1) >> 2) - ky0 + 1;
+    const int64_t trow0 = D.tile0 + (int64_t)D.tx * (ky0 + (int64_t)D.ty * (z >> 2));
     bool band = false;
-    for (int r = lane; r < nr; r += 32)
-        band |= a.row_gen[D.row0 + plane_row0 + y0 + r] == gen;
+    for (int q = lane; q < nty * D.tx; q += 32)
+        band |= a.tile_gen[trow0 + q] == gen;
     band = __any_sync(0xffffffffu, band);
     const uint32_t rowb = (uint32_t)(P * sizeof(S));
     // copies of this lane: up to two pieces (source row, destination row, rows)
