@@ -261,6 +261,25 @@ int iblb_mesh_observe_dev(const double *d_xyz, int n_nodes, const int32_t *d_tri
                           double R0, double zcut_frac, double eps_flat, void *stream,
                           double *out);
 
+/* The same observables as iblb_mesh_observe_dev, with the same arguments and
+ * output, computed without allocating any memory: the scratch is a fixed
+ * array in device global memory, one per device.  The paper has no
+ * counterpart to this call; it serves callers that cannot allocate device
+ * memory at that moment (all free memory held by a caching allocator, or an
+ * out-of-memory handler).
+ *   Limit: n_tri <= 1,048,576 and n_nodes <= 524,288; larger meshes return
+ *   IBLB_E_ARG without touching the device.
+ *   Nothing needs to be zeroed beforehand.
+ *   The first call on a device (with that device current) looks up the
+ *   array's address with cudaGetSymbolAddress and caches it; make that first
+ *   call before capturing any stream.  Any CUDA error returns IBLB_E_CUDA.
+ *   Not reentrant: calls in flight at the same time on the same device (other
+ *   host threads, other streams) share the array and race.  Each call
+ *   synchronises `stream` before it returns. */
+int iblb_mesh_observe_dev_noalloc(const double *d_xyz, int n_nodes, const int32_t *d_tri, int n_tri,
+                                  double R0, double zcut_frac, double eps_flat, void *stream,
+                                  double *out);
+
 #ifdef __cplusplus
 }
 #endif

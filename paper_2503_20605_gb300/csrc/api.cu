@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -1297,6 +1298,73 @@ int iblb_mesh_observe_dev(const double *d_xyz, int n_nodes, const int32_t *d_tri
                                         eps_flat, scr, out, s);
     cudaFreeAsync(scr, s);
     CK(e);
+    CK(cudaStreamSynchronize(s));
+    return IBLB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Mesh observables with their scratch in a fixed device array.
+//
+// iblb_mesh_observe_dev takes its scratch from cudaMallocAsync.  Some callers
+// cannot allocate device memory at the moment they want the observables: a
+// monitor that samples a droplet while a caching allocator (PyTorch's, for
+// instance) has claimed all free device memory, where any further allocation
+// fails with out-of-memory; or a handler that runs because an allocation just
+// failed and wants to record the droplet's state before giving up.  This
+// variant runs the same kernels on a statically sized __device__ array, so it
+// makes no allocation of any kind.  The array holds the scratch of meshes up
+// to kNoAllocMaxChunks reduction chunks (each RED_FACES faces and RED_NODES
+// nodes): 1,048,576 faces and 524,288 nodes, 53.6 KB of doubles.
+//
+// Nothing in the array needs to start at zero: every element the kernels read
+// is written earlier in the same call.  The array is one per device and the
+// call is not reentrant: two calls in flight at once on the same device (from
+// two host threads, or on two streams) share it and race.  A call returns only
+// after its stream has drained, so calls made one after another are safe.
+namespace {
+constexpr int kNoAllocMaxChunks = 512;
+constexpr int kNoAllocMaxFaces = kNoAllocMaxChunks * RED_FACES;
+constexpr int kNoAllocMaxNodes = kNoAllocMaxChunks * RED_NODES;
+constexpr int64_t kNoAllocScratch = (int64_t)NRED * kNoAllocMaxChunks + 32 + 5 * (int64_t)kNoAllocMaxChunks + 8;
+constexpr int kNoAllocMaxDevices = 256;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) double g_observe_scratch[kNoAllocScratch];
+
+extern "C" {
+
+int iblb_mesh_observe_dev_noalloc(const double *d_xyz, int n_nodes, const int32_t *d_tri, int n_tri, double R0,
+                                  double zcut_frac, double eps_flat, void *stream, double *out)
+{
+    iblb_ctx *c = nullptr;
+    if (!d_xyz || !d_tri || !out || n_nodes < 1 || n_tri < 1 || !(R0 > 0.0))
+        return fail(nullptr, IBLB_E_ARG, "iblb_mesh_observe_dev_noalloc: bad arguments");
+    if (n_tri > kNoAllocMaxFaces || n_nodes > kNoAllocMaxNodes ||
+        observe_scratch_doubles(n_nodes, n_tri) > kNoAllocScratch)
+        return fail(nullptr, IBLB_E_ARG,
+                    "iblb_mesh_observe_dev_noalloc: mesh too large for the static scratch (at most " +
+                        std::to_string(kNoAllocMaxFaces) + " faces and " + std::to_string(kNoAllocMaxNodes) +
+                        " nodes); use iblb_mesh_observe_dev");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(nullptr, IBLB_E_ARG, "iblb_mesh_observe_dev_noalloc: device ordinal out of range");
+    double *scr = nullptr;
+    {
+        // The address of the array on this device is looked up once, on the
+        // first call made with the device current, and cached.
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev])
+            CK(cudaGetSymbolAddress((void **)&g_noalloc_ptr[dev], g_observe_scratch));
+        scr = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_observe_view(d_xyz, d_xyz + 1, d_xyz + 2, 3, d_tri, n_tri, 0, n_nodes, R0, zcut_frac, eps_flat, scr,
+                           out, s));
     CK(cudaStreamSynchronize(s));
     return IBLB_OK;
 }

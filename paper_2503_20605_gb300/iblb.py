@@ -96,6 +96,8 @@ _SIGS = {
     "iblb_save": (C.c_int, [_P, C.c_char_p]),
     "iblb_load": (C.c_int, [_P, C.c_char_p]),
     "iblb_mesh_observe_dev": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, C.c_double, C.c_double, _P, _D]),
+    "iblb_mesh_observe_dev_noalloc": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, C.c_double, C.c_double, _P,
+                                                _D]),
 }
 
 _lib = None
@@ -304,4 +306,12 @@ def iblb_mesh_observe_dev(d_xyz, n_nodes, d_tri, n_tri, R0, zcut_frac=0.05, eps_
     out = np.empty(13)
     _check(None, lib().iblb_mesh_observe_dev(_P(d_xyz), n_nodes, _P(d_tri), n_tri, R0, zcut_frac, eps_flat,
                                              _P(stream), _d(out)))
+    return out
+
+
+def iblb_mesh_observe_dev_noalloc(d_xyz, n_nodes, d_tri, n_tri, R0, zcut_frac=0.05, eps_flat=0.1, stream=0):
+    """As iblb_mesh_observe_dev, with the scratch in a fixed device array (no allocation)."""
+    out = np.empty(13)
+    _check(None, lib().iblb_mesh_observe_dev_noalloc(_P(d_xyz), n_nodes, _P(d_tri), n_tri, R0, zcut_frac,
+                                                     eps_flat, _P(stream), _d(out)))
     return out
