@@ -124,12 +124,44 @@ def make_ctx(iblb, spec, storage, stream):
 
 
 def launches_per_step(spec):
-    n = 1 + 3 + 1 + 1 + 1            # forces; scan x2 + fill; spread; stream-collide; interp/advect
+    n = 2 + 4 + 1 + 1                # step opening + forces; scan x2, fill, spread; stream-collide; advect
     if spec.lam != 1.0:
-        n += 3
+        n += 3                       # column reset, face crossings, column sort
     if spec.volume_correction:
-        n += 3
+        n += 2                       # FP64 volume/centroid reduction, rescale
     return n
+
+
+def run_accuracy(I, iblb, torch, steps, angles=(30.0, 60.0, 90.0, 120.0, 150.0)):
+    """Contact angle after `steps` steps of the 128^3 statics droplet for each
+    theta_eq, all angles in one batched context per storage; reduced storage
+    against FP32 storage on the same GPU."""
+    stream = torch.cuda.current_stream().cuda_stream
+    res = {}
+    for storage in ("f32", "f16", "bf16"):
+        specs = [I.workload_statics_128(th, storage) for th in angles]
+        lats = [iblb.lattice_desc(w.nx, w.ny, w.nz, tau_out=w.tau, lam=w.lam, storage=storage) for w in specs]
+        phys = [iblb.physics_desc(sigma=w.sigma, theta_eq_deg=w.theta_deg, xi=w.xi,
+                                  volume_correction=int(w.volume_correction)) for w in specs]
+        ctx = iblb.iblb_batch_create(lats, phys, stream)
+        try:
+            for k, w in enumerate(specs):
+                xyz, tri = w.mesh()
+                iblb.iblb_set_membrane(ctx, k, xyz, tri)
+            iblb.iblb_step(ctx, steps)
+            obs = [iblb.iblb_observe(ctx, k) for k in range(len(angles))]
+        finally:
+            iblb.iblb_destroy(ctx)
+        res[storage] = obs
+    out = {"steps": steps, "theta_eq_deg": list(angles),
+           "theta_RV_deg": {s: [o["theta_RV_deg"] for o in res[s]] for s in res},
+           "volume": {s: [o["volume"] for o in res[s]] for s in res}}
+    for s in ("f16", "bf16"):
+        out[f"max_abs_dtheta_{s}_vs_f32_deg"] = max(abs(a["theta_RV_deg"] - b["theta_RV_deg"])
+                                                   for a, b in zip(res[s], res["f32"]))
+        out[f"max_rel_dvolume_{s}_vs_f32"] = max(abs(a["volume"] / b["volume"] - 1.0)
+                                                for a, b in zip(res[s], res["f32"]))
+    return out
 
 
 def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
@@ -229,6 +261,8 @@ def main():
     ap.add_argument("--only-main", action="store_true",
                     help="time only the headline storage (no FP32 line, no e2e loop); for profiler runs")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--accuracy-steps", type=int, default=20000,
+                    help="steps of the FP16/BF16-vs-FP32 contact-angle comparison at 128^3 (0: skip)")
     args = ap.parse_args()
 
     from paper_2503_20605_gb300 import inputs as I
@@ -308,6 +342,10 @@ def main():
                 "lb_kernel_gbs": cells * BYTES_PER_CELL["f32"] / (lb32 * 1e-3) / 1e9,
                 "theta_RV_deg_after": run32["obs"]["theta_RV_deg"]}
 
+    accuracy = None
+    if rank == 0 and not args.only_main and args.accuracy_steps > 0:
+        accuracy = run_accuracy(I, iblb, torch, args.accuracy_steps)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n, dt, c_cells, _ = cpu_oracle(spec, args.cpu_budget, 1000)
@@ -333,6 +371,7 @@ def main():
             "gpu_launches": launches_per_step(spec) * K,
             "clocks": clk.summary(),
             "theta_RV_deg_after": main_run["obs"]["theta_RV_deg"],
+            "accuracy": accuracy,
         }
         print(json.dumps(line))
     if world > 1:

@@ -1,0 +1,122 @@
+"""Reduced-precision population storage (offsets s_i = f_i - w_i rho0 held
+in FP16 or BF16, arithmetic in FP32) through the C ABI.
+
+* The codec: populations written through iblb_set_populations and read back
+  are w_i rho0 + round_to_nearest_even(f_i - w_i rho0) in the storage type,
+  bit for bit (FP32, FP16, BF16).
+* The accuracy bar for reduced storage: the half-scale statics case (64^3,
+  R = 12, L4 mesh, theta_eq in {30, 60, 90, 120, 150} deg; Sec. III statics)
+  run on the GPU in FP32, FP16 and BF16 storage, all five angles as one
+  batched context, against the FP64 oracle's trajectory stored in
+  tests/golden/statics64_oracle.txt (written by make_statics64.py from the
+  oracle alone): contact angle (Eq. angleh, with R0 and with the
+  volume-equivalent radius) within 1 degree, droplet volume and height within
+  0.5% at every observation up to 10000 steps (angles below 175 degrees,
+  where Eq. angleh is well conditioned).  FP32 storage is held to 0.05
+  degree and 0.05%."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2503_20605_gb300 import iblb
+from paper_2503_20605_gb300 import inputs as I
+from gpu_util import stream
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "statics64_oracle.txt")
+W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+BAR = {"f32": (0.05, 5e-4), "f16": (1.0, 5e-3), "bf16": (1.0, 5e-3)}   # (degrees, relative volume)
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    iblb.lib()
+
+
+def round_bf16(x):
+    """Round float64 values to the nearest bfloat16 (ties to even), exact for
+    results in the normal range: keep 8 significant bits of the binary64."""
+    b = np.ascontiguousarray(x, np.float64).view(np.uint64)
+    lsb = (b >> np.uint64(45)) & np.uint64(1)
+    b = (b + (np.uint64((1 << 44) - 1) + lsb)) & ~np.uint64((1 << 45) - 1)
+    return b.view(np.float64)
+
+
+def expected_codec(f, storage):
+    s = f - np.repeat(W, f.size // 19)
+    if storage == "f32":
+        s = s.astype(np.float32).astype(np.float64)
+    elif storage == "f16":
+        s = s.astype(np.float16).astype(np.float64)
+    else:
+        s = round_bf16(s)
+    return np.repeat(W, f.size // 19) + s
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_offset_codec_roundtrip(storage):
+    lat = iblb.lattice_desc(20, 12, 9, storage=storage)
+    ctx = iblb.iblb_create(lat, iblb.physics_desc(), stream())
+    try:
+        cells = iblb.iblb_info(ctx, 0)["cells"]
+        rng = np.random.default_rng(11)
+        f = np.repeat(W, cells) * (1.0 + rng.uniform(-0.05, 0.05, 19 * cells))
+        iblb.iblb_set_populations(ctx, 0, f)
+        back = iblb.iblb_get_populations(ctx, 0)
+        np.testing.assert_array_equal(back, expected_codec(f, storage))
+    finally:
+        iblb.iblb_destroy(ctx)
+
+
+def load_golden():
+    rows = np.loadtxt(GOLDEN)
+    cols = ["theta_eq", "step", "volume", "area", "zmin", "zmax", "theta_R0", "theta_RV", "rc_cut", "rc_flat",
+            "mass"]
+    return {c: rows[:, i] for i, c in enumerate(cols)}
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_statics64_against_oracle(storage):
+    g = load_golden()
+    angles = sorted(set(g["theta_eq"]))
+    specs = [I.workload_statics_64(th, storage) for th in angles]
+    lats = [iblb.lattice_desc(w.nx, w.ny, w.nz, tau_out=w.tau, lam=w.lam, storage=storage) for w in specs]
+    phys = [iblb.physics_desc(sigma=w.sigma, theta_eq_deg=w.theta_deg, xi=w.xi, volume_correction=0)
+            for w in specs]
+    ctx = iblb.iblb_batch_create(lats, phys, stream())
+    dth, dv = BAR[storage]
+    worst = [0.0, 0.0]
+    try:
+        for k, w in enumerate(specs):
+            xyz, tri = w.mesh()
+            iblb.iblb_set_membrane(ctx, k, xyz, tri)
+        steps = sorted(set(g["step"]))
+        done = 0
+        for st in steps:
+            iblb.iblb_step(ctx, int(st) - done)
+            done = int(st)
+            for k, th in enumerate(angles):
+                o = iblb.iblb_observe(ctx, k, 0.05, 0.1)
+                assert o["status"] == 0, (storage, th, st, o["status"])
+                sel = (g["theta_eq"] == th) & (g["step"] == st)
+                ref = {c: float(g[c][sel][0]) for c in g}
+                # eq. angleh has an infinite slope at 180 deg (l -> R): angles are
+                # compared where the oracle's is below 175 deg; the half-height
+                # l = (zmax - zmin) / 2 is compared everywhere instead
+                e_th = max(abs(o["theta_R0_deg"] - ref["theta_R0"]) if ref["theta_R0"] < 175.0 else 0.0,
+                           abs(o["theta_RV_deg"] - ref["theta_RV"]) if ref["theta_RV"] < 175.0 else 0.0)
+                e_l = abs((o["zmax"] - o["zmin"]) / (ref["zmax"] - ref["zmin"]) - 1.0)
+                assert e_l <= dv, (storage, th, st, o["zmax"] - o["zmin"], ref["zmax"] - ref["zmin"])
+                e_v = abs(o["volume"] / ref["volume"] - 1.0)
+                worst = [max(worst[0], e_th), max(worst[1], e_v)]
+                assert e_th <= dth, (storage, th, st, o["theta_R0_deg"], ref["theta_R0"], o["theta_RV_deg"],
+                                     ref["theta_RV"])
+                assert e_v <= dv, (storage, th, st, o["volume"], ref["volume"])
+    finally:
+        iblb.iblb_destroy(ctx)
+    print(f"{storage}: worst angle error {worst[0]:.4f} deg, worst volume error {worst[1]:.2e}")
