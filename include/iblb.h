@@ -280,6 +280,82 @@ int iblb_mesh_observe_dev_noalloc(const double *d_xyz, int n_nodes, const int32_
                                   double R0, double zcut_frac, double eps_flat, void *stream,
                                   double *out);
 
+/* ---- learned warm start ---------------------------------------------------
+ * Not in the paper: a network that predicts the equilibrium shape so that a
+ * run can start from it instead of from a sphere.  The shape is the App. B
+ * parametrisation: the radial distance r = G(phi) of the surface from the
+ * droplet's centre (node centroid), phi the polar angle from +z, made
+ * dimensionless as g = G / R0 and averaged over the azimuth (as in eq.
+ * L2-error_equilibrium), sampled at nphi polar angles phi_k = (k + 1/2) pi /
+ * nphi (nphi = 64 for the network).  These four calls need no GPU.          */
+
+/* Profile of a mesh: nodes xyz[3 * n_nodes] (host); node j falls in bin
+ * floor(phi_j nphi / pi); g[k] = mean radial distance of the bin's nodes / R0;
+ * empty bins interpolate linearly between the nearest filled bins (constant
+ * beyond the first / last).  Writes g[nphi].  IBLB_E_ARG on bad arguments,
+ * IBLB_E_MESH if every node sits at the centroid. */
+int iblb_mesh_profile(const double *xyz, int n_nodes, double R0, int nphi, double *g);
+
+/* Deform a sphere-like closed mesh (xyz[3 * n_nodes], faces tri[3 * n_tri],
+ * host) to the profile g[nphi]: each node moves along its direction from the
+ * centroid to distance R0 g(phi) (g linear between samples, constant beyond
+ * the end samples); the result is scaled about the centroid to the input
+ * mesh's enclosed volume, centred at (cx, cy) and shifted so that its lowest
+ * node is at z = z_bottom.  Writes xyz_out[3 * n_nodes].  IBLB_E_ARG /
+ * IBLB_E_MESH on bad input (non-positive g, bad indices, non-positive
+ * volume). */
+int iblb_deform_mesh(const double *g, int nphi, double R0, const double *xyz, int n_nodes,
+                     const int32_t *tri, int n_tri, double cx, double cy, double z_bottom,
+                     double *xyz_out);
+
+/* Message of the last failed iblb_mesh_profile / iblb_deform_mesh call of
+ * this thread. */
+const char *iblb_warmstart_last_error(void);
+
+/* The network: multilayer perceptron 3 -> 256 -> 256 -> 256 -> 64, tanh
+ * hidden units, linear output g at the 64 polar samples.  Inputs per sample:
+ * (theta_eq in degrees, R0, lambda), mapped to the features
+ * ((theta_eq - 90) / 70, (R0 - 16) / 8, log10 lambda).  Parameters: one
+ * float vector, layer by layer W_l (out x in, row major) then b_l
+ * (iblb_mlp_param_count() = 149056 values).  The three 256-input layers run
+ * on the tensor cores (tcgen05, BF16 operands, FP32 accumulation); the
+ * input layer, the reductions and Adam in FP32.  An iblb_mlp owns its device
+ * memory and works on the stream given at creation; it must not be used from
+ * two host threads at once. */
+typedef struct iblb_mlp iblb_mlp;
+
+int64_t iblb_mlp_param_count(void);
+
+/* Create from initial parameters (host, n_params = iblb_mlp_param_count());
+ * max_batch (1 .. 2^20) bounds the batch of iblb_mlp_grad / iblb_mlp_train
+ * and the chunk of iblb_mlp_predict.  Adam's moments start at zero. */
+int iblb_mlp_create(const float *params, int64_t n_params, int max_batch, void *stream,
+                    iblb_mlp **out);
+void iblb_mlp_destroy(iblb_mlp *m);
+const char *iblb_mlp_last_error(const iblb_mlp *m);
+
+/* Copy the current FP32 parameters to out[n] (n = iblb_mlp_param_count()). */
+int iblb_mlp_get_params(iblb_mlp *m, float *out, int64_t n);
+
+/* Inference: x[3 * S] raw inputs (host) -> y[64 * S] (host).  Any S >= 1
+ * (processed in chunks of max_batch).  lambda must be > 0. */
+int iblb_mlp_predict(iblb_mlp *m, const double *x, int S, double *y);
+
+/* Loss L = mean over the S x 64 outputs of (yhat - y)^2 and its gradient
+ * with respect to the parameters, for one batch (1 <= S <= max_batch):
+ * grad[iblb_mlp_param_count()] and *loss (host).  Parameters unchanged. */
+int iblb_mlp_grad(iblb_mlp *m, const double *x, const double *y, int S, double *grad, double *loss);
+
+/* Training: `epochs` passes over the S samples (x[3 * S], y[64 * S], host),
+ * each in a fresh order (Fisher-Yates with a splitmix64 stream from `seed`)
+ * cut into floor(S / batch) batches; one Adam step per batch (beta1 0.9,
+ * beta2 0.999, eps 1e-8, learning rate lr, bias-corrected; the step counter
+ * continues across calls).  loss_per_epoch[epochs] (may be NULL) receives
+ * the mean batch loss of each epoch.  IBLB_E_TIMEOUT if a bounded wait in
+ * the tensor-core kernel gave up. */
+int iblb_mlp_train(iblb_mlp *m, const double *x, const double *y, int S, int epochs, int batch,
+                   double lr, uint64_t seed, double *loss_per_epoch);
+
 #ifdef __cplusplus
 }
 #endif

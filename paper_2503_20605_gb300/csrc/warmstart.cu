@@ -1,0 +1,160 @@
+// warmstart.cu -- host-side geometry of the learned warm start: the radial
+// profile of a droplet mesh about its centre (the App. B parametrisation
+// r = G(phi), g = G / R0, phi the polar angle from the z axis, averaged over
+// the azimuth as in eq. L2-error_equilibrium), and the inverse map that
+// deforms a sphere-like mesh to a given profile before a run starts.
+// Neither is part of the time step; both run once per droplet.
+#include <math.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/iblb.h"
+
+namespace {
+
+thread_local std::string g_ws_error;
+
+int wfail(int code, const char *msg)
+{
+    g_ws_error = msg;
+    return code;
+}
+
+double mesh_volume(const std::vector<double> &q, const int32_t *tri, int n_tri)
+{
+    double V = 0.0;
+    for (int t = 0; t < n_tri; ++t) {
+        const double *a = &q[3 * (size_t)tri[3 * t]], *b = &q[3 * (size_t)tri[3 * t + 1]],
+                     *c = &q[3 * (size_t)tri[3 * t + 2]];
+        V += a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+             a[2] * (b[0] * c[1] - b[1] * c[0]);
+    }
+    return V / 6.0;
+}
+
+// linear interpolation of the samples g[k] at phi_k = (k + 1/2) pi / n,
+// constant beyond the first and last sample
+double profile_at(const double *g, int n, double phi)
+{
+    const double s = phi / M_PI * n - 0.5;
+    if (s <= 0.0)
+        return g[0];
+    if (s >= n - 1)
+        return g[n - 1];
+    const int k = (int)s;
+    const double f = s - k;
+    return (1.0 - f) * g[k] + f * g[k + 1];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *iblb_warmstart_last_error(void) { return g_ws_error.c_str(); }
+
+int iblb_mesh_profile(const double *xyz, int n_nodes, double R0, int nphi, double *g)
+{
+    if (!xyz || !g || n_nodes < 1 || !(R0 > 0.0) || nphi < 2)
+        return wfail(IBLB_E_ARG, "iblb_mesh_profile: bad arguments");
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < n_nodes; ++j)
+        for (int a = 0; a < 3; ++a)
+            c[a] += xyz[3 * (size_t)j + a];
+    for (int a = 0; a < 3; ++a)
+        c[a] /= n_nodes;
+    std::vector<double> sum(nphi, 0.0);
+    std::vector<int> cnt(nphi, 0);
+    for (int j = 0; j < n_nodes; ++j) {
+        const double dx = xyz[3 * (size_t)j] - c[0], dy = xyz[3 * (size_t)j + 1] - c[1],
+                     dz = xyz[3 * (size_t)j + 2] - c[2];
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (!(r > 0.0) || !std::isfinite(r))
+            continue;
+        const double phi = acos(fmax(-1.0, fmin(1.0, dz / r)));
+        int k = (int)(phi / M_PI * nphi);
+        k = k < 0 ? 0 : (k >= nphi ? nphi - 1 : k);
+        sum[k] += r;
+        cnt[k] += 1;
+    }
+    int first = -1;
+    for (int k = 0; k < nphi; ++k)
+        if (cnt[k]) {
+            g[k] = sum[k] / cnt[k] / R0;
+            if (first < 0)
+                first = k;
+        }
+    if (first < 0)
+        return wfail(IBLB_E_MESH, "iblb_mesh_profile: every node sits at the centroid");
+    // empty bins: linear interpolation between the nearest filled bins
+    // (constant beyond the first and the last filled bin)
+    int prev = -1;
+    for (int k = 0; k < nphi; ++k) {
+        if (cnt[k]) {
+            prev = k;
+            continue;
+        }
+        int next = k + 1;
+        while (next < nphi && !cnt[next])
+            ++next;
+        if (prev < 0)
+            g[k] = g[next];
+        else if (next >= nphi)
+            g[k] = g[prev];
+        else
+            g[k] = g[prev] + (g[next] - g[prev]) * (double)(k - prev) / (double)(next - prev);
+    }
+    return IBLB_OK;
+}
+
+int iblb_deform_mesh(const double *g, int nphi, double R0, const double *xyz, int n_nodes, const int32_t *tri,
+                     int n_tri, double cx, double cy, double z_bottom, double *xyz_out)
+{
+    if (!g || !xyz || !tri || !xyz_out || nphi < 2 || n_nodes < 4 || n_tri < 4 || !(R0 > 0.0))
+        return wfail(IBLB_E_ARG, "iblb_deform_mesh: bad arguments");
+    for (int k = 0; k < nphi; ++k)
+        if (!(g[k] > 0.0) || !std::isfinite(g[k]))
+            return wfail(IBLB_E_ARG, "iblb_deform_mesh: the profile must be positive and finite");
+    for (int t = 0; t < 3 * n_tri; ++t)
+        if (tri[t] < 0 || tri[t] >= n_nodes)
+            return wfail(IBLB_E_MESH, "iblb_deform_mesh: face index out of range");
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < n_nodes; ++j)
+        for (int a = 0; a < 3; ++a)
+            c[a] += xyz[3 * (size_t)j + a];
+    for (int a = 0; a < 3; ++a)
+        c[a] /= n_nodes;
+    std::vector<double> q0(3 * (size_t)n_nodes), q(3 * (size_t)n_nodes);
+    for (int j = 0; j < n_nodes; ++j) {
+        double d[3], r = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            d[a] = xyz[3 * (size_t)j + a] - c[a];
+            r += d[a] * d[a];
+        }
+        r = sqrt(r);
+        if (!(r > 0.0))
+            return wfail(IBLB_E_MESH, "iblb_deform_mesh: a node sits at the centroid");
+        const double phi = acos(fmax(-1.0, fmin(1.0, d[2] / r)));
+        const double G = R0 * profile_at(g, nphi, phi);
+        for (int a = 0; a < 3; ++a) {
+            q0[3 * (size_t)j + a] = d[a];
+            q[3 * (size_t)j + a] = G * d[a] / r;
+        }
+    }
+    const double V0 = mesh_volume(q0, tri, n_tri), V = mesh_volume(q, tri, n_tri);
+    if (!(V0 > 0.0) || !(V > 0.0))
+        return wfail(IBLB_E_MESH, "iblb_deform_mesh: the mesh must enclose a positive volume before and after");
+    const double s = cbrt(V0 / V);
+    double zmin = INFINITY;
+    for (int j = 0; j < n_nodes; ++j)
+        zmin = fmin(zmin, s * q[3 * (size_t)j + 2]);
+    for (int j = 0; j < n_nodes; ++j) {
+        xyz_out[3 * (size_t)j] = cx + s * q[3 * (size_t)j];
+        xyz_out[3 * (size_t)j + 1] = cy + s * q[3 * (size_t)j + 1];
+        xyz_out[3 * (size_t)j + 2] = z_bottom + (s * q[3 * (size_t)j + 2] - zmin);
+    }
+    return IBLB_OK;
+}
+
+}  // extern "C"

@@ -98,6 +98,18 @@ _SIGS = {
     "iblb_mesh_observe_dev": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, C.c_double, C.c_double, _P, _D]),
     "iblb_mesh_observe_dev_noalloc": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, C.c_double, C.c_double, _P,
                                                 _D]),
+    "iblb_mesh_profile": (C.c_int, [_D, C.c_int, C.c_double, C.c_int, _D]),
+    "iblb_deform_mesh": (C.c_int, [_D, C.c_int, C.c_double, _D, C.c_int, _I32, C.c_int, C.c_double, C.c_double,
+                                   C.c_double, _D]),
+    "iblb_warmstart_last_error": (C.c_char_p, []),
+    "iblb_mlp_param_count": (C.c_int64, []),
+    "iblb_mlp_create": (C.c_int, [C.POINTER(C.c_float), C.c_int64, C.c_int, _P, C.POINTER(_P)]),
+    "iblb_mlp_destroy": (None, [_P]),
+    "iblb_mlp_last_error": (C.c_char_p, [_P]),
+    "iblb_mlp_get_params": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int64]),
+    "iblb_mlp_predict": (C.c_int, [_P, _D, C.c_int, _D]),
+    "iblb_mlp_grad": (C.c_int, [_P, _D, _D, C.c_int, _D, _D]),
+    "iblb_mlp_train": (C.c_int, [_P, _D, _D, C.c_int, C.c_int, C.c_int, C.c_double, C.c_uint64, _D]),
 }
 
 _lib = None
@@ -315,3 +327,83 @@ def iblb_mesh_observe_dev_noalloc(d_xyz, n_nodes, d_tri, n_tri, R0, zcut_frac=0.
     _check(None, lib().iblb_mesh_observe_dev_noalloc(_P(d_xyz), n_nodes, _P(d_tri), n_tri, R0, zcut_frac,
                                                      eps_flat, _P(stream), _d(out)))
     return out
+
+
+# ------------------------------------------------------------ learned warm start
+NPHI = 64
+
+
+def _wcheck(rc):
+    if rc != IBLB_OK:
+        msg = lib().iblb_warmstart_last_error()
+        raise IblbError(rc, msg.decode() if msg else "")
+
+
+def _mcheck(m, rc):
+    if rc != IBLB_OK:
+        msg = lib().iblb_mlp_last_error(m)
+        raise IblbError(rc, msg.decode() if msg else "")
+
+
+def iblb_mesh_profile(xyz, R0, nphi=NPHI):
+    xyz = _f64(xyz)
+    g = np.empty(nphi)
+    _wcheck(lib().iblb_mesh_profile(_d(xyz), xyz.size // 3, R0, nphi, _d(g)))
+    return g
+
+
+def iblb_deform_mesh(g, R0, xyz, tri, cx, cy, z_bottom):
+    g = _f64(g)
+    xyz = _f64(xyz)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    out = np.empty_like(xyz)
+    _wcheck(lib().iblb_deform_mesh(_d(g), g.size, R0, _d(xyz), xyz.size // 3, tri.ctypes.data_as(_I32),
+                                   tri.size // 3, cx, cy, z_bottom, _d(out)))
+    return out
+
+
+def iblb_mlp_param_count():
+    return int(lib().iblb_mlp_param_count())
+
+
+def iblb_mlp_create(params, max_batch=256, stream=0):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    h = _P()
+    _mcheck(None, lib().iblb_mlp_create(p.ctypes.data_as(C.POINTER(C.c_float)), p.size, max_batch, _P(stream),
+                                        C.byref(h)))
+    return h
+
+
+def iblb_mlp_destroy(m):
+    lib().iblb_mlp_destroy(m)
+
+
+def iblb_mlp_get_params(m):
+    out = np.empty(iblb_mlp_param_count(), dtype=np.float32)
+    _mcheck(m, lib().iblb_mlp_get_params(m, out.ctypes.data_as(C.POINTER(C.c_float)), out.size))
+    return out
+
+
+def iblb_mlp_predict(m, x):
+    x = _f64(x)
+    S = x.size // 3
+    y = np.empty((S, NPHI))
+    _mcheck(m, lib().iblb_mlp_predict(m, _d(x), S, _d(y)))
+    return y
+
+
+def iblb_mlp_grad(m, x, y):
+    x, y = _f64(x), _f64(y)
+    S = x.size // 3
+    g = np.empty(iblb_mlp_param_count())
+    loss = C.c_double()
+    _mcheck(m, lib().iblb_mlp_grad(m, _d(x), _d(y), S, _d(g), C.byref(loss)))
+    return g, loss.value
+
+
+def iblb_mlp_train(m, x, y, epochs, batch=256, lr=1e-3, seed=0):
+    x, y = _f64(x), _f64(y)
+    S = x.size // 3
+    losses = np.zeros(max(epochs, 1))
+    _mcheck(m, lib().iblb_mlp_train(m, _d(x), _d(y), S, epochs, batch, lr, seed, _d(losses)))
+    return losses[:epochs]

@@ -174,3 +174,31 @@ def workload_batch(n=64, seed=2025, storage="f16"):
         xi = max(2.0, 0.1 * R)
         out.append(DropletSpec(s, s, s, R, level_for_radius(R), 0.01, th, xi, tau=tau, storage=storage))
     return out
+
+
+# ----------------------------------------------------------- learned warm start
+MLP_SIZES = (3, 256, 256, 256, 64)
+
+
+def mlp_init(seed=0, sizes=MLP_SIZES):
+    """Seeded initial parameters of the warm-start network as one float32
+    vector, layer by layer W_l (out x in, row major) then b_l: weights
+    uniform in +-1/sqrt(in), hidden biases 0, output biases 1 (the sphere,
+    g = 1)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l, (i, o) in enumerate(zip(sizes[:-1], sizes[1:])):
+        lim = 1.0 / np.sqrt(i)
+        parts.append(rng.uniform(-lim, lim, o * i))
+        parts.append(np.ones(o) if l == len(sizes) - 2 else np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def warmstart_cases(n, seed):
+    """n cases (theta_eq deg, R0, lambda): theta_eq ~ U[20, 160], R0 ~ U[8, 24],
+    lambda log-uniform in [0.1, 10]; numpy PCG64 with `seed`."""
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(20.0, 160.0, n)
+    R = rng.uniform(8.0, 24.0, n)
+    lam = 10.0 ** rng.uniform(-1.0, 1.0, n)
+    return np.stack([th, R, lam], axis=1)
