@@ -42,6 +42,24 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks of the process group (x itself
+    for one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells_per_rank, steps, max_step_ms, world):
+    """Cells updated by all ranks (one replica each) over the slowest
+    rank's time."""
+    return world * cells_per_rank * steps / (max_step_ms * 1e-3) / 1e6
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -114,20 +132,28 @@ class Clocks:
 
 
 def make_ctx(iblb, spec, storage, stream):
-    lat = iblb.lattice_desc(spec.nx, spec.ny, spec.nz, tau_out=spec.tau, lam=spec.lam, storage=storage)
-    phys = iblb.physics_desc(sigma=spec.sigma, theta_eq_deg=spec.theta_deg, xi=spec.xi,
-                             volume_correction=int(spec.volume_correction))
-    ctx = iblb.iblb_create(lat, phys, stream)
-    xyz, tri = spec.mesh()
-    iblb.iblb_set_membrane(ctx, 0, xyz, tri)
+    """One context for a droplet spec, or a batched context for a list."""
+    specs = spec if isinstance(spec, list) else [spec]
+    lats = [iblb.lattice_desc(w.nx, w.ny, w.nz, tau_out=w.tau, lam=w.lam, storage=storage) for w in specs]
+    phys = [iblb.physics_desc(sigma=w.sigma, theta_eq_deg=w.theta_deg, xi=w.xi,
+                              volume_correction=int(w.volume_correction)) for w in specs]
+    if len(specs) == 1:
+        ctx = iblb.iblb_create(lats[0], phys[0], stream)
+    else:
+        ctx = iblb.iblb_batch_create(lats, phys, stream)
+    for k, w in enumerate(specs):
+        xyz, tri = w.mesh()
+        iblb.iblb_set_membrane(ctx, k, xyz, tri)
+    xyz, tri = specs[0].mesh()
     return ctx, xyz, tri
 
 
 def launches_per_step(spec):
+    specs = spec if isinstance(spec, list) else [spec]
     n = 2 + 4 + 1 + 1                # step opening + forces; scan x2, fill, spread; stream-collide; advect
-    if spec.lam != 1.0:
+    if any(w.lam != 1.0 for w in specs):
         n += 3                       # column reset, face crossings, column sort
-    if spec.volume_correction:
+    if any(w.volume_correction for w in specs):
         n += 2                       # FP64 volume/centroid reduction, rescale
     return n
 
@@ -191,11 +217,27 @@ def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
         _, step_ms, n = timed(2, steps)
         phases, phase_step_ms, n_ph = timed(1, steps)
         obs = iblb.iblb_observe(ctx, 0)
-        info = iblb.iblb_info(ctx, 0)
+        nd = iblb.iblb_info(ctx, 0)["n_drops"]
+        infos = [iblb.iblb_info(ctx, k) for k in range(nd)]
     finally:
         iblb.iblb_destroy(ctx)
-    return dict(phases=phases, step_ms=step_ms, n=n, n_ph=n_ph, obs=obs, cells=info["cells"],
-                nodes=info["n_nodes"])
+    return dict(phases=phases, step_ms=step_ms, n=n, n_ph=n_ph, obs=obs, cells=sum(i["cells"] for i in infos),
+                nodes=sum(i["n_nodes"] for i in infos), drops=nd)
+
+
+def extra_workload(name, specs, storage, steps, warmup, torch, iblb, flush, autotune):
+    """Throughput line of a further workload (same timing as the headline)."""
+    r = run_gpu(specs, storage, steps, warmup, torch, iblb, flush, autotune=autotune)
+    KP = r["n_ph"]
+    ph = {k: v / KP for k, v in r["phases"].items()}
+    ib = ph["forces"] + ph["spread"] + ph["inout"] + ph["advect"] + ph["reduce"]
+    bpc = BYTES_PER_CELL[storage]
+    return {"workload": name, "storage": storage, "droplets": r["drops"], "cells": r["cells"], "nodes": r["nodes"],
+            "value": r["cells"] * r["n"] / (r["step_ms"] * 1e-3) / 1e6, "unit": "MLUPS",
+            "ms_per_step": r["step_ms"] / r["n"], "phase_ms_per_step": ph,
+            "ib_nodes_per_s": r["nodes"] / (ib * 1e-3),
+            "lb_kernel_gbs": r["cells"] * bpc / (ph["lb"] * 1e-3) / 1e9,
+            "gpu_launches_per_step": launches_per_step(specs)}
 
 
 def run_e2e(spec, storage, steps, warmup, torch, iblb):
@@ -261,6 +303,8 @@ def main():
     ap.add_argument("--only-main", action="store_true",
                     help="time only the headline storage (no FP32 line, no e2e loop); for profiler runs")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the spreading (256x256x128, lambda=10, BF16) and 64-droplet batch lines")
     ap.add_argument("--accuracy-steps", type=int, default=20000,
                     help="steps of the FP16/BF16-vs-FP32 contact-angle comparison at 128^3 (0: skip)")
     args = ap.parse_args()
@@ -313,14 +357,10 @@ def main():
         run32 = run_gpu(spec32, "f32", args.steps, args.warmup, torch, iblb, flush, autotune=not args.no_autotune)
         e2e = run_e2e(spec, args.storage, max(20, args.steps // 4), 3, torch, iblb)
 
-    step_ms = main_run["step_ms"]
-    if world > 1:
-        t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(main_run["step_ms"], world, "cuda")
     K = main_run["n"]
     cells, nodes = main_run["cells"], main_run["nodes"]
-    value = world * cells * K / (step_ms * 1e-3) / 1e6
+    value = whole_job_mlups(cells, K, step_ms, world)
     ph = main_run["phases"]
     KP = main_run["n_ph"]
     ib_ms = (ph["forces"] + ph["spread"] + ph["inout"] + ph["advect"] + ph["reduce"]) / KP   # per step
@@ -341,6 +381,16 @@ def main():
                 "ib_nodes_per_s": nodes / (ib32 * 1e-3),
                 "lb_kernel_gbs": cells * BYTES_PER_CELL["f32"] / (lb32 * 1e-3) / 1e9,
                 "theta_RV_deg_after": run32["obs"]["theta_RV_deg"]}
+
+    extra = None
+    if not args.only_main and not args.no_extra:
+        extra = [
+            extra_workload("spreading droplet 256x256x128 (tau_out=0.8, lambda=10, L6 icosphere 40962 nodes, R=40, "
+                           "theta_eq=20, sigma=0.005, xi=2)", I.workload_spreading_256("bf16"), "bf16",
+                           max(20, args.steps // 2), args.warmup, torch, iblb, flush, not args.no_autotune),
+            extra_workload("batch of 64 droplets (sides U{48..96}, R U[6,20], theta_eq U[20,160], tau U[0.6,1.2], "
+                           "sigma=0.01, seed 2025)", I.workload_batch(64, 2025, "f16"), "f16",
+                           max(20, args.steps // 2), args.warmup, torch, iblb, flush, not args.no_autotune)]
 
     accuracy = None
     if rank == 0 and not args.only_main and args.accuracy_steps > 0:
@@ -372,6 +422,7 @@ def main():
             "clocks": clk.summary(),
             "theta_RV_deg_after": main_run["obs"]["theta_RV_deg"],
             "accuracy": accuracy,
+            "other_workloads": extra,
         }
         print(json.dumps(line))
     if world > 1:

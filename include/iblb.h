@@ -120,7 +120,7 @@ typedef struct {
     double rc_flat;        /* contact radius, protocol (ii): sqrt(chi_eps / pi)         */
     double n_cut;          /* number of edges crossing the protocol (i) plane           */
     double chi_flat;       /* area of the flat lower-half faces, protocol (ii)          */
-    int status;            /* IBLB_OK or the pending device status                      */
+    int status;            /* IBLB_OK or the pending device status of this droplet      */
     int clamped;           /* nodes clamped by the near-wall guard in the last step     */
 } iblb_obs;
 
@@ -225,6 +225,10 @@ int iblb_sync(iblb_ctx *ctx);
  * height over R0 (the paper's optimum 0.05); eps_flat: protocol (ii)
  * flatness parameter (the paper's optimum 0.1). */
 int iblb_observe(iblb_ctx *ctx, int k, double zcut_frac, double eps_flat, iblb_obs *out);
+
+/* Observables of every droplet of the context, out[ndrops] (synchronises);
+ * one pass over the lattice for all the masses. */
+int iblb_observe_all(iblb_ctx *ctx, double zcut_frac, double eps_flat, iblb_obs *out);
 
 /* IBLB_OPT_* switches; IBLB_E_ARG for unknown options or values. */
 int iblb_set_option(iblb_ctx *ctx, int option, int value);

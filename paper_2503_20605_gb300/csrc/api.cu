@@ -74,6 +74,8 @@ struct iblb_ctx {
     int64_t step_count = 0;
     LaunchCfg cfg{0, 2, 148};
     int *h_status = nullptr;     // pinned, 4 per droplet
+    double *obs_scr = nullptr;   // scratch of the mesh observation kernels
+    int64_t obs_scr_n = 0;
     std::string err;
 };
 
@@ -750,6 +752,7 @@ void iblb_destroy(iblb_ctx *c)
     dfree(A.clamped);
     dfree(c->d_mass);
     dfree(c->d_drops);
+    dfree(c->obs_scr);
     if (c->h_status)
         cudaFreeHost(c->h_status);
     for (int k = 0; k <= IBLB_NPHASE; ++k)
@@ -1021,25 +1024,23 @@ int iblb_sync(iblb_ctx *c)
     return IBLB_OK;
 }
 
-int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs *out)
+// mesh observables and status of droplet k into out (the mass is filled by
+// the caller); the observation scratch is kept in the context
+int observe_mesh(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs *out)
 {
-    int r = check_k(c, k);
-    if (r || (r = ensure_ready(c)))
-        return r;
-    if (!out)
-        return fail(c, IBLB_E_ARG, "null output");
-    memset(out, 0, sizeof(*out));
     const Drop &D = c->drops[k];
-    enter(c);
-    CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
-    CK(cudaMemcpyAsync(&out->mass, c->d_mass + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
     if (D.nnodes) {
-        Tmp t;
-        CK(cudaMalloc(&t.p, sizeof(double) * observe_scratch_doubles(D.nnodes, D.ntri)));
+        const int64_t need = observe_scratch_doubles(D.nnodes, D.ntri);
+        if (need > c->obs_scr_n) {
+            dfree(c->obs_scr);
+            c->obs_scr = nullptr;
+            c->obs_scr_n = 0;
+            CK(dalloc(&c->obs_scr, (size_t)need));
+            c->obs_scr_n = need;
+        }
         double h[13];
         CK(launch_observe_view(c->A.qx, c->A.qy, c->A.qz, 1, c->A.tri + 3 * (int64_t)D.tri0, D.ntri, D.node0,
-                               D.nnodes, D.R0, zcut_frac, eps_flat, (double *)t.p, h, c->stream));
+                               D.nnodes, D.R0, zcut_frac, eps_flat, c->obs_scr, h, c->stream));
         out->volume = h[0];
         out->area = h[1];
         out->centroid[0] = h[2];
@@ -1054,11 +1055,58 @@ int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs
         out->n_cut = h[11];
         out->chi_flat = h[12];
     }
+    // this droplet's flags (c->h_status was refreshed by the caller); a
+    // bounded-wait timeout is recorded on droplet 0 and concerns every droplet
+    out->status = status_code(c->h_status[4 * k] | (c->h_status[0] & ST_TIMEOUT));
+    return IBLB_OK;
+}
+
+int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs *out)
+{
+    int r = check_k(c, k);
+    if (r || (r = ensure_ready(c)))
+        return r;
+    if (!out)
+        return fail(c, IBLB_E_ARG, "null output");
+    memset(out, 0, sizeof(*out));
+    enter(c);
+    CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
+    CK(cudaMemcpyAsync(&out->mass, c->d_mass + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&out->clamped, c->A.clamped + k, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    int flags = 0;
+    if ((r = read_status(c, false, &flags)))   // synchronises the stream
+        return r;
+    if ((r = observe_mesh(c, k, zcut_frac, eps_flat, out)))
+        return r;
+    leave(c);
+    return IBLB_OK;
+}
+
+int iblb_observe_all(iblb_ctx *c, double zcut_frac, double eps_flat, iblb_obs *out)
+{
+    if (!c)
+        return fail(nullptr, IBLB_E_ARG, "null context");
+    int r = ensure_ready(c);
+    if (r)
+        return r;
+    if (!out)
+        return fail(c, IBLB_E_ARG, "null output");
+    memset(out, 0, sizeof(*out) * (size_t)c->ndrops);
+    std::vector<double> mass(c->ndrops);
+    std::vector<int> clamped(c->ndrops);
+    enter(c);
+    CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
+    CK(cudaMemcpyAsync(mass.data(), c->d_mass, sizeof(double) * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(clamped.data(), c->A.clamped, sizeof(int) * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
     int flags = 0;
     if ((r = read_status(c, false, &flags)))
         return r;
-    out->status = status_code(flags);
-    CK(cudaMemcpy(&out->clamped, c->A.clamped + k, sizeof(int), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < c->ndrops; ++k) {
+        out[k].mass = mass[k];
+        out[k].clamped = clamped[k];
+        if ((r = observe_mesh(c, k, zcut_frac, eps_flat, &out[k])))
+            return r;
+    }
     leave(c);
     return IBLB_OK;
 }

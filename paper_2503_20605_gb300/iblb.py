@@ -89,6 +89,7 @@ _SIGS = {
     "iblb_step": (C.c_int, [_P, C.c_int]),
     "iblb_sync": (C.c_int, [_P]),
     "iblb_observe": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.POINTER(Obs)]),
+    "iblb_observe_all": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(Obs)]),
     "iblb_set_option": (C.c_int, [_P, C.c_int, C.c_int]),
     "iblb_get_profile": (C.c_int, [_P, _D, _D, C.POINTER(C.c_int64)]),
     "iblb_reset_profile": (C.c_int, [_P]),
@@ -284,6 +285,13 @@ def iblb_observe(ctx, k=0, zcut_frac=0.05, eps_flat=0.1):
     o = Obs()
     _check(ctx, lib().iblb_observe(ctx, k, zcut_frac, eps_flat, C.byref(o)))
     return o.as_dict()
+
+
+def iblb_observe_all(ctx, zcut_frac=0.05, eps_flat=0.1):
+    n = iblb_info(ctx, 0)["n_drops"]
+    arr = (Obs * n)()
+    _check(ctx, lib().iblb_observe_all(ctx, zcut_frac, eps_flat, arr))
+    return [o.as_dict() for o in arr]
 
 
 def iblb_set_option(ctx, option, value):

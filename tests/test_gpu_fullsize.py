@@ -1,0 +1,159 @@
+"""Parity at the benchmarked sizes, in the launch configurations the bench
+times, through the C ABI:
+
+* the 128^3 statics droplet (L5 mesh, volume correction on) and the
+  256 x 256 x 128 spreading droplet (lambda = 10, in/out classification every
+  step) against the FP64 oracle over a few full steps from seeded perturbed
+  populations (FP32 storage: rel-L2 <= 1e-5 on u and rho, nodes to 1e-6;
+  FP16 / BF16 storage within their rounding: 5e-3 on u);
+* the in/out flags of the spreading case bit-exact at full size;
+* three sampled members of the 64-droplet batch against the oracle run on
+  each alone;
+* every launch shape the autotuner may choose gives bit-identical results;
+* a checkpoint written mid-run and loaded into a fresh context resumes bit
+  for bit."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+from paper_2503_20605_gb300 import iblb
+from paper_2503_20605_gb300 import inputs as I
+from gpu_util import gpu_ctx, oracle_sim, rel_l2, stream
+
+pytestmark = pytest.mark.gpu
+
+W = O.d3q19()[1]
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    iblb.lib()
+
+
+def _pair(spec, storage):
+    xyz, tri = spec.mesh()
+    kw = dict(nx=spec.nx, ny=spec.ny, nz=spec.nz, tau=spec.tau, lam=spec.lam, sigma=spec.sigma,
+              theta=spec.theta_deg, xi=spec.xi, volume_correction=int(spec.volume_correction), mesh=(xyz, tri))
+    g = gpu_ctx(storage=storage, **kw)
+    s = oracle_sim(**kw)
+    cells = iblb.iblb_info(g, 0)["cells"]
+    f0 = I.perturbed_populations(cells, W, seed=17, amp=1e-3)
+    iblb.iblb_set_populations(g, 0, f0)
+    f0 = iblb.iblb_get_populations(g, 0)       # the stored (rounded) state is the common start
+    s.set_populations(f0)
+    return g, s, xyz
+
+
+def _compare(g, s, steps, tol_u, tol_q):
+    iblb.iblb_step(g, steps)
+    iblb.iblb_sync(g)
+    rho_g, u_g = iblb.iblb_get_macros(g, 0)
+    q_g = iblb.iblb_get_nodes(g, 0)
+    s.step(steps)
+    rho_o, u_o = s.macros()
+    q_o = s.nodes()
+    e_u, e_r = rel_l2(u_g, u_o), rel_l2(rho_g, rho_o)
+    dq = np.abs(q_g - q_o).max()
+    print(f"rel-L2 u {e_u:.2e} rho {e_r:.2e} max|dq| {dq:.2e}")
+    assert e_u <= tol_u and e_r <= 1e-5 and dq <= tol_q, (e_u, e_r, dq)
+
+
+@pytest.mark.parametrize("storage,tol_u,tol_q", [("f32", 1e-5, 1e-6), ("f16", 5e-3, 1e-5)])
+def test_statics128_parity(storage, tol_u, tol_q):
+    g, s, _ = _pair(I.workload_statics_128(90.0, storage), storage)
+    try:
+        _compare(g, s, 2, tol_u, tol_q)
+    finally:
+        iblb.iblb_destroy(g)
+
+
+@pytest.mark.parametrize("storage,tol_u,tol_q", [("f32", 1e-5, 1e-6), ("bf16", 5e-3, 1e-5)])
+def test_spreading256_parity_and_inside(storage, tol_u, tol_q):
+    spec = I.workload_spreading_256(storage)
+    g, s, _ = _pair(spec, storage)
+    try:
+        _compare(g, s, 2, tol_u, tol_q)
+        # the step's in/out flags: tau_in exactly where the oracle's parity says inside
+        inside_g = iblb.iblb_get_inside(g, 0)
+        inside_o = (s.tau() == spec.tau_in).astype(np.uint8)
+        assert inside_o.sum() > 100000
+        np.testing.assert_array_equal(inside_g, inside_o)
+    finally:
+        iblb.iblb_destroy(g)
+
+
+def test_batch64_sampled_members():
+    specs = I.workload_batch(64, 2025, "f32")
+    lats = [iblb.lattice_desc(w.nx, w.ny, w.nz, tau_out=w.tau, lam=w.lam) for w in specs]
+    phys = [iblb.physics_desc(sigma=w.sigma, theta_eq_deg=w.theta_deg, xi=w.xi,
+                              volume_correction=int(w.volume_correction)) for w in specs]
+    b = iblb.iblb_batch_create(lats, phys, stream())
+    sizes = np.array([w.nx * w.ny * w.nz for w in specs])
+    picks = [int(np.argmin(sizes)), int(np.argsort(sizes)[len(sizes) // 2]), int(np.argmax(sizes))]
+    try:
+        for k, w in enumerate(specs):
+            iblb.iblb_set_membrane(b, k, *w.mesh())
+        iblb.iblb_step(b, 3)
+        iblb.iblb_sync(b)
+        for k in picks:
+            w = specs[k]
+            s = oracle_sim(nx=w.nx, ny=w.ny, nz=w.nz, tau=w.tau, lam=w.lam, sigma=w.sigma, theta=w.theta_deg,
+                           xi=w.xi, volume_correction=int(w.volume_correction), mesh=w.mesh())
+            s.step(3)
+            rho_g, u_g = iblb.iblb_get_macros(b, k)
+            rho_o, u_o = s.macros()
+            assert rel_l2(u_g, u_o) <= 1e-5 and rel_l2(rho_g, rho_o) <= 1e-5, k
+            assert np.abs(iblb.iblb_get_nodes(b, k) - s.nodes()).max() <= 1e-6, k
+    finally:
+        iblb.iblb_destroy(b)
+
+
+def test_autotune_candidates_bit_identical():
+    spec = I.workload_statics_128(60.0, "f16")
+    outs = []
+    for mult, bps in ((2, 0), (1, 0), (4, 0), (2, 1), (1, 1)):
+        g = gpu_ctx(spec.nx, spec.ny, spec.nz, tau=spec.tau, storage="f16", sigma=spec.sigma, theta=spec.theta_deg,
+                    xi=spec.xi, volume_correction=1, mesh=spec.mesh())
+        try:
+            iblb.iblb_set_option(g, iblb.IBLB_OPT_LB_ROW_MULT, mult)
+            iblb.iblb_set_option(g, iblb.IBLB_OPT_LB_BLOCKS_PER_SM, bps)
+            iblb.iblb_step(g, 25)
+            iblb.iblb_sync(g)
+            outs.append((iblb.iblb_get_populations(g, 0), iblb.iblb_get_nodes(g, 0)))
+        finally:
+            iblb.iblb_destroy(g)
+    for f, q in outs[1:]:
+        assert np.array_equal(f, outs[0][0]) and np.array_equal(q, outs[0][1])
+
+
+def test_checkpoint_resume_bitwise(tmp_path):
+    sp = I.workload_parity_32()
+    xyz, tri = sp.mesh()
+    kw = dict(tau=0.9, lam=4.0, storage="f16", sigma=sp.sigma, theta=sp.theta_deg, xi=sp.xi,
+              volume_correction=1, mesh=(xyz, tri))
+    path = str(tmp_path / "ck.bin")
+    a = gpu_ctx(32, 32, 32, **kw)
+    try:
+        iblb.iblb_step(a, 30)
+        iblb.iblb_save(a, path)
+        iblb.iblb_step(a, 30)
+        iblb.iblb_sync(a)
+        want = (iblb.iblb_get_populations(a, 0), iblb.iblb_get_nodes(a, 0))
+    finally:
+        iblb.iblb_destroy(a)
+    b = gpu_ctx(32, 32, 32, **kw)
+    try:
+        iblb.iblb_load(b, path)
+        iblb.iblb_step(b, 30)
+        iblb.iblb_sync(b)
+        assert np.array_equal(iblb.iblb_get_populations(b, 0), want[0])
+        assert np.array_equal(iblb.iblb_get_nodes(b, 0), want[1])
+    finally:
+        iblb.iblb_destroy(b)
+    assert os.path.getsize(path) > 0
