@@ -150,7 +150,7 @@ def make_ctx(iblb, spec, storage, stream):
 
 def launches_per_step(spec):
     specs = spec if isinstance(spec, list) else [spec]
-    n = 2 + 4 + 1 + 1                # step opening + forces; scan x2, fill, spread; stream-collide; advect
+    n = 1 + 3 + 1 + 1                # forces (opens the step); scan, fill, spread; stream-collide; advect
     if any(w.lam != 1.0 for w in specs):
         n += 3                       # column reset, face crossings, column sort
     if any(w.volume_correction for w in specs):
@@ -190,12 +190,21 @@ def run_accuracy(I, iblb, torch, steps, angles=(30.0, 60.0, 90.0, 120.0, 150.0))
     return out
 
 
+LB_SHAPE = {}
+
+
 def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
     """Device-timed steps with L2 flushed before each; returns per-phase sums."""
     stream = torch.cuda.current_stream().cuda_stream
     ctx, xyz, tri = make_ctx(iblb, spec, storage, stream)
     try:
-        if autotune:
+        if "mult" in LB_SHAPE:
+            iblb.iblb_set_option(ctx, iblb.IBLB_OPT_LB_ROW_MULT, LB_SHAPE["mult"])
+        if "bps" in LB_SHAPE:
+            iblb.iblb_set_option(ctx, iblb.IBLB_OPT_LB_BLOCKS_PER_SM, LB_SHAPE["bps"])
+        if "stages" in LB_SHAPE:
+            iblb.iblb_set_option(ctx, iblb.IBLB_OPT_LB_STAGES, LB_SHAPE["stages"])
+        if autotune and not LB_SHAPE:
             iblb.iblb_autotune(ctx, os.path.join(ROOT, "paper_2503_20605_gb300", "_build", "autotune.txt"))
         def timed(mode, n):
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_PROFILE, mode)
@@ -272,6 +281,45 @@ def run_e2e(spec, storage, steps, warmup, torch, iblb):
                 d2h_bytes_per_step=n * 3 * 8 + 8 + 8 * 15)
 
 
+def run_mlp(I, iblb, torch):
+    """Warm-start network: Adam training steps (batch 256) and inference of
+    200 cases, wall-clock around the library calls after a warm-up call."""
+    stream = torch.cuda.current_stream().cuda_stream
+    rng = np.random.default_rng(0)
+    x = I.warmstart_cases(2048, 3)
+    y = 1.0 + 0.1 * rng.standard_normal((2048, 64))
+    m = iblb.iblb_mlp_create(I.mlp_init(0), 256, stream)
+    try:
+        iblb.iblb_mlp_train(m, x, y, 2, 256, 1e-3, 1)
+        torch.cuda.synchronize()
+        epochs = 50
+        t0 = time.perf_counter()
+        iblb.iblb_mlp_train(m, x, y, epochs, 256, 1e-3, 2)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        steps = epochs * (2048 // 256)
+        xt = I.warmstart_cases(200, 4)
+        iblb.iblb_mlp_predict(m, xt)
+        t1 = time.perf_counter()
+        for _ in range(20):
+            iblb.iblb_mlp_predict(m, xt)
+        dp = (time.perf_counter() - t1) / 20
+    finally:
+        iblb.iblb_mlp_destroy(m)
+    flop_fwd = 2 * (3 * 256 + 2 * 256 * 256 + 256 * 64)      # per sample
+    flop_step = 3 * flop_fwd * 256                            # forward + backward (two GEMMs per layer)
+    return {"train_step_ms": dt / steps * 1e3, "train_tflops": flop_step * steps / dt / 1e12,
+            "predict_200_ms": dp * 1e3, "bf16_peak_sustained_tflops": peaks_bf16(),
+            "note": "latency-bound: 128 x 256 x 256 tiles, one CTA per 128 rows"}
+
+
+def peaks_bf16():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)).get("bf16_tflops_sustained")
+    return 1700.0
+
+
 def cpu_oracle(spec, budget_s, steps_cap):
     """The FP64 oracle on the host cores: full steps of the same workload
     until the time budget is used (at least one)."""
@@ -303,6 +351,12 @@ def main():
     ap.add_argument("--only-main", action="store_true",
                     help="time only the headline storage (no FP32 line, no e2e loop); for profiler runs")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--lb-row-mult", type=int, default=0,
+                    help="stream-collide rows per group multiple (implies --no-autotune)")
+    ap.add_argument("--lb-stages", type=int, default=0,
+                    help="stream-collide pipeline stages 2..4 (implies --no-autotune)")
+    ap.add_argument("--lb-blocks-per-sm", type=int, default=-1,
+                    help="stream-collide blocks per SM, 0 = as many as fit (implies --no-autotune)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the spreading (256x256x128, lambda=10, BF16) and 64-droplet batch lines")
     ap.add_argument("--accuracy-steps", type=int, default=20000,
@@ -310,6 +364,12 @@ def main():
     args = ap.parse_args()
 
     from paper_2503_20605_gb300 import inputs as I
+    if args.lb_row_mult > 0:
+        LB_SHAPE["mult"] = args.lb_row_mult
+    if args.lb_blocks_per_sm >= 0:
+        LB_SHAPE["bps"] = args.lb_blocks_per_sm
+    if args.lb_stages > 0:
+        LB_SHAPE["stages"] = args.lb_stages
     spec = I.workload_statics_128(90.0, args.storage)
     rank, world, local = dist_env()
     workload = "statics droplet 128^3 (D3Q19 tau=1, walls z, L5 icosphere 10242 nodes, R=24, sigma=0.005, " \
@@ -392,6 +452,10 @@ def main():
                            "sigma=0.01, seed 2025)", I.workload_batch(64, 2025, "f16"), "f16",
                            max(20, args.steps // 2), args.warmup, torch, iblb, flush, not args.no_autotune)]
 
+    mlp = None
+    if rank == 0 and not args.only_main:
+        mlp = run_mlp(I, iblb, torch)
+
     accuracy = None
     if rank == 0 and not args.only_main and args.accuracy_steps > 0:
         accuracy = run_accuracy(I, iblb, torch, args.accuracy_steps)
@@ -423,6 +487,7 @@ def main():
             "theta_RV_deg_after": main_run["obs"]["theta_RV_deg"],
             "accuracy": accuracy,
             "other_workloads": extra,
+            "warmstart_mlp": mlp,
         }
         print(json.dumps(line))
     if world > 1:

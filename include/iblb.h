@@ -142,6 +142,8 @@ typedef struct {
                                  stream-collide kernel (0..8; 0 = as many as fit)       */
 #define IBLB_OPT_LB_ROW_MULT 3 /* cell rows per stream-collide group, in units of
                                  max(1, 256 / nx) rows (1..4; 0 = 1)                     */
+#define IBLB_OPT_LB_STAGES 4  /* shared-memory stages of the stream-collide pipeline:
+                                 groups in flight + 1 (2..4; default 2)                  */
 
 typedef struct iblb_ctx iblb_ctx;
 

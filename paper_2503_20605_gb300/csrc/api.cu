@@ -72,7 +72,7 @@ struct iblb_ctx {
     double step_ms = 0.0;
     int64_t prof_steps = 0;
     int64_t step_count = 0;
-    LaunchCfg cfg{0, 2, 148};
+    LaunchCfg cfg{0, 2, 148, 2};
     int *h_status = nullptr;     // pinned, 4 per droplet
     double *obs_scr = nullptr;   // scratch of the mesh observation kernels
     int64_t obs_scr_n = 0;
@@ -371,8 +371,7 @@ void free_membrane_arrays(iblb_ctx *c)
     dfree(c->d_adj_start);
     dfree(c->d_adj);
     dfree(c->A.rec);
-    dfree(c->A.tile_list);
-    dfree(c->A.pair_rank);
+    dfree(c->A.clamped);
     dfree(c->A.red_part);
     dfree(c->A.red_out);
     dfree(c->A.vc_done);
@@ -382,7 +381,7 @@ void free_membrane_arrays(iblb_ctx *c)
     c->d_tri = c->d_adj_start = c->d_adj = nullptr;
     c->A.tri = c->A.adj_start = c->A.adj = nullptr;
     c->A.rec = nullptr;
-    c->A.tile_list = c->A.pair_rank = nullptr;
+    c->A.clamped = nullptr;
     c->A.red_part = c->A.red_out = nullptr;
 }
 
@@ -455,8 +454,8 @@ int rebuild_membranes(iblb_ctx *c)
     CK(dalloc(&c->d_adj_start, N + 1));
     CK(dalloc(&c->d_adj, adj.size()));
     CK(dalloc(&c->A.rec, N));
-    CK(dalloc(&c->A.tile_list, (size_t)MAXPAIR * N));
-    CK(dalloc(&c->A.pair_rank, (size_t)MAXPAIR * N));
+    CK(dalloc(&c->A.clamped, N));
+    CK(cudaMemsetAsync(c->A.clamped, 0, N, c->stream));
     CK(dalloc(&c->A.red_part, (size_t)NRED * std::max(chunks, 1)));
     CK(dalloc(&c->A.red_out, (size_t)NRED * c->ndrops));
     CK(dalloc(&c->A.vc_done, (size_t)c->ndrops));
@@ -475,7 +474,7 @@ int rebuild_membranes(iblb_ctx *c)
     CK(up(c->A.face_drop, fd.data(), sizeof(int) * NT));
     CK(up(c->d_adj_start, start.data(), sizeof(int) * (N + 1)));
     CK(up(c->d_adj, adj.data(), sizeof(int) * adj.size()));
-    CK(cudaMemsetAsync(c->A.bin_cnt, 0, sizeof(int) * (c->A.total_tiles + 1), c->stream));
+    CK(cudaMemsetAsync(c->A.bin_cnt, 0, sizeof(int) * c->A.total_tiles, c->stream));
     c->mem_dirty = false;
     int r = upload_drops(c);
     invalidate_graphs(c);
@@ -678,7 +677,6 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
     A.ndrops = n;
     const size_t sb = storage_bytes(c->storage);
     const int64_t T = A.total_tiles;
-    A.n_scan_blocks = (int)((T + 1 + SCAN_ITEMS - 1) / SCAN_ITEMS);
     A.active_cap = (int)T;
     if ((e = cudaMalloc(&c->fbuf[0], sb * Q * A.total_pcells)) != cudaSuccess ||
         (e = cudaMalloc(&c->fbuf[1], sb * Q * A.total_pcells)) != cudaSuccess ||
@@ -686,14 +684,13 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
         (e = dalloc(&A.U, 3 * (size_t)A.total_pcells)) != cudaSuccess ||
         (e = dalloc(&A.tile_gen, (size_t)T)) != cudaSuccess || (e = dalloc(&A.gen, 1)) != cudaSuccess ||
         (e = dalloc(&A.n_active, 2)) != cudaSuccess || (e = dalloc(&A.active, 2 * (size_t)T)) != cudaSuccess ||
-        (e = dalloc(&A.bin_cnt, (size_t)T + 1)) != cudaSuccess ||
-        (e = dalloc(&A.bin_off, (size_t)T + 1)) != cudaSuccess ||
-        (e = dalloc(&A.blk_sum, (size_t)A.n_scan_blocks)) != cudaSuccess ||
-        (e = dalloc(&A.blk_off, (size_t)A.n_scan_blocks)) != cudaSuccess ||
+        (e = dalloc(&A.bin_cnt, (size_t)T)) != cudaSuccess ||
+        (e = dalloc(&A.tile_list, (size_t)T * TILE_CAP)) != cudaSuccess ||
+        (e = dalloc(&A.spread_done, 1)) != cudaSuccess ||
         (e = dalloc(&A.col_cnt, (size_t)A.total_cols)) != cudaSuccess ||
         (e = dalloc(&A.col_z, (size_t)A.total_cols * MAXC)) != cudaSuccess ||
         (e = dalloc(&A.mass_part, (size_t)c->mass_blocks)) != cudaSuccess ||
-        (e = dalloc(&A.status, 4 * (size_t)n)) != cudaSuccess || (e = dalloc(&A.clamped, (size_t)n)) != cudaSuccess ||
+        (e = dalloc(&A.status, 4 * (size_t)n)) != cudaSuccess ||
         (e = dalloc(&c->d_mass, (size_t)n)) != cudaSuccess || (e = dalloc(&c->d_drops, (size_t)n)) != cudaSuccess)
         return bad(e, "cudaMalloc");
     if ((e = cudaMallocHost(&c->h_status, sizeof(int) * 4 * n)) != cudaSuccess)
@@ -704,10 +701,10 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
     if ((e = cudaMemsetAsync(A.tile_gen, 0, sizeof(uint32_t) * T, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(A.gen, &one, sizeof(one), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.n_active, 0, 2 * sizeof(int), s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(A.bin_cnt, 0, sizeof(int) * (T + 1), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.spread_done, 0, sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.bin_cnt, 0, sizeof(int) * T, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.col_cnt, 0, sizeof(int) * A.total_cols, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.status, 0, sizeof(int) * 4 * n, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(A.clamped, 0, sizeof(int) * n, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.F, 0, sizeof(float) * 3 * A.total_pcells, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.U, 0, sizeof(float) * 3 * A.total_pcells, s)) != cudaSuccess ||
         (e = launch_init_populations(A, c->storage, c->fbuf[0], s)) != cudaSuccess ||
@@ -742,14 +739,12 @@ void iblb_destroy(iblb_ctx *c)
     dfree(A.n_active);
     dfree(A.active);
     dfree(A.bin_cnt);
-    dfree(A.bin_off);
-    dfree(A.blk_sum);
-    dfree(A.blk_off);
+    dfree(A.tile_list);
+    dfree(A.spread_done);
     dfree(A.col_cnt);
     dfree(A.col_z);
     dfree(A.mass_part);
     dfree(A.status);
-    dfree(A.clamped);
     dfree(c->d_mass);
     dfree(c->d_drops);
     dfree(c->obs_scr);
@@ -1030,6 +1025,12 @@ int observe_mesh(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs
 {
     const Drop &D = c->drops[k];
     if (D.nnodes) {
+        std::vector<uint8_t> cl(D.nnodes);
+        CK(cudaMemcpy(cl.data(), c->A.clamped + D.node0, D.nnodes, cudaMemcpyDeviceToHost));
+        int n = 0;
+        for (uint8_t v : cl)
+            n += v;
+        out->clamped = n;
         const int64_t need = observe_scratch_doubles(D.nnodes, D.ntri);
         if (need > c->obs_scr_n) {
             dfree(c->obs_scr);
@@ -1072,7 +1073,6 @@ int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs
     enter(c);
     CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
     CK(cudaMemcpyAsync(&out->mass, c->d_mass + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&out->clamped, c->A.clamped + k, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     int flags = 0;
     if ((r = read_status(c, false, &flags)))   // synchronises the stream
         return r;
@@ -1093,17 +1093,14 @@ int iblb_observe_all(iblb_ctx *c, double zcut_frac, double eps_flat, iblb_obs *o
         return fail(c, IBLB_E_ARG, "null output");
     memset(out, 0, sizeof(*out) * (size_t)c->ndrops);
     std::vector<double> mass(c->ndrops);
-    std::vector<int> clamped(c->ndrops);
     enter(c);
     CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
     CK(cudaMemcpyAsync(mass.data(), c->d_mass, sizeof(double) * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(clamped.data(), c->A.clamped, sizeof(int) * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
     int flags = 0;
     if ((r = read_status(c, false, &flags)))
         return r;
     for (int k = 0; k < c->ndrops; ++k) {
         out[k].mass = mass[k];
-        out[k].clamped = clamped[k];
         if ((r = observe_mesh(c, k, zcut_frac, eps_flat, &out[k])))
             return r;
     }
@@ -1145,6 +1142,12 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
         invalidate_graphs(c);
         return upload_drops(c);
     }
+    case IBLB_OPT_LB_STAGES:
+        if (value < 2 || value > 4)
+            return fail(c, IBLB_E_ARG, "pipeline stages must be in [2, 4]");
+        c->cfg.lb_stages = value;
+        invalidate_graphs(c);
+        return IBLB_OK;
     }
     return fail(c, IBLB_E_ARG, "unknown option");
 }
@@ -1189,12 +1192,13 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
         if (fp) {
             char line[256];
             while (fgets(line, sizeof(line), fp)) {
-                int bps = 0, mult = 0;
+                int bps = 0, mult = 0, ns = 2;
                 const char *bar = strchr(line, '|');
                 if (bar && (size_t)(bar - line) == strlen(key) && !strncmp(line, key, strlen(key)) &&
-                    sscanf(bar + 1, "%d %d", &bps, &mult) == 2) {
+                    sscanf(bar + 1, "%d %d %d", &bps, &mult, &ns) == 3) {
                     fclose(fp);
-                    if ((r = iblb_set_option(c, IBLB_OPT_LB_BLOCKS_PER_SM, bps)))
+                    if ((r = iblb_set_option(c, IBLB_OPT_LB_BLOCKS_PER_SM, bps)) ||
+                        (r = iblb_set_option(c, IBLB_OPT_LB_STAGES, ns)))
                         return r;
                     return iblb_set_option(c, IBLB_OPT_LB_ROW_MULT, mult);
                 }
@@ -1206,39 +1210,49 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
     // spare one: the current state is left untouched
     const int bpsm[2] = {0, 1};
     float best = 1e30f;
-    int bb = 0, bm = 1;
+    int bb = c->cfg.lb_blocks_per_sm, bm = c->cfg.lb_row_mult;
+    int dev = 0, smem_max = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     enter(c);
+    int bs = c->cfg.lb_stages;
     for (int mult = 1; mult <= 4; mult *= 2)
-        for (int bi = 0; bi < 2; ++bi) {
-            c->cfg.lb_blocks_per_sm = bpsm[bi];
-            c->cfg.lb_row_mult = mult;
-            layout(c);
-            if ((r = upload_drops(c)))
-                return r;
-            const bool vt = c->A.total_nodes > 0 && c->any_vartau;
-            for (int w = 0; w < 2; ++w)
-                CK(launch_lb(c->A, c->storage, c->fbuf[c->cur], c->fbuf[c->cur ^ 1], vt, c->cfg, c->stream));
-            CK(cudaEventRecord(e0, c->stream));
-            for (int w = 0; w < 5; ++w)
-                CK(launch_lb(c->A, c->storage, c->fbuf[c->cur], c->fbuf[c->cur ^ 1], vt, c->cfg, c->stream));
-            CK(cudaEventRecord(e1, c->stream));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
-                best = ms;
-                bb = bpsm[bi];
-                bm = mult;
+        for (int bi = 0; bi < 2; ++bi)
+            for (int ns = 2; ns <= 4; ++ns) {
+                c->cfg.lb_blocks_per_sm = bpsm[bi];
+                c->cfg.lb_row_mult = mult;
+                c->cfg.lb_stages = ns;
+                layout(c);
+                if (ns * (int64_t)c->A.lb_stage_bytes + 1024 > smem_max)
+                    continue;                  // these stages do not fit
+                if ((r = upload_drops(c)))
+                    return r;
+                const bool vt = c->A.total_nodes > 0 && c->any_vartau;
+                for (int w = 0; w < 2; ++w)
+                    CK(launch_lb(c->A, c->storage, c->fbuf[c->cur], c->fbuf[c->cur ^ 1], vt, c->cfg, c->stream));
+                CK(cudaEventRecord(e0, c->stream));
+                for (int w = 0; w < 5; ++w)
+                    CK(launch_lb(c->A, c->storage, c->fbuf[c->cur], c->fbuf[c->cur ^ 1], vt, c->cfg, c->stream));
+                CK(cudaEventRecord(e1, c->stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    bb = bpsm[bi];
+                    bm = mult;
+                    bs = ns;
+                }
             }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     leave(c);
     c->cfg.lb_blocks_per_sm = bb;
     c->cfg.lb_row_mult = bm;
+    c->cfg.lb_stages = bs;
     layout(c);
     invalidate_graphs(c);
     if ((r = upload_drops(c)))
@@ -1246,7 +1260,7 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
     if (cache_path) {
         FILE *fp = fopen(cache_path, "a");
         if (fp) {
-            fprintf(fp, "%s|%d %d\n", key, bb, bm);
+            fprintf(fp, "%s|%d %d %d\n", key, bb, bm, bs);
             fclose(fp);
         }
     }

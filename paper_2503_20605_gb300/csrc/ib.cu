@@ -76,22 +76,13 @@ __device__ __forceinline__ int support_tiles(int b, int n, bool periodic, int *o
     return cnt;
 }
 
-// Opens a step: generation += 1, an empty band list for this generation (the
-// other list keeps the previous band), clamped-node counters reset.
-__global__ void begin_step_kernel(Arrays a)
-{
-    if (threadIdx.x == 0) {
-        const uint32_t g = *a.gen + 1u;
-        *a.gen = g;
-        a.n_active[g & 1u] = 0;
-    }
-    for (int d = threadIdx.x; d < a.ndrops; d += blockDim.x)
-        a.clamped[d] = 0;
-}
-
 // FL lanes per node; lane l takes the node's incident faces l, l + FL, ...
 // Lane 0 writes the node record; the lanes then list the node in the tiles
-// its kernel support touches (rank in each tile's list from the counter).
+// its kernel support touches: its slot in a tile's list (TILE_CAP slots per
+// tile) comes from the tile's counter, and the node that takes slot 0 stamps
+// the tile with this step's generation and appends it to the band list.
+// (Nothing in this kernel reads the generation counter's new value; the
+// spread kernel commits it.)
 __global__ void __launch_bounds__(128) node_force_kernel(Arrays a)
 {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,6 +169,7 @@ __global__ void __launch_bounds__(128) node_force_kernel(Arrays a)
         r.bz = bz;
         r.key = ncombo;
         r.spare = d;
+        uint8_t clamped = 0;
         if (!sane) {
             atomicOr(&a.status[4 * d], ST_NAN);
             for (int k = 0; k < 4; ++k)
@@ -189,7 +181,7 @@ __global__ void __launch_bounds__(128) node_force_kernel(Arrays a)
                 float h = (float)(qz - 0.5);
                 if (h < D.hmin) {
                     h = D.hmin;
-                    atomicAdd(&a.clamped[d], 1);
+                    clamped = 1;
                 }
                 const float r0 = D.xi / h;
                 const float Pi = D.A * (ipow(r0, D.n) - ipow(r0, D.m));
@@ -209,154 +201,25 @@ __global__ void __launch_bounds__(128) node_force_kernel(Arrays a)
                 atomicOr(&a.status[4 * d], ST_ESCAPE);
         }
         a.rec[j] = r;
+        a.clamped[j] = clamped;
     }
-    for (int c = l; c < ncombo; c += FL) {
-        const int ix = c % ntx, iy = (c / ntx) % nty, iz = c / (ntx * nty);
-        const int64_t t = D.tile0 + txs[ix] + (int64_t)D.tx * (tys[iy] + (int64_t)D.ty * tzs[iz]);
-        a.pair_rank[(int64_t)j * MAXPAIR + c] = atomicAdd(&a.bin_cnt[t], 1);
-    }
-}
-
-// Block-level exclusive scan of the per-tile list lengths (SCAN_ITEMS per
-// block); the non-empty tiles are the band of this step: stamped with the
-// generation and appended to this step's band list (warp-aggregated).
-__global__ void __launch_bounds__(1024) scan_mark_kernel(Arrays a)
-{
-    __shared__ int warp_tot[32];
-    const int64_t n = a.total_tiles + 1;   // the last count is a zero sentinel
-    const int64_t base = (int64_t)blockIdx.x * SCAN_ITEMS + 4 * threadIdx.x;
-    int v[4];
-    for (int i = 0; i < 4; ++i)
-        v[i] = base + i < n ? a.bin_cnt[base + i] : 0;
-    const int local = v[0] + v[1] + v[2] + v[3];
-    int inc = local;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o)
-            inc += t;
-    }
-    if (lane == 31)
-        warp_tot[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        int t = lane < (blockDim.x >> 5) ? warp_tot[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o)
-                t += u;
-        }
-        warp_tot[lane] = t;
-    }
-    __syncthreads();
-    int run = inc - local + (w ? warp_tot[w - 1] : 0);
-    for (int i = 0; i < 4; ++i) {
-        if (base + i < n)
-            a.bin_off[base + i] = run;
-        run += v[i];
-    }
-    if (threadIdx.x == blockDim.x - 1)
-        a.blk_sum[blockIdx.x] = warp_tot[(blockDim.x >> 5) - 1];
-
-    const uint32_t gen = *a.gen;
+    // this step's generation (committed by the spread kernel when it ends)
+    const uint32_t gen = *a.gen + 1u;
     const int cur = (int)(gen & 1u);
-    int *list = a.active + (int64_t)cur * a.active_cap;
-    for (int i = 0; i < 4; ++i) {
-        const int64_t t = base + i;
-        const bool band = t < a.total_tiles && v[i] > 0;
-        if (band)
-            a.tile_gen[t] = gen;
-        const unsigned m = __ballot_sync(0xffffffffu, band);
-        if (!m)
-            continue;
-        int slot0 = 0;
-        if (lane == __ffs(m) - 1)
-            slot0 = atomicAdd(&a.n_active[cur], __popc(m));
-        slot0 = __shfl_sync(0xffffffffu, slot0, __ffs(m) - 1);
-        if (band) {
-            const int s = slot0 + __popc(m & ((1u << lane) - 1u));
-            if (s < a.active_cap)
-                list[s] = (int)t;
-        }
-    }
-}
-
-// Exclusive scan of the block totals by one block (serial over chunks of 1024).
-__global__ void __launch_bounds__(1024) scan_top_kernel(const int *__restrict__ blk_sum, int nb,
-                                                        int *__restrict__ blk_off)
-{
-    __shared__ int warp_tot[32];
-    __shared__ int carry;
-    if (threadIdx.x == 0)
-        carry = 0;
-    __syncthreads();
-    for (int c0 = 0; c0 < nb; c0 += 1024) {
-        const int i = c0 + threadIdx.x;
-        const int v = i < nb ? blk_sum[i] : 0;
-        int inc = v;
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o)
-                inc += t;
-        }
-        if (lane == 31)
-            warp_tot[w] = inc;
-        __syncthreads();
-        if (w == 0) {
-            int t = warp_tot[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                int u = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o)
-                    t += u;
-            }
-            warp_tot[lane] = t;
-        }
-        __syncthreads();
-        const int ex = inc - v + (w ? warp_tot[w - 1] : 0) + carry;
-        if (i < nb)
-            blk_off[i] = ex;
-        __syncthreads();
-        if (threadIdx.x == 1023)
-            carry = ex + v;
-        __syncthreads();
-    }
-}
-
-// start of tile t's node list; the scan covers total_tiles + 1 entries (the
-// last count is always zero), so list t ends where list t + 1 begins
-__device__ __forceinline__ int list_begin(const Arrays &a, int64_t t)
-{
-    return a.bin_off[t] + a.blk_off[t / SCAN_ITEMS];
-}
-
-// Write every node into the lists of the tiles its support touches (same
-// enumeration as the force kernel, position = list start + rank).  The order
-// inside a list is the arrival order of the counting atomics, which does not
-// matter: the gather sorts by node index.  The entry of rank 0 resets the
-// tile's counter for the next step.
-__global__ void __launch_bounds__(128) fill_kernel(Arrays a)
-{
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = gid / FL, l = gid % FL;
-    if (j >= a.total_nodes)
-        return;
-    const NodeRec &r = a.rec[j];
-    const int ncombo = r.key;
-    if (l >= ncombo)
-        return;
-    const Drop &D = a.drops[r.spare];
-    int txs[3], tys[3], tzs[3];
-    const int ntx = support_tiles(r.bx, D.nx, true, txs);
-    const int nty = support_tiles(r.by, D.ny, true, tys);
-    support_tiles(r.bz, D.nzf, !D.walls, tzs);
     for (int c = l; c < ncombo; c += FL) {
         const int ix = c % ntx, iy = (c / ntx) % nty, iz = c / (ntx * nty);
         const int64_t t = D.tile0 + txs[ix] + (int64_t)D.tx * (tys[iy] + (int64_t)D.ty * tzs[iz]);
-        const int rank = a.pair_rank[(int64_t)j * MAXPAIR + c];
-        a.tile_list[list_begin(a, t) + rank] = j;
-        if (rank == 0)
-            a.bin_cnt[t] = 0;
+        const int rank = atomicAdd(&a.bin_cnt[t], 1);
+        if (rank == 0) {        // first node of the tile: the tile joins the band
+            a.tile_gen[t] = gen;
+            const int slot = atomicAdd(&a.n_active[cur], 1);
+            if (slot < a.active_cap)
+                a.active[(int64_t)cur * a.active_cap + slot] = (int)t;
+        }
+        if (rank < TILE_CAP)
+            a.tile_list[t * TILE_CAP + rank] = j;
+        else
+            atomicOr(&a.status[4 * d], ST_SPREAD_OVF);
     }
 }
 
@@ -386,7 +249,7 @@ __global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
     __shared__ float s_w[12][SPREAD_CAP];
     __shared__ float s_phi[3][SPREAD_CAP];
     __shared__ float s_part[3][TILE_CELLS];
-    const uint32_t gen = *a.gen;
+    const uint32_t gen = *a.gen + 1u;          // this step's generation, committed below
     const int cur = (int)(gen & 1u);
     const int nact = min(a.n_active[cur], a.active_cap);
     const int *list = a.active + (int64_t)cur * a.active_cap;
@@ -420,13 +283,8 @@ __global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
         const Drop &D = a.drops[d];
         const int local = (int)(T - D.tile0);
         const int X0 = 4 * (local % D.tx), Y0 = 4 * ((local / D.tx) % D.ty), Z0 = 4 * (local / (D.tx * D.ty));
-        const int e0 = list_begin(a, T);
-        int cnt = list_begin(a, T + 1) - e0;
-        if (cnt > SPREAD_CAP) {
-            if (tid == 0)
-                atomicOr(&a.status[4 * d], ST_SPREAD_OVF);
-            cnt = SPREAD_CAP;
-        }
+        const int64_t e0 = T * TILE_CAP;
+        const int cnt = min(a.bin_cnt[T], TILE_CAP);     // overflow was flagged by the force kernel
         for (int e = tid; e < cnt; e += SPREAD_THREADS) {
             const int j = a.tile_list[e0 + e];
             const NodeRec &r = a.rec[j];
@@ -444,6 +302,8 @@ __global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
             s_phi[2][e] = r.phi[2];
         }
         __syncthreads();
+        if (tid == 0)
+            a.bin_cnt[T] = 0;                            // empty for the next step
         // rank sort by node index: contributions are added in increasing j
         for (int e = tid; e < cnt; e += SPREAD_THREADS) {
             const int key = s_node[e];
@@ -485,6 +345,19 @@ __global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
             a.F[2 * a.total_pcells + g] = fz;
         }
         __syncthreads();
+    }
+    // the last block to finish commits the generation and empties the
+    // previous step's band list, which the next step fills
+    __shared__ int s_last;
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(a.spread_done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && tid == 0) {
+        *a.gen = gen;
+        a.n_active[cur ^ 1] = 0;
+        *a.spread_done = 0;
     }
 }
 
@@ -547,7 +420,6 @@ cudaError_t launch_node_force(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    begin_step_kernel<<<1, 64, 0, s>>>(a);
     const int64_t threads = (int64_t)a.total_nodes * FL;
     node_force_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
@@ -562,10 +434,6 @@ cudaError_t launch_spread(const Arrays &a, cudaStream_t s)
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
     }
-    scan_mark_kernel<<<a.n_scan_blocks, 1024, 0, s>>>(a);
-    scan_top_kernel<<<1, 1024, 0, s>>>(a.blk_sum, a.n_scan_blocks, a.blk_off);
-    const int64_t threads = (int64_t)a.total_nodes * FL;
-    fill_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a);
     spread_kernel<<<g_sm_count * 5, SPREAD_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }

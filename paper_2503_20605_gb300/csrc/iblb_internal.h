@@ -15,9 +15,8 @@ constexpr int Q = 19;
 constexpr int TILE = 4;            // band tiles are 4x4x4 fluid cells
 constexpr int TILE_CELLS = 64;
 constexpr int MAXC = 16;           // ray crossings kept per lattice column
-constexpr int SPREAD_CAP = 512;    // nodes whose stencil overlaps one tile
-constexpr int MAXPAIR = 27;        // tiles one node's 4x4x4 support can touch
-constexpr int SCAN_ITEMS = 4096;   // elements per block of the tile scan
+constexpr int TILE_CAP = 256;      // nodes whose kernel support may touch one tile
+constexpr int SPREAD_CAP = TILE_CAP;  // nodes the spread kernel stages per tile
 constexpr int RED_FACES = 2048;    // faces per chunk of the observation reductions
 constexpr int RED_NODES = 1024;    // nodes per chunk of the observation reductions
 constexpr int VC_ITEMS = 256;      // faces (and nodes) per chunk of the volume correction
@@ -26,7 +25,7 @@ constexpr int NRED = 8;            // partial sums per chunk (see reduce.cu)
 // device status bits (Arrays::status[4 * d + 0])
 constexpr int ST_NAN = 1;          // NaN / Inf in a node velocity or position
 constexpr int ST_JUMP = 2;         // |qdot| > 1/2 in one step
-constexpr int ST_SPREAD_OVF = 4;   // more than SPREAD_CAP nodes overlap a tile
+constexpr int ST_SPREAD_OVF = 4;   // more than TILE_CAP nodes overlap a tile
 constexpr int ST_COL_OVF = 8;      // more than MAXC crossings in a column
 constexpr int ST_ESCAPE = 16;      // a node left the fluid in z
 constexpr int ST_TIMEOUT = 32;     // a bounded wait for a bulk copy gave up
@@ -89,14 +88,10 @@ struct Arrays {
     int *n_active;                 // 2: band tiles of this step / of the previous step
     int *active;                   // 2 * active_cap: band tiles, indexed by generation parity
     int active_cap;
-    // bins
-    int *bin_cnt;                  // total_tiles, returns to 0 after the fill
-    int *bin_off;                  // total_tiles + 1, block-local exclusive scan
-    int *blk_sum;                  // blocks of the scan
-    int *blk_off;
-    int n_scan_blocks;
-    int *pair_rank;                // MAXPAIR per node: rank of the node in each touched tile's list
-    int *tile_list;                // MAXPAIR * total_nodes: node indices listed per tile
+    // per-tile node lists
+    int *bin_cnt;                  // total_tiles: nodes listed in this step (returns to 0 in the spread)
+    int *tile_list;                // TILE_CAP * total_tiles: node indices per tile, arrival order
+    int *spread_done;              // blocks of the spread kernel finished (returns to 0)
     // membrane
     double *qx, *qy, *qz;          // node positions (FP64)
     int *node_drop;                // droplet of each node
@@ -115,7 +110,7 @@ struct Arrays {
     int *vc_done;                  // per droplet: finished chunks (returns to 0)
     double *mass_part;
     int *status;                   // 4 ints per droplet: flags (ST_*), -, -, -
-    int *clamped;                  // per droplet: nodes clamped by the near-wall guard this step
+    uint8_t *clamped;              // per node: 1 if the near-wall guard clamped it in this step
 };
 
 __host__ __device__ inline int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
@@ -123,51 +118,16 @@ __host__ __device__ inline int wrapi(int a, int n) { return a < 0 ? a + n : (a >
 // floor(a / b) for b > 0
 __host__ __device__ inline int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-// Tiles along one axis whose cells a support 4 wide, keyed by tile k, can
-// touch: k-1, k, k+1 (periodic axes wrap), plus, on a periodic axis whose
-// last tile holds a single cell, tile 0 for k = t-2 (the support of a base
-// cell n-2 wraps onto cell 0).  Returns the count written to out[0..3].
-__host__ __device__ inline int tile_neighbours(int k, int t, int ncell, bool periodic, int *out)
-{
-    int cnt = 0;
-    for (int dk = -1; dk <= 1; ++dk) {
-        int v = k + dk;
-        if (periodic)
-            v = (v % t + t) % t;
-        else if (v < 0 || v >= t)
-            continue;
-        bool dup = false;
-        for (int i = 0; i < cnt; ++i)
-            dup |= out[i] == v;
-        if (!dup)
-            out[cnt++] = v;
-    }
-    if (periodic && (ncell & 3) == 1 && t >= 2) {
-        int extra = -1;
-        if (k == t - 2)
-            extra = 0;
-        else if (k == 0)
-            extra = t - 2;
-        if (extra >= 0) {
-            bool dup = false;
-            for (int i = 0; i < cnt; ++i)
-                dup |= out[i] == extra;
-            if (!dup)
-                out[cnt++] = extra;
-        }
-    }
-    return cnt;
-}
-
 // Host-side launchers (lb.cu, ib.cu, inout.cu, reduce.cu, fields.cu).
 struct LaunchCfg {
     int lb_blocks_per_sm;          // resident stream-collide blocks per SM (0: as many as fit)
     int lb_row_mult;               // cell rows per group = lb_row_mult * lb_rows_per_group(nx)
     int sm_count;
+    int lb_stages;                 // shared-memory stages of the stream-collide pipeline (2..4)
 };
 int lb_rows_per_group(int nx);     // 256-thread groups: max(1, 256 / nx) rows
-// bytes of one stage of the stream-collide kernel: 19 population rows and 3
-// force rows per cell row, plus one band flag per row (128-byte multiple)
+// bytes of one stage of the stream-collide kernel: a 128-byte group header,
+// 19 population rows and 3 force rows per cell row (128-byte multiple)
 int lb_stage_bytes(int rows, int pitch, int storage_bytes);
 
 cudaError_t launch_lb(const Arrays &a, int storage, const void *src, void *dst, bool vartau,

@@ -15,8 +15,8 @@
 // apply the x shift and the periodic x wrap inside shared memory.  Every
 // population row is read from HBM exactly once per step; the consumers
 // touch global memory only to store results.  Blocks are persistent and
-// double-buffer: the next group is in flight while the current one is
-// computed; one block barrier per group.
+// keep a ring of 2 to 4 stages: up to three groups are in flight while the
+// current one is computed; one block barrier per group.
 //
 // Memory traffic per fluid cell: 19 reads + 19 writes of the storage type
 // (152 B for FP32, 76 B for 16-bit storage); the force density is read and
@@ -30,6 +30,7 @@ namespace {
 constexpr int LB_THREADS = 256;                   // consumer threads per block
 constexpr int LB_BLOCK = LB_THREADS + 32;         // + one producer warp
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: bounded mbarrier wait
+constexpr int LB_MAX_STAGES = 4;
 
 __device__ __forceinline__ float cvt(float v) { return v; }
 __device__ __forceinline__ float cvt(__half v) { return __half2float(v); }
@@ -214,41 +215,50 @@ __device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t 
     }
 
 template <typename S, bool VARTAU>
-__global__ void __launch_bounds__(LB_BLOCK, 2) lb_kernel(Arrays a, const S *__restrict__ src, S *__restrict__ dst)
+__global__ void __launch_bounds__(LB_BLOCK, 2)
+    lb_kernel(Arrays a, const S *__restrict__ src, S *__restrict__ dst, int ns)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[LB_MAX_STAGES];
     const uint32_t gen = *a.gen;
     const int total = a.lb_blocks_total;
     const bool producer = threadIdx.x >= LB_THREADS;
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 32);
-        mbar_init(&bar[1], 32);
+        for (int i = 0; i < ns; ++i)
+            mbar_init(&bar[i], 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    int g = blockIdx.x;
-    if (g < total && producer)
-        produce<S>(a, src, gen, g, smem_raw, &bar[0]);
-    int k = 0;
+    // the producer keeps ns - 1 groups in flight ahead of the consumers
+    if (producer)
+        for (int p = 0; p < ns - 1; ++p) {
+            const int gp = blockIdx.x + p * (int)gridDim.x;
+            if (gp < total)
+                produce<S>(a, src, gen, gp, smem_raw + p * a.lb_stage_bytes, &bar[p]);
+        }
+    // group k of this block uses stage st_i = k mod ns, barrier phase
+    // (k / ns) mod 2
+    int st_i = 0;
+    uint32_t phase = 0;
     bool failed = false;
-    for (; g < total; g += gridDim.x, ++k) {
-        const int st_i = k & 1;
+    for (int g = blockIdx.x; g < total;
+         g += gridDim.x, st_i = (st_i + 1 == ns) ? 0 : st_i + 1, phase ^= (st_i == 0) ? 1u : 0u) {
         // consumers wait for this group (bounded); the barrier makes the
-        // outcome uniform and ends the previous group, so the other stage is
-        // free to be refilled
-        const bool ok = producer || mbar_wait_bounded(&bar[st_i], (uint32_t)((k >> 1) & 1));
+        // outcome uniform and ends the previous group, so its stage is free
+        // to be refilled
+        const bool ok = producer || mbar_wait_bounded(&bar[st_i], phase);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
         if (producer) {
-            const int gn = g + gridDim.x;
+            const int gn = g + (ns - 1) * (int)gridDim.x;
             if (gn < total) {
+                const int sn = st_i ? st_i - 1 : ns - 1;      // the stage of the previous group
                 // order the generic reads of the previous group before the
                 // asynchronous writes into the same stage
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                produce<S>(a, src, gen, gn, smem_raw + (st_i ^ 1) * a.lb_stage_bytes, &bar[st_i ^ 1]);
+                produce<S>(a, src, gen, gn, smem_raw + sn * a.lb_stage_bytes, &bar[sn]);
             }
             continue;
         }
@@ -369,8 +379,8 @@ __global__ void __launch_bounds__(LB_BLOCK, 2) lb_kernel(Arrays a, const S *__re
             PAIR(17, 18, a2, q2, wr2, kw2, kw23, ux - uz, Fx - Fz, s17, s18);
         }
     }
-    // a timed-out group was the only one in flight (the next one is issued
-    // after the barrier that reported the failure): flag it and leave
+    // a bounded wait gave up: flag it and leave (every block reaches this
+    // point; nothing waits on this block)
     if (failed && threadIdx.x == 0)
         atomicOr(&a.status[0], ST_TIMEOUT);
 }
@@ -383,7 +393,8 @@ cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, c
     const int total = a.lb_blocks_total;
     if (total <= 0)
         return cudaSuccess;
-    const size_t smem = 2 * (size_t)a.lb_stage_bytes;
+    const int ns = cfg.lb_stages < 2 ? 2 : (cfg.lb_stages > LB_MAX_STAGES ? LB_MAX_STAGES : cfg.lb_stages);
+    const size_t smem = (size_t)ns * a.lb_stage_bytes;
     const void *fn = vartau ? (const void *)lb_kernel<S, true> : (const void *)lb_kernel<S, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
@@ -399,9 +410,9 @@ cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, c
     int grid = cfg.sm_count * per_sm;
     grid = grid < total ? grid : total;
     if (vartau)
-        lb_kernel<S, true><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst);
+        lb_kernel<S, true><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst, ns);
     else
-        lb_kernel<S, false><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst);
+        lb_kernel<S, false><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst, ns);
     return cudaGetLastError();
 }
 

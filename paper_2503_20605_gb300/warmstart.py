@@ -174,6 +174,8 @@ def main(argv=None):
     ap.add_argument("--max-steps", type=int, default=40000)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=2000)
+    ap.add_argument("--mlp-batch", type=int, default=64)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default="warmstart_results")
     args = ap.parse_args(argv)
     import torch
@@ -188,7 +190,9 @@ def main(argv=None):
     tr = generate(xtr, batch=args.batch, max_steps=args.max_steps, stream=stream, log=log)
     ok = tr["steps"] >= 0
     log(f"  {ok.sum()} converged ({time.time() - t0:.0f} s)")
-    params, losses = train(xtr[ok], tr["profile"][ok], epochs=args.epochs, stream=stream)
+    np.savez(os.path.join(args.out, "train_data.npz"), x=xtr, **tr)
+    params, losses = train(xtr[ok], tr["profile"][ok], epochs=args.epochs, batch=args.mlp_batch, lr=args.lr,
+                           stream=stream)
     log(f"trained: loss {losses[0]:.3e} -> {losses[-1]:.3e} ({time.time() - t0:.0f} s)")
     g = predict(params, xte, stream)
     log("held-out cases from the sphere")

@@ -239,3 +239,20 @@ def test_batch_member_equals_single_run():
             assert np.array_equal(iblb.iblb_get_nodes(c, 0), got[k][1])
         finally:
             iblb.iblb_destroy(c)
+
+
+def test_near_wall_guard_count_matches_oracle():
+    """Nodes below h_min_frac * xi are clamped by the guard; the GPU's
+    per-node flags add up to the oracle's count after one step."""
+    sp = I.workload_parity_32()
+    xyz, tri = sp.mesh()
+    xyz = xyz - np.array([0.0, 0.0, xyz[:, 2].min() - 1.2])      # lowest node at z = 1.2, h = 0.7
+    g, s = pair(nx=32, ny=32, nz=32, tau=1.0, sigma=sp.sigma, theta=sp.theta_deg, xi=sp.xi, mesh=(xyz, tri))
+    try:
+        iblb.iblb_step(g, 1)
+        ob = iblb.iblb_observe(g, 0)
+    finally:
+        iblb.iblb_destroy(g)
+    s.step(1)
+    assert s.clamped() > 0
+    assert ob["clamped"] == s.clamped()
