@@ -191,6 +191,7 @@ def run_accuracy(I, iblb, torch, steps, angles=(30.0, 60.0, 90.0, 120.0, 150.0))
 
 
 LB_SHAPE = {}
+IB_SHAPE = {}
 
 
 def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
@@ -204,6 +205,10 @@ def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_LB_BLOCKS_PER_SM, LB_SHAPE["bps"])
         if "stages" in LB_SHAPE:
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_LB_STAGES, LB_SHAPE["stages"])
+        if "fused" in IB_SHAPE:
+            iblb.iblb_set_option(ctx, iblb.IBLB_OPT_FUSED_IB, IB_SHAPE["fused"])
+        if "bps" in IB_SHAPE:
+            iblb.iblb_set_option(ctx, iblb.IBLB_OPT_IB_BLOCKS_PER_SM, IB_SHAPE["bps"])
         if autotune and not LB_SHAPE:
             iblb.iblb_autotune(ctx, os.path.join(ROOT, "paper_2503_20605_gb300", "_build", "autotune.txt"))
         def timed(mode, n):
@@ -353,6 +358,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--lb-row-mult", type=int, default=0,
                     help="stream-collide rows per group multiple (implies --no-autotune)")
+    ap.add_argument("--fused-ib", type=int, default=-1, help="1/0: cooperative or separate membrane kernels")
+    ap.add_argument("--ib-blocks-per-sm", type=int, default=-1, help="blocks per SM of the cooperative kernels")
     ap.add_argument("--lb-stages", type=int, default=0,
                     help="stream-collide pipeline stages 2..4 (implies --no-autotune)")
     ap.add_argument("--lb-blocks-per-sm", type=int, default=-1,
@@ -370,6 +377,10 @@ def main():
         LB_SHAPE["bps"] = args.lb_blocks_per_sm
     if args.lb_stages > 0:
         LB_SHAPE["stages"] = args.lb_stages
+    if args.fused_ib >= 0:
+        IB_SHAPE["fused"] = args.fused_ib
+    if args.ib_blocks_per_sm >= 0:
+        IB_SHAPE["bps"] = args.ib_blocks_per_sm
     spec = I.workload_statics_128(90.0, args.storage)
     rank, world, local = dist_env()
     workload = "statics droplet 128^3 (D3Q19 tau=1, walls z, L5 icosphere 10242 nodes, R=24, sigma=0.005, " \

@@ -144,6 +144,14 @@ typedef struct {
                                  max(1, 256 / nx) rows (1..4; 0 = 1)                     */
 #define IBLB_OPT_LB_STAGES 4  /* shared-memory stages of the stream-collide pipeline:
                                  groups in flight + 1 (2..4; default 2)                  */
+#define IBLB_OPT_FUSED_IB 5   /* 1: the membrane work of a step runs as two cooperative
+                                 kernels (forces + spread; advection + volume
+                                 correction) with grid barriers between their phases,
+                                 reported as the forces and advect phases; 0 (default):
+                                 one kernel per stage.  Results are bit-identical
+                                 either way; on GB300 the separate kernels are faster. */
+#define IBLB_OPT_IB_BLOCKS_PER_SM 6 /* blocks per SM of the two cooperative membrane
+                                 kernels (0..8; 0 = as many as fit; default 1)           */
 
 typedef struct iblb_ctx iblb_ctx;
 

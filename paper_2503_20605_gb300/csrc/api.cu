@@ -65,6 +65,7 @@ struct iblb_ctx {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaEvent_t ph[IBLB_NPHASE + 1] = {};
     bool graphs = true;
+    bool fused_ib = false;         // membrane work as two cooperative kernels
     int profile = 0;               // 0 off, 1 every phase, 2 whole step only
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     bool gvalid[2] = {false, false};
@@ -72,7 +73,7 @@ struct iblb_ctx {
     double step_ms = 0.0;
     int64_t prof_steps = 0;
     int64_t step_count = 0;
-    LaunchCfg cfg{0, 2, 148, 2};
+    LaunchCfg cfg{0, 2, 148, 2, 1};
     int *h_status = nullptr;     // pinned, 4 per droplet
     double *obs_scr = nullptr;   // scratch of the mesh observation kernels
     int64_t obs_scr_n = 0;
@@ -500,11 +501,16 @@ int enqueue_step(iblb_ctx *c, int par, bool forces_only)
         return prof && on ? cudaEventRecordWithFlags(c->ph[k], s, cudaEventRecordExternal) : cudaSuccess;
     };
     CK(mark(0));
-    if (nodes)
-        CK(launch_node_force(a, s));
-    CK(mark(1));
-    if (nodes)
-        CK(launch_spread(a, s));
+    if (nodes && c->fused_ib) {
+        CK(launch_ib_front(a, c->cfg.ib_blocks_per_sm, s));     // forces and spread: both in the forces phase
+        CK(mark(1));
+    } else {
+        if (nodes)
+            CK(launch_node_force(a, s));
+        CK(mark(1));
+        if (nodes)
+            CK(launch_spread(a, s));
+    }
     CK(mark(2));
     if (nodes && c->any_vartau)
         CK(launch_inout(a, s));
@@ -513,12 +519,17 @@ int enqueue_step(iblb_ctx *c, int par, bool forces_only)
         return IBLB_OK;
     CK(launch_lb(a, c->storage, c->fbuf[par], c->fbuf[par ^ 1], nodes && c->any_vartau, c->cfg, s));
     CK(mark(4));
-    if (nodes)
-        CK(launch_interp_advect(a, s));
-    CK(mark(5));
-    if (nodes && c->any_volcorr) {
-        CK(launch_mesh_reduce(a, c->n_red_chunks, s));
-        CK(launch_volume_correct(a, s));
+    if (nodes && c->fused_ib) {
+        CK(launch_ib_back(a, c->n_red_chunks, c->any_volcorr, c->cfg.ib_blocks_per_sm, s));   // advection, volume correction
+        CK(mark(5));
+    } else {
+        if (nodes)
+            CK(launch_interp_advect(a, s));
+        CK(mark(5));
+        if (nodes && c->any_volcorr) {
+            CK(launch_mesh_reduce(a, c->n_red_chunks, s));
+            CK(launch_volume_correct(a, s));
+        }
     }
     CK(mark(6));
     return IBLB_OK;
@@ -686,7 +697,8 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
         (e = dalloc(&A.n_active, 2)) != cudaSuccess || (e = dalloc(&A.active, 2 * (size_t)T)) != cudaSuccess ||
         (e = dalloc(&A.bin_cnt, (size_t)T)) != cudaSuccess ||
         (e = dalloc(&A.tile_list, (size_t)T * TILE_CAP)) != cudaSuccess ||
-        (e = dalloc(&A.spread_done, 1)) != cudaSuccess ||
+        (e = dalloc(&A.spread_done, 1)) != cudaSuccess || (e = dalloc(&A.bar_count, 1)) != cudaSuccess ||
+        (e = dalloc(&A.bar_flag, 1)) != cudaSuccess ||
         (e = dalloc(&A.col_cnt, (size_t)A.total_cols)) != cudaSuccess ||
         (e = dalloc(&A.col_z, (size_t)A.total_cols * MAXC)) != cudaSuccess ||
         (e = dalloc(&A.mass_part, (size_t)c->mass_blocks)) != cudaSuccess ||
@@ -702,6 +714,8 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
         (e = cudaMemcpyAsync(A.gen, &one, sizeof(one), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.n_active, 0, 2 * sizeof(int), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.spread_done, 0, sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.bar_count, 0, sizeof(unsigned), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.bar_flag, 0, sizeof(unsigned), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.bin_cnt, 0, sizeof(int) * T, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.col_cnt, 0, sizeof(int) * A.total_cols, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.status, 0, sizeof(int) * 4 * n, s)) != cudaSuccess ||
@@ -741,6 +755,8 @@ void iblb_destroy(iblb_ctx *c)
     dfree(A.bin_cnt);
     dfree(A.tile_list);
     dfree(A.spread_done);
+    dfree(A.bar_count);
+    dfree(A.bar_flag);
     dfree(A.col_cnt);
     dfree(A.col_z);
     dfree(A.mass_part);
@@ -1142,6 +1158,16 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
         invalidate_graphs(c);
         return upload_drops(c);
     }
+    case IBLB_OPT_FUSED_IB:
+        c->fused_ib = value != 0;
+        invalidate_graphs(c);
+        return IBLB_OK;
+    case IBLB_OPT_IB_BLOCKS_PER_SM:
+        if (value < 0 || value > 8)
+            return fail(c, IBLB_E_ARG, "membrane blocks per SM must be in [0, 8]");
+        c->cfg.ib_blocks_per_sm = value;
+        invalidate_graphs(c);
+        return IBLB_OK;
     case IBLB_OPT_LB_STAGES:
         if (value < 2 || value > 4)
             return fail(c, IBLB_E_ARG, "pipeline stages must be in [2, 4]");

@@ -2,25 +2,37 @@
 //   * nodal forces: surface tension phi_sigma,j = -sigma dA/dq_j (Sec. II B)
 //     plus the wall interaction phi_Pi,j = -(chi_j/3) Pi(h_j) n_j (Sec. II C);
 //     8 lanes per node share its incident faces, partial sums meet in a fixed
-//     shuffle tree;
+//     shuffle tree; every node is listed in the 4^3 tiles its 4x4x4 kernel
+//     support touches (at most 8, or 27 across a partial periodic tile), and
+//     the tiles with a node form the band;
 //   * force spreading F(x) = sum_j phi_j Delta(q_j - x) (eq. force_spread) as
-//     a deterministic binned gather: every node is listed in the 4^3 tiles its
-//     4x4x4 kernel support touches (at most 8, or 27 across a partial periodic
-//     tile); the non-empty tiles form the band; every band tile gathers its
-//     nodes, orders them by node index and each cell adds their contributions
-//     in that order, so the result depends neither on launch shapes nor on the
-//     other droplets of a batch;
+//     a deterministic gather: every band tile orders its nodes by index and
+//     each cell adds their contributions in that order, so the result depends
+//     neither on launch shapes nor on the other droplets of a batch;
 //   * interpolation qdot_j = sum_x U(x) Delta(q_j - x) (eq. vel_interpolation)
-//     and forward-Euler advection q_j += qdot_j, 16 lanes per node.
+//     and forward-Euler advection q_j += qdot_j, 16 lanes per node;
+//   * the volume correction q <- c + (q - c)(V0/V)^(1/3) about the node
+//     centroid (not in the paper), FP64 volume and centroid per droplet.
+// The work runs either as separate kernels or as two cooperative kernels
+// (forces + lists + spread before the stream-collide kernel; advection +
+// volume correction after it) whose phases are separated by a grid barrier:
+// the same device functions, the same arithmetic, bit-identical results.
 // Node positions are FP64 so that edge vectors and kernel offsets are exact
 // before they are rounded to FP32 for the force and kernel arithmetic.
+#include <algorithm>
+
 #include "iblb_internal.h"
+#include "reduce_util.cuh"
 
 namespace iblb {
 
 namespace {
 
-constexpr int FL = 8;          // lanes per node in the force and fill kernels
+constexpr int FL = 8;            // lanes per node in the force computation
+constexpr int IB_THREADS = 256;  // block size of every membrane kernel
+constexpr int SPREAD_PARTS = IB_THREADS / TILE_CELLS;   // threads per cell in the spread
+constexpr int VC_RB = 256;       // threads per volume-correction chunk (= VC_ITEMS)
+constexpr long long BARRIER_CYCLES = 4000000000LL;      // ~2 s: bounded grid-barrier wait
 
 __device__ __forceinline__ float psi_near(float r)  // 0 <= r <= 1
 {
@@ -76,17 +88,16 @@ __device__ __forceinline__ int support_tiles(int b, int n, bool periodic, int *o
     return cnt;
 }
 
-// FL lanes per node; lane l takes the node's incident faces l, l + FL, ...
-// Lane 0 writes the node record; the lanes then list the node in the tiles
-// its kernel support touches: its slot in a tile's list (TILE_CAP slots per
-// tile) comes from the tile's counter, and the node that takes slot 0 stamps
-// the tile with this step's generation and appends it to the band list.
-// (Nothing in this kernel reads the generation counter's new value; the
-// spread kernel commits it.)
-__global__ void __launch_bounds__(128) node_force_kernel(Arrays a)
+// Force work item gid = FL * j + l: lane l of node j takes the node's
+// incident faces l, l + FL, ...  Lane 0 writes the node record; the lanes
+// then list the node in the tiles its kernel support touches: its slot in a
+// tile's list (TILE_CAP slots per tile) comes from the tile's counter, and
+// the node that takes slot 0 stamps the tile with the step's generation gen
+// and appends it to the band list.  All 32 lanes of a warp must take part
+// (the partial sums are combined with warp shuffles).
+__device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_t gen)
 {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = gid / FL, l = gid % FL;
+    const int j = (int)(gid / FL), l = (int)(gid % FL);
     const bool valid = j < a.total_nodes;
     float gx = 0.f, gy = 0.f, gz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, chi = 0.f;
     if (valid) {
@@ -203,8 +214,6 @@ __global__ void __launch_bounds__(128) node_force_kernel(Arrays a)
         a.rec[j] = r;
         a.clamped[j] = clamped;
     }
-    // this step's generation (committed by the spread kernel when it ends)
-    const uint32_t gen = *a.gen + 1u;
     const int cur = (int)(gen & 1u);
     for (int c = l; c < ncombo; c += FL) {
         const int ix = c % ntx, iy = (c / ntx) % nty, iz = c / (ntx * nty);
@@ -235,49 +244,55 @@ __device__ __forceinline__ int per_off(int X, int b, int n)
     return d;
 }
 
-// One 128-thread block per band tile (block-stride over the band list).  The
-// tile's nodes are staged in parallel and sorted by node index; two threads
-// per cell add the two halves of the sorted list and the halves are summed
-// in a fixed order, so every cell's force is the same for any launch shape.
-constexpr int SPREAD_THREADS = 2 * TILE_CELLS;
+// Shared memory of one spread block: the staged records of a tile's nodes.
+struct SpreadSmem {
+    int node[SPREAD_CAP];
+    short perm[SPREAD_CAP];
+    int b[3][SPREAD_CAP];
+    float w[12][SPREAD_CAP];
+    float phi[3][SPREAD_CAP];
+    float part[3][SPREAD_PARTS][TILE_CELLS];
+    int last;
+};
 
-__global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
+// Tiles of the previous band that are not in this step's band: zero their
+// force so that F vanishes outside the band (band tiles are rewritten).
+// Block bid of nb takes SPREAD_PARTS tiles per pass, 64 threads each.
+__device__ void zero_left_tiles(const Arrays &a, uint32_t gen, int cur, int bid, int nb)
 {
-    __shared__ int s_node[SPREAD_CAP];
-    __shared__ short s_perm[SPREAD_CAP];
-    __shared__ int s_b[3][SPREAD_CAP];
-    __shared__ float s_w[12][SPREAD_CAP];
-    __shared__ float s_phi[3][SPREAD_CAP];
-    __shared__ float s_part[3][TILE_CELLS];
-    const uint32_t gen = *a.gen + 1u;          // this step's generation, committed below
-    const int cur = (int)(gen & 1u);
-    const int nact = min(a.n_active[cur], a.active_cap);
-    const int *list = a.active + (int64_t)cur * a.active_cap;
     const int tid = threadIdx.x;
-    // tiles that left the band since the previous step: zero their force, so
-    // F vanishes outside this step's band (band tiles are rewritten below)
-    {
-        const int nprev = min(a.n_active[cur ^ 1], a.active_cap);
-        const int *plist = a.active + (int64_t)(cur ^ 1) * a.active_cap;
-        for (int it = blockIdx.x * 2 + (tid >> 6); it < nprev; it += gridDim.x * 2) {
-            const int64_t T = plist[it];
-            if (a.tile_gen[T] == gen)
-                continue;
-            const int d = find_drop_tile(a.drops, a.ndrops, T);
-            const Drop &D = a.drops[d];
-            const int local = (int)(T - D.tile0), cell = tid & 63;
-            const int X = 4 * (local % D.tx) + (cell & 3);
-            const int Y = 4 * ((local / D.tx) % D.ty) + ((cell >> 2) & 3);
-            const int Z = 4 * (local / (D.tx * D.ty)) + (cell >> 4);
-            if (X < D.nx && Y < D.ny && Z < D.nzf) {
-                const int64_t g = D.pcell0 + X + (int64_t)D.pitch * (Y + (int64_t)D.ny * Z);
-                a.F[g] = 0.0f;
-                a.F[a.total_pcells + g] = 0.0f;
-                a.F[2 * a.total_pcells + g] = 0.0f;
-            }
+    const int nprev = min(a.n_active[cur ^ 1], a.active_cap);
+    const int *plist = a.active + (int64_t)(cur ^ 1) * a.active_cap;
+    for (int it = bid * SPREAD_PARTS + tid / TILE_CELLS; it < nprev; it += nb * SPREAD_PARTS) {
+        const int64_t T = plist[it];
+        if (a.tile_gen[T] == gen)
+            continue;
+        const int d = find_drop_tile(a.drops, a.ndrops, T);
+        const Drop &D = a.drops[d];
+        const int local = (int)(T - D.tile0), cell = tid & (TILE_CELLS - 1);
+        const int X = 4 * (local % D.tx) + (cell & 3);
+        const int Y = 4 * ((local / D.tx) % D.ty) + ((cell >> 2) & 3);
+        const int Z = 4 * (local / (D.tx * D.ty)) + (cell >> 4);
+        if (X < D.nx && Y < D.ny && Z < D.nzf) {
+            const int64_t g = D.pcell0 + X + (int64_t)D.pitch * (Y + (int64_t)D.ny * Z);
+            a.F[g] = 0.0f;
+            a.F[a.total_pcells + g] = 0.0f;
+            a.F[2 * a.total_pcells + g] = 0.0f;
         }
     }
-    for (int it = blockIdx.x; it < nact; it += gridDim.x) {
+}
+
+// Band tiles bid, bid + nb, ...: the tile's nodes are staged in parallel and
+// sorted by node index; SPREAD_PARTS threads per cell add consecutive parts
+// of the sorted list and the parts are summed in a fixed order, so every
+// cell's force is the same for any launch shape.  The tile's counter returns
+// to zero for the next step.
+__device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, int nb, SpreadSmem &sm)
+{
+    const int tid = threadIdx.x;
+    const int nact = min(a.n_active[cur], a.active_cap);
+    const int *list = a.active + (int64_t)cur * a.active_cap;
+    for (int it = bid; it < nact; it += nb) {
         const int64_t T = list[it];
         const int d = find_drop_tile(a.drops, a.ndrops, T);
         const Drop &D = a.drops[d];
@@ -285,76 +300,81 @@ __global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
         const int X0 = 4 * (local % D.tx), Y0 = 4 * ((local / D.tx) % D.ty), Z0 = 4 * (local / (D.tx * D.ty));
         const int64_t e0 = T * TILE_CAP;
         const int cnt = min(a.bin_cnt[T], TILE_CAP);     // overflow was flagged by the force kernel
-        for (int e = tid; e < cnt; e += SPREAD_THREADS) {
+        for (int e = tid; e < cnt; e += IB_THREADS) {
             const int j = a.tile_list[e0 + e];
             const NodeRec &r = a.rec[j];
-            s_node[e] = j;
-            s_b[0][e] = r.bx;
-            s_b[1][e] = r.by;
-            s_b[2][e] = r.bz;
+            sm.node[e] = j;
+            sm.b[0][e] = r.bx;
+            sm.b[1][e] = r.by;
+            sm.b[2][e] = r.bz;
             for (int q = 0; q < 4; ++q) {
-                s_w[q][e] = r.wx[q];
-                s_w[4 + q][e] = r.wy[q];
-                s_w[8 + q][e] = r.wz[q];
+                sm.w[q][e] = r.wx[q];
+                sm.w[4 + q][e] = r.wy[q];
+                sm.w[8 + q][e] = r.wz[q];
             }
-            s_phi[0][e] = r.phi[0];
-            s_phi[1][e] = r.phi[1];
-            s_phi[2][e] = r.phi[2];
+            sm.phi[0][e] = r.phi[0];
+            sm.phi[1][e] = r.phi[1];
+            sm.phi[2][e] = r.phi[2];
         }
         __syncthreads();
         if (tid == 0)
             a.bin_cnt[T] = 0;                            // empty for the next step
         // rank sort by node index: contributions are added in increasing j
-        for (int e = tid; e < cnt; e += SPREAD_THREADS) {
-            const int key = s_node[e];
+        for (int e = tid; e < cnt; e += IB_THREADS) {
+            const int key = sm.node[e];
             int rank = 0;
             for (int k = 0; k < cnt; ++k)
-                rank += s_node[k] < key;
-            s_perm[rank] = (short)e;
+                rank += sm.node[k] < key;
+            sm.perm[rank] = (short)e;
         }
         __syncthreads();
-        const int cell = tid & (TILE_CELLS - 1), part = tid >> 6;
+        const int cell = tid & (TILE_CELLS - 1), part = tid / TILE_CELLS;
         const int X = X0 + (cell & 3), Y = Y0 + ((cell >> 2) & 3), Z = Z0 + (cell >> 4);
-        const int k0 = part ? (cnt >> 1) : 0, k1 = part ? cnt : (cnt >> 1);
+        const int k0 = (int)(((int64_t)cnt * part) / SPREAD_PARTS), k1 = (int)(((int64_t)cnt * (part + 1)) / SPREAD_PARTS);
         float fx = 0.f, fy = 0.f, fz = 0.f;
         for (int k = k0; k < k1; ++k) {
-            const int e = s_perm[k];
-            const int dx = per_off(X, s_b[0][e], D.nx);
-            const int dy = per_off(Y, s_b[1][e], D.ny);
-            const int dz = D.walls ? Z - s_b[2][e] : per_off(Z, s_b[2][e], D.nzf);
+            const int e = sm.perm[k];
+            const int dx = per_off(X, sm.b[0][e], D.nx);
+            const int dy = per_off(Y, sm.b[1][e], D.ny);
+            const int dz = D.walls ? Z - sm.b[2][e] : per_off(Z, sm.b[2][e], D.nzf);
             if (dx < -1 || dx > 2 || dy < -1 || dy > 2 || dz < -1 || dz > 2)
                 continue;
-            const float w = (s_w[dx + 1][e] * s_w[4 + dy + 1][e]) * s_w[8 + dz + 1][e];
-            fx += s_phi[0][e] * w;
-            fy += s_phi[1][e] * w;
-            fz += s_phi[2][e] * w;
+            const float w = (sm.w[dx + 1][e] * sm.w[4 + dy + 1][e]) * sm.w[8 + dz + 1][e];
+            fx += sm.phi[0][e] * w;
+            fy += sm.phi[1][e] * w;
+            fz += sm.phi[2][e] * w;
         }
-        if (part) {
-            s_part[0][cell] = fx;
-            s_part[1][cell] = fy;
-            s_part[2][cell] = fz;
-        }
+        sm.part[0][part][cell] = fx;
+        sm.part[1][part][cell] = fy;
+        sm.part[2][part][cell] = fz;
         __syncthreads();
-        if (!part && X < D.nx && Y < D.ny && Z < D.nzf) {
-            fx += s_part[0][cell];
-            fy += s_part[1][cell];
-            fz += s_part[2][cell];
+        if (part == 0 && X < D.nx && Y < D.ny && Z < D.nzf) {
+            float sx = sm.part[0][0][cell], sy = sm.part[1][0][cell], sz = sm.part[2][0][cell];
+            for (int p = 1; p < SPREAD_PARTS; ++p) {
+                sx += sm.part[0][p][cell];
+                sy += sm.part[1][p][cell];
+                sz += sm.part[2][p][cell];
+            }
             const int64_t g = D.pcell0 + X + (int64_t)D.pitch * (Y + (int64_t)D.ny * Z);
-            a.F[g] = fx;
-            a.F[a.total_pcells + g] = fy;
-            a.F[2 * a.total_pcells + g] = fz;
+            a.F[g] = sx;
+            a.F[a.total_pcells + g] = sy;
+            a.F[2 * a.total_pcells + g] = sz;
         }
         __syncthreads();
     }
-    // the last block to finish commits the generation and empties the
-    // previous step's band list, which the next step fills
-    __shared__ int s_last;
-    if (tid == 0) {
+}
+
+// The last block to finish the spread commits the generation and empties the
+// previous step's band list, which the next step fills.
+__device__ void spread_finish(const Arrays &a, uint32_t gen, int cur, SpreadSmem &sm)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
         __threadfence();
-        s_last = atomicAdd(a.spread_done, 1) == (int)gridDim.x - 1;
+        sm.last = atomicAdd(a.spread_done, 1) == (int)gridDim.x - 1;
     }
     __syncthreads();
-    if (s_last && tid == 0) {
+    if (sm.last && threadIdx.x == 0) {
         *a.gen = gen;
         a.n_active[cur ^ 1] = 0;
         *a.spread_done = 0;
@@ -363,10 +383,9 @@ __global__ void __launch_bounds__(SPREAD_THREADS) spread_kernel(Arrays a)
 
 // 16 lanes per node: lane l covers support row (dy, dz) = (l & 3, l >> 2)
 // and the four cells of that row; partial sums meet in a fixed shuffle tree.
-__global__ void __launch_bounds__(256) interp_advect_kernel(Arrays a)
+__device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
 {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = gid >> 4, l = gid & 15;
+    const int j = (int)(gid >> 4), l = (int)(gid & 15);
     const bool valid = j < a.total_nodes;
     float ax = 0.f, ay = 0.f, az = 0.f;
     int d = 0;
@@ -412,7 +431,214 @@ __global__ void __launch_bounds__(256) interp_advect_kernel(Arrays a)
     }
 }
 
+__device__ __forceinline__ int find_drop_chunk(const Drop *D, int n, int c)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (D[mid].red_chunk0 <= c)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Volume-correction chunk c (one block of VC_RB threads): faces and nodes
+// [k*VC_RB, (k+1)*VC_RB) of its droplet (k = c - chunk0) give 6V and the
+// node-coordinate sums; the chunk that finishes its droplet last folds the
+// droplet's chunks in a fixed order and stores
+// red_out = {(V0/V)^(1/3), cx, cy, cz, V}.
+__device__ void vc_chunk(const Arrays &a, int c)
+{
+    const int KIND[4] = {0, 0, 0, 0};
+    __shared__ int s_last;
+    const int d = find_drop_chunk(a.drops, a.ndrops, c);
+    const Drop &D = a.drops[d];
+    if (D.nnodes == 0 || !D.volcorr)
+        return;                                        // block-uniform
+    const int k = c - D.red_chunk0;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const int t = k * VC_RB + threadIdx.x;
+    if (t < D.ntri) {
+        const int *f = a.tri + 3 * ((int64_t)D.tri0 + t);
+        const int ia = f[0], ib = f[1], ic = f[2];
+        const double ax = a.qx[ia], ay = a.qy[ia], az = a.qz[ia];
+        const double bx = a.qx[ib], by = a.qy[ib], bz = a.qz[ib];
+        const double cx = a.qx[ic], cy = a.qy[ic], cz = a.qz[ic];
+        v[0] = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
+    }
+    if (t < D.nnodes) {
+        const int j = D.node0 + t;
+        v[1] = a.qx[j];
+        v[2] = a.qy[j];
+        v[3] = a.qz[j];
+    }
+    block_reduce<4, VC_RB>(v, KIND);
+    double *part = a.red_part + (int64_t)NRED * c;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i)
+            part[i] = v[i];
+        __threadfence();
+        s_last = atomicAdd(&a.vc_done[d], 1) == D.red_nchunks - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+        __threadfence();
+        const int lane = threadIdx.x;
+        double w[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = lane; i < D.red_nchunks; i += 32) {
+            const volatile double *p = a.red_part + (int64_t)NRED * (D.red_chunk0 + i);
+            for (int q = 0; q < 4; ++q)
+                w[q] += p[q];
+        }
+        for (int q = 0; q < 4; ++q)
+            w[q] = warp_sum(w[q]);
+        if (lane == 0) {
+            const double V = w[0] / 6.0;
+            double *o = a.red_out + (int64_t)NRED * d;
+            o[0] = cbrt(D.V0 / V);
+            o[1] = w[1] / D.nnodes;
+            o[2] = w[2] / D.nnodes;
+            o[3] = w[3] / D.nnodes;
+            o[4] = V;
+            a.vc_done[d] = 0;
+        }
+    }
+    __syncthreads();
+}
+
+// q <- c + (q - c) (V0/V)^(1/3) about the node centroid c
+__device__ __forceinline__ void vc_scale_node(const Arrays &a, int j)
+{
+    const int d = a.rec[j].spare;
+    if (!a.drops[d].volcorr)
+        return;
+    const double *r = a.red_out + (int64_t)NRED * d;
+    const double k = r[0];
+    a.qx[j] = r[1] + (a.qx[j] - r[1]) * k;
+    a.qy[j] = r[2] + (a.qy[j] - r[2]) * k;
+    a.qz[j] = r[3] + (a.qz[j] - r[3]) * k;
+}
+
+// ------------------------------------------------------------- grid barrier
+// Sense-reversing barrier over the blocks of a cooperative launch (all of
+// them resident).  `sense` is thread 0's copy of the release flag, read once
+// when the kernel starts.  The wait is bounded: a block that gives up flags
+// ST_TIMEOUT and returns false, and its caller leaves the kernel.
+__device__ bool grid_barrier(const Arrays &a, unsigned &sense)
+{
+    __shared__ int s_fail;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        sense ^= 1u;
+        __threadfence();
+        if (atomicAdd(a.bar_count, 1u) == gridDim.x - 1) {
+            *a.bar_count = 0;
+            __threadfence();
+            atomicExch(a.bar_flag, sense);
+        } else {
+            const long long t0 = clock64();
+            while (*(volatile unsigned *)a.bar_flag != sense) {
+                if (clock64() - t0 > BARRIER_CYCLES) {
+                    s_fail = 1;
+                    atomicOr(&a.status[0], ST_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return !s_fail;
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void __launch_bounds__(IB_THREADS) node_force_kernel(Arrays a)
+{
+    const uint32_t gen = *a.gen + 1u;                  // committed by the spread
+    force_item(a, (int64_t)blockIdx.x * IB_THREADS + threadIdx.x, gen);
+}
+
+__global__ void __launch_bounds__(IB_THREADS) spread_kernel(Arrays a)
+{
+    __shared__ SpreadSmem sm;
+    const uint32_t gen = *a.gen + 1u;
+    const int cur = (int)(gen & 1u);
+    zero_left_tiles(a, gen, cur, blockIdx.x, gridDim.x);
+    spread_tiles(a, gen, cur, blockIdx.x, gridDim.x, sm);
+    spread_finish(a, gen, cur, sm);
+}
+
+__global__ void __launch_bounds__(IB_THREADS) interp_advect_kernel(Arrays a)
+{
+    interp_item(a, (int64_t)blockIdx.x * IB_THREADS + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(VC_RB) vc_reduce_kernel(Arrays a) { vc_chunk(a, blockIdx.x); }
+
+__global__ void __launch_bounds__(IB_THREADS) volume_correct_kernel(Arrays a)
+{
+    const int j = blockIdx.x * IB_THREADS + threadIdx.x;
+    if (j < a.total_nodes)
+        vc_scale_node(a, j);
+}
+
+// Before the stream-collide kernel: forces and tile lists of every node,
+// grid barrier, spread of every band tile.
+__global__ void __launch_bounds__(IB_THREADS) ib_front_kernel(Arrays a)
+{
+    __shared__ SpreadSmem sm;
+    unsigned sense = *(volatile unsigned *)a.bar_flag;
+    const uint32_t gen = *a.gen + 1u;
+    const int cur = (int)(gen & 1u);
+    const int64_t nf = ((int64_t)a.total_nodes * FL + 31) & ~(int64_t)31;   // whole warps
+    const int64_t stride = (int64_t)gridDim.x * IB_THREADS;
+    for (int64_t gid = (int64_t)blockIdx.x * IB_THREADS + threadIdx.x; gid < nf; gid += stride)
+        force_item(a, gid, gen);
+    if (!grid_barrier(a, sense))
+        return;
+    zero_left_tiles(a, gen, cur, blockIdx.x, gridDim.x);
+    spread_tiles(a, gen, cur, blockIdx.x, gridDim.x, sm);
+    spread_finish(a, gen, cur, sm);
+}
+
+// After the stream-collide kernel: interpolation and advection of every
+// node; then, if some droplet corrects its volume, grid barrier, FP64 volume
+// and centroid of every droplet, grid barrier, rescale.
+__global__ void __launch_bounds__(IB_THREADS) ib_back_kernel(Arrays a, int n_chunks, int volcorr)
+{
+    unsigned sense = *(volatile unsigned *)a.bar_flag;
+    const int64_t ni = ((int64_t)a.total_nodes * 16 + 31) & ~(int64_t)31;
+    const int64_t stride = (int64_t)gridDim.x * IB_THREADS;
+    for (int64_t gid = (int64_t)blockIdx.x * IB_THREADS + threadIdx.x; gid < ni; gid += stride)
+        interp_item(a, gid);
+    if (!volcorr)
+        return;
+    if (!grid_barrier(a, sense))
+        return;
+    for (int c = blockIdx.x; c < n_chunks; c += gridDim.x)
+        vc_chunk(a, c);
+    if (!grid_barrier(a, sense))
+        return;
+    for (int64_t j = (int64_t)blockIdx.x * IB_THREADS + threadIdx.x; j < a.total_nodes; j += stride)
+        vc_scale_node(a, (int)j);
+}
+
 int g_sm_count = 0;
+int g_front_blocks = 0, g_back_blocks = 0;
+
+int sm_count()
+{
+    if (!g_sm_count) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return g_sm_count;
+}
 
 }  // namespace
 
@@ -421,7 +647,7 @@ cudaError_t launch_node_force(const Arrays &a, cudaStream_t s)
     if (a.total_nodes <= 0)
         return cudaSuccess;
     const int64_t threads = (int64_t)a.total_nodes * FL;
-    node_force_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a);
+    node_force_kernel<<<(unsigned)((threads + IB_THREADS - 1) / IB_THREADS), IB_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -429,12 +655,7 @@ cudaError_t launch_spread(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    if (!g_sm_count) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-    }
-    spread_kernel<<<g_sm_count * 5, SPREAD_THREADS, 0, s>>>(a);
+    spread_kernel<<<sm_count() * 4, IB_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -443,8 +664,76 @@ cudaError_t launch_interp_advect(const Arrays &a, cudaStream_t s)
     if (a.total_nodes <= 0)
         return cudaSuccess;
     const int64_t threads = (int64_t)a.total_nodes * 16;
-    interp_advect_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+    interp_advect_kernel<<<(unsigned)((threads + IB_THREADS - 1) / IB_THREADS), IB_THREADS, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_mesh_reduce(const Arrays &a, int n_chunks_total, cudaStream_t s)
+{
+    if (a.total_nodes <= 0 || n_chunks_total <= 0)
+        return cudaSuccess;
+    vc_reduce_kernel<<<n_chunks_total, VC_RB, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_volume_correct(const Arrays &a, cudaStream_t s)
+{
+    if (a.total_nodes <= 0)
+        return cudaSuccess;
+    volume_correct_kernel<<<(a.total_nodes + IB_THREADS - 1) / IB_THREADS, IB_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Cooperative launches: every block must be resident, so the grid is at
+// most the number of blocks that fit on the device at once; per_sm > 0 asks
+// for fewer (a grid barrier over fewer blocks is cheaper), and the grid never
+// exceeds what the work needs.
+static cudaError_t coop_grid(const void *fn, int64_t want, int per_sm_req, int &grid, int &cache)
+{
+    if (!cache) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, IB_THREADS, 0);
+        if (e != cudaSuccess)
+            return e;
+        if (per_sm < 1)
+            return cudaErrorInvalidConfiguration;
+        cache = per_sm;
+    }
+    const int per_sm = per_sm_req > 0 && per_sm_req < cache ? per_sm_req : cache;
+    const int64_t cap = (int64_t)per_sm * sm_count();
+    grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    return cudaSuccess;
+}
+
+cudaError_t launch_ib_front(const Arrays &a, int per_sm, cudaStream_t s)
+{
+    if (a.total_nodes <= 0)
+        return cudaSuccess;
+    int grid = 0;
+    const int64_t want = ((int64_t)a.total_nodes * FL + IB_THREADS - 1) / IB_THREADS;
+    cudaError_t e = coop_grid((const void *)ib_front_kernel, std::max<int64_t>(want, (int64_t)sm_count()), per_sm,
+                              grid, g_front_blocks);
+    if (e != cudaSuccess)
+        return e;
+    Arrays arg = a;
+    void *args[] = {&arg};
+    return cudaLaunchCooperativeKernel((const void *)ib_front_kernel, grid, IB_THREADS, args, 0, s);
+}
+
+cudaError_t launch_ib_back(const Arrays &a, int n_chunks_total, bool volcorr, int per_sm, cudaStream_t s)
+{
+    if (a.total_nodes <= 0)
+        return cudaSuccess;
+    int grid = 0;
+    const int64_t want = ((int64_t)a.total_nodes * 16 + IB_THREADS - 1) / IB_THREADS;
+    cudaError_t e = coop_grid((const void *)ib_back_kernel, std::max<int64_t>(want, n_chunks_total), per_sm, grid,
+                              g_back_blocks);
+    if (e != cudaSuccess)
+        return e;
+    Arrays arg = a;
+    int nc = n_chunks_total, vc = volcorr ? 1 : 0;
+    void *args[] = {&arg, &nc, &vc};
+    return cudaLaunchCooperativeKernel((const void *)ib_back_kernel, grid, IB_THREADS, args, 0, s);
 }
 
 }  // namespace iblb

@@ -92,6 +92,8 @@ struct Arrays {
     int *bin_cnt;                  // total_tiles: nodes listed in this step (returns to 0 in the spread)
     int *tile_list;                // TILE_CAP * total_tiles: node indices per tile, arrival order
     int *spread_done;              // blocks of the spread kernel finished (returns to 0)
+    unsigned *bar_count;           // grid barrier of the cooperative kernels: arrivals
+    unsigned *bar_flag;            // and release flag (flips at every barrier)
     // membrane
     double *qx, *qy, *qz;          // node positions (FP64)
     int *node_drop;                // droplet of each node
@@ -124,6 +126,7 @@ struct LaunchCfg {
     int lb_row_mult;               // cell rows per group = lb_row_mult * lb_rows_per_group(nx)
     int sm_count;
     int lb_stages;                 // shared-memory stages of the stream-collide pipeline (2..4)
+    int ib_blocks_per_sm;          // blocks per SM of the cooperative membrane kernels (0: all that fit)
 };
 int lb_rows_per_group(int nx);     // 256-thread groups: max(1, 256 / nx) rows
 // bytes of one stage of the stream-collide kernel: a 128-byte group header,
@@ -136,6 +139,10 @@ cudaError_t launch_node_force(const Arrays &a, cudaStream_t s);
 cudaError_t launch_spread(const Arrays &a, cudaStream_t s);
 cudaError_t launch_inout(const Arrays &a, cudaStream_t s);
 cudaError_t launch_interp_advect(const Arrays &a, cudaStream_t s);
+// cooperative kernels: forces + tile lists + spread; advection + volume correction
+// (per_sm: resident blocks per SM of the cooperative grid, 0 = as many as fit)
+cudaError_t launch_ib_front(const Arrays &a, int per_sm, cudaStream_t s);
+cudaError_t launch_ib_back(const Arrays &a, int n_chunks_total, bool volcorr, int per_sm, cudaStream_t s);
 cudaError_t launch_mesh_reduce(const Arrays &a, int n_chunks_total, cudaStream_t s);
 cudaError_t launch_volume_correct(const Arrays &a, cudaStream_t s);
 cudaError_t launch_mass(const Arrays &a, int storage, const void *f, double *d_out, int mass_blocks,

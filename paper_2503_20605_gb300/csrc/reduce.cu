@@ -1,7 +1,6 @@
 // reduce.cu -- FP64 reductions over the membrane and the lattice:
 //   * mesh volume V = (1/6) sum_t q_a . (q_b x q_c), area, node centroid,
 //     z_min and z_max (the half-height l = (z_max - z_min)/2 of App. C, eq. ell);
-//   * the volume correction q <- c + (q - c)(V0/V)^(1/3) (not in the paper);
 //   * contact-radius protocols (i) and (ii) of Sec. III B;
 //   * lattice mass sum_x sum_i f_i.
 // Every reduction uses a fixed assignment of items to threads and a fixed
@@ -10,6 +9,7 @@
 #include <math.h>
 
 #include "iblb_internal.h"
+#include "reduce_util.cuh"
 
 namespace iblb {
 
@@ -24,48 +24,6 @@ struct MeshView {
 namespace {
 
 constexpr int RB = 256;          // threads per reduction block
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o >= 1; o >>= 1)
-        v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_min(double v)
-{
-    for (int o = 16; o >= 1; o >>= 1)
-        v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v)
-{
-    for (int o = 16; o >= 1; o >>= 1)
-        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Reduce NV values per thread over a block of RB threads; kind[k]: 0 sum,
-// 1 min, 2 max.  Result valid in thread 0.
-template <int NV>
-__device__ void block_reduce(double *v, const int *kind)
-{
-    __shared__ double sh[NV][RB / 32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int k = 0; k < NV; ++k) {
-        double x = kind[k] == 0 ? warp_sum(v[k]) : (kind[k] == 1 ? warp_min(v[k]) : warp_max(v[k]));
-        if (lane == 0)
-            sh[k][w] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int k = 0; k < NV; ++k) {
-            double x = sh[k][0];
-            for (int i = 1; i < RB / 32; ++i)
-                x = kind[k] == 0 ? x + sh[k][i] : (kind[k] == 1 ? fmin(x, sh[k][i]) : fmax(x, sh[k][i]));
-            v[k] = x;
-        }
-    __syncthreads();
-}
 
 // chunk k of a mesh: faces [k*RED_FACES, ...) and nodes [k*RED_NODES, ...)
 // -> 6V, area, sum x, sum y, sum z, z_min, z_max
@@ -94,88 +52,10 @@ __device__ void pass1_chunk(const MeshView &m, int k, double *out)
         v[5] = fmin(v[5], z);
         v[6] = fmax(v[6], z);
     }
-    block_reduce<7>(v, KIND);
+    block_reduce<7, RB>(v, KIND);
     if (threadIdx.x == 0)
         for (int i = 0; i < 7; ++i)
             out[i] = v[i];
-}
-
-__device__ __forceinline__ int find_drop_chunk(const Drop *D, int n, int c)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (D[mid].red_chunk0 <= c)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-
-// Volume-correction reduction of every droplet in one launch: block c takes
-// faces and nodes [k*RB, (k+1)*RB) of its droplet (k = c - chunk0) and
-// writes 6V and the node-coordinate sums; the last block of a droplet to
-// finish folds that droplet's chunks in a fixed order and stores
-// red_out = {(V0/V)^(1/3), cx, cy, cz, V}.
-__global__ void __launch_bounds__(RB) vc_reduce_kernel(Arrays a)
-{
-    const int KIND[4] = {0, 0, 0, 0};
-    __shared__ int s_last;
-    const int c = blockIdx.x;
-    const int d = find_drop_chunk(a.drops, a.ndrops, c);
-    const Drop &D = a.drops[d];
-    if (D.nnodes == 0 || !D.volcorr)
-        return;
-    const int k = c - D.red_chunk0;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    const int t = k * RB + threadIdx.x;
-    if (t < D.ntri) {
-        const int *f = a.tri + 3 * ((int64_t)D.tri0 + t);
-        const int ia = f[0], ib = f[1], ic = f[2];
-        const double ax = a.qx[ia], ay = a.qy[ia], az = a.qz[ia];
-        const double bx = a.qx[ib], by = a.qy[ib], bz = a.qz[ib];
-        const double cx = a.qx[ic], cy = a.qy[ic], cz = a.qz[ic];
-        v[0] = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
-    }
-    if (t < D.nnodes) {
-        const int j = D.node0 + t;
-        v[1] = a.qx[j];
-        v[2] = a.qy[j];
-        v[3] = a.qz[j];
-    }
-    block_reduce<4>(v, KIND);
-    double *part = a.red_part + (int64_t)NRED * c;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < 4; ++i)
-            part[i] = v[i];
-        __threadfence();
-        s_last = atomicAdd(&a.vc_done[d], 1) == D.red_nchunks - 1;
-    }
-    __syncthreads();
-    if (!s_last || threadIdx.x >= 32)
-        return;
-    __threadfence();
-    const int lane = threadIdx.x;
-    double w[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = lane; i < D.red_nchunks; i += 32) {
-        const volatile double *p = a.red_part + (int64_t)NRED * (D.red_chunk0 + i);
-        for (int q = 0; q < 4; ++q)
-            w[q] += p[q];
-    }
-    for (int q = 0; q < 4; ++q)
-        w[q] = warp_sum(w[q]);
-    if (lane == 0) {
-        const double V = w[0] / 6.0;
-        double *o = a.red_out + (int64_t)NRED * d;
-        o[0] = cbrt(D.V0 / V);
-        o[1] = w[1] / D.nnodes;
-        o[2] = w[2] / D.nnodes;
-        o[3] = w[3] / D.nnodes;
-        o[4] = V;
-        a.vc_done[d] = 0;
-    }
 }
 
 // Fold the chunks of droplet blockIdx.x (one warp; chunk i goes to lane i % 32,
@@ -205,22 +85,6 @@ __device__ void fold_chunks(const double *part, int nch, int nnodes, double *out
         out[5] = v[5];
         out[6] = v[6];
     }
-}
-
-// q <- c + (q - c) (V0/V)^(1/3) about the node centroid c
-__global__ void volume_correct_kernel(Arrays a)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.total_nodes)
-        return;
-    const int d = a.rec[j].spare;
-    if (!a.drops[d].volcorr)
-        return;
-    const double *r = a.red_out + (int64_t)NRED * d;
-    const double k = r[0];
-    a.qx[j] = r[1] + (a.qx[j] - r[1]) * k;
-    a.qy[j] = r[2] + (a.qy[j] - r[2]) * k;
-    a.qz[j] = r[3] + (a.qz[j] - r[3]) * k;
 }
 
 // --- observation of one mesh (view), used by iblb_observe and the stateless
@@ -277,7 +141,7 @@ __global__ void __launch_bounds__(RB) pass2_view_kernel(MeshView m, const double
             }
         }
     }
-    block_reduce<4>(v, KIND);
+    block_reduce<4, RB>(v, KIND);
     if (threadIdx.x == 0)
         for (int i = 0; i < 4; ++i)
             part[4 * k + i] = v[i];
@@ -305,7 +169,7 @@ __global__ void __launch_bounds__(RB) pass3_view_kernel(MeshView m, double zp, c
             const double py = ya + s * (m.qy[ib * m.stride] - ya) - cy;
             v[0] += sqrt(px * px + py * py);
         }
-    block_reduce<1>(v, KIND);
+    block_reduce<1, RB>(v, KIND);
     if (threadIdx.x == 0)
         part[k] = v[0];
 }
@@ -364,7 +228,7 @@ __global__ void __launch_bounds__(RB) mass_kernel(Arrays a, const S *f)
         for (int i = 0; i < Q; ++i)
             v[0] += tod<S>(p[(int64_t)i * D.pcells]);
     }
-    block_reduce<1>(v, KIND);
+    block_reduce<1, RB>(v, KIND);
     if (threadIdx.x == 0)
         a.mass_part[b] = v[0];
 }
@@ -382,21 +246,6 @@ __global__ void mass_fold_kernel(Arrays a, double *out)
 
 }  // namespace
 
-cudaError_t launch_mesh_reduce(const Arrays &a, int n_chunks_total, cudaStream_t s)
-{
-    if (a.total_nodes <= 0)
-        return cudaSuccess;
-    vc_reduce_kernel<<<n_chunks_total, RB, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_volume_correct(const Arrays &a, cudaStream_t s)
-{
-    if (a.total_nodes <= 0)
-        return cudaSuccess;
-    volume_correct_kernel<<<(a.total_nodes + 255) / 256, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
 
 // scratch: at least NRED*nch + 32 + 4*nch + nch doubles
 static cudaError_t observe_view(const MeshView &m, double R0, double zcut_frac, double eps_flat,
