@@ -209,6 +209,10 @@ def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_FUSED_IB, IB_SHAPE["fused"])
         if "bps" in IB_SHAPE:
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_IB_BLOCKS_PER_SM, IB_SHAPE["bps"])
+        if "split" in IB_SHAPE:
+            iblb.iblb_set_option(ctx, iblb.IBLB_OPT_SPLIT_LB, IB_SHAPE["split"])
+        if "far_bps" in IB_SHAPE:
+            iblb.iblb_set_option(ctx, iblb.IBLB_OPT_LB_FAR_BLOCKS_PER_SM, IB_SHAPE["far_bps"])
         if autotune and not LB_SHAPE:
             iblb.iblb_autotune(ctx, os.path.join(ROOT, "paper_2503_20605_gb300", "_build", "autotune.txt"))
         def timed(mode, n):
@@ -359,6 +363,8 @@ def main():
     ap.add_argument("--lb-row-mult", type=int, default=0,
                     help="stream-collide rows per group multiple (implies --no-autotune)")
     ap.add_argument("--fused-ib", type=int, default=-1, help="1/0: cooperative or separate membrane kernels")
+    ap.add_argument("--split-lb", type=int, default=-1, help="1/0: far stream-collide groups on a second stream")
+    ap.add_argument("--lb-far-blocks-per-sm", type=int, default=-1, help="blocks per SM of the far groups")
     ap.add_argument("--ib-blocks-per-sm", type=int, default=-1, help="blocks per SM of the cooperative kernels")
     ap.add_argument("--lb-stages", type=int, default=0,
                     help="stream-collide pipeline stages 2..4 (implies --no-autotune)")
@@ -381,6 +387,10 @@ def main():
         IB_SHAPE["fused"] = args.fused_ib
     if args.ib_blocks_per_sm >= 0:
         IB_SHAPE["bps"] = args.ib_blocks_per_sm
+    if args.split_lb >= 0:
+        IB_SHAPE["split"] = args.split_lb
+    if args.lb_far_blocks_per_sm >= 0:
+        IB_SHAPE["far_bps"] = args.lb_far_blocks_per_sm
     spec = I.workload_statics_128(90.0, args.storage)
     rank, world, local = dist_env()
     workload = "statics droplet 128^3 (D3Q19 tau=1, walls z, L5 icosphere 10242 nodes, R=24, sigma=0.005, " \

@@ -152,6 +152,16 @@ typedef struct {
                                  either way; on GB300 the separate kernels are faster. */
 #define IBLB_OPT_IB_BLOCKS_PER_SM 6 /* blocks per SM of the two cooperative membrane
                                  kernels (0..8; 0 = as many as fit; default 1)           */
+#define IBLB_OPT_SPLIT_LB 7   /* 1: stream-collide groups whose rows cannot meet the
+                                 step's band (more than one tile row from the previous
+                                 step's band) run on a second stream while the membrane
+                                 kernels compute the forces; the others run after the
+                                 spread.  0 (default): one stream-collide launch after
+                                 the spread.  Results are bit-identical; on GB300 the
+                                 two launches compete for the SMs and gain nothing.    */
+#define IBLB_OPT_LB_FAR_BLOCKS_PER_SM 8 /* resident blocks per SM of those far groups
+                                 (0..8; 0 = as many as fit; default 1, which leaves room
+                                 for the membrane kernels)                               */
 
 typedef struct iblb_ctx iblb_ctx;
 

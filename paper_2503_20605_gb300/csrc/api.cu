@@ -63,6 +63,10 @@ struct iblb_ctx {
     double *d_mass = nullptr;
     cudaStream_t user = nullptr, stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t side = nullptr;   // stream-collide of the groups far from the band
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool split_lb = false;         // run those groups concurrently with the membrane kernels
+    int lb_far_blocks_per_sm = 1;
     cudaEvent_t ph[IBLB_NPHASE + 1] = {};
     bool graphs = true;
     bool fused_ib = false;         // membrane work as two cooperative kernels
@@ -293,12 +297,13 @@ void fill_drop_params(Drop &D, const iblb_lattice_desc &l, const iblb_physics_de
 // Offsets of cells, tiles, columns, launch blocks for the current launch shape.
 void layout(iblb_ctx *c)
 {
-    int64_t cell0 = 0, tile0 = 0, col0 = 0, pcell0 = 0, row0 = 0;
+    int64_t cell0 = 0, tile0 = 0, col0 = 0, pcell0 = 0, row0 = 0, trow0 = 0;
     int lb0 = 0, mb0 = 0, stage = 0;
     const int sb = (int)storage_bytes(c->storage);
     for (auto &D : c->drops) {
         D.cell0 = cell0;
         D.tile0 = tile0;
+        D.trow0 = trow0;
         D.col0 = col0;
         // rows padded to 16 bytes of population storage (and of the float
         // force / velocity rows, whose pitch is the same)
@@ -318,6 +323,7 @@ void layout(iblb_ctx *c)
         pcell0 += D.pcells;
         row0 += (int64_t)D.ny * D.nzf;
         tile0 += D.ntiles;
+        trow0 += (int64_t)D.ty * D.tz;
         col0 += (int64_t)D.nx * D.ny;
         lb0 += D.lb_nblocks;
         mb0 += D.mass_nblocks;
@@ -326,6 +332,7 @@ void layout(iblb_ctx *c)
     c->A.total_pcells = pcell0;
     c->A.total_rows = row0;
     c->A.total_tiles = tile0;
+    c->A.total_trows = trow0;
     c->A.total_cols = col0;
     c->A.lb_blocks_total = lb0;
     c->A.lb_stage_bytes = stage;
@@ -476,6 +483,7 @@ int rebuild_membranes(iblb_ctx *c)
     CK(up(c->d_adj_start, start.data(), sizeof(int) * (N + 1)));
     CK(up(c->d_adj, adj.data(), sizeof(int) * adj.size()));
     CK(cudaMemsetAsync(c->A.bin_cnt, 0, sizeof(int) * c->A.total_tiles, c->stream));
+    CK(cudaMemsetAsync(c->A.split_ok, 0, sizeof(int), c->stream));   // no previous band for these nodes
     c->mem_dirty = false;
     int r = upload_drops(c);
     invalidate_graphs(c);
@@ -501,6 +509,20 @@ int enqueue_step(iblb_ctx *c, int par, bool forces_only)
         return prof && on ? cudaEventRecordWithFlags(c->ph[k], s, cudaEventRecordExternal) : cudaSuccess;
     };
     CK(mark(0));
+    // groups far from the band: on the side stream, concurrently with the
+    // membrane kernels (the in/out test goes first: the far groups inside a
+    // droplet need it, and the node positions are final)
+    const bool split = nodes && c->split_lb && !forces_only;
+    if (split) {
+        CK(launch_classify(a, s));
+        if (c->any_vartau)
+            CK(launch_inout(a, s));
+        CK(cudaEventRecord(c->ev_fork, s));
+        CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        CK(launch_lb(a, c->storage, c->fbuf[par], c->fbuf[par ^ 1], c->any_vartau, c->cfg, c->side,
+                     a.grp_list + a.total_rows, a.grp_cnt + 1, true, c->lb_far_blocks_per_sm));
+        CK(cudaEventRecord(c->ev_join, c->side));
+    }
     if (nodes && c->fused_ib) {
         CK(launch_ib_front(a, c->cfg.ib_blocks_per_sm, s));     // forces and spread: both in the forces phase
         CK(mark(1));
@@ -512,12 +534,16 @@ int enqueue_step(iblb_ctx *c, int par, bool forces_only)
             CK(launch_spread(a, s));
     }
     CK(mark(2));
-    if (nodes && c->any_vartau)
+    if (nodes && c->any_vartau && !split)
         CK(launch_inout(a, s));
     CK(mark(3));
     if (forces_only)
         return IBLB_OK;
-    CK(launch_lb(a, c->storage, c->fbuf[par], c->fbuf[par ^ 1], nodes && c->any_vartau, c->cfg, s));
+    if (split)   // the groups near the band, after the spread
+        CK(launch_lb(a, c->storage, c->fbuf[par], c->fbuf[par ^ 1], c->any_vartau, c->cfg, s, a.grp_list,
+                     a.grp_cnt, false));
+    else
+        CK(launch_lb(a, c->storage, c->fbuf[par], c->fbuf[par ^ 1], nodes && c->any_vartau, c->cfg, s));
     CK(mark(4));
     if (nodes && c->fused_ib) {
         CK(launch_ib_back(a, c->n_red_chunks, c->any_volcorr, c->cfg.ib_blocks_per_sm, s));   // advection, volume correction
@@ -531,6 +557,8 @@ int enqueue_step(iblb_ctx *c, int par, bool forces_only)
             CK(launch_volume_correct(a, s));
         }
     }
+    if (split)
+        CK(cudaStreamWaitEvent(s, c->ev_join, 0));
     CK(mark(6));
     return IBLB_OK;
 }
@@ -577,7 +605,7 @@ int status_code(int flags)
         return IBLB_E_TIMEOUT;
     if (flags & (ST_SPREAD_OVF | ST_COL_OVF))
         return IBLB_E_OVERFLOW;
-    if (flags & (ST_NAN | ST_JUMP | ST_ESCAPE))
+    if (flags & (ST_NAN | ST_JUMP | ST_ESCAPE | ST_BAND_MISS))
         return IBLB_E_UNSTABLE;
     return IBLB_OK;
 }
@@ -590,7 +618,8 @@ std::string status_text(int flags)
     if (flags & ST_ESCAPE) s += " a node left the fluid layers;";
     if (flags & ST_SPREAD_OVF) s += " more nodes overlap a band tile than the spread holds;";
     if (flags & ST_COL_OVF) s += " more ray crossings in a column than kept;";
-    if (flags & ST_TIMEOUT) s += " a bounded wait for a bulk copy gave up;";
+    if (flags & ST_TIMEOUT) s += " a bounded wait gave up;";
+    if (flags & ST_BAND_MISS) s += " the band moved by more than one tile row in one step;";
     return s;
 }
 
@@ -677,8 +706,12 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
     cudaDeviceGetAttribute(&c->cfg.sm_count, cudaDevAttrMultiProcessorCount, dev);
     if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bad(e, "cudaStreamCreate");
+    if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess)
+        return bad(e, "cudaStreamCreate");
     if ((e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+        (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess)
         return bad(e, "cudaEventCreate");
     for (int k = 0; k <= IBLB_NPHASE; ++k)
         if ((e = cudaEventCreate(&c->ph[k])) != cudaSuccess)
@@ -699,6 +732,10 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
         (e = dalloc(&A.tile_list, (size_t)T * TILE_CAP)) != cudaSuccess ||
         (e = dalloc(&A.spread_done, 1)) != cudaSuccess || (e = dalloc(&A.bar_count, 1)) != cudaSuccess ||
         (e = dalloc(&A.bar_flag, 1)) != cudaSuccess ||
+        (e = dalloc(&A.rowgen, (size_t)A.total_trows)) != cudaSuccess ||
+        (e = dalloc(&A.candrow, (size_t)A.total_trows)) != cudaSuccess ||
+        (e = dalloc(&A.grp_list, 2 * (size_t)A.total_rows)) != cudaSuccess ||
+        (e = dalloc(&A.grp_cnt, 3)) != cudaSuccess || (e = dalloc(&A.split_ok, 1)) != cudaSuccess ||
         (e = dalloc(&A.col_cnt, (size_t)A.total_cols)) != cudaSuccess ||
         (e = dalloc(&A.col_z, (size_t)A.total_cols * MAXC)) != cudaSuccess ||
         (e = dalloc(&A.mass_part, (size_t)c->mass_blocks)) != cudaSuccess ||
@@ -716,6 +753,10 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
         (e = cudaMemsetAsync(A.spread_done, 0, sizeof(int), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.bar_count, 0, sizeof(unsigned), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.bar_flag, 0, sizeof(unsigned), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.rowgen, 0, sizeof(uint32_t) * A.total_trows, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.candrow, 1, A.total_trows, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.grp_cnt, 0, 3 * sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.split_ok, 0, sizeof(int), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.bin_cnt, 0, sizeof(int) * T, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.col_cnt, 0, sizeof(int) * A.total_cols, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.status, 0, sizeof(int) * 4 * n, s)) != cudaSuccess ||
@@ -757,6 +798,11 @@ void iblb_destroy(iblb_ctx *c)
     dfree(A.spread_done);
     dfree(A.bar_count);
     dfree(A.bar_flag);
+    dfree(A.rowgen);
+    dfree(A.candrow);
+    dfree(A.grp_list);
+    dfree(A.grp_cnt);
+    dfree(A.split_ok);
     dfree(A.col_cnt);
     dfree(A.col_z);
     dfree(A.mass_part);
@@ -773,6 +819,12 @@ void iblb_destroy(iblb_ctx *c)
         cudaEventDestroy(c->ev_in);
     if (c->ev_out)
         cudaEventDestroy(c->ev_out);
+    if (c->ev_fork)
+        cudaEventDestroy(c->ev_fork);
+    if (c->ev_join)
+        cudaEventDestroy(c->ev_join);
+    if (c->side)
+        cudaStreamDestroy(c->side);
     if (c->stream)
         cudaStreamDestroy(c->stream);
     delete c;
@@ -835,6 +887,7 @@ int iblb_set_nodes(iblb_ctx *c, int k, const double *xyz)
     CK(cudaMemcpyAsync(c->A.qx + D.node0, x.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->A.qy + D.node0, y.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->A.qz + D.node0, z.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->A.split_ok, 0, sizeof(int), c->stream));   // the previous band says nothing now
     CK(cudaStreamSynchronize(c->stream));   // the host vectors die here
     leave(c);
     return IBLB_OK;
@@ -1160,6 +1213,16 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
     }
     case IBLB_OPT_FUSED_IB:
         c->fused_ib = value != 0;
+        invalidate_graphs(c);
+        return IBLB_OK;
+    case IBLB_OPT_SPLIT_LB:
+        c->split_lb = value != 0;
+        invalidate_graphs(c);
+        return IBLB_OK;
+    case IBLB_OPT_LB_FAR_BLOCKS_PER_SM:
+        if (value < 0 || value > 8)
+            return fail(c, IBLB_E_ARG, "blocks per SM must be in [0, 8]");
+        c->lb_far_blocks_per_sm = value;
         invalidate_graphs(c);
         return IBLB_OK;
     case IBLB_OPT_IB_BLOCKS_PER_SM:

@@ -224,6 +224,12 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
             const int slot = atomicAdd(&a.n_active[cur], 1);
             if (slot < a.active_cap)
                 a.active[(int64_t)cur * a.active_cap + slot] = (int)t;
+            // its tile row too; the stream-collide rows run before this step's
+            // band was known assumed that this row could not hold band tiles
+            const int64_t tr = D.trow0 + tys[iy] + (int64_t)D.ty * tzs[iz];
+            a.rowgen[tr] = gen;
+            if (a.grp_cnt[2] && !a.candrow[tr])
+                atomicOr(&a.status[4 * d], ST_BAND_MISS);
         }
         if (rank < TILE_CAP)
             a.tile_list[t * TILE_CAP + rank] = j;
@@ -378,6 +384,8 @@ __device__ void spread_finish(const Arrays &a, uint32_t gen, int cur, SpreadSmem
         *a.gen = gen;
         a.n_active[cur ^ 1] = 0;
         *a.spread_done = 0;
+        *a.split_ok = 1;        // this band predicts the next step's
+        a.grp_cnt[2] = 0;
     }
 }
 

@@ -29,6 +29,7 @@ constexpr int ST_SPREAD_OVF = 4;   // more than TILE_CAP nodes overlap a tile
 constexpr int ST_COL_OVF = 8;      // more than MAXC crossings in a column
 constexpr int ST_ESCAPE = 16;      // a node left the fluid in z
 constexpr int ST_TIMEOUT = 32;     // a bounded wait for a bulk copy gave up
+constexpr int ST_BAND_MISS = 64;   // a band tile lay outside the rows predicted for the step
 
 // Per-droplet descriptor (device resident, read-only in kernels).
 struct Drop {
@@ -36,6 +37,7 @@ struct Drop {
     int tx, ty, tz, ntiles;
     int64_t cell0, cells;          // first cell in the pooled (compact) cell arrays, count
     int64_t tile0;                 // first tile in the pooled tile arrays
+    int64_t trow0;                 // first tile row (ty + tyc * tz) in the pooled tile-row arrays
     int64_t col0;                  // first column (nx*ny per droplet)
     int pitch;                     // population row pitch: nx rounded up to 16 elements
     int64_t pcell0, pcells;        // population planes: first padded cell, pitch*ny*nzf
@@ -92,6 +94,14 @@ struct Arrays {
     int *bin_cnt;                  // total_tiles: nodes listed in this step (returns to 0 in the spread)
     int *tile_list;                // TILE_CAP * total_tiles: node indices per tile, arrival order
     int *spread_done;              // blocks of the spread kernel finished (returns to 0)
+    // stream-collide split: groups far from the membrane run concurrently
+    // with the membrane kernels (see classify_groups in lb.cu)
+    int64_t total_trows;           // sum of ty * tz (tile rows)
+    uint32_t *rowgen;              // per tile row: last generation that put a tile of the row in the band
+    uint8_t *candrow;              // per tile row: may hold band tiles in this step
+    int *grp_list;                 // 2 * total_rows: groups near the band | groups far from it
+    int *grp_cnt;                  // 2: their counts
+    int *split_ok;                 // 1: the previous step's band predicts this step's (else all groups near)
     unsigned *bar_count;           // grid barrier of the cooperative kernels: arrivals
     unsigned *bar_flag;            // and release flag (flips at every barrier)
     // membrane
@@ -133,8 +143,15 @@ int lb_rows_per_group(int nx);     // 256-thread groups: max(1, 256 / nx) rows
 // 19 population rows and 3 force rows per cell row (128-byte multiple)
 int lb_stage_bytes(int rows, int pitch, int storage_bytes);
 
+// Stream-collide over every group (list == nullptr) or over the groups
+// list[0 .. *count); no_force: the groups carry no force (skip the band test).
 cudaError_t launch_lb(const Arrays &a, int storage, const void *src, void *dst, bool vartau,
-                      const LaunchCfg &cfg, cudaStream_t s);
+                      const LaunchCfg &cfg, cudaStream_t s, const int *list = nullptr, const int *count = nullptr,
+                      bool no_force = false, int blocks_per_sm = -1);
+// Split the stream-collide groups of the coming step into those whose rows
+// may meet its band (within one tile row of the previous step's band) and
+// the others; also marks the tile rows that may hold band tiles.
+cudaError_t launch_classify(const Arrays &a, cudaStream_t s);
 cudaError_t launch_node_force(const Arrays &a, cudaStream_t s);
 cudaError_t launch_spread(const Arrays &a, cudaStream_t s);
 cudaError_t launch_inout(const Arrays &a, cudaStream_t s);

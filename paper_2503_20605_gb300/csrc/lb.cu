@@ -21,6 +21,8 @@
 // Memory traffic per fluid cell: 19 reads + 19 writes of the storage type
 // (152 B for FP32, 76 B for 16-bit storage); the force density is read and
 // the velocity written only on band rows.
+#include <algorithm>
+
 #include "iblb_internal.h"
 
 namespace iblb {
@@ -134,7 +136,7 @@ __device__ __forceinline__ void group_rows(const Drop &D, int g, int &y0, int &z
 // mbarrier (initialised for 32 arrivals) before issuing them.
 template <typename S>
 __device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t gen, int g, unsigned char *sbase,
-                                        uint64_t *bar)
+                                        uint64_t *bar, bool no_force)
 {
     const int lane = threadIdx.x & 31;
     const int d = find_drop_group(a.drops, a.ndrops, g);
@@ -149,9 +151,11 @@ __device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t 
     const int ky0 = y0 >> 2, nty = ((y0 + nr - 1) >> 2) - ky0 + 1;
     const int64_t trow0 = D.tile0 + (int64_t)D.tx * (ky0 + (int64_t)D.ty * (z >> 2));
     bool band = false;
-    for (int q = lane; q < nty * D.tx; q += 32)
-        band |= a.tile_gen[trow0 + q] == gen;
-    band = __any_sync(0xffffffffu, band);
+    if (!no_force) {
+        for (int q = lane; q < nty * D.tx; q += 32)
+            band |= a.tile_gen[trow0 + q] == gen;
+        band = __any_sync(0xffffffffu, band);
+    }
     const uint32_t rowb = (uint32_t)(P * sizeof(S));
     // copies of this lane: up to two pieces (source row, destination row, rows)
     int src_pop = 0, src_z = 0, y_a = 0, n_a = 0, y_b = 0, n_b = 0, d_b = 0;
@@ -216,12 +220,14 @@ __device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t 
 
 template <typename S, bool VARTAU>
 __global__ void __launch_bounds__(LB_BLOCK, 2)
-    lb_kernel(Arrays a, const S *__restrict__ src, S *__restrict__ dst, int ns)
+    lb_kernel(Arrays a, const S *__restrict__ src, S *__restrict__ dst, int ns, const int *__restrict__ list,
+              const int *__restrict__ count, int no_force)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[LB_MAX_STAGES];
     const uint32_t gen = *a.gen;
-    const int total = a.lb_blocks_total;
+    // the groups of this launch: list[0 .. *count) or all of them
+    const int total = list ? *count : a.lb_blocks_total;
     const bool producer = threadIdx.x >= LB_THREADS;
     if (threadIdx.x == 0) {
         for (int i = 0; i < ns; ++i)
@@ -232,17 +238,19 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
     // the producer keeps ns - 1 groups in flight ahead of the consumers
     if (producer)
         for (int p = 0; p < ns - 1; ++p) {
-            const int gp = blockIdx.x + p * (int)gridDim.x;
-            if (gp < total)
-                produce<S>(a, src, gen, gp, smem_raw + p * a.lb_stage_bytes, &bar[p]);
+            const int ip = blockIdx.x + p * (int)gridDim.x;
+            if (ip < total)
+                produce<S>(a, src, gen, list ? list[ip] : ip, smem_raw + p * a.lb_stage_bytes, &bar[p],
+                           no_force != 0);
         }
     // group k of this block uses stage st_i = k mod ns, barrier phase
     // (k / ns) mod 2
     int st_i = 0;
     uint32_t phase = 0;
     bool failed = false;
-    for (int g = blockIdx.x; g < total;
-         g += gridDim.x, st_i = (st_i + 1 == ns) ? 0 : st_i + 1, phase ^= (st_i == 0) ? 1u : 0u) {
+    for (int ig = blockIdx.x; ig < total;
+         ig += gridDim.x, st_i = (st_i + 1 == ns) ? 0 : st_i + 1, phase ^= (st_i == 0) ? 1u : 0u) {
+        const int g = list ? list[ig] : ig;
         // consumers wait for this group (bounded); the barrier makes the
         // outcome uniform and ends the previous group, so its stage is free
         // to be refilled
@@ -252,13 +260,14 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
             break;
         }
         if (producer) {
-            const int gn = g + (ns - 1) * (int)gridDim.x;
-            if (gn < total) {
+            const int in = ig + (ns - 1) * (int)gridDim.x;
+            if (in < total) {
+                const int gn = list ? list[in] : in;
                 const int sn = st_i ? st_i - 1 : ns - 1;      // the stage of the previous group
                 // order the generic reads of the previous group before the
                 // asynchronous writes into the same stage
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                produce<S>(a, src, gen, gn, smem_raw + sn * a.lb_stage_bytes, &bar[sn]);
+                produce<S>(a, src, gen, gn, smem_raw + sn * a.lb_stage_bytes, &bar[sn], no_force != 0);
             }
             continue;
         }
@@ -388,9 +397,9 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
 
 template <typename S>
 cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, const LaunchCfg &cfg,
-                     cudaStream_t s)
+                     cudaStream_t s, const int *list, const int *count, bool no_force, int blocks_per_sm)
 {
-    const int total = a.lb_blocks_total;
+    const int total = a.lb_blocks_total;      // at most this many groups in a list
     if (total <= 0)
         return cudaSuccess;
     const int ns = cfg.lb_stages < 2 ? 2 : (cfg.lb_stages > LB_MAX_STAGES ? LB_MAX_STAGES : cfg.lb_stages);
@@ -405,14 +414,16 @@ cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, c
         return e;
     if (per_sm < 1)
         return cudaErrorInvalidConfiguration;
-    if (cfg.lb_blocks_per_sm > 0 && cfg.lb_blocks_per_sm < per_sm)
-        per_sm = cfg.lb_blocks_per_sm;
+    const int want = blocks_per_sm >= 0 ? blocks_per_sm : cfg.lb_blocks_per_sm;
+    if (want > 0 && want < per_sm)
+        per_sm = want;
     int grid = cfg.sm_count * per_sm;
     grid = grid < total ? grid : total;
+    const int nf = no_force ? 1 : 0;
     if (vartau)
-        lb_kernel<S, true><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst, ns);
+        lb_kernel<S, true><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst, ns, list, count, nf);
     else
-        lb_kernel<S, false><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst, ns);
+        lb_kernel<S, false><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst, ns, list, count, nf);
     return cudaGetLastError();
 }
 
@@ -427,14 +438,96 @@ int lb_stage_bytes(int rows, int pitch, int sb)
 }
 
 cudaError_t launch_lb(const Arrays &a, int storage, const void *src, void *dst, bool vartau,
-                      const LaunchCfg &cfg, cudaStream_t s)
+                      const LaunchCfg &cfg, cudaStream_t s, const int *list, const int *count, bool no_force,
+                      int blocks_per_sm)
 {
     switch (storage) {
-    case 0: return launch_t<float>(a, src, dst, vartau, cfg, s);
-    case 1: return launch_t<__half>(a, src, dst, vartau, cfg, s);
-    case 2: return launch_t<__nv_bfloat16>(a, src, dst, vartau, cfg, s);
+    case 0: return launch_t<float>(a, src, dst, vartau, cfg, s, list, count, no_force, blocks_per_sm);
+    case 1: return launch_t<__half>(a, src, dst, vartau, cfg, s, list, count, no_force, blocks_per_sm);
+    case 2: return launch_t<__nv_bfloat16>(a, src, dst, vartau, cfg, s, list, count, no_force, blocks_per_sm);
     }
     return cudaErrorInvalidValue;
+}
+
+namespace {
+
+__device__ __forceinline__ int find_drop_trow(const Drop *D, int n, int64_t r)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (D[mid].trow0 <= r)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Did the previous step (generation gprev) put a tile into a tile row within
+// one row of rows ty0 .. ty1 (y wraps) and tz (z wraps without walls)?
+__device__ bool near_band(const Arrays &a, const Drop &D, int ty0, int ty1, int tz, uint32_t gprev)
+{
+    for (int dz = -1; dz <= 1; ++dz) {
+        int zz = tz + dz;
+        if (D.walls) {
+            if (zz < 0 || zz >= D.tz)
+                continue;
+        } else {
+            zz = wrapi(zz, D.tz);
+        }
+        const int ny = ty1 - ty0 + 3 < D.ty ? ty1 - ty0 + 3 : D.ty;
+        for (int k = 0; k < ny; ++k) {
+            const int yy = ny == D.ty ? k : wrapi(ty0 - 1 + k, D.ty);
+            if (a.rowgen[D.trow0 + yy + (int64_t)D.ty * zz] == gprev)
+                return true;
+        }
+    }
+    return false;
+}
+
+// One thread per tile row, then one per stream-collide group.  A node moves
+// less than half a cell per step (faster nodes stop the run with an error),
+// so a tile of the coming step's band lies within one tile of a tile of the
+// previous band: its tile row is within one row of a row that held band
+// tiles.  The groups that cross no such row carry no force in the coming
+// step and can run before its forces are known.  Without a previous band
+// (*split_ok == 0) every row and group counts as near.
+__global__ void __launch_bounds__(256) classify_kernel(Arrays a)
+{
+    const uint32_t gprev = *a.gen;
+    const bool ok = *a.split_ok != 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid == 0)
+        a.grp_cnt[2] = 1;             // the force kernel checks this step's band against candrow
+    for (int64_t r = gid; r < a.total_trows; r += stride) {
+        const Drop &D = a.drops[find_drop_trow(a.drops, a.ndrops, r)];
+        const int local = (int)(r - D.trow0);
+        const int ty = local % D.ty, tz = local / D.ty;
+        a.candrow[r] = (!ok || near_band(a, D, ty, ty, tz, gprev)) ? 1 : 0;
+    }
+    for (int64_t g = gid; g < a.lb_blocks_total; g += stride) {
+        const Drop &D = a.drops[find_drop_group(a.drops, a.ndrops, (int)g)];
+        int y0, z, nr;
+        group_rows(D, (int)g, y0, z, nr);
+        const bool near = !ok || near_band(a, D, y0 >> 2, (y0 + nr - 1) >> 2, z >> 2, gprev);
+        const int slot = atomicAdd(&a.grp_cnt[near ? 0 : 1], 1);
+        a.grp_list[(near ? 0 : a.total_rows) + slot] = (int)g;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_classify(const Arrays &a, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(a.grp_cnt, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess)
+        return e;
+    const int64_t n = a.total_trows > a.lb_blocks_total ? a.total_trows : a.lb_blocks_total;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    classify_kernel<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace iblb
