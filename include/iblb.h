@@ -321,11 +321,13 @@ int iblb_mesh_observe_dev_noalloc(const double *d_xyz, int n_nodes, const int32_
 int iblb_mesh_profile(const double *xyz, int n_nodes, double R0, int nphi, double *g);
 
 /* Deform a sphere-like closed mesh (xyz[3 * n_nodes], faces tri[3 * n_tri],
- * host) to the profile g[nphi]: each node moves along its direction from the
- * centroid to distance R0 g(phi) (g linear between samples, constant beyond
- * the end samples); the result is scaled about the centroid to the input
- * mesh's enclosed volume, centred at (cx, cy) and shifted so that its lowest
- * node is at z = z_bottom.  Writes xyz_out[3 * n_nodes].  IBLB_E_ARG /
+ * host) to the profile g[nphi]: each node moves onto the surface of
+ * revolution r = R0 g(phi) about the centroid (g linear between samples,
+ * constant beyond the end samples), keeping its azimuth and its fraction of
+ * the surface area measured from the top pole, so that nodes stay evenly
+ * spread; the result is scaled about the centroid to the input mesh's
+ * enclosed volume, centred at (cx, cy) and shifted so that its lowest node
+ * is at z = z_bottom.  Writes xyz_out[3 * n_nodes].  IBLB_E_ARG /
  * IBLB_E_MESH on bad input (non-positive g, bad indices, non-positive
  * volume). */
 int iblb_deform_mesh(const double *g, int nphi, double R0, const double *xyz, int n_nodes,

@@ -10,12 +10,16 @@ library.
   only) -- here node by node in nphi equal bins of phi; g = G / R0; a bin
   without nodes takes the linear interpolation of its nearest filled
   neighbours (the end value beyond the first or last filled bin).
-* deform(g, R0, xyz, tri, cx, cy, z_bottom): the inverse map, a star-shaped
-  surface r = R0 g(phi) built on the directions of a sphere-like mesh's
-  nodes from their centroid (g linear between the bin centres
-  phi_k = (k + 1/2) pi / nphi, constant beyond the end ones), rescaled to
-  the input mesh's enclosed volume, centred at (cx, cy), lowest node at
-  z_bottom.
+* deform(g, R0, xyz, tri, cx, cy, z_bottom): the inverse map, nodes of a
+  sphere-like mesh moved onto the star-shaped surface of revolution
+  r = R0 g(phi) (g linear between the bin centres phi_k = (k + 1/2) pi / nphi,
+  constant beyond the end ones): each node keeps its azimuth about its
+  centroid and the fraction of surface area between it and the top pole
+  ((1 - cos phi)/2 on the sphere; on the target, the area of the surface of
+  revolution, dA = 2 pi r sin(phi) sqrt(r^2 + r'^2) dphi, integrated by the
+  midpoint rule on 4096 intervals and inverted by linear interpolation);
+  then rescaled to the input mesh's enclosed volume, centred at (cx, cy),
+  lowest node at z_bottom.
 * cap_profile(theta, nphi): g of an exact spherical cap of contact angle
   theta resting on a plane, about the centroid of its surface (cap and
   base disc), for a cap of the volume of a unit sphere; by ray casting from
@@ -57,14 +61,30 @@ def profile_at(g, phi):
     return np.interp(phi, centres, g)
 
 
+def surface_area_fraction(g, R0, n=4096):
+    """Cumulative area of r = R0 g(phi) from the top pole at phi_i = pi i / n."""
+    h = np.pi / n
+    mid = (np.arange(n) + 0.5) * h
+    r = R0 * profile_at(g, mid)
+    dr = R0 * (profile_at(g, mid + 0.5 * h) - profile_at(g, mid - 0.5 * h)) / h
+    dA = 2.0 * np.pi * r * np.sin(mid) * np.sqrt(r * r + dr * dr) * h
+    return np.concatenate([[0.0], np.cumsum(dA)])
+
+
 def deform(g, R0, xyz, tri, cx, cy, z_bottom):
+    g = np.asarray(g, np.float64)
     xyz = np.asarray(xyz, np.float64)
     tri = np.asarray(tri)
     c = xyz.mean(axis=0)
     d = xyz - c
     r = np.sqrt(np.sum(d * d, axis=1))
-    phi = np.arccos(np.clip(d[:, 2] / r, -1.0, 1.0))
-    q = (R0 * profile_at(np.asarray(g, np.float64), phi) / r)[:, None] * d
+    frac = 0.5 * (1.0 - np.clip(d[:, 2] / r, -1.0, 1.0))
+    A = surface_area_fraction(g, R0)
+    n = len(A) - 1
+    phi = np.interp(frac * A[-1], A, np.pi * np.arange(n + 1) / n)
+    psi = np.arctan2(d[:, 1], d[:, 0])
+    G = R0 * profile_at(g, phi)
+    q = np.stack([G * np.sin(phi) * np.cos(psi), G * np.sin(phi) * np.sin(psi), G * np.cos(phi)], axis=1)
     s = np.cbrt(mesh_volume(d, tri) / mesh_volume(q, tri))
     q = s * q
     out = q + np.array([cx, cy, 0.0])

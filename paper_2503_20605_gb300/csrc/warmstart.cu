@@ -48,6 +48,41 @@ double profile_at(const double *g, int n, double phi)
     return (1.0 - f) * g[k] + f * g[k + 1];
 }
 
+// Cumulative area of the surface of revolution r(phi) = R0 g(phi) between the
+// pole phi = 0 and phi_i = pi i / n (i = 0 .. n), dA = 2 pi r sin(phi)
+// sqrt(r^2 + r'^2) dphi, by the midpoint rule on n intervals (r and r' of the
+// piecewise-linear profile at the interval midpoints).
+void cumulative_area(const double *g, int nphi, double R0, int n, std::vector<double> &A)
+{
+    A.assign(n + 1, 0.0);
+    const double h = M_PI / n;
+    for (int i = 0; i < n; ++i) {
+        const double phi = (i + 0.5) * h;
+        const double r = R0 * profile_at(g, nphi, phi);
+        const double dr = R0 * (profile_at(g, nphi, phi + 0.5 * h) - profile_at(g, nphi, phi - 0.5 * h)) / h;
+        A[i + 1] = A[i] + 2.0 * M_PI * r * sin(phi) * sqrt(r * r + dr * dr) * h;
+    }
+}
+
+constexpr int kAreaSteps = 4096;
+
+// polar angle on the target surface below which lies the area fraction f
+double angle_at_fraction(const std::vector<double> &A, double f)
+{
+    const int n = (int)A.size() - 1;
+    const double t = f * A[n];
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (A[mid] <= t)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const double w = A[hi] > A[lo] ? (t - A[lo]) / (A[hi] - A[lo]) : 0.0;
+    return M_PI * (lo + w) / n;
+}
+
 }  // namespace
 
 extern "C" {
@@ -125,6 +160,8 @@ int iblb_deform_mesh(const double *g, int nphi, double R0, const double *xyz, in
             c[a] += xyz[3 * (size_t)j + a];
     for (int a = 0; a < 3; ++a)
         c[a] /= n_nodes;
+    std::vector<double> area;
+    cumulative_area(g, nphi, R0, kAreaSteps, area);
     std::vector<double> q0(3 * (size_t)n_nodes), q(3 * (size_t)n_nodes);
     for (int j = 0; j < n_nodes; ++j) {
         double d[3], r = 0.0;
@@ -135,12 +172,19 @@ int iblb_deform_mesh(const double *g, int nphi, double R0, const double *xyz, in
         r = sqrt(r);
         if (!(r > 0.0))
             return wfail(IBLB_E_MESH, "iblb_deform_mesh: a node sits at the centroid");
-        const double phi = acos(fmax(-1.0, fmin(1.0, d[2] / r)));
-        const double G = R0 * profile_at(g, nphi, phi);
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < 3; ++a)
             q0[3 * (size_t)j + a] = d[a];
-            q[3 * (size_t)j + a] = G * d[a] / r;
-        }
+        // the node keeps its azimuth and its area fraction from the pole:
+        // on the unit sphere the fraction below polar angle phi is
+        // (1 - cos phi) / 2
+        const double cs = fmax(-1.0, fmin(1.0, d[2] / r));
+        const double phi = angle_at_fraction(area, 0.5 * (1.0 - cs));
+        const double rho = sqrt(d[0] * d[0] + d[1] * d[1]);
+        const double ca = rho > 0.0 ? d[0] / rho : 1.0, sa = rho > 0.0 ? d[1] / rho : 0.0;
+        const double G = R0 * profile_at(g, nphi, phi);
+        q[3 * (size_t)j] = G * sin(phi) * ca;
+        q[3 * (size_t)j + 1] = G * sin(phi) * sa;
+        q[3 * (size_t)j + 2] = G * cos(phi);
     }
     const double V0 = mesh_volume(q0, tri, n_tri), V = mesh_volume(q, tri, n_tri);
     if (!(V0 > 0.0) || !(V > 0.0))

@@ -21,7 +21,8 @@ Definitions (this project's; the paper uses no network):
     mesh at equilibrium about the node centroid (App. B parametrisation,
     64 polar samples);
   * a warm start deforms the sphere mesh to the network's predicted profile
-    at the sphere's volume, lowest node at h = xi.
+    (nodes keep their azimuth and share of the surface area) at the
+    sphere's volume, lowest node at h = xi.
 
     python -m paper_2503_20605_gb300.warmstart --train 2000 --test 200
 """
@@ -159,6 +160,15 @@ def train(x, y, epochs=2000, batch=256, lr=1e-3, seed=0, init_seed=0, stream=0):
         iblb.iblb_mlp_destroy(m)
 
 
+PARAMS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "warmstart_mlp_params.npy")
+
+
+def load_params(path=PARAMS_PATH):
+    """The trained network's parameters shipped with the package (made by
+    this module's command line; provenance in the .json beside them)."""
+    return np.load(path).astype(np.float32)
+
+
 def predict(params, x, stream=0):
     m = iblb.iblb_mlp_create(params, 256, stream)
     try:
@@ -211,6 +221,7 @@ def main(argv=None):
         "profile_rms_pred_vs_sphere_eq": float(np.sqrt(np.mean((g[both] - sph["profile"][both]) ** 2))),
         "final_loss": float(losses[-1]), "seconds": time.time() - t0,
     }
+    np.save(os.path.join(args.out, "warmstart_mlp_params.npy"), params)
     np.savez(os.path.join(args.out, "warmstart.npz"), xtr=xtr, ytr=tr["profile"], steps_tr=tr["steps"], xte=xte,
              params=params, losses=losses, g=g, sph_steps=sph["steps"], warm_steps=warm["steps"],
              sph_theta=sph["theta"], warm_theta=warm["theta"], sph_profile=sph["profile"])
