@@ -209,6 +209,8 @@ def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_FUSED_IB, IB_SHAPE["fused"])
         if "bps" in IB_SHAPE:
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_IB_BLOCKS_PER_SM, IB_SHAPE["bps"])
+        if "pdl" in IB_SHAPE:
+            iblb.iblb_set_option(ctx, iblb.IBLB_OPT_PDL, IB_SHAPE["pdl"])
         if "split" in IB_SHAPE:
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_SPLIT_LB, IB_SHAPE["split"])
         if "far_bps" in IB_SHAPE:
@@ -364,6 +366,7 @@ def main():
                     help="stream-collide rows per group multiple (implies --no-autotune)")
     ap.add_argument("--fused-ib", type=int, default=-1, help="1/0: cooperative or separate membrane kernels")
     ap.add_argument("--split-lb", type=int, default=-1, help="1/0: far stream-collide groups on a second stream")
+    ap.add_argument("--pdl", type=int, default=-1, help="1/0: programmatic dependent launch in the step")
     ap.add_argument("--lb-far-blocks-per-sm", type=int, default=-1, help="blocks per SM of the far groups")
     ap.add_argument("--ib-blocks-per-sm", type=int, default=-1, help="blocks per SM of the cooperative kernels")
     ap.add_argument("--lb-stages", type=int, default=0,
@@ -387,6 +390,8 @@ def main():
         IB_SHAPE["fused"] = args.fused_ib
     if args.ib_blocks_per_sm >= 0:
         IB_SHAPE["bps"] = args.ib_blocks_per_sm
+    if args.pdl >= 0:
+        IB_SHAPE["pdl"] = args.pdl
     if args.split_lb >= 0:
         IB_SHAPE["split"] = args.split_lb
     if args.lb_far_blocks_per_sm >= 0:

@@ -159,6 +159,11 @@ typedef struct {
                                  spread.  0 (default): one stream-collide launch after
                                  the spread.  Results are bit-identical; on GB300 the
                                  two launches compete for the SMs and gain nothing.    */
+#define IBLB_OPT_PDL 9         /* 1: the kernels of a step are launched with programmatic
+                                 dependent launch (each may start while the previous one
+                                 finishes, and waits for it before reading its results);
+                                 0 (default): plain stream order.  Bit-identical; on
+                                 GB300 it gains nothing measurable.                     */
 #define IBLB_OPT_LB_FAR_BLOCKS_PER_SM 8 /* resident blocks per SM of those far groups
                                  (0..8; 0 = as many as fit; default 1, which leaves room
                                  for the membrane kernels)                               */

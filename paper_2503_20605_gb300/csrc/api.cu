@@ -70,6 +70,7 @@ struct iblb_ctx {
     cudaEvent_t ph[IBLB_NPHASE + 1] = {};
     bool graphs = true;
     bool fused_ib = false;         // membrane work as two cooperative kernels
+    bool pdl = false;              // programmatic dependent launch between the kernels of a step
     int profile = 0;               // 0 off, 1 every phase, 2 whole step only
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     bool gvalid[2] = {false, false};
@@ -499,6 +500,7 @@ int ensure_ready(iblb_ctx *c)
 int enqueue_step(iblb_ctx *c, int par, bool forces_only)
 {
     cudaStream_t s = c->stream;
+    c->A.pdl = c->pdl && !c->fused_ib;
     const Arrays &a = c->A;
     const bool nodes = a.total_nodes > 0;
     const bool prof = c->profile;
@@ -1213,6 +1215,10 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
     }
     case IBLB_OPT_FUSED_IB:
         c->fused_ib = value != 0;
+        invalidate_graphs(c);
+        return IBLB_OK;
+    case IBLB_OPT_PDL:
+        c->pdl = value != 0;
         invalidate_graphs(c);
         return IBLB_OK;
     case IBLB_OPT_SPLIT_LB:

@@ -566,12 +566,14 @@ __device__ bool grid_barrier(const Arrays &a, unsigned &sense)
 // ------------------------------------------------------------------ kernels
 __global__ void __launch_bounds__(IB_THREADS) node_force_kernel(Arrays a)
 {
+    griddep_wait();
     const uint32_t gen = *a.gen + 1u;                  // committed by the spread
     force_item(a, (int64_t)blockIdx.x * IB_THREADS + threadIdx.x, gen);
 }
 
 __global__ void __launch_bounds__(IB_THREADS) spread_kernel(Arrays a)
 {
+    griddep_wait();
     __shared__ SpreadSmem sm;
     const uint32_t gen = *a.gen + 1u;
     const int cur = (int)(gen & 1u);
@@ -582,13 +584,19 @@ __global__ void __launch_bounds__(IB_THREADS) spread_kernel(Arrays a)
 
 __global__ void __launch_bounds__(IB_THREADS) interp_advect_kernel(Arrays a)
 {
+    griddep_wait();
     interp_item(a, (int64_t)blockIdx.x * IB_THREADS + threadIdx.x);
 }
 
-__global__ void __launch_bounds__(VC_RB) vc_reduce_kernel(Arrays a) { vc_chunk(a, blockIdx.x); }
+__global__ void __launch_bounds__(VC_RB) vc_reduce_kernel(Arrays a)
+{
+    griddep_wait();
+    vc_chunk(a, blockIdx.x);
+}
 
 __global__ void __launch_bounds__(IB_THREADS) volume_correct_kernel(Arrays a)
 {
+    griddep_wait();
     const int j = blockIdx.x * IB_THREADS + threadIdx.x;
     if (j < a.total_nodes)
         vc_scale_node(a, j);
@@ -655,16 +663,15 @@ cudaError_t launch_node_force(const Arrays &a, cudaStream_t s)
     if (a.total_nodes <= 0)
         return cudaSuccess;
     const int64_t threads = (int64_t)a.total_nodes * FL;
-    node_force_kernel<<<(unsigned)((threads + IB_THREADS - 1) / IB_THREADS), IB_THREADS, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(node_force_kernel, dim3((unsigned)((threads + IB_THREADS - 1) / IB_THREADS)), dim3(IB_THREADS), 0,
+                    s, a.pdl != 0, a);
 }
 
 cudaError_t launch_spread(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    spread_kernel<<<sm_count() * 4, IB_THREADS, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(spread_kernel, dim3(sm_count() * 4), dim3(IB_THREADS), 0, s, a.pdl != 0, a);
 }
 
 cudaError_t launch_interp_advect(const Arrays &a, cudaStream_t s)
@@ -672,24 +679,23 @@ cudaError_t launch_interp_advect(const Arrays &a, cudaStream_t s)
     if (a.total_nodes <= 0)
         return cudaSuccess;
     const int64_t threads = (int64_t)a.total_nodes * 16;
-    interp_advect_kernel<<<(unsigned)((threads + IB_THREADS - 1) / IB_THREADS), IB_THREADS, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(interp_advect_kernel, dim3((unsigned)((threads + IB_THREADS - 1) / IB_THREADS)),
+                    dim3(IB_THREADS), 0, s, a.pdl != 0, a);
 }
 
 cudaError_t launch_mesh_reduce(const Arrays &a, int n_chunks_total, cudaStream_t s)
 {
     if (a.total_nodes <= 0 || n_chunks_total <= 0)
         return cudaSuccess;
-    vc_reduce_kernel<<<n_chunks_total, VC_RB, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(vc_reduce_kernel, dim3(n_chunks_total), dim3(VC_RB), 0, s, a.pdl != 0, a);
 }
 
 cudaError_t launch_volume_correct(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    volume_correct_kernel<<<(a.total_nodes + IB_THREADS - 1) / IB_THREADS, IB_THREADS, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(volume_correct_kernel, dim3((a.total_nodes + IB_THREADS - 1) / IB_THREADS), dim3(IB_THREADS), 0, s,
+                    a.pdl != 0, a);
 }
 
 // Cooperative launches: every block must be resident, so the grid is at

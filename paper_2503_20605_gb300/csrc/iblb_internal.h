@@ -75,6 +75,7 @@ struct __align__(16) NodeRec {
 struct Arrays {
     const Drop *drops;
     int ndrops;
+    int pdl;                       // launch the kernels of the step with programmatic dependent launch
     int64_t total_cells;
     int64_t total_tiles;
     int total_nodes, total_tri;
@@ -124,6 +125,31 @@ struct Arrays {
     int *status;                   // 4 ints per droplet: flags (ST_*), -, -, -
     uint8_t *clamped;              // per node: 1 if the near-wall guard clamped it in this step
 };
+
+// Programmatic dependent launch: a kernel of the step may be launched while
+// the previous one finishes; griddep_wait() returns once the previous kernel
+// has completed and its writes are visible, and it is the first statement of
+// every kernel of the step (a no-op for a kernel launched without the
+// attribute).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch with or without programmatic dependent launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                     Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
 
 __host__ __device__ inline int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 

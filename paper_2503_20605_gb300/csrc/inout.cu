@@ -52,6 +52,7 @@ __device__ __forceinline__ double face_orient(const Arrays &a, int v0, int v1, i
 
 __global__ void clear_cols_kernel(Arrays a)
 {
+    griddep_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.total_cols)
         a.col_cnt[i] = 0;
@@ -59,6 +60,7 @@ __global__ void clear_cols_kernel(Arrays a)
 
 __global__ void face_cross_kernel(Arrays a)
 {
+    griddep_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.total_tri)
         return;
@@ -115,6 +117,7 @@ __global__ void face_cross_kernel(Arrays a)
 // insertion sort of the crossings of one column (at most MAXC values)
 __global__ void col_sort_kernel(Arrays a)
 {
+    griddep_wait();
     const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= a.total_cols)
         return;
@@ -144,9 +147,13 @@ cudaError_t launch_inout(const Arrays &a, cudaStream_t s)
     if (a.total_tri <= 0 || a.total_cols <= 0)
         return cudaSuccess;
     const unsigned cb = (unsigned)((a.total_cols + 255) / 256);
-    clear_cols_kernel<<<cb, 256, 0, s>>>(a);
-    face_cross_kernel<<<(a.total_tri + 127) / 128, 128, 0, s>>>(a);
-    col_sort_kernel<<<cb, 256, 0, s>>>(a);
+    cudaError_t e = launch_k(clear_cols_kernel, dim3(cb), dim3(256), 0, s, a.pdl != 0, a);
+    if (e == cudaSuccess)
+        e = launch_k(face_cross_kernel, dim3((a.total_tri + 127) / 128), dim3(128), 0, s, a.pdl != 0, a);
+    if (e == cudaSuccess)
+        e = launch_k(col_sort_kernel, dim3(cb), dim3(256), 0, s, a.pdl != 0, a);
+    if (e != cudaSuccess)
+        return e;
     return cudaGetLastError();
 }
 

@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[LB_MAX_STAGES];
+    griddep_wait();
     const uint32_t gen = *a.gen;
     // the groups of this launch: list[0 .. *count) or all of them
     const int total = list ? *count : a.lb_blocks_total;
@@ -421,10 +422,10 @@ cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, c
     grid = grid < total ? grid : total;
     const int nf = no_force ? 1 : 0;
     if (vartau)
-        lb_kernel<S, true><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst, ns, list, count, nf);
-    else
-        lb_kernel<S, false><<<grid, LB_BLOCK, smem, s>>>(a, (const S *)src, (S *)dst, ns, list, count, nf);
-    return cudaGetLastError();
+        return launch_k(lb_kernel<S, true>, dim3(grid), dim3(LB_BLOCK), smem, s, a.pdl != 0, a, (const S *)src,
+                        (S *)dst, ns, list, count, nf);
+    return launch_k(lb_kernel<S, false>, dim3(grid), dim3(LB_BLOCK), smem, s, a.pdl != 0, a, (const S *)src, (S *)dst,
+                    ns, list, count, nf);
 }
 
 }  // namespace

@@ -312,3 +312,22 @@ def test_split_stream_collide_bit_identical():
             iblb.iblb_destroy(b)
     for (f1, q1), (f0, q0) in zip(outs[0], outs[1]):
         assert np.array_equal(f1, f0) and np.array_equal(q1, q0)
+
+
+def test_programmatic_dependent_launch_bit_identical():
+    """Kernels launched with programmatic dependent launch wait for their
+    predecessor before reading its results: same bits as plain stream order."""
+    sp = I.workload_parity_32()
+    xyz, tri = sp.mesh()
+    outs = []
+    for pdl in (1, 0):
+        g = gpu_ctx(32, 32, 32, tau=0.9, lam=3.0, storage="f16", sigma=sp.sigma, theta=sp.theta_deg, xi=sp.xi,
+                    volume_correction=1, mesh=(xyz, tri))
+        try:
+            iblb.iblb_set_option(g, iblb.IBLB_OPT_PDL, pdl)
+            iblb.iblb_step(g, 80)
+            iblb.iblb_sync(g)
+            outs.append((iblb.iblb_get_populations(g, 0), iblb.iblb_get_nodes(g, 0)))
+        finally:
+            iblb.iblb_destroy(g)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
