@@ -1,0 +1,57 @@
+"""Pins of the axisymmetric equilibrium-shape solver (oracle/shape.py, App.
+B) against what the paper fixes independently of the solver: the exact
+spherical cap eq. gcap solves eq. YL without the wall term (to the order of
+the finite differences); the measured angle at theta_eq = pi/4, xi/R0 = 0.1
+is the 0.32 pi printed in the caption of Fig. 8 (tests/golden/paper_fig8.txt);
+the film gap matches the planar solution of App. C; the measured angle moves
+toward the imposed one as xi/R0 decreases.
+
+The 0.28 pi printed for xi/R0 = 0.01 is not pinned: on a grid uniform in u
+the solution is not yet grid-converged there (0.2499 pi with 3201 points,
+0.2534 pi with 6401), the contact-line region needing a finer local
+resolution than this solver has."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle.shape as S
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_fig8.txt")
+
+
+def _cap_residual(n_grid, theta):
+    u = np.linspace(-1.0, 1.0, n_grid)
+    g, c = S.cap_g(u, theta)
+    x = np.concatenate([g, [0.0, 2.0 / c]])
+    return np.max(np.abs(S.residual(x, u, 0.1, theta, wall=False)[:n_grid]))
+
+
+@pytest.mark.parametrize("theta", [np.pi / 4, np.pi / 2, 3 * np.pi / 4])
+def test_cap_solves_young_laplace_without_wall(theta):
+    r1, r2 = _cap_residual(401, theta), _cap_residual(801, theta)
+    assert r1 < 1e-3 and r2 < r1 / 3.5            # second-order convergence
+
+
+@pytest.fixture(scope="module")
+def sol_01():
+    return S.solve(np.pi / 4, 0.1, n_grid=401)
+
+
+def test_measured_angle_fig8(sol_01):
+    rows = np.loadtxt(GOLD)
+    want = rows[(rows[:, 0] == 0.25) & (rows[:, 1] == 0.1)][0, 2]
+    u, g, delta, k = sol_01
+    assert abs(S.angle_from_height(g) / np.pi - want) < 0.005
+    assert abs(np.trapezoid(g ** 3, u) - 2.0) < 1e-10 and abs(g[0] - g[-1]) < 1e-12
+
+
+def test_film_gap_matches_planar_solution(sol_01):
+    u, g, delta, k = sol_01
+    assert abs(delta / S.film_thickness(0.1, k, np.pi / 4) - 1.0) < 1e-4
+
+
+def test_angle_moves_toward_imposed_as_eps_shrinks(sol_01):
+    th01 = S.angle_from_height(sol_01[1])
+    th005 = S.angle_from_height(S.solve(np.pi / 4, 0.05, n_grid=1601)[1])
+    assert np.pi / 4 < th005 < th01
