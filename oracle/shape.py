@@ -180,6 +180,27 @@ def profile_phi(u, g, phi):
     return np.interp(np.cos(phi), u, g)
 
 
+def centroid_height(u, g):
+    """Height of the volume centroid above the origin of r = g(u) (R0 = 1):
+    the z-moment of the body, 2 pi int g^4 u du / 4, over its volume,
+    2 pi int g^3 du / 3 (trapezoidal in u)."""
+    return 0.75 * np.trapezoid(g ** 4 * u, u) / np.trapezoid(g ** 3, u)
+
+
+def profile_about_centroid(u, g, phi):
+    """The surface r = g(u) re-expressed as the distance G(phi) from the
+    body's volume centroid at polar angle phi about that point (the form in
+    which a simulated profile is measured: node distances from the
+    droplet's centroid)."""
+    zc = centroid_height(u, g)
+    x = g * np.sqrt(np.clip(1.0 - u * u, 0.0, None))
+    z = g * u - zc
+    r = np.hypot(x, z)
+    ph = np.arctan2(x, z)                      # 0 at the top, pi at the bottom
+    order = np.argsort(ph)
+    return np.interp(phi, ph[order], r[order])
+
+
 def e_l2(phi, g_sim, g_theo):
     """Eq. L2-error_equilibrium on samples phi (trapezoidal in phi)."""
     return np.sqrt(np.trapezoid((g_sim - g_theo) ** 2, phi) / np.trapezoid(g_theo ** 2, phi))

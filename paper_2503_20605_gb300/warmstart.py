@@ -187,6 +187,8 @@ def main(argv=None):
     ap.add_argument("--mlp-batch", type=int, default=64)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default="warmstart_results")
+    ap.add_argument("--train-data", default=None,
+                    help="train_data.npz of an earlier run: train on its equilibria instead of generating them")
     args = ap.parse_args(argv)
     import torch
     torch.cuda.init()
@@ -196,11 +198,19 @@ def main(argv=None):
     t0 = time.time()
     xtr = I.warmstart_cases(args.train, 1)
     xte = I.warmstart_cases(args.test, 2)
-    log(f"generating {args.train} training equilibria")
-    tr = generate(xtr, batch=args.batch, max_steps=args.max_steps, stream=stream, log=log)
-    ok = tr["steps"] >= 0
-    log(f"  {ok.sum()} converged ({time.time() - t0:.0f} s)")
-    np.savez(os.path.join(args.out, "train_data.npz"), x=xtr, **tr)
+    if args.train_data:
+        with np.load(args.train_data) as z:
+            tr = {k: z[k] for k in z.files if k != "x"}
+            xtr = z["x"]
+        args.train = len(xtr)
+        ok = tr["steps"] >= 0
+        log(f"{ok.sum()} of {len(xtr)} training equilibria from {args.train_data}")
+    else:
+        log(f"generating {args.train} training equilibria")
+        tr = generate(xtr, batch=args.batch, max_steps=args.max_steps, stream=stream, log=log)
+        ok = tr["steps"] >= 0
+        log(f"  {ok.sum()} converged ({time.time() - t0:.0f} s)")
+        np.savez(os.path.join(args.out, "train_data.npz"), x=xtr, **tr)
     params, losses = train(xtr[ok], tr["profile"][ok], epochs=args.epochs, batch=args.mlp_batch, lr=args.lr,
                            stream=stream)
     log(f"trained: loss {losses[0]:.3e} -> {losses[-1]:.3e} ({time.time() - t0:.0f} s)")

@@ -55,3 +55,33 @@ def test_angle_moves_toward_imposed_as_eps_shrinks(sol_01):
     th01 = S.angle_from_height(sol_01[1])
     th005 = S.angle_from_height(S.solve(np.pi / 4, 0.05, n_grid=1601)[1])
     assert np.pi / 4 < th005 < th01
+
+
+def test_profile_about_centroid_of_offset_sphere():
+    # a sphere of radius a centred a height s above the origin: r(u) = s u +
+    # sqrt(a^2 - s^2 (1 - u^2)); its centroid is its centre, about which the
+    # profile is the constant a
+    a, s = 1.3, -0.55
+    u = np.linspace(-1.0, 1.0, 4001)
+    r = s * u + np.sqrt(a * a - s * s * (1.0 - u * u))
+    assert abs(S.centroid_height(u, r) - s) < 1e-6
+    phi = np.linspace(0.0, np.pi, 97)
+    assert np.abs(S.profile_about_centroid(u, r, phi) - a).max() < 1e-6
+
+
+def test_profile_about_centroid_of_hemisphere():
+    # a unit hemisphere, flat face down at z = -1/2 (origin at mid-height):
+    # centroid 3/8 above the flat face, so the top is 5/8 and the bottom
+    # 3/8 away from it, and the rim at sqrt(1 + (3/8)^2)
+    u = np.linspace(-1.0, 1.0, 20001)
+    # ray from (0, 0) along (sqrt(1-u^2), u) hits the sphere x^2 + (z + 1/2)^2 = 1
+    # (for z >= -1/2) or the plane z = -1/2
+    b = 0.5 * u
+    t_sph = -b + np.sqrt(b * b + 0.75)
+    with np.errstate(divide="ignore"):
+        t_pl = np.where(u < 0, -0.5 / np.where(u < 0, u, -1.0), np.inf)
+    r = np.minimum(t_sph, t_pl)
+    zc = S.centroid_height(u, r)
+    assert abs(zc - (-0.5 + 0.375)) < 1e-4
+    G = S.profile_about_centroid(u, r, np.array([0.0, np.pi]))
+    assert abs(G[0] - 0.625) < 1e-4 and abs(G[1] - 0.375) < 1e-4
