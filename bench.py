@@ -370,7 +370,7 @@ def main():
     ap.add_argument("--lb-far-blocks-per-sm", type=int, default=-1, help="blocks per SM of the far groups")
     ap.add_argument("--ib-blocks-per-sm", type=int, default=-1, help="blocks per SM of the cooperative kernels")
     ap.add_argument("--lb-stages", type=int, default=0,
-                    help="stream-collide pipeline stages 2..4 (implies --no-autotune)")
+                    help="stream-collide pipeline stages 2..8 (implies --no-autotune)")
     ap.add_argument("--lb-blocks-per-sm", type=int, default=-1,
                     help="stream-collide blocks per SM, 0 = as many as fit (implies --no-autotune)")
     ap.add_argument("--no-extra", action="store_true",

@@ -143,7 +143,7 @@ typedef struct {
 #define IBLB_OPT_LB_ROW_MULT 3 /* cell rows per stream-collide group, in units of
                                  max(1, 256 / nx) rows (1..4; 0 = 1)                     */
 #define IBLB_OPT_LB_STAGES 4  /* shared-memory stages of the stream-collide pipeline:
-                                 groups in flight + 1 (2..4; default 2)                  */
+                                 the most groups in flight per block (2..8; default 2)   */
 #define IBLB_OPT_FUSED_IB 5   /* 1: the membrane work of a step runs as two cooperative
                                  kernels (forces + spread; advection + volume
                                  correction) with grid barriers between their phases,

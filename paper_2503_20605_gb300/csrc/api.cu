@@ -1238,8 +1238,8 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
         invalidate_graphs(c);
         return IBLB_OK;
     case IBLB_OPT_LB_STAGES:
-        if (value < 2 || value > 4)
-            return fail(c, IBLB_E_ARG, "pipeline stages must be in [2, 4]");
+        if (value < 2 || value > 8)
+            return fail(c, IBLB_E_ARG, "pipeline stages must be in [2, 8]");
         c->cfg.lb_stages = value;
         invalidate_graphs(c);
         return IBLB_OK;
@@ -1316,7 +1316,7 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
     int bs = c->cfg.lb_stages;
     for (int mult = 1; mult <= 4; mult *= 2)
         for (int bi = 0; bi < 2; ++bi)
-            for (int ns = 2; ns <= 4; ++ns) {
+            for (int ns = 2; ns <= 8; ++ns) {
                 c->cfg.lb_blocks_per_sm = bpsm[bi];
                 c->cfg.lb_row_mult = mult;
                 c->cfg.lb_stages = ns;

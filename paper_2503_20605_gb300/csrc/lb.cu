@@ -15,8 +15,10 @@
 // apply the x shift and the periodic x wrap inside shared memory.  Every
 // population row is read from HBM exactly once per step; the consumers
 // touch global memory only to store results.  Blocks are persistent and
-// keep a ring of 2 to 4 stages: up to three groups are in flight while the
-// current one is computed; one block barrier per group.
+// keep a ring of 2 to 8 stages with a pair of mbarriers each: "full" (the
+// bulk copies landed) and "empty" (every consumer thread finished reading).
+// The producer refills a stage as soon as it is empty, so up to ns groups
+// are in flight, and no consumer warp waits for the others.
 //
 // Memory traffic per fluid cell: 19 reads + 19 writes of the storage type
 // (152 B for FP32, 76 B for 16-bit storage); the force density is read and
@@ -32,7 +34,7 @@ namespace {
 constexpr int LB_THREADS = 256;                   // consumer threads per block
 constexpr int LB_BLOCK = LB_THREADS + 32;         // + one producer warp
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: bounded mbarrier wait
-constexpr int LB_MAX_STAGES = 4;
+constexpr int LB_MAX_STAGES = 8;
 
 __device__ __forceinline__ float cvt(float v) { return v; }
 __device__ __forceinline__ float cvt(__half v) { return __half2float(v); }
@@ -63,6 +65,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
@@ -202,21 +208,153 @@ __device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t 
     }
 }
 
-// BGK + Guo for the pair (i, opp(i)), c_opp = -c_i:  with cu = c_i.U and
-// cF = c_i.F the equilibrium offsets are  A +- B  and the sources  C +- D,
-//   A = w drho + w rho (9/2 cu^2 - 3/2 U.U),   B = 3 w rho cu,
-//   C = (1 - omega/2) w (9 cu cF - 3 U.F),     D = 3 (1 - omega/2) w cF,
-// and s*_i = s_i + omega (s_eq_i - s_i) + S_i.
-#define PAIR(i, j, A0, WR45, WR3, KW, KW3, cu_e, cF_e, si, sj)                                     \
-    {                                                                                              \
-        const float cu_ = (cu_e), cF_ = (cF_e);                                                    \
-        const float Ae = fmaf(WR45 * cu_, cu_, A0);                                                \
-        const float Be = WR3 * cu_;                                                                \
-        const float Ce = KW * fmaf(9.0f * cu_, cF_, -uF3);                                         \
-        const float De = KW3 * cF_;                                                                \
-        st(o + (i) * PC, fmaf(omega, (Ae + Be) - (si), (si)) + (Ce + De));                         \
-        st(o + (j) * PC, fmaf(omega, (Ae - Be) - (sj), (sj)) + (Ce - De));                         \
+// BGK + Guo for one group's cells.  For the pair (i, opp(i)), c_opp = -c_i,
+// with cu = c_i.U and cF = c_i.F the post-collision offsets
+// s*_i = (1 - omega) s_i + omega s_eq_i + S_i  regroup as
+//   s*_i   = (1 - omega) s_i   + P + M,
+//   s*_opp = (1 - omega) s_opp + P - M,
+//   P = w X + cu (9/2 w omega rho cu + 9 w k cF),   M = 3 w (omega rho cu + k cF),
+//   X = omega (drho - 3/2 rho U.U) - 3 k U.F,         k = 1 - omega/2,
+// (the equilibrium's even part w drho + w rho (9/2 cu^2 - 3/2 U.U) and odd
+// part 3 w rho cu, Guo's source (1 - omega/2) w (3 (c_i - U) + 9 cu c_i).F),
+// and the rest population is s*_0 = (1 - omega) s_0 + w_0 X.  FORCE false
+// is the case F = 0 (a group outside the band without a body force), where
+// every F term drops out; it rounds exactly as the FORCE path does with
+// F = 0, so a cell's result does not depend on which group shape holds it.
+template <typename S, bool VARTAU, bool FORCE>
+__device__ __forceinline__ void collide_group(const Arrays &a, const Drop &D, const Stage<S> &stg, int y0, int z,
+                                              int nr, bool band, S *__restrict__ dst)
+{
+    const int nx = D.nx, ny = D.ny, P = D.pitch, R = D.lb_rows;
+    const int PC = (int)D.pcells;
+    const int64_t pcell0 = D.pcell0;
+    const float bfx = D.bf[0], bfy = D.bf[1], bfz = D.bf[2], rho0 = D.rho0;
+    const float omega_out = D.omega_out, omega_in = D.omega_in;
+    const int vartau = D.vartau, walls = D.walls;
+    const int64_t col0 = D.col0;
+    const bool bbm = walls && z == 0;              // rows pulled from z-1 bounced at the bottom
+    const bool bbp = walls && z == D.nzf - 1;      // rows pulled from z+1 bounced at the top
+    const int RP = R * P;
+    S *outb = dst + (int64_t)Q * pcell0 + (int64_t)P * ny * z;
+    const int64_t TP = a.total_pcells;
+    float *U = a.U;
+    // cell e = r * nx + x of the group, walked without divisions
+    const int step_r = LB_THREADS / nx, step_x = LB_THREADS - step_r * nx;
+    int r = threadIdx.x / nx, x = threadIdx.x - r * nx;
+    for (; r < nr; r += step_r, x += step_x) {
+        if (x >= nx) {
+            x -= nx;
+            ++r;
+            if (r >= nr)
+                break;
+        }
+        const int y = y0 + r;
+        float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
+        if (FORCE) {
+            Fx = bfx;
+            Fy = bfy;
+            Fz = bfz;
+            if (band) {     // F vanishes outside band tiles
+                const float *Fr = stg.F + r * P + x;
+                Fx += Fr[0];
+                Fy += Fr[RP];
+                Fz += Fr[2 * RP];
+            }
+        }
+        float omega = omega_out;
+        if (VARTAU && vartau) {
+            const int64_t col = col0 + x + (int64_t)nx * y;
+            const int cnt = min(a.col_cnt[col], MAXC);
+            const double Z = (double)(z + walls);
+            int par = 0;
+            for (int q = 0; q < cnt; ++q)
+                par ^= a.col_z[col * MAXC + q] < Z;
+            if (par)
+                omega = omega_in;
+        }
+        const int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
+        const S *Rr = stg.pop + r * P;
+#define IN(i, xx) cvt(Rr[(i) * RP + (xx)])
+        const float s0 = IN(0, x);
+        const float s1 = IN(1, xm);
+        const float s2 = IN(2, xp);
+        const float s3 = IN(3, x);
+        const float s4 = IN(4, x);
+        const float s5 = IN(5, x);
+        const float s6 = IN(6, x);
+        const float s7 = IN(7, xm);
+        const float s8 = IN(8, xp);
+        const float s9 = IN(9, xm);
+        const float s10 = IN(10, xp);
+        const float s11 = IN(11, x);
+        const float s12 = IN(12, x);
+        const float s13 = IN(13, x);
+        const float s14 = IN(14, x);
+        const float s15 = IN(15, bbm ? x : xm);
+        const float s16 = IN(16, bbp ? x : xp);
+        const float s17 = IN(17, bbp ? x : xm);
+        const float s18 = IN(18, bbm ? x : xp);
+#undef IN
+        // moments (eqs. hydro_var1, hydro_var2) in offset form, from the
+        // sums and differences of opposite pairs
+        const float p1 = s1 + s2, m1 = s1 - s2, p3 = s3 + s4, m3 = s3 - s4, p5 = s5 + s6, m5 = s5 - s6;
+        const float p7 = s7 + s8, m7 = s7 - s8, p9 = s9 + s10, m9 = s9 - s10;
+        const float p11 = s11 + s12, m11 = s11 - s12, p13 = s13 + s14, m13 = s13 - s14;
+        const float p15 = s15 + s16, m15 = s15 - s16, p17 = s17 + s18, m17 = s17 - s18;
+        const float drho = ((s0 + p1) + (p3 + p5)) + ((p7 + p9) + (p11 + p13)) + (p15 + p17);
+        const float jx = ((m1 + m7) + (m9 + m15)) + m17;
+        const float jy = ((m3 + m7) - (m9 - m11)) + m13;
+        const float jz = ((m5 + m11) - (m13 - m15)) - m17;
+        const float rho = rho0 + drho;
+        const float irho = __fdividef(1.0f, rho);
+        const float ux = (FORCE ? fmaf(0.5f, Fx, jx) : jx) * irho;
+        const float uy = (FORCE ? fmaf(0.5f, Fy, jy) : jy) * irho;
+        const float uz = (FORCE ? fmaf(0.5f, Fz, jz) : jz) * irho;
+        const int64_t cell = (int64_t)P * (y + (int64_t)ny * z) + x;
+        if (FORCE && band) {
+            const int64_t gi = pcell0 + cell;
+            U[gi] = ux;
+            U[TP + gi] = uy;
+            U[2 * TP + gi] = uz;
+        }
+        const float om1 = 1.0f - omega, k = fmaf(-0.5f, omega, 1.0f), er = omega * rho;
+        float X = omega * fmaf(-1.5f * rho, fmaf(ux, ux, fmaf(uy, uy, uz * uz)), drho);
+        if (FORCE)
+            X = fmaf(-3.0f * k, fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz)), X);
+        S *o = outb + P * y + x;
+        st(o, fmaf(om1, s0, W0 * X));
+        // per weight class: b = w X, ea = 9/2 w omega rho, ec = 3 w omega rho,
+        // kf = 9 w k, kd = 3 w k
+        const float b1 = W1 * X, ea1 = (4.5f * W1) * er, ec1 = (3.0f * W1) * er;
+        const float b2 = W2 * X, ea2 = (4.5f * W2) * er, ec2 = (3.0f * W2) * er;
+        const float kf1 = (9.0f * W1) * k, kd1 = (3.0f * W1) * k, kf2 = (9.0f * W2) * k, kd2 = (3.0f * W2) * k;
+#define PAIR(i, j, b, ea, ec, kf, kd, cu_e, cF_e, si, sj)                                                 \
+        {                                                                                                \
+            const float cu_ = (cu_e);                                                                    \
+            float Pp, Mm;                                                                                \
+            if (FORCE) {                                                                                 \
+                const float cF_ = (cF_e);                                                                \
+                Mm = fmaf(ec, cu_, kd * cF_);                                                            \
+                Pp = fmaf(fmaf(ea, cu_, kf * cF_), cu_, b);                                              \
+            } else { /* unfused products: the same roundings as with F = 0 above */                    \
+                Mm = __fmul_rn(ec, cu_);                                                                 \
+                Pp = fmaf(__fmul_rn(ea, cu_), cu_, b);                                                   \
+            }                                                                                            \
+            st(o + (i) * PC, fmaf(om1, (si), Pp + Mm));                                                  \
+            st(o + (j) * PC, fmaf(om1, (sj), Pp - Mm));                                                  \
+        }
+        PAIR(1, 2, b1, ea1, ec1, kf1, kd1, ux, Fx, s1, s2);
+        PAIR(3, 4, b1, ea1, ec1, kf1, kd1, uy, Fy, s3, s4);
+        PAIR(5, 6, b1, ea1, ec1, kf1, kd1, uz, Fz, s5, s6);
+        PAIR(7, 8, b2, ea2, ec2, kf2, kd2, ux + uy, Fx + Fy, s7, s8);
+        PAIR(9, 10, b2, ea2, ec2, kf2, kd2, ux - uy, Fx - Fy, s9, s10);
+        PAIR(11, 12, b2, ea2, ec2, kf2, kd2, uy + uz, Fy + Fz, s11, s12);
+        PAIR(13, 14, b2, ea2, ec2, kf2, kd2, uy - uz, Fy - Fz, s13, s14);
+        PAIR(15, 16, b2, ea2, ec2, kf2, kd2, ux + uz, Fx + Fz, s15, s16);
+        PAIR(17, 18, b2, ea2, ec2, kf2, kd2, ux - uz, Fx - Fz, s17, s18);
+#undef PAIR
     }
+}
 
 template <typename S, bool VARTAU>
 __global__ void __launch_bounds__(LB_BLOCK, 2)
@@ -224,178 +362,76 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
               const int *__restrict__ count, int no_force)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar[LB_MAX_STAGES];
+    // full[s]: the stage's bulk copies landed (32 producer lanes arrive with
+    // the byte count); empty[s]: every consumer thread is done reading it
+    __shared__ __align__(8) uint64_t full[LB_MAX_STAGES], empty[LB_MAX_STAGES];
     griddep_wait();
     const uint32_t gen = *a.gen;
     // the groups of this launch: list[0 .. *count) or all of them
     const int total = list ? *count : a.lb_blocks_total;
-    const bool producer = threadIdx.x >= LB_THREADS;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < ns; ++i)
-            mbar_init(&bar[i], 32);
+        for (int i = 0; i < ns; ++i) {
+            mbar_init(&full[i], 32);
+            mbar_init(&empty[i], LB_THREADS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    // the producer keeps ns - 1 groups in flight ahead of the consumers
-    if (producer)
-        for (int p = 0; p < ns - 1; ++p) {
-            const int ip = blockIdx.x + p * (int)gridDim.x;
-            if (ip < total)
-                produce<S>(a, src, gen, list ? list[ip] : ip, smem_raw + p * a.lb_stage_bytes, &bar[p],
-                           no_force != 0);
-        }
-    // group k of this block uses stage st_i = k mod ns, barrier phase
-    // (k / ns) mod 2
-    int st_i = 0;
-    uint32_t phase = 0;
+    // Group k of this block (ig = blockIdx.x + k gridDim.x) goes through
+    // stage k mod ns, whose (k / ns)-th use it is.  The producer refills a
+    // stage as soon as the consumers released its previous use, so up to ns
+    // groups are in flight; each consumer warp moves on to the next group as
+    // soon as its data landed, without waiting for the other warps.
     bool failed = false;
-    for (int ig = blockIdx.x; ig < total;
-         ig += gridDim.x, st_i = (st_i + 1 == ns) ? 0 : st_i + 1, phase ^= (st_i == 0) ? 1u : 0u) {
-        const int g = list ? list[ig] : ig;
-        // consumers wait for this group (bounded); the barrier makes the
-        // outcome uniform and ends the previous group, so its stage is free
-        // to be refilled
-        const bool ok = producer || mbar_wait_bounded(&bar[st_i], phase);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
+    if (threadIdx.x >= LB_THREADS) {
+        int st_i = 0;
+        uint32_t use = 0;
+        for (int ig = blockIdx.x; ig < total; ig += gridDim.x) {
+            if (use > 0 && !mbar_wait_bounded(&empty[st_i], (use - 1) & 1u)) {
+                failed = true;
+                break;
+            }
+            // order the consumers' generic reads of the stage before the
+            // asynchronous writes into it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            produce<S>(a, src, gen, list ? list[ig] : ig, smem_raw + st_i * a.lb_stage_bytes, &full[st_i],
+                       no_force != 0);
+            if (++st_i == ns) {
+                st_i = 0;
+                ++use;
+            }
         }
-        if (producer) {
-            const int in = ig + (ns - 1) * (int)gridDim.x;
-            if (in < total) {
-                const int gn = list ? list[in] : in;
-                const int sn = st_i ? st_i - 1 : ns - 1;      // the stage of the previous group
-                // order the generic reads of the previous group before the
-                // asynchronous writes into the same stage
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                produce<S>(a, src, gen, gn, smem_raw + sn * a.lb_stage_bytes, &bar[sn], no_force != 0);
+    } else {
+        int st_i = 0;
+        uint32_t phase = 0;
+        for (int ig = blockIdx.x; ig < total; ig += gridDim.x) {
+            const int g = list ? list[ig] : ig;
+            if (!mbar_wait_bounded(&full[st_i], phase)) {
+                failed = true;
+                break;
             }
-            continue;
-        }
-
-        // the droplet's parameters, copied to registers once per group (the
-        // stores below could otherwise force reloads from the table)
-        const int d = find_drop_group(a.drops, a.ndrops, g);
-        const Drop &D = a.drops[d];
-        int y0, z, nr;
-        group_rows(D, g, y0, z, nr);
-        const int nx = D.nx, ny = D.ny, P = D.pitch, R = D.lb_rows;
-        const int PC = (int)D.pcells;
-        const int64_t pcell0 = D.pcell0;
-        const float bfx = D.bf[0], bfy = D.bf[1], bfz = D.bf[2], rho0 = D.rho0;
-        const float omega_out = D.omega_out, omega_in = D.omega_in;
-        const int vartau = D.vartau, walls = D.walls;
-        const int64_t col0 = D.col0;
-        const Stage<S> stg(smem_raw + st_i * a.lb_stage_bytes, R, P);
-        const bool band = *stg.flag != 0;
-        const bool bbm = walls && z == 0;              // rows pulled from z-1 bounced at the bottom
-        const bool bbp = walls && z == D.nzf - 1;      // rows pulled from z+1 bounced at the top
-        const int RP = R * P;
-        S *outb = dst + (int64_t)Q * pcell0 + (int64_t)P * ny * z;
-        const int64_t TP = a.total_pcells;
-        float *U = a.U;
-        // cell e = r * nx + x of the group, walked without divisions
-        const int step_r = LB_THREADS / nx, step_x = LB_THREADS - step_r * nx;
-        int r = threadIdx.x / nx, x = threadIdx.x - r * nx;
-        for (; r < nr; r += step_r, x += step_x) {
-            if (x >= nx) {
-                x -= nx;
-                ++r;
-                if (r >= nr)
-                    break;
+            const int d = find_drop_group(a.drops, a.ndrops, g);
+            const Drop &D = a.drops[d];
+            int y0, z, nr;
+            group_rows(D, g, y0, z, nr);
+            const Stage<S> stg(smem_raw + st_i * a.lb_stage_bytes, D.lb_rows, D.pitch);
+            const bool band = *stg.flag != 0;
+            if (band || D.bf[0] != 0.0f || D.bf[1] != 0.0f || D.bf[2] != 0.0f)
+                collide_group<S, VARTAU, true>(a, D, stg, y0, z, nr, band, dst);
+            else
+                collide_group<S, VARTAU, false>(a, D, stg, y0, z, nr, false, dst);
+            mbar_arrive(&empty[st_i]);
+            if (++st_i == ns) {
+                st_i = 0;
+                phase ^= 1u;
             }
-            const int y = y0 + r;
-            float Fx = bfx, Fy = bfy, Fz = bfz;
-            if (band) {     // F vanishes outside band tiles
-                const float *Fr = stg.F + r * P + x;
-                Fx += Fr[0];
-                Fy += Fr[RP];
-                Fz += Fr[2 * RP];
-            }
-            float omega = omega_out;
-            if (VARTAU && vartau) {
-                const int64_t col = col0 + x + (int64_t)nx * y;
-                const int cnt = min(a.col_cnt[col], MAXC);
-                const double Z = (double)(z + walls);
-                int par = 0;
-                for (int q = 0; q < cnt; ++q)
-                    par ^= a.col_z[col * MAXC + q] < Z;
-                if (par)
-                    omega = omega_in;
-            }
-            const int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
-            const S *Rr = stg.pop + r * P;
-#define IN(i, xx) cvt(Rr[(i) * RP + (xx)])
-            const float s0 = IN(0, x);
-            const float s1 = IN(1, xm);
-            const float s2 = IN(2, xp);
-            const float s3 = IN(3, x);
-            const float s4 = IN(4, x);
-            const float s5 = IN(5, x);
-            const float s6 = IN(6, x);
-            const float s7 = IN(7, xm);
-            const float s8 = IN(8, xp);
-            const float s9 = IN(9, xm);
-            const float s10 = IN(10, xp);
-            const float s11 = IN(11, x);
-            const float s12 = IN(12, x);
-            const float s13 = IN(13, x);
-            const float s14 = IN(14, x);
-            const float s15 = IN(15, bbm ? x : xm);
-            const float s16 = IN(16, bbp ? x : xp);
-            const float s17 = IN(17, bbp ? x : xm);
-            const float s18 = IN(18, bbm ? x : xp);
-#undef IN
-            // moments (eqs. hydro_var1, hydro_var2) in offset form, from the
-            // sums and differences of opposite pairs
-            const float p1 = s1 + s2, m1 = s1 - s2, p3 = s3 + s4, m3 = s3 - s4, p5 = s5 + s6, m5 = s5 - s6;
-            const float p7 = s7 + s8, m7 = s7 - s8, p9 = s9 + s10, m9 = s9 - s10;
-            const float p11 = s11 + s12, m11 = s11 - s12, p13 = s13 + s14, m13 = s13 - s14;
-            const float p15 = s15 + s16, m15 = s15 - s16, p17 = s17 + s18, m17 = s17 - s18;
-            const float drho = ((s0 + p1) + (p3 + p5)) + ((p7 + p9) + (p11 + p13)) + (p15 + p17);
-            const float jx = ((m1 + m7) + (m9 + m15)) + m17;
-            const float jy = ((m3 + m7) - (m9 - m11)) + m13;
-            const float jz = ((m5 + m11) - (m13 - m15)) - m17;
-            const float rho = rho0 + drho;
-            const float irho = 1.0f / rho;
-            const float ux = (jx + 0.5f * Fx) * irho;
-            const float uy = (jy + 0.5f * Fy) * irho;
-            const float uz = (jz + 0.5f * Fz) * irho;
-            const int64_t cell = (int64_t)P * (y + (int64_t)ny * z) + x;
-            if (band) {
-                const int64_t gi = pcell0 + cell;
-                U[gi] = ux;
-                U[TP + gi] = uy;
-                U[2 * TP + gi] = uz;
-            }
-            const float uu15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-            const float uF3 = 3.0f * (ux * Fx + uy * Fy + uz * Fz);
-            const float kS = 1.0f - 0.5f * omega;
-            S *o = outb + P * y + x;
-            // rest population: s_eq_0 = w0 (drho - rho 3/2 U.U), S_0 = -(1 - omega/2) w0 3 U.F
-            st(o, fmaf(omega, W0 * fmaf(-rho, uu15, drho) - s0, s0) - kS * W0 * uF3);
-            const float wr1 = 3.0f * W1 * rho, wr2 = 3.0f * W2 * rho;
-            const float a1 = fmaf(-W1 * rho, uu15, W1 * drho), a2 = fmaf(-W2 * rho, uu15, W2 * drho);
-            const float q1 = 1.5f * wr1, q2 = 1.5f * wr2;
-            const float kw1 = kS * W1, kw13 = 3.0f * kw1, kw2 = kS * W2, kw23 = 3.0f * kw2;
-            PAIR(1, 2, a1, q1, wr1, kw1, kw13, ux, Fx, s1, s2);
-            PAIR(3, 4, a1, q1, wr1, kw1, kw13, uy, Fy, s3, s4);
-            PAIR(5, 6, a1, q1, wr1, kw1, kw13, uz, Fz, s5, s6);
-            PAIR(7, 8, a2, q2, wr2, kw2, kw23, ux + uy, Fx + Fy, s7, s8);
-            PAIR(9, 10, a2, q2, wr2, kw2, kw23, ux - uy, Fx - Fy, s9, s10);
-            PAIR(11, 12, a2, q2, wr2, kw2, kw23, uy + uz, Fy + Fz, s11, s12);
-            PAIR(13, 14, a2, q2, wr2, kw2, kw23, uy - uz, Fy - Fz, s13, s14);
-            PAIR(15, 16, a2, q2, wr2, kw2, kw23, ux + uz, Fx + Fz, s15, s16);
-            PAIR(17, 18, a2, q2, wr2, kw2, kw23, ux - uz, Fx - Fz, s17, s18);
         }
     }
-    // a bounded wait gave up: flag it and leave (every block reaches this
-    // point; nothing waits on this block)
-    if (failed && threadIdx.x == 0)
+    // a bounded wait gave up: flag it and leave (a thread that leaves early
+    // makes the waits of the others on it give up in turn)
+    if (failed)
         atomicOr(&a.status[0], ST_TIMEOUT);
 }
-#undef PAIR
-
 template <typename S>
 cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, const LaunchCfg &cfg,
                      cudaStream_t s, const int *list, const int *count, bool no_force, int blocks_per_sm)
