@@ -208,6 +208,61 @@ __device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t 
     }
 }
 
+// A droplet's stream-collide constants, loaded once and kept in registers
+// while consecutive groups of the same droplet run (one droplet per launch
+// is the common case), with the thread's first cell (r0, x0) of a group.
+struct DropC {
+    int d, nx, ny, P, R, PC, nzf, walls, vartau, gpp, block0, step_r, step_x, r0, x0;
+    float inv_gpp, bfx, bfy, bfz, rho0, omega_out, omega_in;
+    bool has_bf;
+    int64_t pcell0, col0;
+    __device__ __forceinline__ void load(const Drop &D, int dd)
+    {
+        d = dd;
+        nx = D.nx;
+        ny = D.ny;
+        P = D.pitch;
+        R = D.lb_rows;
+        PC = (int)D.pcells;
+        nzf = D.nzf;
+        walls = D.walls;
+        vartau = D.vartau;
+        gpp = D.lb_gpp;
+        block0 = D.lb_block0;
+        step_r = LB_THREADS / nx;
+        step_x = LB_THREADS - step_r * nx;
+        r0 = threadIdx.x / nx;
+        x0 = threadIdx.x - r0 * nx;
+        inv_gpp = 1.0f / (float)gpp;
+        bfx = D.bf[0];
+        bfy = D.bf[1];
+        bfz = D.bf[2];
+        rho0 = D.rho0;
+        omega_out = D.omega_out;
+        omega_in = D.omega_in;
+        has_bf = bfx != 0.0f || bfy != 0.0f || bfz != 0.0f;
+        pcell0 = D.pcell0;
+        col0 = D.col0;
+    }
+    // rows y0 .. y0 + nr - 1 of plane z in group g (as group_rows, without
+    // an integer division: a float estimate of the quotient, corrected once)
+    __device__ __forceinline__ void rows(int g, int &y0, int &z, int &nr) const
+    {
+        const int lg = g - block0;
+        z = (int)((float)lg * inv_gpp);
+        int rem = lg - z * gpp;
+        if (rem < 0) {
+            --z;
+            rem += gpp;
+        } else if (rem >= gpp) {
+            ++z;
+            rem -= gpp;
+        }
+        y0 = rem * R;
+        nr = min(R, ny - y0);
+    }
+};
+
 // BGK + Guo for one group's cells.  For the pair (i, opp(i)), c_opp = -c_i,
 // with cu = c_i.U and cF = c_i.F the post-collision offsets
 // s*_i = (1 - omega) s_i + omega s_eq_i + S_i  regroup as
@@ -222,25 +277,25 @@ __device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t 
 // every F term drops out; it rounds exactly as the FORCE path does with
 // F = 0, so a cell's result does not depend on which group shape holds it.
 template <typename S, bool VARTAU, bool FORCE>
-__device__ __forceinline__ void collide_group(const Arrays &a, const Drop &D, const Stage<S> &stg, int y0, int z,
+__device__ __forceinline__ void collide_group(const Arrays &a, const DropC &c, const Stage<S> &stg, int y0, int z,
                                               int nr, bool band, S *__restrict__ dst)
 {
-    const int nx = D.nx, ny = D.ny, P = D.pitch, R = D.lb_rows;
-    const int PC = (int)D.pcells;
-    const int64_t pcell0 = D.pcell0;
-    const float bfx = D.bf[0], bfy = D.bf[1], bfz = D.bf[2], rho0 = D.rho0;
-    const float omega_out = D.omega_out, omega_in = D.omega_in;
-    const int vartau = D.vartau, walls = D.walls;
-    const int64_t col0 = D.col0;
+    const int nx = c.nx, ny = c.ny, P = c.P, R = c.R;
+    const int PC = c.PC;
+    const int64_t pcell0 = c.pcell0;
+    const float bfx = c.bfx, bfy = c.bfy, bfz = c.bfz, rho0 = c.rho0;
+    const float omega_out = c.omega_out, omega_in = c.omega_in;
+    const int vartau = c.vartau, walls = c.walls;
+    const int64_t col0 = c.col0;
     const bool bbm = walls && z == 0;              // rows pulled from z-1 bounced at the bottom
-    const bool bbp = walls && z == D.nzf - 1;      // rows pulled from z+1 bounced at the top
+    const bool bbp = walls && z == c.nzf - 1;      // rows pulled from z+1 bounced at the top
     const int RP = R * P;
     S *outb = dst + (int64_t)Q * pcell0 + (int64_t)P * ny * z;
     const int64_t TP = a.total_pcells;
     float *U = a.U;
     // cell e = r * nx + x of the group, walked without divisions
-    const int step_r = LB_THREADS / nx, step_x = LB_THREADS - step_r * nx;
-    int r = threadIdx.x / nx, x = threadIdx.x - r * nx;
+    const int step_r = c.step_r, step_x = c.step_x;
+    int r = c.r0, x = c.x0;
     for (; r < nr; r += step_r, x += step_x) {
         if (x >= nx) {
             x -= nx;
@@ -404,22 +459,25 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
     } else {
         int st_i = 0;
         uint32_t phase = 0;
+        DropC c;
+        c.d = -1;
         for (int ig = blockIdx.x; ig < total; ig += gridDim.x) {
             const int g = list ? list[ig] : ig;
+            const int d = find_drop_group(a.drops, a.ndrops, g);
+            if (d != c.d)
+                c.load(a.drops[d], d);
+            int y0, z, nr;
+            c.rows(g, y0, z, nr);
             if (!mbar_wait_bounded(&full[st_i], phase)) {
                 failed = true;
                 break;
             }
-            const int d = find_drop_group(a.drops, a.ndrops, g);
-            const Drop &D = a.drops[d];
-            int y0, z, nr;
-            group_rows(D, g, y0, z, nr);
-            const Stage<S> stg(smem_raw + st_i * a.lb_stage_bytes, D.lb_rows, D.pitch);
+            const Stage<S> stg(smem_raw + st_i * a.lb_stage_bytes, c.R, c.P);
             const bool band = *stg.flag != 0;
-            if (band || D.bf[0] != 0.0f || D.bf[1] != 0.0f || D.bf[2] != 0.0f)
-                collide_group<S, VARTAU, true>(a, D, stg, y0, z, nr, band, dst);
+            if (band || c.has_bf)
+                collide_group<S, VARTAU, true>(a, c, stg, y0, z, nr, band, dst);
             else
-                collide_group<S, VARTAU, false>(a, D, stg, y0, z, nr, false, dst);
+                collide_group<S, VARTAU, false>(a, c, stg, y0, z, nr, false, dst);
             mbar_arrive(&empty[st_i]);
             if (++st_i == ns) {
                 st_i = 0;
