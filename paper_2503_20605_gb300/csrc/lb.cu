@@ -132,17 +132,40 @@ __device__ __forceinline__ void group_rows(const Drop &D, int g, int &y0, int &z
     nr = min(D.lb_rows, D.ny - y0);
 }
 
+// Band flags of 32 consecutive groups of a block, one per lane: lane l
+// takes group ig0 + l * stride.  A group carries force iff one of the tile
+// rows its cell rows cross put a tile into this step's band (the force
+// kernel stamps the row with the step's generation; F vanishes outside band
+// tiles).  Bit l of the result is lane l's flag.
+__device__ __forceinline__ uint32_t band_ballot(const Arrays &a, const int *list, int total, int ig0, int stride,
+                                                uint32_t gen)
+{
+    const int lane = threadIdx.x & 31;
+    const int ig = ig0 + lane * stride;
+    bool band = false;
+    if (ig < total) {
+        const int g = list ? list[ig] : ig;
+        const Drop &D = a.drops[find_drop_group(a.drops, a.ndrops, g)];
+        int y0, z, nr;
+        group_rows(D, g, y0, z, nr);
+        const int64_t tr0 = D.trow0 + (int64_t)D.ty * (z >> 2);
+        for (int ty = y0 >> 2; ty <= (y0 + nr - 1) >> 2; ++ty)
+            band |= a.rowgen[tr0 + ty] == gen;
+    }
+    return __ballot_sync(0xffffffffu, band);
+}
+
 // Producer warp: fetch group g into a stage.  The source rows of population i
 // for rows y0 .. y0+nr-1 of plane z are rows y0-c_iy .. of plane z-c_iz
 // (or the group's own rows of the opposite population at a wall), which are
 // contiguous in memory except across the periodic y seam: lane i < 19 issues
-// one bulk copy for population i (two at the seam).  If a row of the group
-// meets the band, lanes 19..21 copy the three force-density components of
-// the group's rows.  Every lane announces the bytes of its own copies on the
+// one bulk copy for population i (two at the seam).  If the group carries
+// force (band), lanes 19..21 copy the three force-density components of the
+// group's rows.  Every lane announces the bytes of its own copies on the
 // mbarrier (initialised for 32 arrivals) before issuing them.
 template <typename S>
-__device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t gen, int g, unsigned char *sbase,
-                                        uint64_t *bar, bool no_force)
+__device__ __forceinline__ void produce(const Arrays &a, const S *src, int g, unsigned char *sbase, uint64_t *bar,
+                                        bool band)
 {
     const int lane = threadIdx.x & 31;
     const int d = find_drop_group(a.drops, a.ndrops, g);
@@ -152,16 +175,6 @@ __device__ __forceinline__ void produce(const Arrays &a, const S *src, uint32_t 
     const int P = D.pitch, ny = D.ny, R = D.lb_rows;
     Stage<S> stg(sbase, R, P);
     const int64_t plane_row0 = (int64_t)ny * z;
-    // the group carries force iff one of the tiles its rows cross is in this
-    // step's band (F vanishes elsewhere)
-    const int ky0 = y0 >> 2, nty = ((y0 + nr - 1) >> 2) - ky0 + 1;
-    const int64_t trow0 = D.tile0 + (int64_t)D.tx * (ky0 + (int64_t)D.ty * (z >> 2));
-    bool band = false;
-    if (!no_force) {
-        for (int q = lane; q < nty * D.tx; q += 32)
-            band |= a.tile_gen[trow0 + q] == gen;
-        band = __any_sync(0xffffffffu, band);
-    }
     const uint32_t rowb = (uint32_t)(P * sizeof(S));
     // copies of this lane: up to two pieces (source row, destination row, rows)
     int src_pop = 0, src_z = 0, y_a = 0, n_a = 0, y_b = 0, n_b = 0, d_b = 0;
@@ -440,8 +453,12 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
     bool failed = false;
     if (threadIdx.x >= LB_THREADS) {
         int st_i = 0;
-        uint32_t use = 0;
-        for (int ig = blockIdx.x; ig < total; ig += gridDim.x) {
+        uint32_t use = 0, bits = 0;
+        for (int ig = blockIdx.x, k = 0; ig < total; ig += gridDim.x, ++k) {
+            // the band flags of the next 32 groups at once: one round trip
+            // to memory per 32 groups, off the path of each group's copies
+            if ((k & 31) == 0)
+                bits = no_force ? 0u : band_ballot(a, list, total, ig, gridDim.x, gen);
             if (use > 0 && !mbar_wait_bounded(&empty[st_i], (use - 1) & 1u)) {
                 failed = true;
                 break;
@@ -449,8 +466,8 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
             // order the consumers' generic reads of the stage before the
             // asynchronous writes into it
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            produce<S>(a, src, gen, list ? list[ig] : ig, smem_raw + st_i * a.lb_stage_bytes, &full[st_i],
-                       no_force != 0);
+            produce<S>(a, src, list ? list[ig] : ig, smem_raw + st_i * a.lb_stage_bytes, &full[st_i],
+                       ((bits >> (k & 31)) & 1u) != 0);
             if (++st_i == ns) {
                 st_i = 0;
                 ++use;
