@@ -132,95 +132,6 @@ __device__ __forceinline__ void group_rows(const Drop &D, int g, int &y0, int &z
     nr = min(D.lb_rows, D.ny - y0);
 }
 
-// Band flags of 32 consecutive groups of a block, one per lane: lane l
-// takes group ig0 + l * stride.  A group carries force iff one of the tile
-// rows its cell rows cross put a tile into this step's band (the force
-// kernel stamps the row with the step's generation; F vanishes outside band
-// tiles).  Bit l of the result is lane l's flag.
-__device__ __forceinline__ uint32_t band_ballot(const Arrays &a, const int *list, int total, int ig0, int stride,
-                                                uint32_t gen)
-{
-    const int lane = threadIdx.x & 31;
-    const int ig = ig0 + lane * stride;
-    bool band = false;
-    if (ig < total) {
-        const int g = list ? list[ig] : ig;
-        const Drop &D = a.drops[find_drop_group(a.drops, a.ndrops, g)];
-        int y0, z, nr;
-        group_rows(D, g, y0, z, nr);
-        const int64_t tr0 = D.trow0 + (int64_t)D.ty * (z >> 2);
-        for (int ty = y0 >> 2; ty <= (y0 + nr - 1) >> 2; ++ty)
-            band |= a.rowgen[tr0 + ty] == gen;
-    }
-    return __ballot_sync(0xffffffffu, band);
-}
-
-// Producer warp: fetch group g into a stage.  The source rows of population i
-// for rows y0 .. y0+nr-1 of plane z are rows y0-c_iy .. of plane z-c_iz
-// (or the group's own rows of the opposite population at a wall), which are
-// contiguous in memory except across the periodic y seam: lane i < 19 issues
-// one bulk copy for population i (two at the seam).  If the group carries
-// force (band), lanes 19..21 copy the three force-density components of the
-// group's rows.  Every lane announces the bytes of its own copies on the
-// mbarrier (initialised for 32 arrivals) before issuing them.
-template <typename S>
-__device__ __forceinline__ void produce(const Arrays &a, const S *src, int g, unsigned char *sbase, uint64_t *bar,
-                                        bool band)
-{
-    const int lane = threadIdx.x & 31;
-    const int d = find_drop_group(a.drops, a.ndrops, g);
-    const Drop &D = a.drops[d];
-    int y0, z, nr;
-    group_rows(D, g, y0, z, nr);
-    const int P = D.pitch, ny = D.ny, R = D.lb_rows;
-    Stage<S> stg(sbase, R, P);
-    const int64_t plane_row0 = (int64_t)ny * z;
-    const uint32_t rowb = (uint32_t)(P * sizeof(S));
-    // copies of this lane: up to two pieces (source row, destination row, rows)
-    int src_pop = 0, src_z = 0, y_a = 0, n_a = 0, y_b = 0, n_b = 0, d_b = 0;
-    uint32_t mine = 0;
-    if (lane < Q) {
-        const int i = lane;
-        int zs = z - kCz[i], ys = y0 - kCy[i];
-        src_pop = i;
-        if (D.walls && (zs < 0 || zs >= D.nzf)) {
-            src_pop = kOpp[i];          // halfway bounce-back: own rows, opposite population
-            zs = z;
-            ys = y0;
-        } else {
-            zs = wrapi(zs, D.nzf);
-        }
-        src_z = zs;
-        if (ys < 0) {                   // first row wraps to y = ny - 1
-            y_a = ny - 1; n_a = 1;
-            y_b = 0; n_b = nr - 1; d_b = 1;
-        } else if (ys + nr > ny) {      // last row wraps to y = 0
-            y_a = ys; n_a = ny - ys;
-            y_b = 0; n_b = nr - n_a; d_b = n_a;
-        } else {
-            y_a = ys; n_a = nr;
-        }
-        mine = rowb * (uint32_t)(n_a + n_b);
-    } else if (band && lane < Q + 3) {
-        mine = (uint32_t)(nr * P * sizeof(float));
-    }
-    if (lane == 0)
-        *stg.flag = band;
-    mbar_arrive_expect_tx(bar, mine);
-    if (lane < Q) {
-        const S *plane = src + (int64_t)Q * D.pcell0 + (int64_t)src_pop * D.pcells + (int64_t)P * ny * src_z;
-        S *dst = stg.pop + (int64_t)lane * R * P;
-        if (n_a > 0)
-            bulk_g2s(dst, plane + (int64_t)P * y_a, rowb * n_a, bar);
-        if (n_b > 0)
-            bulk_g2s(dst + (int64_t)d_b * P, plane + (int64_t)P * y_b, rowb * n_b, bar);
-    } else if (band && lane < Q + 3) {
-        const int c = lane - Q;
-        bulk_g2s(stg.F + (int64_t)c * R * P, a.F + c * a.total_pcells + D.pcell0 + (int64_t)P * (plane_row0 + y0),
-                 (uint32_t)(nr * P * sizeof(float)), bar);
-    }
-}
-
 // A droplet's stream-collide constants, loaded once and kept in registers
 // while consecutive groups of the same droplet run (one droplet per launch
 // is the common case), with the thread's first cell (r0, x0) of a group.
@@ -275,6 +186,91 @@ struct DropC {
         nr = min(R, ny - y0);
     }
 };
+
+// Band flags of 32 consecutive groups of a block, one per lane: lane l
+// takes group ig0 + l * stride.  A group carries force iff one of the tile
+// rows its cell rows cross put a tile into this step's band (the force
+// kernel stamps the row with the step's generation; F vanishes outside band
+// tiles).  Bit l of the result is lane l's flag.
+__device__ __forceinline__ uint32_t band_ballot(const Arrays &a, const int *list, int total, int ig0, int stride,
+                                                uint32_t gen)
+{
+    const int lane = threadIdx.x & 31;
+    const int ig = ig0 + lane * stride;
+    bool band = false;
+    if (ig < total) {
+        const int g = list ? list[ig] : ig;
+        const Drop &D = a.drops[find_drop_group(a.drops, a.ndrops, g)];
+        int y0, z, nr;
+        group_rows(D, g, y0, z, nr);
+        const int64_t tr0 = D.trow0 + (int64_t)D.ty * (z >> 2);
+        for (int ty = y0 >> 2; ty <= (y0 + nr - 1) >> 2; ++ty)
+            band |= a.rowgen[tr0 + ty] == gen;
+    }
+    return __ballot_sync(0xffffffffu, band);
+}
+
+// Producer warp: fetch group g into a stage.  The source rows of population i
+// for rows y0 .. y0+nr-1 of plane z are rows y0-c_iy .. of plane z-c_iz
+// (or the group's own rows of the opposite population at a wall), which are
+// contiguous in memory except across the periodic y seam: lane i < 19 issues
+// one bulk copy for population i (two at the seam).  If the group carries
+// force (band), lanes 19..21 copy the three force-density components of the
+// group's rows.  Every lane announces the bytes of its own copies on the
+// mbarrier (initialised for 32 arrivals) before issuing them.
+template <typename S>
+__device__ __forceinline__ void produce(const Arrays &a, const DropC &c, const S *src, int y0, int z, int nr,
+                                        unsigned char *sbase, uint64_t *bar, bool band)
+{
+    const int lane = threadIdx.x & 31;
+    const int P = c.P, ny = c.ny, R = c.R;
+    Stage<S> stg(sbase, R, P);
+    const int64_t plane_row0 = (int64_t)ny * z;
+    const uint32_t rowb = (uint32_t)(P * sizeof(S));
+    // copies of this lane: up to two pieces (source row, destination row, rows)
+    int src_pop = 0, src_z = 0, y_a = 0, n_a = 0, y_b = 0, n_b = 0, d_b = 0;
+    uint32_t mine = 0;
+    if (lane < Q) {
+        const int i = lane;
+        int zs = z - kCz[i], ys = y0 - kCy[i];
+        src_pop = i;
+        if (c.walls && (zs < 0 || zs >= c.nzf)) {
+            src_pop = kOpp[i];          // halfway bounce-back: own rows, opposite population
+            zs = z;
+            ys = y0;
+        } else {
+            zs = wrapi(zs, c.nzf);
+        }
+        src_z = zs;
+        if (ys < 0) {                   // first row wraps to y = ny - 1
+            y_a = ny - 1; n_a = 1;
+            y_b = 0; n_b = nr - 1; d_b = 1;
+        } else if (ys + nr > ny) {      // last row wraps to y = 0
+            y_a = ys; n_a = ny - ys;
+            y_b = 0; n_b = nr - n_a; d_b = n_a;
+        } else {
+            y_a = ys; n_a = nr;
+        }
+        mine = rowb * (uint32_t)(n_a + n_b);
+    } else if (band && lane < Q + 3) {
+        mine = (uint32_t)(nr * P * sizeof(float));
+    }
+    if (lane == 0)
+        *stg.flag = band;
+    mbar_arrive_expect_tx(bar, mine);
+    if (lane < Q) {
+        const S *plane = src + (int64_t)Q * c.pcell0 + (int64_t)src_pop * c.PC + (int64_t)P * ny * src_z;
+        S *dst = stg.pop + (int64_t)lane * R * P;
+        if (n_a > 0)
+            bulk_g2s(dst, plane + (int64_t)P * y_a, rowb * n_a, bar);
+        if (n_b > 0)
+            bulk_g2s(dst + (int64_t)d_b * P, plane + (int64_t)P * y_b, rowb * n_b, bar);
+    } else if (band && lane < Q + 3) {
+        const int k = lane - Q;
+        bulk_g2s(stg.F + (int64_t)k * R * P, a.F + k * a.total_pcells + c.pcell0 + (int64_t)P * (plane_row0 + y0),
+                 (uint32_t)(nr * P * sizeof(float)), bar);
+    }
+}
 
 // BGK + Guo for one group's cells.  For the pair (i, opp(i)), c_opp = -c_i,
 // with cu = c_i.U and cF = c_i.F the post-collision offsets
@@ -454,6 +450,8 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
     if (threadIdx.x >= LB_THREADS) {
         int st_i = 0;
         uint32_t use = 0, bits = 0;
+        DropC c;
+        c.d = -1;
         for (int ig = blockIdx.x, k = 0; ig < total; ig += gridDim.x, ++k) {
             // the band flags of the next 32 groups at once: one round trip
             // to memory per 32 groups, off the path of each group's copies
@@ -466,7 +464,13 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
             // order the consumers' generic reads of the stage before the
             // asynchronous writes into it
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            produce<S>(a, src, list ? list[ig] : ig, smem_raw + st_i * a.lb_stage_bytes, &full[st_i],
+            const int g = list ? list[ig] : ig;
+            const int d = find_drop_group(a.drops, a.ndrops, g);
+            if (d != c.d)
+                c.load(a.drops[d], d);
+            int y0, z, nr;
+            c.rows(g, y0, z, nr);
+            produce<S>(a, c, src, y0, z, nr, smem_raw + st_i * a.lb_stage_bytes, &full[st_i],
                        ((bits >> (k & 31)) & 1u) != 0);
             if (++st_i == ns) {
                 st_i = 0;
