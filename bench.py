@@ -201,6 +201,8 @@ def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
     try:
         if "mult" in LB_SHAPE:
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_LB_ROW_MULT, LB_SHAPE["mult"])
+        if "cells" in LB_SHAPE:
+            iblb.iblb_set_option(ctx, iblb.IBLB_OPT_LB_GROUP_CELLS, LB_SHAPE["cells"])
         if "bps" in LB_SHAPE:
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_LB_BLOCKS_PER_SM, LB_SHAPE["bps"])
         if "stages" in LB_SHAPE:
@@ -369,6 +371,8 @@ def main():
     ap.add_argument("--pdl", type=int, default=-1, help="1/0: programmatic dependent launch in the step")
     ap.add_argument("--lb-far-blocks-per-sm", type=int, default=-1, help="blocks per SM of the far groups")
     ap.add_argument("--ib-blocks-per-sm", type=int, default=-1, help="blocks per SM of the cooperative kernels")
+    ap.add_argument("--lb-group-cells", type=int, default=0,
+                    help="about this many cells per stream-collide group (implies --no-autotune)")
     ap.add_argument("--lb-stages", type=int, default=0,
                     help="stream-collide pipeline stages 2..8 (implies --no-autotune)")
     ap.add_argument("--lb-blocks-per-sm", type=int, default=-1,
@@ -382,6 +386,8 @@ def main():
     from paper_2503_20605_gb300 import inputs as I
     if args.lb_row_mult > 0:
         LB_SHAPE["mult"] = args.lb_row_mult
+    if args.lb_group_cells > 0:
+        LB_SHAPE["cells"] = args.lb_group_cells
     if args.lb_blocks_per_sm >= 0:
         LB_SHAPE["bps"] = args.lb_blocks_per_sm
     if args.lb_stages > 0:

@@ -167,6 +167,10 @@ typedef struct {
 #define IBLB_OPT_LB_FAR_BLOCKS_PER_SM 8 /* resident blocks per SM of those far groups
                                  (0..8; 0 = as many as fit; default 1, which leaves room
                                  for the membrane kernels)                               */
+#define IBLB_OPT_LB_GROUP_CELLS 10 /* about this many cells per stream-collide group
+                                 (whole rows: max(1, round(cells / nx)) rows, at most ny),
+                                 in place of IBLB_OPT_LB_ROW_MULT (1..16384; 0 = use the
+                                 multiplier)                                             */
 
 typedef struct iblb_ctx iblb_ctx;
 

@@ -313,7 +313,9 @@ void layout(iblb_ctx *c)
         D.pcells = (int64_t)D.pitch * D.ny * D.nzf;
         D.pcell0 = pcell0;
         D.row0 = row0;
-        D.lb_rows = std::min(D.ny, c->cfg.lb_row_mult * lb_rows_per_group(D.nx));
+        D.lb_rows = std::min(D.ny, c->cfg.lb_group_cells > 0
+                                       ? std::max(1, (c->cfg.lb_group_cells + D.nx / 2) / D.nx)
+                                       : c->cfg.lb_row_mult * lb_rows_per_group(D.nx));
         D.lb_gpp = (D.ny + D.lb_rows - 1) / D.lb_rows;
         D.lb_block0 = lb0;
         D.lb_nblocks = D.lb_gpp * D.nzf;
@@ -1200,6 +1202,17 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
         c->cfg.lb_blocks_per_sm = value;
         invalidate_graphs(c);
         return IBLB_OK;
+    case IBLB_OPT_LB_GROUP_CELLS: {
+        if (value < 0 || value > 16384)
+            return fail(c, IBLB_E_ARG, "cells per group must be in [0, 16384]");
+        int r = ensure_ready(c);
+        if (r)
+            return r;
+        c->cfg.lb_group_cells = value;
+        layout(c);
+        invalidate_graphs(c);
+        return upload_drops(c);
+    }
     case IBLB_OPT_LB_ROW_MULT: {
         if (value == 0)
             value = 1;
@@ -1287,15 +1300,16 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
         if (fp) {
             char line[256];
             while (fgets(line, sizeof(line), fp)) {
-                int bps = 0, mult = 0, ns = 2;
+                int bps = 0, mult = 0, ns = 2, cells = 0;
                 const char *bar = strchr(line, '|');
                 if (bar && (size_t)(bar - line) == strlen(key) && !strncmp(line, key, strlen(key)) &&
-                    sscanf(bar + 1, "%d %d %d", &bps, &mult, &ns) == 3) {
+                    sscanf(bar + 1, "%d %d %d %d", &bps, &mult, &ns, &cells) == 4) {
                     fclose(fp);
                     if ((r = iblb_set_option(c, IBLB_OPT_LB_BLOCKS_PER_SM, bps)) ||
-                        (r = iblb_set_option(c, IBLB_OPT_LB_STAGES, ns)))
+                        (r = iblb_set_option(c, IBLB_OPT_LB_STAGES, ns)) ||
+                        (r = iblb_set_option(c, IBLB_OPT_LB_ROW_MULT, mult)))
                         return r;
-                    return iblb_set_option(c, IBLB_OPT_LB_ROW_MULT, mult);
+                    return iblb_set_option(c, IBLB_OPT_LB_GROUP_CELLS, cells);
                 }
             }
             fclose(fp);
@@ -1305,7 +1319,7 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
     // spare one: the current state is left untouched
     const int bpsm[2] = {0, 1};
     float best = 1e30f;
-    int bb = c->cfg.lb_blocks_per_sm, bm = c->cfg.lb_row_mult;
+    int bb = c->cfg.lb_blocks_per_sm, bm = c->cfg.lb_row_mult, bcells = c->cfg.lb_group_cells;
     int dev = 0, smem_max = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -1314,11 +1328,13 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
     CK(cudaEventCreate(&e1));
     enter(c);
     int bs = c->cfg.lb_stages;
-    for (int mult = 1; mult <= 4; mult *= 2)
+    // group sizes of 256 .. 1024 cells in steps of 128 (whole rows), with
+    // every pipeline depth and both residencies whose stages fit
+    for (int cells = 256; cells <= 1024; cells += 128)
         for (int bi = 0; bi < 2; ++bi)
             for (int ns = 2; ns <= 8; ++ns) {
                 c->cfg.lb_blocks_per_sm = bpsm[bi];
-                c->cfg.lb_row_mult = mult;
+                c->cfg.lb_group_cells = cells;
                 c->cfg.lb_stages = ns;
                 layout(c);
                 if (ns * (int64_t)c->A.lb_stage_bytes + 1024 > smem_max)
@@ -1338,7 +1354,7 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
                 if (ms < best) {
                     best = ms;
                     bb = bpsm[bi];
-                    bm = mult;
+                    bcells = cells;
                     bs = ns;
                 }
             }
@@ -1347,6 +1363,7 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
     leave(c);
     c->cfg.lb_blocks_per_sm = bb;
     c->cfg.lb_row_mult = bm;
+    c->cfg.lb_group_cells = bcells;
     c->cfg.lb_stages = bs;
     layout(c);
     invalidate_graphs(c);
@@ -1355,7 +1372,7 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
     if (cache_path) {
         FILE *fp = fopen(cache_path, "a");
         if (fp) {
-            fprintf(fp, "%s|%d %d %d\n", key, bb, bm, bs);
+            fprintf(fp, "%s|%d %d %d %d\n", key, bb, bm, bs, bcells);
             fclose(fp);
         }
     }

@@ -161,12 +161,13 @@ struct LaunchCfg {
     int lb_blocks_per_sm;          // resident stream-collide blocks per SM (0: as many as fit)
     int lb_row_mult;               // cell rows per group = lb_row_mult * lb_rows_per_group(nx)
     int sm_count;
-    int lb_stages;                 // shared-memory stages of the stream-collide pipeline (2..4)
+    int lb_stages;                 // shared-memory stages of the stream-collide pipeline (2..8)
     int ib_blocks_per_sm;          // blocks per SM of the cooperative membrane kernels (0: all that fit)
+    int lb_group_cells = 0;        // if > 0: about this many cells per group (whole rows), in place of the multiplier
 };
 int lb_rows_per_group(int nx);     // 256-thread groups: max(1, 256 / nx) rows
-// bytes of one stage of the stream-collide kernel: a 128-byte group header,
-// 19 population rows and 3 force rows per cell row (128-byte multiple)
+// bytes of one stage of the stream-collide kernel: 19 population rows and 3
+// force rows per cell row and the band flag (128-byte multiple)
 int lb_stage_bytes(int rows, int pitch, int storage_bytes);
 
 // Stream-collide over every group (list == nullptr) or over the groups

@@ -117,13 +117,15 @@ def test_batch64_sampled_members():
 def test_autotune_candidates_bit_identical():
     spec = I.workload_statics_128(60.0, "f16")
     outs = []
-    for mult, bps, ns in ((2, 0, 2), (1, 0, 2), (4, 0, 2), (2, 1, 2), (1, 1, 4), (2, 0, 3), (2, 0, 4), (4, 0, 3)):
+    for mult, bps, ns, cells in ((2, 0, 2, 0), (1, 0, 2, 0), (4, 0, 2, 0), (2, 1, 2, 0), (1, 1, 4, 0), (2, 0, 3, 0),
+                                 (2, 0, 4, 0), (4, 0, 3, 0), (1, 0, 8, 0), (1, 0, 3, 640), (1, 0, 2, 896)):
         g = gpu_ctx(spec.nx, spec.ny, spec.nz, tau=spec.tau, storage="f16", sigma=spec.sigma, theta=spec.theta_deg,
                     xi=spec.xi, volume_correction=1, mesh=spec.mesh())
         try:
             iblb.iblb_set_option(g, iblb.IBLB_OPT_LB_ROW_MULT, mult)
             iblb.iblb_set_option(g, iblb.IBLB_OPT_LB_BLOCKS_PER_SM, bps)
             iblb.iblb_set_option(g, iblb.IBLB_OPT_LB_STAGES, ns)
+            iblb.iblb_set_option(g, iblb.IBLB_OPT_LB_GROUP_CELLS, cells)
             iblb.iblb_step(g, 25)
             iblb.iblb_sync(g)
             outs.append((iblb.iblb_get_populations(g, 0), iblb.iblb_get_nodes(g, 0)))
