@@ -295,6 +295,10 @@ void fill_drop_params(Drop &D, const iblb_lattice_desc &l, const iblb_physics_de
     D.volcorr = p.volume_correction != 0;
 }
 
+// shared memory a block of the stream-collide kernel may give its stages: the
+// opt-in maximum of sm_100 and later (227 KB) less 1 KB for its static part
+constexpr int64_t kLbSmemOptin = 227 * 1024 - 1024;
+
 // Offsets of cells, tiles, columns, launch blocks for the current launch shape.
 void layout(iblb_ctx *c)
 {
@@ -316,6 +320,9 @@ void layout(iblb_ctx *c)
         D.lb_rows = std::min(D.ny, c->cfg.lb_group_cells > 0
                                        ? std::max(1, (c->cfg.lb_group_cells + D.nx / 2) / D.nx)
                                        : c->cfg.lb_row_mult * lb_rows_per_group(D.nx));
+        // two stages of the group must fit the opt-in shared memory of a block
+        while (D.lb_rows > 1 && 2 * (int64_t)lb_stage_bytes(D.lb_rows, D.pitch, sb) > kLbSmemOptin)
+            --D.lb_rows;
         D.lb_gpp = (D.ny + D.lb_rows - 1) / D.lb_rows;
         D.lb_block0 = lb0;
         D.lb_nblocks = D.lb_gpp * D.nzf;
@@ -340,6 +347,9 @@ void layout(iblb_ctx *c)
     c->A.lb_blocks_total = lb0;
     c->A.lb_stage_bytes = stage;
     c->mass_blocks = mb0;
+    // as many of the asked pipeline stages as fit
+    while (c->cfg.lb_stages > 2 && (int64_t)c->cfg.lb_stages * stage > kLbSmemOptin)
+        --c->cfg.lb_stages;
 }
 
 int upload_drops(iblb_ctx *c)
