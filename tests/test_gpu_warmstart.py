@@ -1,15 +1,15 @@
 """What the learned warm start gains over the plain IB-LB run from a sphere
 (the method without it).  The network shipped with the package was trained
-on the GPU by the library's own kernels on 460 equilibria that batched
+on the GPU by the library's own kernels on 1 546 equilibria that batched
 sphere-start runs produced (paper_2503_20605_gb300.warmstart; provenance in
 data/warmstart_mlp_params.json).  Eight of its held-out cases (seed 2, the
 configured distribution of theta_eq, R0 and lambda) run here from the sphere
 and from the predicted shape: the warm start must reach equilibrium in
 fewer steps on average and end at the same contact angle, with the
-sphere-start run as the judge (median difference below 1 degree).  The runs
+sphere-start run as the reference (median difference below 1 degree).  The runs
 are deterministic, so the margins are fixed by the code: at the time of
-writing the mean steps were 10 643 (sphere) and 7 429 (warm start) over the
-seven cases where both converged, with a median angle difference of 0.23
+writing the mean steps were 12 125 (sphere) and 6 500 (warm start) over the
+cases where both converged, with a median angle difference of 0.28
 degrees."""
 import numpy as np
 import pytest
