@@ -313,6 +313,16 @@ int iblb_mesh_observe_dev_noalloc(const double *d_xyz, int n_nodes, const int32_
                                   double R0, double zcut_frac, double eps_flat, void *stream,
                                   double *out);
 
+/* Self-test of the bounded waits (no counterpart in the paper).  Every wait
+ * of the stream-collide pipeline on an mbarrier gives up after a cycle limit
+ * (about 2 s) and reports IBLB_E_TIMEOUT instead of hanging.  This call runs
+ * that same wait, with a limit of `cycles` SM clock cycles (1e3 .. 1e10), on
+ * a barrier that nothing completes, on `stream` (synchronised before the
+ * call returns).  Returns IBLB_E_TIMEOUT when every waiting thread gave up
+ * (the expected outcome), IBLB_E_ARG for a limit out of range, IBLB_E_CUDA
+ * if a CUDA call failed, IBLB_E_STATE for any other outcome. */
+int iblb_selftest_wait_timeout(long long cycles, void *stream);
+
 /* ---- learned warm start ---------------------------------------------------
  * Not in the paper: a network that predicts the equilibrium shape so that a
  * run can start from it instead of from a sphere.  The shape is the App. B

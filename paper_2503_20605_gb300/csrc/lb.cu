@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "iblb_internal.h"
+#include "mbarrier.cuh"
 
 namespace iblb {
 
@@ -42,53 +43,6 @@ __device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(
 __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-// bounded wait on an mbarrier phase; false if the limit was reached
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity))
-        return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES)
-            return false;
-    return true;
-}
 
 __device__ __forceinline__ int find_drop_group(const Drop *D, int n, int g)
 {
@@ -457,7 +411,7 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
             // to memory per 32 groups, off the path of each group's copies
             if ((k & 31) == 0)
                 bits = no_force ? 0u : band_ballot(a, list, total, ig, gridDim.x, gen);
-            if (use > 0 && !mbar_wait_bounded(&empty[st_i], (use - 1) & 1u)) {
+            if (use > 0 && !mbar_wait_bounded(&empty[st_i], (use - 1) & 1u, WAIT_CYCLES)) {
                 failed = true;
                 break;
             }
@@ -489,7 +443,7 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
                 c.load(a.drops[d], d);
             int y0, z, nr;
             c.rows(g, y0, z, nr);
-            if (!mbar_wait_bounded(&full[st_i], phase)) {
+            if (!mbar_wait_bounded(&full[st_i], phase, WAIT_CYCLES)) {
                 failed = true;
                 break;
             }

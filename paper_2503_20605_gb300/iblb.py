@@ -70,6 +70,7 @@ _D = C.POINTER(C.c_double)
 _I32 = C.POINTER(C.c_int32)
 _SIGS = {
     "iblb_version": (C.c_char_p, []),
+    "iblb_selftest_wait_timeout": (C.c_int, [C.c_longlong, _P]),
     "iblb_last_error": (C.c_char_p, [_P]),
     "iblb_wetting_A": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _D]),
     "iblb_create": (C.c_int, [C.POINTER(LatticeDesc), C.POINTER(PhysicsDesc), _P, C.POINTER(_P)]),
@@ -417,3 +418,9 @@ def iblb_mlp_train(m, x, y, epochs, batch=256, lr=1e-3, seed=0):
     losses = np.zeros(max(epochs, 1))
     _mcheck(m, lib().iblb_mlp_train(m, _d(x), _d(y), S, epochs, batch, lr, seed, _d(losses)))
     return losses[:epochs]
+
+
+def iblb_selftest_wait_timeout(cycles, stream=0):
+    """Run the bounded mbarrier wait on a barrier that never completes;
+    returns the status code (IBLB_E_TIMEOUT is the expected outcome)."""
+    return lib().iblb_selftest_wait_timeout(int(cycles), _P(stream))

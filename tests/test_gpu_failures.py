@@ -3,7 +3,9 @@ are refused before any device work, and conditions the kernels detect
 (non-finite values, a node moving more than half a cell in one step, a node
 leaving the fluid) come back from iblb_sync as IBLB_E_UNSTABLE with a
 message, never as a device fault.  After each error the context is reset
-through the API and runs on, bit for bit like a fresh context."""
+through the API and runs on, bit for bit like a fresh context.  The bounded
+wait of the stream-collide pipeline is made to run out on a barrier that
+nothing completes: it reports IBLB_E_TIMEOUT and the device stays usable."""
 import numpy as np
 import pytest
 
@@ -114,3 +116,22 @@ def test_device_conditions_report_and_recover():
     finally:
         iblb.iblb_destroy(ctx)
         iblb.iblb_destroy(fresh)
+
+
+def test_bounded_wait_runs_out_and_reports():
+    from gpu_util import stream
+    # about 1 ms at GB300 clocks: the wait gives up, every thread reports it
+    assert iblb.iblb_selftest_wait_timeout(2_000_000, stream()) == iblb.IBLB_E_TIMEOUT
+    assert iblb.iblb_selftest_wait_timeout(10, stream()) == iblb.IBLB_E_ARG
+    # the context is still usable: a clean run matches a fresh one bit for bit
+    ctx, xyz, tri = parity_ctx()
+    fresh, _, _ = parity_ctx()
+    try:
+        q_ref, f_ref = run_clean(fresh, xyz, 5)
+        q, f = run_clean(ctx, xyz, 5)
+        np.testing.assert_array_equal(q, q_ref)
+        np.testing.assert_array_equal(f, f_ref)
+    finally:
+        iblb.iblb_destroy(ctx)
+        iblb.iblb_destroy(fresh)
+
