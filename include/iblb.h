@@ -141,9 +141,11 @@ typedef struct {
 #define IBLB_OPT_LB_BLOCKS_PER_SM 2 /* resident blocks per SM of the persistent
                                  stream-collide kernel (0..8; 0 = as many as fit)       */
 #define IBLB_OPT_LB_ROW_MULT 3 /* cell rows per stream-collide group, in units of
-                                 max(1, 256 / nx) rows (1..4; 0 = 1)                     */
+                                 max(1, 256 / nx) rows (1..4; 0 = 1); setting it sets
+                                 IBLB_OPT_LB_GROUP_CELLS to 0                            */
 #define IBLB_OPT_LB_STAGES 4  /* shared-memory stages of the stream-collide pipeline:
-                                 the most groups in flight per block (2..8; default 2)   */
+                                 the most groups in flight per block (2..8; default 3;
+                                 lowered to the most that fit in shared memory)          */
 #define IBLB_OPT_FUSED_IB 5   /* 1: the membrane work of a step runs as two cooperative
                                  kernels (forces + spread; advection + volume
                                  correction) with grid barriers between their phases,
@@ -170,7 +172,7 @@ typedef struct {
 #define IBLB_OPT_LB_GROUP_CELLS 10 /* about this many cells per stream-collide group
                                  (whole rows: max(1, round(cells / nx)) rows, at most ny),
                                  in place of IBLB_OPT_LB_ROW_MULT (1..16384; 0 = use the
-                                 multiplier)                                             */
+                                 multiplier; default 768)                                */
 
 typedef struct iblb_ctx iblb_ctx;
 

@@ -78,7 +78,7 @@ struct iblb_ctx {
     double step_ms = 0.0;
     int64_t prof_steps = 0;
     int64_t step_count = 0;
-    LaunchCfg cfg{0, 2, 148, 2, 1};
+    LaunchCfg cfg{0, 2, 148, 3, 1, 768};
     int *h_status = nullptr;     // pinned, 4 per droplet
     double *obs_scr = nullptr;   // scratch of the mesh observation kernels
     int64_t obs_scr_n = 0;
@@ -1232,6 +1232,7 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
         if (r)
             return r;
         c->cfg.lb_row_mult = value;
+        c->cfg.lb_group_cells = 0;             // the multiplier takes over
         layout(c);
         invalidate_graphs(c);
         return upload_drops(c);
