@@ -252,7 +252,7 @@ __device__ __forceinline__ int per_off(int X, int b, int n)
 
 // Shared memory of one spread block: the staged records of a tile's nodes.
 struct SpreadSmem {
-    int node[SPREAD_CAP];
+    __align__(16) int node[SPREAD_CAP];
     short perm[SPREAD_CAP];
     int b[3][SPREAD_CAP];
     float w[12][SPREAD_CAP];
@@ -322,15 +322,20 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
             sm.phi[1][e] = r.phi[1];
             sm.phi[2][e] = r.phi[2];
         }
+        if (tid < ((cnt + 3) & ~3) - cnt)
+            sm.node[cnt + tid] = 0x7fffffff;             // pad the keys to a multiple of 4
         __syncthreads();
         if (tid == 0)
             a.bin_cnt[T] = 0;                            // empty for the next step
         // rank sort by node index: contributions are added in increasing j
+        const int4 *keys4 = reinterpret_cast<const int4 *>(sm.node);
         for (int e = tid; e < cnt; e += IB_THREADS) {
             const int key = sm.node[e];
             int rank = 0;
-            for (int k = 0; k < cnt; ++k)
-                rank += sm.node[k] < key;
+            for (int k = 0; k < (cnt + 3) >> 2; ++k) {
+                const int4 v = keys4[k];
+                rank += (v.x < key) + (v.y < key) + (v.z < key) + (v.w < key);
+            }
             sm.perm[rank] = (short)e;
         }
         __syncthreads();
@@ -397,9 +402,15 @@ __device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
     const bool valid = j < a.total_nodes;
     float ax = 0.f, ay = 0.f, az = 0.f;
     int d = 0;
+    double qx = 0.0, qy = 0.0, qz = 0.0;
+    if (valid && l == 0) {      // the position, read early: it does not depend on the record
+        qx = a.qx[j];
+        qy = a.qy[j];
+        qz = a.qz[j];
+    }
     if (valid) {
+        d = a.node_drop[j];
         const NodeRec &r = a.rec[j];
-        d = r.spare;
         const Drop &D = a.drops[d];
         if (r.key > 0) {
             const int dy = l & 3, dz = l >> 2;
@@ -433,9 +444,9 @@ __device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
             atomicOr(&a.status[4 * d], ST_NAN);
         else if (ax * ax + ay * ay + az * az > 0.25f)
             atomicOr(&a.status[4 * d], ST_JUMP);
-        a.qx[j] += (double)ax;
-        a.qy[j] += (double)ay;
-        a.qz[j] += (double)az;
+        a.qx[j] = qx + (double)ax;
+        a.qy[j] = qy + (double)ay;
+        a.qz[j] = qz + (double)az;
     }
 }
 
