@@ -20,7 +20,10 @@ angleh) changes by less than 0.05 degree over 2000 steps.  Then:
   decreases, the paper's trend.
 
 Both storages are run: FP32 and FP16 offsets (the reduced-precision path
-must reach the same shape)."""
+must reach the same shape).  Two more runs: the error must fall with the
+membrane's resolution (the paper's study of N_t), and the 128^3 benchmark
+droplet (xi/R0 = 0.1) must reach the theory's shapes and angles at five
+contact angles, its error falling as theta_eq grows."""
 import math
 
 import numpy as np
@@ -55,15 +58,20 @@ def volume_centroid(xyz, tri):
 
 
 def sim_profile(xyz, tri, edges):
-    """Azimuthally averaged node distance from the centroid per phi bin."""
+    """Azimuthally averaged node distance from the centroid per phi bin (a
+    bin without nodes, which a flat droplet can leave near its poles, takes
+    the linear interpolation of its filled neighbours)."""
     c, vol = volume_centroid(xyz, tri)
     d = xyz - c
     r = np.linalg.norm(d, axis=1)
     phi = np.arccos(np.clip(d[:, 2] / r, -1.0, 1.0))
     idx = np.clip(np.digitize(phi, edges) - 1, 0, len(edges) - 2)
     cnt = np.bincount(idx, minlength=len(edges) - 1)
-    assert cnt.min() > 0, cnt
-    return np.bincount(idx, weights=r, minlength=len(edges) - 1) / cnt, vol
+    assert (cnt > 0).sum() >= 0.9 * len(cnt), cnt
+    g = np.bincount(idx, weights=r, minlength=len(edges) - 1) / np.maximum(cnt, 1)
+    mids = 0.5 * (edges[1:] + edges[:-1])
+    full = cnt > 0
+    return np.interp(mids, mids[full], g[full]), vol
 
 
 def run_statics(specs, storage):
@@ -145,3 +153,23 @@ def test_error_falls_with_mesh_resolution():
     errs = [shape_error(nodes[k], tris[k], 45.0, specs[k].xi, nbin=24)[0] for k in range(2)]
     print("E_L2 with 5 120 and 20 480 triangles:", errs, "steps", eq, "angles", theta_sim)
     assert errs[1] < errs[0], errs
+
+
+def test_benchmark_droplet_reaches_theory():
+    # the 128^3 benchmark droplet (R0 = 24, xi/R0 = 0.1, 20 480 triangles,
+    # FP16 storage) at theta_eq = 30 .. 150 degrees, with sigma = 0.01 to
+    # settle sooner: the shape error falls as theta_eq grows (the paper's
+    # trend at a small xi/R0), within 0.01 from 60 degrees on and 0.02 at 30,
+    # and the angles agree with the theory's within 2 degrees
+    angles = [30.0, 60.0, 90.0, 120.0, 150.0]
+    specs = [I.workload_statics_128(t, "f16") for t in angles]
+    for s in specs:
+        s.sigma = SIGMA
+    eq, nodes, tris, theta_sim = run_statics(specs, "f16")
+    rows = [(t,) + shape_error(nodes[k], tris[k], t, specs[k].xi) for k, t in enumerate(angles)]
+    for (t, err, tht), ths, n in zip(rows, theta_sim, eq):
+        print(f"theta_eq {t:5.1f}: {n} steps, E_L2 {err:.5f}, theta {ths:.3f} (theory {tht:.3f})")
+    errs = [r[1] for r in rows]
+    assert errs[0] <= 0.02 and max(errs[1:]) <= E_L2_BAR, errs
+    assert all(errs[k + 1] < errs[k] for k in range(len(errs) - 1)), errs
+    assert max(abs(ths - r[2]) for r, ths in zip(rows, theta_sim)) <= 2.0, (rows, theta_sim)
