@@ -2,7 +2,9 @@
 //   * mesh volume V = (1/6) sum_t q_a . (q_b x q_c), area, node centroid,
 //     z_min and z_max (the half-height l = (z_max - z_min)/2 of App. C, eq. ell);
 //   * contact-radius protocols (i) and (ii) of Sec. III B;
-//   * lattice mass sum_x sum_i f_i.
+//   * lattice mass sum_x sum_i f_i: each cell's 19 stored offsets are added
+//     in FP32 (a few rounding errors of the offsets' size, about 1e-3 of a
+//     cell's density) and the cells in FP64 with the fixed tree.
 // Every reduction uses a fixed assignment of items to threads and a fixed
 // shuffle tree, so results are bitwise reproducible and a droplet's values
 // do not depend on the other droplets of a batch.
@@ -195,10 +197,10 @@ __global__ void fold_sums_kernel(const double *part, int nch, int width, double 
 
 // ---- lattice mass: sum over cells of sum_i s_i (FP64), per droplet
 template <typename S>
-__device__ __forceinline__ double tod(S v);
-template <> __device__ __forceinline__ double tod<float>(float v) { return (double)v; }
-template <> __device__ __forceinline__ double tod<__half>(__half v) { return (double)__half2float(v); }
-template <> __device__ __forceinline__ double tod<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ float tof(S v);
+template <> __device__ __forceinline__ float tof<float>(float v) { return v; }
+template <> __device__ __forceinline__ float tof<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 __device__ __forceinline__ int find_drop_mass(const Drop *D, int n, int b)
 {
@@ -225,8 +227,10 @@ __global__ void __launch_bounds__(RB) mass_kernel(Arrays a, const S *f)
     if (c < D.cells) {
         const int64_t row = c / D.nx;
         const S *p = f + (int64_t)Q * D.pcell0 + (c - row * D.nx) + (int64_t)D.pitch * row;
+        float cell = 0.0f;
         for (int i = 0; i < Q; ++i)
-            v[0] += tod<S>(p[(int64_t)i * D.pcells]);
+            cell += tof<S>(p[(int64_t)i * D.pcells]);
+        v[0] = (double)cell;
     }
     block_reduce<1, RB>(v, KIND);
     if (threadIdx.x == 0)
