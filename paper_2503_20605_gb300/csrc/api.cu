@@ -96,11 +96,16 @@ int fail(iblb_ctx *c, int code, const std::string &msg)
     return code;
 }
 
+// A failed CUDA call is reported and its error cleared from the runtime's
+// last-error slot, so that it does not surface again in a later, unrelated
+// call (of this or another context).  Sticky errors stay sticky.
 #define CK(call)                                                                                  \
     do {                                                                                          \
         cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess)                                                                    \
+        if (e_ != cudaSuccess) {                                                                  \
+            (void)cudaGetLastError();                                                             \
             return fail(c, IBLB_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+        }                                                                                         \
     } while (0)
 
 template <typename T>
@@ -299,6 +304,13 @@ void fill_drop_params(Drop &D, const iblb_lattice_desc &l, const iblb_physics_de
 // opt-in maximum of sm_100 and later (227 KB) less 1 KB for its static part
 constexpr int64_t kLbSmemOptin = 227 * 1024 - 1024;
 
+// as many of the asked pipeline stages as fit the block's shared memory
+void fit_stages(iblb_ctx *c)
+{
+    while (c->cfg.lb_stages > 2 && (int64_t)c->cfg.lb_stages * c->A.lb_stage_bytes > kLbSmemOptin)
+        --c->cfg.lb_stages;
+}
+
 // Offsets of cells, tiles, columns, launch blocks for the current launch shape.
 void layout(iblb_ctx *c)
 {
@@ -347,9 +359,7 @@ void layout(iblb_ctx *c)
     c->A.lb_blocks_total = lb0;
     c->A.lb_stage_bytes = stage;
     c->mass_blocks = mb0;
-    // as many of the asked pipeline stages as fit
-    while (c->cfg.lb_stages > 2 && (int64_t)c->cfg.lb_stages * stage > kLbSmemOptin)
-        --c->cfg.lb_stages;
+    fit_stages(c);
 }
 
 int upload_drops(iblb_ctx *c)
@@ -1265,6 +1275,7 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
         if (value < 2 || value > 8)
             return fail(c, IBLB_E_ARG, "pipeline stages must be in [2, 8]");
         c->cfg.lb_stages = value;
+        fit_stages(c);
         invalidate_graphs(c);
         return IBLB_OK;
     }

@@ -196,6 +196,31 @@ def test_observe_parity():
 
 
 # ---------------------------------------------------------- determinism
+def test_wide_lattice_group_shapes_fit_and_agree():
+    # a wide FP32 lattice on which the asked groups and stages do not fit the
+    # block's shared memory: the layout gives groups fewer rows and lowers the
+    # stage count, and every shape gives the default shape's result bit for bit
+    nx, ny, nz = 512, 8, 10
+    W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    outs = []
+    for cells, ns in ((0, 0), (1024, 8), (4096, 3), (512, 2)):
+        g = gpu_ctx(nx, ny, nz, tau=0.8, storage="f32", body_force=(1e-5, 0.0, 0.0))
+        try:
+            if cells:
+                iblb.iblb_set_option(g, iblb.IBLB_OPT_LB_GROUP_CELLS, cells)
+                iblb.iblb_set_option(g, iblb.IBLB_OPT_LB_STAGES, ns)
+            n = iblb.iblb_info(g, 0)["cells"]
+            iblb.iblb_set_populations(g, 0, I.perturbed_populations(n, W, seed=5))
+            iblb.iblb_step(g, 6)
+            iblb.iblb_sync(g)
+            outs.append(iblb.iblb_get_populations(g, 0))
+        finally:
+            iblb.iblb_destroy(g)
+    for f in outs[1:]:
+        np.testing.assert_array_equal(f, outs[0])
+
+
+# ---------------------------------------------------------- determinism
 def test_bitwise_determinism_graph_and_eager():
     sp = I.workload_parity_32()
     xyz, tri = sp.mesh()
