@@ -44,3 +44,26 @@ def test_warm_start_reaches_equilibrium_sooner():
     assert mw < 0.85 * ms
     assert np.median(dth) < 1.0
     assert np.all(warm["status"] == 0)
+
+
+def test_cap_start_against_sphere_and_network():
+    # the spherical-cap start of Sec. III B (the exact cap of angle theta_eq)
+    # as the non-learned warm start: it must also save steps over the
+    # sphere and end at the same angle; how it compares with the network is
+    # printed (the finite xi moves the equilibrium away from a cap of angle
+    # theta_eq, which is what the network learns)
+    s = stream()
+    x = I.warmstart_cases(64, 2)[:8]
+    caps = np.stack([W.cap_profile(t) for t in x[:, 0]])
+    sph = W.run_to_equilibrium(x, max_steps=25000, stream=s)
+    cap = W.run_to_equilibrium(x, profiles=caps, max_steps=25000, stream=s)
+    net = W.run_to_equilibrium(x, profiles=W.predict(W.load_params(), x, s), max_steps=25000, stream=s)
+    ok = (sph["steps"] >= 0) & (cap["steps"] >= 0) & (net["steps"] >= 0)
+    assert ok.sum() >= 6, (sph["steps"], cap["steps"], net["steps"])
+    ms, mc, mn = (r["steps"][ok].mean() for r in (sph, cap, net))
+    dth = np.abs(cap["theta"][ok] - sph["theta"][ok])
+    print(f"mean steps to equilibrium over {ok.sum()} cases: sphere {ms:.0f}, cap {mc:.0f}, network {mn:.0f}; "
+          f"cap |dtheta| median {np.median(dth):.2f} deg")
+    assert mc < ms
+    assert np.median(dth) < 1.0
+

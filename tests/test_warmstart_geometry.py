@@ -99,3 +99,12 @@ def test_equal_area_map_keeps_faces_even():
     radial = (10.0 * W.profile_at(g, np.arccos(np.clip(xyz[:, 2] / r, -1, 1))) / r)[:, None] * xyz
     cv = lambda q: np.std(_face_areas(q, tri)) / np.mean(_face_areas(q, tri))
     assert cv(ours) < 0.5 * cv(radial), (cv(ours), cv(radial))
+
+
+@pytest.mark.parametrize("theta_deg", [20, 45, 90, 135, 160])
+def test_package_cap_profile_equals_oracle(theta_deg):
+    # the spherical-cap start of the package (paper_2503_20605_gb300.warmstart)
+    # against the oracle's exact cap, which the volume constraint pins above
+    from paper_2503_20605_gb300 import warmstart as PW
+    np.testing.assert_allclose(PW.cap_profile(theta_deg), W.cap_profile(np.radians(theta_deg), 64),
+                               rtol=1e-12, atol=1e-12)
