@@ -337,6 +337,67 @@ int orc_membrane_forces(const orc_params *p, const double *xyz, int n_nodes, con
     return clamped;
 }
 
+/* Elastic membrane (the strain-energy framework of Sec. II B with another
+ * energy than the droplet's w = sigma e^a).  With the invariants of eq.
+ * strain_inv, a = log(A / A0) and b = tr(D D^T) / 2 - 1 per triangle, the
+ * Skalak energy per unit reference area is
+ *   w_el = (k_s / 12) (I1^2 + 2 I1 - 2 I2) + (k_alpha / 12) I2^2,
+ *   I1 = 2 b,  I2 = e^(2a) - 1,
+ * and phi_j = -d/dq_j sum_t A0_t w_el(a_t, b_t) is added to phi.  The linear
+ * triangle's D maps the reference edges E1, E2 (from the mesh given at set-up)
+ * to the current ones e1, e2, so with the reference Gram matrix
+ * H = [E_i . E_j] and S = H^-1:  tr(D D^T) = S11 e1.e1 + 2 S12 e1.e2 + S22 e2.e2,
+ * A0 = sqrt(det H) / 2.  Then, with r = A / A0,
+ *   phi_k = -(A0 w_a / A) dA/dq_k - A0 w_b (1/2) dtr/dq_k,
+ *   A0 w_a / A = -(k_s / 3) r + (k_alpha / 3) r (r^2 - 1),   w_b = (k_s / 3)(2 b + 1),
+ *   (1/2) dtr/de1 = S11 e1 + S12 e2,  (1/2) dtr/de2 = S12 e1 + S22 e2,
+ * e1 = q_1 - q_0, e2 = q_2 - q_0 in the face's vertex order.                 */
+void orc_membrane_elastic(const orc_params *p, const double *xyz_ref, const double *xyz, int n_nodes,
+                          const int *tri, int n_tri, double *phi)
+{
+    (void)n_nodes;
+    const double ks = p->shear_modulus, ka = p->area_modulus;
+    for (int t = 0; t < n_tri; ++t) {
+        const int *v = tri + 3 * t;
+        double E1[3], E2[3], e1[3], e2[3], N[3];
+        sub3(xyz_ref + 3 * v[1], xyz_ref + 3 * v[0], E1);
+        sub3(xyz_ref + 3 * v[2], xyz_ref + 3 * v[0], E2);
+        const double h11 = E1[0] * E1[0] + E1[1] * E1[1] + E1[2] * E1[2];
+        const double h12 = E1[0] * E2[0] + E1[1] * E2[1] + E1[2] * E2[2];
+        const double h22 = E2[0] * E2[0] + E2[1] * E2[1] + E2[2] * E2[2];
+        const double det = h11 * h22 - h12 * h12;
+        const double S11 = h22 / det, S12 = -h12 / det, S22 = h11 / det;
+        const double A0 = 0.5 * sqrt(det);
+        sub3(xyz + 3 * v[1], xyz + 3 * v[0], e1);
+        sub3(xyz + 3 * v[2], xyz + 3 * v[0], e2);
+        cross3(e1, e2, N);
+        const double len = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+        const double A = 0.5 * len;
+        const double nh[3] = {N[0] / len, N[1] / len, N[2] / len};
+        const double g11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+        const double g12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+        const double g22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+        const double b = 0.5 * (S11 * g11 + 2.0 * S12 * g12 + S22 * g22) - 1.0;
+        const double r = A / A0;
+        const double cA = -(ks / 3.0) * r + (ka / 3.0) * r * (r * r - 1.0);
+        const double cB = A0 * (ks / 3.0) * (2.0 * b + 1.0);
+        double h1[3], h2[3];     /* (1/2) dtr/de1, (1/2) dtr/de2 */
+        for (int a = 0; a < 3; ++a) {
+            h1[a] = S11 * e1[a] + S12 * e2[a];
+            h2[a] = S12 * e1[a] + S22 * e2[a];
+        }
+        for (int k = 0; k < 3; ++k) {
+            double d[3], gA[3];
+            sub3(xyz + 3 * v[(k + 2) % 3], xyz + 3 * v[(k + 1) % 3], d);
+            cross3(nh, d, gA);   /* 2 dA/dq_k */
+            for (int a = 0; a < 3; ++a) {
+                const double htr = k == 0 ? -(h1[a] + h2[a]) : (k == 1 ? h1[a] : h2[a]);
+                phi[3 * v[k] + a] -= cA * 0.5 * gA[a] + cB * htr;
+            }
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* In/out classification, Sec. II A: tau = tau_in inside the closed interface */
 /* and tau_out outside, re-identified every step by ray tracing.              */
@@ -552,7 +613,7 @@ struct orc_sim {
     double *F;             /* 3*cells: force density of the last step         */
     double *tau;           /* cells                                            */
     int n_nodes, n_tri;
-    double *q, *phi, *qdot;
+    double *q, *phi, *qdot, *qref;
     int *tri;
     double V0, R0;
     long clamped;
@@ -594,6 +655,7 @@ void orc_destroy(orc_sim *s)
     free(s->q);
     free(s->phi);
     free(s->qdot);
+    free(s->qref);
     free(s->tri);
     free(s);
 }
@@ -603,6 +665,7 @@ int orc_set_membrane(orc_sim *s, const double *xyz, int n_nodes, const int *tri,
     free(s->q);
     free(s->phi);
     free(s->qdot);
+    free(s->qref);
     free(s->tri);
     s->n_nodes = n_nodes;
     s->n_tri = n_tri;
@@ -610,7 +673,9 @@ int orc_set_membrane(orc_sim *s, const double *xyz, int n_nodes, const int *tri,
     s->phi = calloc((size_t)3 * (n_nodes ? n_nodes : 1), sizeof(double));
     s->qdot = calloc((size_t)3 * (n_nodes ? n_nodes : 1), sizeof(double));
     s->tri = malloc(sizeof(int) * 3 * (n_tri ? n_tri : 1));
+    s->qref = malloc(sizeof(double) * 3 * (n_nodes ? n_nodes : 1));
     memcpy(s->q, xyz, sizeof(double) * 3 * n_nodes);
+    memcpy(s->qref, xyz, sizeof(double) * 3 * n_nodes);   /* the elastic reference */
     memcpy(s->tri, tri, sizeof(int) * 3 * n_tri);
     s->V0 = n_tri ? orc_mesh_volume(xyz, tri, n_tri) : 0.0;
     s->R0 = cbrt(3.0 * s->V0 / (4.0 * M_PI));
@@ -654,6 +719,8 @@ static void one_step(orc_sim *s)
         s->F[k] = 0.0;
     if (s->n_nodes) {
         s->clamped = orc_membrane_forces(p, s->q, s->n_nodes, s->tri, s->n_tri, s->phi, NULL, NULL);
+        if (p->shear_modulus != 0.0 || p->area_modulus != 0.0)
+            orc_membrane_elastic(p, s->qref, s->q, s->n_nodes, s->tri, s->n_tri, s->phi);
         orc_spread(p, s->q, s->phi, s->n_nodes, s->F);
     }
     for (int a = 0; a < 3; ++a)

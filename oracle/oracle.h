@@ -38,6 +38,8 @@ typedef struct {
     int n, m;
     double h_min_frac;       /* near-wall guard h_eff = max(h, h_min_frac*xi)   */
     int volume_correction;   /* 1: rescale the mesh about its centroid to V0    */
+    double shear_modulus;    /* Skalak membrane moduli k_s, k_alpha added to the */
+    double area_modulus;     /* surface tension (0, 0: the paper's droplet)     */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -62,6 +64,8 @@ double orc_Pi(double h, double A, double xi, int n, int m);
 int    orc_membrane_forces(const orc_params *p, const double *xyz, int n_nodes,
                            const int *tri, int n_tri, double *phi /* 3*n */,
                            double *phi_sigma /* 3*n or NULL */, double *phi_pi /* 3*n or NULL */);
+void   orc_membrane_elastic(const orc_params *p, const double *xyz_ref, const double *xyz, int n_nodes,
+                            const int *tri, int n_tri, double *phi /* 3*n, added to */);
 double orc_mesh_area(const double *xyz, const int *tri, int n_tri);
 double orc_mesh_volume(const double *xyz, const int *tri, int n_tri);
 

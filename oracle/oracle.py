@@ -36,7 +36,8 @@ class Params(C.Structure):
                 ("tau_out", C.c_double), ("tau_in", C.c_double), ("rho0", C.c_double),
                 ("body_force", C.c_double * 3), ("sigma", C.c_double), ("wetting", C.c_int),
                 ("A", C.c_double), ("xi", C.c_double), ("n", C.c_int), ("m", C.c_int),
-                ("h_min_frac", C.c_double), ("volume_correction", C.c_int)]
+                ("h_min_frac", C.c_double), ("volume_correction", C.c_int),
+                ("shear_modulus", C.c_double), ("area_modulus", C.c_double)]
 
 
 _lib = None
@@ -60,6 +61,7 @@ def lib():
             "orc_wetting_A": (C.c_double, [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int]),
             "orc_Pi": (C.c_double, [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int]),
             "orc_membrane_forces": (C.c_int, [pp, dp, C.c_int, ip, C.c_int, dp, dp, dp]),
+            "orc_membrane_elastic": (None, [pp, dp, dp, C.c_int, ip, C.c_int, dp]),
             "orc_mesh_area": (C.c_double, [dp, ip, C.c_int]),
             "orc_mesh_volume": (C.c_double, [dp, ip, C.c_int]),
             "orc_inside": (None, [pp, dp, ip, C.c_int, C.POINTER(C.c_ubyte)]),
@@ -108,7 +110,7 @@ def i32(a):
 
 def make_params(nx, ny, nz, walls=1, tau_out=1.0, tau_in=None, rho0=1.0, body_force=(0, 0, 0),
                 sigma=0.0, wetting=0, A=0.0, xi=1.0, n=6, m=3, h_min_frac=0.5,
-                volume_correction=0) -> Params:
+                volume_correction=0, shear_modulus=0.0, area_modulus=0.0) -> Params:
     p = Params()
     p.nx, p.ny, p.nz, p.walls = nx, ny, nz, walls
     p.tau_out = tau_out
@@ -117,6 +119,7 @@ def make_params(nx, ny, nz, walls=1, tau_out=1.0, tau_in=None, rho0=1.0, body_fo
     p.body_force = (C.c_double * 3)(*body_force)
     p.sigma, p.wetting, p.A, p.xi, p.n, p.m = sigma, wetting, A, xi, n, m
     p.h_min_frac, p.volume_correction = h_min_frac, volume_correction
+    p.shear_modulus, p.area_modulus = shear_modulus, area_modulus
     return p
 
 
@@ -176,6 +179,14 @@ def interp(p, xyz, U):
     out = np.zeros((len(xyz), 3))
     lib().orc_interp(C.byref(p), _d(xyz), len(xyz), _d(U), _d(out))
     return out
+
+
+def membrane_elastic(p, xyz_ref, xyz, tri):
+    """Skalak elastic forces of the mesh xyz against the reference xyz_ref."""
+    xyz_ref, xyz, tri = f64(xyz_ref), f64(xyz), i32(tri)
+    phi = np.zeros((len(xyz), 3))
+    lib().orc_membrane_elastic(C.byref(p), _d(xyz_ref), _d(xyz), len(xyz), _i(tri), len(tri), _d(phi))
+    return phi
 
 
 def membrane_forces(p, xyz, tri):

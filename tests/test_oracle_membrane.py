@@ -203,3 +203,79 @@ def test_near_wall_guard_counts_clamped_nodes(orc):
     h = xyz[:, 2] - 0.5
     assert clamped == int((h < 1.0).sum()) and clamped > 0
     assert np.all(np.isfinite(fp))
+
+
+# ----------------------------------------------- elastic membrane (Skalak)
+def fem_triangle_invariants(X0, X):
+    """The invariants a, b of eq. strain_inv for one linear triangle, from the
+    shape functions of Sec. II B as in fem_triangle_energy, and the
+    reference area A0."""
+    def frame(P):
+        e1 = P[1] - P[0]
+        n = np.cross(e1, P[2] - P[0])
+        e1 = e1 / np.linalg.norm(e1)
+        e2 = np.cross(n / np.linalg.norm(n), e1)
+        return np.array([[(p - P[0]) @ e1, (p - P[0]) @ e2] for p in P])
+    x0, x = frame(X0), frame(X)
+    coef = np.linalg.inv(np.column_stack([x0, np.ones(3)]))
+    D = np.eye(2) + (x - x0).T @ coef[:2, :].T
+    Mdd = D @ D.T
+    a = 0.5 * math.log(0.5 * np.trace(Mdd) ** 2 - 0.5 * np.trace(Mdd @ Mdd))
+    b = 0.5 * np.trace(Mdd) - 1.0
+    A0 = 0.5 * abs(np.linalg.det(np.column_stack([x0[1] - x0[0], x0[2] - x0[0]])))
+    return a, b, A0
+
+
+def skalak_energy(X0, X, ks, ka):
+    """Skalak energy of a mesh triangle by triangle: A0 w with
+    w = ks/12 (I1^2 + 2 I1 - 2 I2) + ka/12 I2^2, I1 = 2b, I2 = e^(2a) - 1."""
+    a, b, A0 = fem_triangle_invariants(X0, X)
+    I1, I2 = 2.0 * b, math.exp(2.0 * a) - 1.0
+    return A0 * (ks / 12.0 * (I1 * I1 + 2.0 * I1 - 2.0 * I2) + ka / 12.0 * I2 * I2)
+
+
+def test_skalak_invariants_match_principal_stretches():
+    # a pure in-plane stretch by (l1, l2) of a right triangle: I1 = l1^2 +
+    # l2^2 - 2 and I2 = l1^2 l2^2 - 1 (the Skalak invariants)
+    X0 = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    l1, l2 = 1.3, 0.8
+    X = X0 * np.array([l1, l2, 1.0])
+    a, b, A0 = fem_triangle_invariants(X0, X)
+    assert math.isclose(2 * b, l1 ** 2 + l2 ** 2 - 2, rel_tol=1e-12)
+    assert math.isclose(math.exp(2 * a) - 1, l1 ** 2 * l2 ** 2 - 1, rel_tol=1e-12)
+    assert math.isclose(A0, 0.5, rel_tol=1e-15)
+
+
+def test_skalak_force_is_minus_energy_gradient(orc):
+    xyz0, tri = I.icosphere(1, 3.0, (8.0, 8.0, 8.0))
+    xyz = I.jitter_nodes(xyz0, 4, 0.25) * 1.05
+    ks, ka = 0.04, 0.3
+    p = params(orc, sigma=0.0, shear_modulus=ks, area_modulus=ka)
+    phi = orc.membrane_elastic(p, xyz0, xyz, tri)
+    h = 1e-6
+
+    def energy(q):
+        return sum(skalak_energy(xyz0[t], q[t], ks, ka) for t in tri)
+    for j, a in ((0, 2), (7, 0), (23, 1), (41, 2)):
+        xp, xm = xyz.copy(), xyz.copy()
+        xp[j, a] += h
+        xm[j, a] -= h
+        assert abs(-(energy(xp) - energy(xm)) / (2 * h) - phi[j, a]) < 1e-7 * max(1.0, abs(phi[j, a]))
+
+
+def test_skalak_force_vanishes_at_rest_and_under_rigid_motion(orc):
+    xyz0, tri = jittered_sphere(level=2, seed=5)
+    p = params(orc, sigma=0.0, shear_modulus=0.05, area_modulus=0.2)
+    assert np.abs(orc.membrane_elastic(p, xyz0, xyz0, tri)).max() < 1e-13
+    c, s = math.cos(0.7), math.sin(0.7)
+    Rz = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    moved = xyz0 @ Rz.T + np.array([1.5, -2.0, 0.25])
+    assert np.abs(orc.membrane_elastic(p, xyz0, moved, tri)).max() < 1e-12
+    # a deformed state: no net force nor torque
+    xyz = I.jitter_nodes(xyz0, 9, 0.3)
+    phi = orc.membrane_elastic(p, xyz0, xyz, tri)
+    assert np.abs(phi).max() > 1e-3
+    assert np.allclose(phi.sum(0), 0.0, atol=1e-13)
+    assert np.allclose(np.cross(xyz, phi).sum(0), 0.0, atol=1e-11)
+    # zero moduli: no elastic force
+    assert not orc.membrane_elastic(params(orc), xyz0, xyz, tri).any()
