@@ -102,6 +102,14 @@ typedef struct {
     double h_min_frac;     /* near-wall guard: h_eff = max(h, h_min_frac * xi); 0 = off */
     int volume_correction; /* 1: after each step rescale the mesh about its node
                               centroid to the initial volume (not in the paper)       */
+    double shear_modulus;  /* k_s >= 0 and k_alpha >= 0 of a Skalak membrane energy   */
+    double area_modulus;   /* w = k_s/12 (I1^2 + 2 I1 - 2 I2) + k_alpha/12 I2^2 per unit
+                              reference area (I1 = 2b, I2 = e^(2a) - 1 with the
+                              invariants of eq. strain_inv), added to the droplet's
+                              sigma e^a; the reference is the mesh given to
+                              iblb_set_membrane.  0, 0: the paper's droplet.  An
+                              extension named by the paper's framework (Sec. II B),
+                              not used in its results.                                */
 } iblb_physics_desc;
 
 /* Observables of one droplet (Sec. III, App. C), FP64. */

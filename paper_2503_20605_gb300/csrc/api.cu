@@ -38,6 +38,7 @@ size_t storage_bytes(int storage) { return storage == IBLB_STORE_F32 ? 4 : 2; }
 
 struct Membrane {
     std::vector<double> xyz;   // current positions (host copy, refreshed on rebuild)
+    std::vector<double> ref;   // the elastic reference: the mesh as given to iblb_set_membrane
     std::vector<int> tri;      // local node indices
     bool set = false;
     double V0 = 0.0;
@@ -59,6 +60,7 @@ struct iblb_ctx {
     void *fbuf[2] = {nullptr, nullptr};
     int cur = 0;
     int *d_tri = nullptr, *d_adj_start = nullptr, *d_adj = nullptr;
+    float4 *d_fref = nullptr;
     int n_red_chunks = 0, mass_blocks = 0;
     double *d_mass = nullptr;
     cudaStream_t user = nullptr, stream = nullptr;
@@ -197,6 +199,10 @@ int check_desc(const iblb_lattice_desc &l, const iblb_physics_desc &p, std::stri
             return 0;
         }
     }
+    if (!(p.shear_modulus >= 0.0) || !(p.area_modulus >= 0.0)) {
+        why = "the membrane moduli must be >= 0";
+        return 0;
+    }
     return 1;
 }
 
@@ -298,6 +304,8 @@ void fill_drop_params(Drop &D, const iblb_lattice_desc &l, const iblb_physics_de
     D.n = p.n;
     D.m = p.m;
     D.volcorr = p.volume_correction != 0;
+    D.ks = (float)p.shear_modulus;
+    D.ka = (float)p.area_modulus;
 }
 
 // shared memory a block of the stream-collide kernel may give its stages: the
@@ -401,6 +409,9 @@ void free_membrane_arrays(iblb_ctx *c)
     dfree(c->A.face_drop);
     dfree(c->d_adj_start);
     dfree(c->d_adj);
+    dfree(c->d_fref);
+    c->d_fref = nullptr;
+    c->A.fref = nullptr;
     dfree(c->A.rec);
     dfree(c->A.clamped);
     dfree(c->A.red_part);
@@ -482,6 +493,35 @@ int rebuild_membranes(iblb_ctx *c)
     CK(dalloc(&c->A.node_drop, N));
     CK(dalloc(&c->d_tri, 3 * (size_t)NT));
     CK(dalloc(&c->A.face_drop, NT));
+    // reference geometry of every face of an elastic droplet: S = H^-1 of the
+    // Gram matrix H = [E_i . E_j] of its reference edges E1 = X1 - X0,
+    // E2 = X2 - X0, and its reference area A0 = sqrt(det H) / 2
+    bool elastic = false;
+    for (int d = 0; d < c->ndrops; ++d)
+        elastic |= c->drops[d].ks != 0.0f || c->drops[d].ka != 0.0f;
+    std::vector<float4> fref;
+    if (elastic) {
+        fref.assign(NT > 0 ? NT : 1, make_float4(0.f, 0.f, 0.f, 1.f));
+        for (int d = 0; d < c->ndrops; ++d) {
+            const Drop &D = c->drops[d];
+            const Membrane &M = c->mem[d];
+            for (int t = 0; t < D.ntri; ++t) {
+                const int *v = &M.tri[3 * (size_t)t];
+                double E1[3], E2[3];
+                for (int a = 0; a < 3; ++a) {
+                    E1[a] = M.ref[3 * (size_t)v[1] + a] - M.ref[3 * (size_t)v[0] + a];
+                    E2[a] = M.ref[3 * (size_t)v[2] + a] - M.ref[3 * (size_t)v[0] + a];
+                }
+                const double h11 = E1[0] * E1[0] + E1[1] * E1[1] + E1[2] * E1[2];
+                const double h12 = E1[0] * E2[0] + E1[1] * E2[1] + E1[2] * E2[2];
+                const double h22 = E2[0] * E2[0] + E2[1] * E2[1] + E2[2] * E2[2];
+                const double det = h11 * h22 - h12 * h12;
+                fref[D.tri0 + t] = make_float4((float)(h22 / det), (float)(-h12 / det), (float)(h11 / det),
+                                               (float)(0.5 * sqrt(det)));
+            }
+        }
+        CK(dalloc(&c->d_fref, fref.size()));
+    }
     CK(dalloc(&c->d_adj_start, N + 1));
     CK(dalloc(&c->d_adj, adj.size()));
     CK(dalloc(&c->A.rec, N));
@@ -505,6 +545,9 @@ int rebuild_membranes(iblb_ctx *c)
     CK(up(c->A.face_drop, fd.data(), sizeof(int) * NT));
     CK(up(c->d_adj_start, start.data(), sizeof(int) * (N + 1)));
     CK(up(c->d_adj, adj.data(), sizeof(int) * adj.size()));
+    if (elastic)
+        CK(up(c->d_fref, fref.data(), sizeof(float4) * fref.size()));
+    c->A.fref = c->d_fref;
     CK(cudaMemsetAsync(c->A.bin_cnt, 0, sizeof(int) * c->A.total_tiles, c->stream));
     CK(cudaMemsetAsync(c->A.split_ok, 0, sizeof(int), c->stream));   // no previous band for these nodes
     c->mem_dirty = false;
@@ -886,6 +929,7 @@ int iblb_set_membrane(iblb_ctx *c, int k, const double *xyz, int n_nodes, const 
         return r;
     Membrane &M = c->mem[k];
     M.xyz.assign(xyz, xyz + 3 * (size_t)n_nodes);
+    M.ref = M.xyz;
     M.tri.assign(tri, tri + 3 * (size_t)n_tri);
     M.set = true;
     M.V0 = V;

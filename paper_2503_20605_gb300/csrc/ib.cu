@@ -100,7 +100,11 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
     const int j = (int)(gid / FL), l = (int)(gid % FL);
     const bool valid = j < a.total_nodes;
     float gx = 0.f, gy = 0.f, gz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, chi = 0.f;
+    float ex = 0.f, ey = 0.f, ez = 0.f;     // elastic (Skalak) force, when the droplet has moduli
     if (valid) {
+        const Drop &Dn = a.drops[a.node_drop[j]];
+        const float ks3 = Dn.ks * (1.0f / 3.0f), ka3 = Dn.ka * (1.0f / 3.0f);
+        const bool elastic = a.fref != nullptr && (ks3 != 0.0f || ka3 != 0.0f);
         const int e1 = a.adj_start[j + 1];
         for (int e = a.adj_start[j] + l; e < e1; e += FL) {
             const int code = a.adj[e];
@@ -126,9 +130,31 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
             } else {
                 dx = (float)(x1 - x0); dy = (float)(y1 - y0); dz = (float)(z1 - z0);
             }
-            gx += 0.5f * (hy * dz - hz * dy);
-            gy += 0.5f * (hz * dx - hx * dz);
-            gz += 0.5f * (hx * dy - hy * dx);
+            const float ax = 0.5f * (hy * dz - hz * dy), ay = 0.5f * (hz * dx - hx * dz),
+                        az = 0.5f * (hx * dy - hy * dx);
+            gx += ax;
+            gy += ay;
+            gz += az;
+            if (elastic) {
+                // Skalak energy against the reference triangle (Sec. II B's
+                // framework): with S = H^-1 and A0 from the reference,
+                // b = (S11 e1.e1 + 2 S12 e1.e2 + S22 e2.e2) / 2 - 1, r = A / A0,
+                // phi_k = -(A0 w_a / A) dA/dq_k - A0 w_b (1/2) dtr/dq_k
+                const float4 R = a.fref[t];
+                const float g11 = e1x * e1x + e1y * e1y + e1z * e1z, g12 = e1x * e2x + e1y * e2y + e1z * e2z;
+                const float g22 = e2x * e2x + e2y * e2y + e2z * e2z;
+                const float b = 0.5f * (R.x * g11 + 2.0f * R.y * g12 + R.z * g22) - 1.0f;
+                const float r = 0.5f * len / R.w;
+                const float cA = r * (ka3 * (r * r - 1.0f) - ks3), cB = R.w * ks3 * (2.0f * b + 1.0f);
+                const float h1x = R.x * e1x + R.y * e2x, h1y = R.x * e1y + R.y * e2y, h1z = R.x * e1z + R.y * e2z;
+                const float h2x = R.y * e1x + R.z * e2x, h2y = R.y * e1y + R.z * e2y, h2z = R.y * e1z + R.z * e2z;
+                const float tx = k == 0 ? -(h1x + h2x) : (k == 1 ? h1x : h2x);
+                const float ty = k == 0 ? -(h1y + h2y) : (k == 1 ? h1y : h2y);
+                const float tz = k == 0 ? -(h1z + h2z) : (k == 1 ? h1z : h2z);
+                ex -= cA * ax + cB * tx;
+                ey -= cA * ay + cB * ty;
+                ez -= cA * az + cB * tz;
+            }
             nx += hx;
             ny += hy;
             nz += hz;
@@ -144,6 +170,12 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
         nz += __shfl_xor_sync(0xffffffffu, nz, o);
         chi += __shfl_xor_sync(0xffffffffu, chi, o);
     }
+    if (a.fref != nullptr)          // the same for every warp of the launch
+        for (int o = FL / 2; o >= 1; o >>= 1) {
+            ex += __shfl_xor_sync(0xffffffffu, ex, o);
+            ey += __shfl_xor_sync(0xffffffffu, ey, o);
+            ez += __shfl_xor_sync(0xffffffffu, ez, o);
+        }
     if (!valid)
         return;
     const int d = a.node_drop[j];
@@ -187,7 +219,7 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
                 r.wx[k] = r.wy[k] = r.wz[k] = 0.0f;
             r.phi[0] = r.phi[1] = r.phi[2] = 0.0f;
         } else {
-            float px = -D.sigma * gx, py = -D.sigma * gy, pz = -D.sigma * gz;
+            float px = -D.sigma * gx + ex, py = -D.sigma * gy + ey, pz = -D.sigma * gz + ez;
             if (D.wetting) {
                 float h = (float)(qz - 0.5);
                 if (h < D.hmin) {

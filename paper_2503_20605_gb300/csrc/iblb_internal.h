@@ -52,6 +52,7 @@ struct Drop {
     float rho0;
     float bf[3];                   // body force density
     float sigma, A, xi, hmin;
+    float ks, ka;                  // Skalak moduli of an elastic membrane (0, 0: a droplet)
     int n, m, wetting, vartau, volcorr;
     double V0, R0;
 };
@@ -117,6 +118,9 @@ struct Arrays {
     double *col_z;                 // MAXC crossings per column (sorted)
     int64_t total_cols;
     int *face_drop;                // droplet of each face
+    const float4 *fref;            // per face, from the mesh given at set-up: S = H^-1 of the
+                                   // reference edge Gram matrix H (x = S11, y = S12, z = S22)
+                                   // and the reference area A0 (w); null when no droplet is elastic
     // reductions
     double *red_part;              // NRED * chunks (volume-correction partials)
     double *red_out;               // NRED * ndrops: (V0/V)^(1/3), cx, cy, cz, V

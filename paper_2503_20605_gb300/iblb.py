@@ -49,7 +49,8 @@ class LatticeDesc(C.Structure):
 class PhysicsDesc(C.Structure):
     _fields_ = [("sigma", C.c_double), ("wetting", C.c_int), ("theta_eq_deg", C.c_double),
                 ("A", C.c_double), ("xi", C.c_double), ("n", C.c_int), ("m", C.c_int),
-                ("h_min_frac", C.c_double), ("volume_correction", C.c_int)]
+                ("h_min_frac", C.c_double), ("volume_correction", C.c_int),
+                ("shear_modulus", C.c_double), ("area_modulus", C.c_double)]
 
 
 class Obs(C.Structure):
@@ -175,10 +176,12 @@ def lattice_desc(nx, ny, nz, tau_out=1.0, lam=1.0, rho0=1.0, storage="f32", wall
     return d
 
 
-def physics_desc(sigma=0.0, theta_eq_deg=None, A=None, xi=2.0, n=6, m=3, h_min_frac=0.5, volume_correction=0):
+def physics_desc(sigma=0.0, theta_eq_deg=None, A=None, xi=2.0, n=6, m=3, h_min_frac=0.5, volume_correction=0,
+                 shear_modulus=0.0, area_modulus=0.0):
     p = PhysicsDesc()
     p.sigma, p.xi, p.n, p.m, p.h_min_frac = sigma, xi, n, m, h_min_frac
     p.volume_correction = int(volume_correction)
+    p.shear_modulus, p.area_modulus = shear_modulus, area_modulus
     if theta_eq_deg is not None:
         p.wetting, p.theta_eq_deg = IBLB_WET_THETA, theta_eq_deg
     elif A is not None:

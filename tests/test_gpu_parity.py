@@ -95,6 +95,52 @@ def test_forces_and_spread_parity(theta, lam):
     assert np.all(F_g[F_o == 0] == 0)
 
 
+# ------------------------------------- elastic membrane (Skalak, Sec. II B framework)
+def test_elastic_membrane_forces_parity():
+    # the reference is the mesh given at set-up; the nodes are then moved to a
+    # stretched, jittered shape whose Skalak forces are of the order of the
+    # surface tension's
+    xyz0, tri = I.icosphere(3, 7.0, (16.3, 15.6, 0.5 + 7.0 + 1.1))
+    c = xyz0.mean(0)
+    xyz = I.jitter_nodes(c + (xyz0 - c) * np.array([1.08, 0.95, 0.97]), 4, 0.12)
+    kw = dict(nx=32, ny=30, nz=24, tau=0.9, sigma=0.02, theta=70.0, xi=2.0, mesh=(xyz0, tri),
+              shear_modulus=0.03, area_modulus=0.2)
+    g, s = pair(**kw)
+    try:
+        iblb.iblb_set_nodes(g, 0, xyz)
+        iblb.iblb_compute_forces(g)
+        phi_g = iblb.iblb_get_node_forces(g, 0)
+    finally:
+        iblb.iblb_destroy(g)
+    phi_o, fs, fp, _ = O.membrane_forces(s.p, xyz, tri)
+    el = O.membrane_elastic(s.p, xyz0, xyz, tri)
+    assert np.abs(el).max() > 0.3 * np.abs(fs).max()
+    phi_o = phi_o + el
+    # FP32 on the GPU: the two elastic terms nearly cancel at small strain
+    assert rel_l2(phi_g, phi_o) < 2e-5
+    assert np.max(np.abs(phi_g - phi_o)) < 1e-4 * np.abs(phi_o).max()
+
+
+def test_elastic_membrane_steps_parity():
+    xyz, tri = I.icosphere(3, 6.0, (16.0, 16.0, 0.5 + 6.0 + 2.0))
+    kw = dict(nx=32, ny=32, nz=24, tau=0.8, sigma=0.01, theta=80.0, xi=2.0, mesh=(xyz, tri),
+              shear_modulus=0.02, area_modulus=0.1)
+    g, s = pair(**kw)
+    try:
+        iblb.iblb_step(g, 200)
+        iblb.iblb_sync(g)
+        rho_g, u_g = iblb.iblb_get_macros(g, 0)
+        q_g = iblb.iblb_get_nodes(g, 0)
+    finally:
+        iblb.iblb_destroy(g)
+    s.step(200)
+    rho_o, u_o = s.macros()
+    q_o = s.nodes()
+    assert rel_l2(u_g, u_o) < 1e-5
+    assert rel_l2(rho_g - 1.0, rho_o - 1.0) < 1e-5
+    assert np.abs(q_g - q_o).max() < 1e-6
+
+
 # ------------------------------------------------------------ a3: in / out
 def _inside_pair(xyz, tri, nx, ny, nz):
     g = gpu_ctx(nx, ny, nz, tau=0.8, lam=10.0, mesh=(xyz, tri))
