@@ -95,6 +95,7 @@ __device__ __forceinline__ int support_tiles(int b, int n, bool periodic, int *o
 // the node that takes slot 0 stamps the tile with the step's generation gen
 // and appends it to the band list.  All 32 lanes of a warp must take part
 // (the partial sums are combined with warp shuffles).
+template <bool EL>     // EL: some droplet of the launch has an elastic membrane (a.fref set)
 __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_t gen)
 {
     const int j = (int)(gid / FL), l = (int)(gid % FL);
@@ -102,9 +103,13 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
     float gx = 0.f, gy = 0.f, gz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, chi = 0.f;
     float ex = 0.f, ey = 0.f, ez = 0.f;     // elastic (Skalak) force, when the droplet has moduli
     if (valid) {
-        const Drop &Dn = a.drops[a.node_drop[j]];
-        const float ks3 = Dn.ks * (1.0f / 3.0f), ka3 = Dn.ka * (1.0f / 3.0f);
-        const bool elastic = a.fref != nullptr && (ks3 != 0.0f || ka3 != 0.0f);
+        float ks3 = 0.0f, ka3 = 0.0f;
+        if (EL) {
+            const Drop &Dn = a.drops[a.node_drop[j]];
+            ks3 = Dn.ks * (1.0f / 3.0f);
+            ka3 = Dn.ka * (1.0f / 3.0f);
+        }
+        const bool elastic = EL && (ks3 != 0.0f || ka3 != 0.0f);
         const int e1 = a.adj_start[j + 1];
         for (int e = a.adj_start[j] + l; e < e1; e += FL) {
             const int code = a.adj[e];
@@ -170,7 +175,7 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
         nz += __shfl_xor_sync(0xffffffffu, nz, o);
         chi += __shfl_xor_sync(0xffffffffu, chi, o);
     }
-    if (a.fref != nullptr)          // the same for every warp of the launch
+    if (EL)
         for (int o = FL / 2; o >= 1; o >>= 1) {
             ex += __shfl_xor_sync(0xffffffffu, ex, o);
             ey += __shfl_xor_sync(0xffffffffu, ey, o);
@@ -219,7 +224,12 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
                 r.wx[k] = r.wy[k] = r.wz[k] = 0.0f;
             r.phi[0] = r.phi[1] = r.phi[2] = 0.0f;
         } else {
-            float px = -D.sigma * gx + ex, py = -D.sigma * gy + ey, pz = -D.sigma * gz + ez;
+            float px = -D.sigma * gx, py = -D.sigma * gy, pz = -D.sigma * gz;
+            if (EL) {
+                px += ex;
+                py += ey;
+                pz += ez;
+            }
             if (D.wetting) {
                 float h = (float)(qz - 0.5);
                 if (h < D.hmin) {
@@ -607,11 +617,12 @@ __device__ bool grid_barrier(const Arrays &a, unsigned &sense)
 }
 
 // ------------------------------------------------------------------ kernels
+template <bool EL>
 __global__ void __launch_bounds__(IB_THREADS) node_force_kernel(Arrays a)
 {
     griddep_wait();
     const uint32_t gen = *a.gen + 1u;                  // committed by the spread
-    force_item(a, (int64_t)blockIdx.x * IB_THREADS + threadIdx.x, gen);
+    force_item<EL>(a, (int64_t)blockIdx.x * IB_THREADS + threadIdx.x, gen);
 }
 
 __global__ void __launch_bounds__(IB_THREADS) spread_kernel(Arrays a)
@@ -647,6 +658,7 @@ __global__ void __launch_bounds__(IB_THREADS) volume_correct_kernel(Arrays a)
 
 // Before the stream-collide kernel: forces and tile lists of every node,
 // grid barrier, spread of every band tile.
+template <bool EL>
 __global__ void __launch_bounds__(IB_THREADS) ib_front_kernel(Arrays a)
 {
     __shared__ SpreadSmem sm;
@@ -656,7 +668,7 @@ __global__ void __launch_bounds__(IB_THREADS) ib_front_kernel(Arrays a)
     const int64_t nf = ((int64_t)a.total_nodes * FL + 31) & ~(int64_t)31;   // whole warps
     const int64_t stride = (int64_t)gridDim.x * IB_THREADS;
     for (int64_t gid = (int64_t)blockIdx.x * IB_THREADS + threadIdx.x; gid < nf; gid += stride)
-        force_item(a, gid, gen);
+        force_item<EL>(a, gid, gen);
     if (!grid_barrier(a, sense))
         return;
     zero_left_tiles(a, gen, cur, blockIdx.x, gridDim.x);
@@ -687,7 +699,7 @@ __global__ void __launch_bounds__(IB_THREADS) ib_back_kernel(Arrays a, int n_chu
 }
 
 int g_sm_count = 0;
-int g_front_blocks = 0, g_back_blocks = 0;
+int g_front_blocks[2] = {0, 0}, g_back_blocks = 0;
 
 int sm_count()
 {
@@ -706,8 +718,10 @@ cudaError_t launch_node_force(const Arrays &a, cudaStream_t s)
     if (a.total_nodes <= 0)
         return cudaSuccess;
     const int64_t threads = (int64_t)a.total_nodes * FL;
-    return launch_k(node_force_kernel, dim3((unsigned)((threads + IB_THREADS - 1) / IB_THREADS)), dim3(IB_THREADS), 0,
-                    s, a.pdl != 0, a);
+    const dim3 grid((unsigned)((threads + IB_THREADS - 1) / IB_THREADS));
+    if (a.fref)
+        return launch_k(node_force_kernel<true>, grid, dim3(IB_THREADS), 0, s, a.pdl != 0, a);
+    return launch_k(node_force_kernel<false>, grid, dim3(IB_THREADS), 0, s, a.pdl != 0, a);
 }
 
 cudaError_t launch_spread(const Arrays &a, cudaStream_t s)
@@ -768,13 +782,14 @@ cudaError_t launch_ib_front(const Arrays &a, int per_sm, cudaStream_t s)
         return cudaSuccess;
     int grid = 0;
     const int64_t want = ((int64_t)a.total_nodes * FL + IB_THREADS - 1) / IB_THREADS;
-    cudaError_t e = coop_grid((const void *)ib_front_kernel, std::max<int64_t>(want, (int64_t)sm_count()), per_sm,
-                              grid, g_front_blocks);
+    const bool el = a.fref != nullptr;
+    const void *fn = el ? (const void *)ib_front_kernel<true> : (const void *)ib_front_kernel<false>;
+    cudaError_t e = coop_grid(fn, std::max<int64_t>(want, (int64_t)sm_count()), per_sm, grid, g_front_blocks[el]);
     if (e != cudaSuccess)
         return e;
     Arrays arg = a;
     void *args[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void *)ib_front_kernel, grid, IB_THREADS, args, 0, s);
+    return cudaLaunchCooperativeKernel(fn, grid, IB_THREADS, args, 0, s);
 }
 
 cudaError_t launch_ib_back(const Arrays &a, int n_chunks_total, bool volcorr, int per_sm, cudaStream_t s)
