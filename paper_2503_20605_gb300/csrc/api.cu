@@ -20,6 +20,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/iblb.h"
 #include "iblb_internal.h"
 
@@ -88,6 +90,12 @@ struct iblb_ctx {
 };
 
 namespace {
+
+// NVTX range around a public call, for timeline tools (no cost without one)
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+};
 
 int fail(iblb_ctx *c, int code, const std::string &msg)
 {
@@ -916,6 +924,7 @@ int iblb_info(const iblb_ctx *ctx, int k, int *n_drops, int64_t *cells, int *n_n
 
 int iblb_set_membrane(iblb_ctx *c, int k, const double *xyz, int n_nodes, const int32_t *tri, int n_tri)
 {
+    Trace trace_("iblb_set_membrane");
     int r = check_k(c, k);
     if (r)
         return r;
@@ -1117,6 +1126,7 @@ int iblb_get_inside(iblb_ctx *c, int k, uint8_t *inside)
 
 int iblb_step(iblb_ctx *c, int nsteps)
 {
+    Trace trace_("iblb_step");
     if (!c)
         return fail(nullptr, IBLB_E_ARG, "null context");
     if (nsteps < 0)
@@ -1145,6 +1155,7 @@ int iblb_step(iblb_ctx *c, int nsteps)
 
 int iblb_sync(iblb_ctx *c)
 {
+    Trace trace_("iblb_sync");
     if (!c)
         return fail(nullptr, IBLB_E_ARG, "null context");
     CK(cudaStreamSynchronize(c->stream));
@@ -1201,6 +1212,7 @@ int observe_mesh(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs
 
 int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs *out)
 {
+    Trace trace_("iblb_observe");
     int r = check_k(c, k);
     if (r || (r = ensure_ready(c)))
         return r;
@@ -1353,6 +1365,7 @@ int iblb_reset_profile(iblb_ctx *c)
 
 int iblb_autotune(iblb_ctx *c, const char *cache_path)
 {
+    Trace trace_("iblb_autotune");
     if (!c)
         return fail(nullptr, IBLB_E_ARG, "null context");
     int r = ensure_ready(c);
