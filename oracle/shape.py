@@ -26,19 +26,46 @@ from __future__ import annotations
 import numpy as np
 
 
-def _derivs(g, du):
+_COEF = {}
+
+
+def _coefficients(u):
+    """Weights of the three-point second-order formulas on the grid u
+    (uniform or not); one-sided for g' at the ends."""
+    key = (u.size, float(u[0]), float(u[1]), float(u[-2]), float(u.sum()))
+    if key not in _COEF:
+        h1, h2 = u[1:-1] - u[:-2], u[2:] - u[1:-1]
+        du = (u[-1] - u[0]) / (u.size - 1)
+        if np.max(np.abs(np.diff(u) - du)) < 1e-12 * abs(du):
+            h1 = h2 = np.full(u.size - 2, du)   # a uniform grid: the symmetric formulas exactly
+        d1 = (-h2 / (h1 * (h1 + h2)), (h2 - h1) / (h1 * h2), h1 / (h2 * (h1 + h2)))
+        d2 = (2.0 / (h1 * (h1 + h2)), -2.0 / (h1 * h2), 2.0 / (h2 * (h1 + h2)))
+        a, b = u[1] - u[0], u[2] - u[1]
+        e0 = (-(2 * a + b) / (a * (a + b)), (a + b) / (a * b), -a / (b * (a + b)))
+        a, b = u[-1] - u[-2], u[-2] - u[-3]
+        e1 = ((2 * a + b) / (a * (a + b)), -(a + b) / (a * b), a / (b * (a + b)))
+        if len(_COEF) > 64:
+            _COEF.clear()
+        _COEF[key] = (d1, d2, e0, e1)
+    return _COEF[key]
+
+
+def _derivs(g, u):
+    """First and second derivatives of g(u) on the grid u (the terms with
+    1 - u^2 vanish at the ends, where only g' is needed)."""
+    d1, d2, e0, e1 = _coefficients(u)
     gd = np.empty_like(g)
     gdd = np.zeros_like(g)
-    gd[1:-1] = (g[2:] - g[:-2]) / (2 * du)
-    gd[0] = (-3 * g[0] + 4 * g[1] - g[2]) / (2 * du)
-    gd[-1] = (3 * g[-1] - 4 * g[-2] + g[-3]) / (2 * du)
-    gdd[1:-1] = (g[2:] - 2 * g[1:-1] + g[:-2]) / du ** 2
+    gd[1:-1] = d1[0] * g[:-2] + d1[1] * g[1:-1] + d1[2] * g[2:]
+    gdd[1:-1] = d2[0] * g[:-2] + d2[1] * g[1:-1] + d2[2] * g[2:]
+    gd[0] = e0[0] * g[0] + e0[1] * g[1] + e0[2] * g[2]
+    gd[-1] = e1[0] * g[-1] + e1[1] * g[-2] + e1[2] * g[-3]
     return gd, gdd
 
 
 def curvature(g, u):
     """div(n) R0 of the surface r = R0 g(u) (the first two terms of eq. YL)."""
-    gd, gdd = _derivs(g, u[1] - u[0])
+    gd, gdd = _derivs(g, u)
     s = 1.0 - u * u
     Q = np.sqrt(s * gd * gd + g * g)
     return (u * g * gd - g * g - s * g * gdd) / Q ** 3 + (u * gd + 3 * g) / (g * Q)
@@ -96,8 +123,9 @@ def _jacobian(x, u, eps, theta, n, m):
                 rows.append(r)
                 cols.append(j)
                 vals.append(d[r] / (2 * hj))
-    w = np.full(N, u[1] - u[0])
-    w[0] = w[-1] = 0.5 * (u[1] - u[0])
+    w = np.empty(N)                             # trapezoid weights on the grid
+    w[1:-1] = 0.5 * (u[2:] - u[:-2])
+    w[0], w[-1] = 0.5 * (u[1] - u[0]), 0.5 * (u[-1] - u[-2])
     rows += [N + 1] * N                         # volume row: d/dg of trapezoid(g^3)
     cols += list(range(N))
     vals += list(3.0 * x[:N] ** 2 * w)
@@ -165,6 +193,48 @@ def solve(theta, eps, n_grid=401, n=6, m=3, steps=None):
             raise RuntimeError(f"no convergence at eps = {e:.4g}")
         e_prev = e
     return u, x[:-2], x[-2], x[-1]
+
+
+def graded_grid(n, uc, beta):
+    """n points on [-1, 1] clustered about uc: u = uc + sinh(x) / beta with x
+    uniform (spacing about 1 / beta times finer at uc than far from it)."""
+    a, b = np.arcsinh((-1.0 - uc) * beta), np.arcsinh((1.0 - uc) * beta)
+    u = uc + np.sinh(np.linspace(a, b, n)) / beta
+    u[0], u[-1] = -1.0, 1.0
+    return u
+
+
+def _sharpest(u, g):
+    _, gdd = _derivs(g, u)
+    return u[np.argmax(np.abs(gdd[2:-2])) + 2]
+
+
+def solve_graded(theta, eps, n_grid=1601, beta=30.0, eps_start=0.05):
+    """Like solve, for small eps: solve at eps_start on a uniform grid, then
+    continue in eps on a grid graded about the sharpest turn of the profile
+    (the contact-line region, whose width shrinks with eps), moving the grid
+    with it.  Returns (u, g, delta, k)."""
+    u, g, d, k = solve(theta, eps_start, n_grid=n_grid)
+    uc = _sharpest(u, g)
+    uu = graded_grid(n_grid, uc, beta)
+    x = np.concatenate([np.interp(uu, u, g), [d, k]])
+    e_prev = eps_start
+    for e in np.geomspace(eps_start, eps, max(2, int(np.ceil(40 * np.log10(eps_start / eps)))) + 1)[1:]:
+        x = x.copy()
+        x[-2] *= e / e_prev
+        x, ok = _newton(x, uu, e, theta, 6, 3)
+        if not ok:
+            raise RuntimeError(f"no convergence at eps = {e:.4g}")
+        e_prev = e
+        uc2 = _sharpest(uu, x[:-2])
+        if abs(uc2 - uc) > 0.02:              # the turn moved: regrid about it
+            uc, un = uc2, graded_grid(n_grid, uc2, beta)
+            x = np.concatenate([np.interp(un, uu, x[:-2]), x[-2:]])
+            uu = un
+            x, ok = _newton(x, uu, e, theta, 6, 3)
+            if not ok:
+                raise RuntimeError(f"no convergence after regridding at eps = {e:.4g}")
+    return uu, x[:-2], x[-2], x[-1]
 
 
 def angle_from_height(g):

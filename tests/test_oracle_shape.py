@@ -6,10 +6,13 @@ is the 0.32 pi printed in the caption of Fig. 8 (tests/golden/paper_fig8.txt);
 the film gap matches the planar solution of App. C; the measured angle moves
 toward the imposed one as xi/R0 decreases.
 
-The 0.28 pi printed for xi/R0 = 0.01 is not pinned: on a grid uniform in u
-the solution is not yet grid-converged there (0.2499 pi with 3201 points,
-0.2534 pi with 6401), the contact-line region needing a finer local
-resolution than this solver has."""
+The 0.28 pi printed for xi/R0 = 0.01 is not used as a pin: on a grid graded
+about the contact line the solution converges to about 0.254 pi there (801
+points 0.2528 pi, 1601 points 0.2540 pi; uniform grids approach it from
+below, 0.2499 pi with 3201 points and 0.2534 pi with 6401), in line with the
+paper's statement that the measured angle tends to theta_eq as xi/R0 -> 0;
+0.28 pi is what the solution gives at xi/R0 = 0.05.  The test below checks
+that approach instead."""
 import os
 
 import numpy as np
@@ -85,3 +88,16 @@ def test_profile_about_centroid_of_hemisphere():
     assert abs(zc - (-0.5 + 0.375)) < 1e-4
     G = S.profile_about_centroid(u, r, np.array([0.0, np.pi]))
     assert abs(G[0] - 0.625) < 1e-4 and abs(G[1] - 0.375) < 1e-4
+
+
+def test_graded_grid_agrees_and_angle_approaches_imposed():
+    # where the uniform grid converges (xi/R0 = 0.05) the graded one agrees
+    th05 = S.angle_from_height(S.solve_graded(np.pi / 4, 0.05, n_grid=801)[1])
+    assert abs(th05 - S.angle_from_height(S.solve(np.pi / 4, 0.05, n_grid=1601)[1])) < 1e-3 * np.pi
+    # at xi/R0 = 0.01 the measured angle is within a fifth of the xi/R0 = 0.1
+    # bias of theta_eq (App. C: theta -> theta_eq as xi/R0 -> 0)
+    th01 = S.angle_from_height(S.solve_graded(np.pi / 4, 0.01, n_grid=801)[1])
+    th10 = S.angle_from_height(S.solve(np.pi / 4, 0.1, n_grid=401)[1])
+    assert np.pi / 4 < th01 < th05 < th10
+    assert th01 - np.pi / 4 < 0.2 * (th10 - np.pi / 4)
+
