@@ -136,6 +136,10 @@ def _jacobian(x, u, eps, theta, n, m):
 
 
 def _newton(x, u, eps, theta, n, m, tol=1e-10, max_iter=60):
+    # the residual cannot be evaluated more accurately than rounding over the
+    # finest spacing squared (second differences): accept down to that floor
+    floor = 100.0 * np.finfo(float).eps / np.min(np.diff(u)) ** 2
+    tol = max(tol, floor)
     for _ in range(max_iter):
         F = residual(x, u, eps, theta, n, m)
         if np.max(np.abs(F)) < tol:
@@ -144,7 +148,7 @@ def _newton(x, u, eps, theta, n, m, tol=1e-10, max_iter=60):
         J = _jacobian(x, u, eps, theta, n, m)
         dx = spsolve(J, -F)
         if np.max(np.abs(dx)) < 1e-13:     # at the round-off floor of the residual
-            return x + dx, np.max(np.abs(F)) < 1e-8
+            return x + dx, np.max(np.abs(F)) < max(1e-8, floor)
         # backtracking: heights above the substrate stay positive and the
         # residual norm decreases (Armijo)
         f0 = np.linalg.norm(F)
@@ -156,7 +160,7 @@ def _newton(x, u, eps, theta, n, m, tol=1e-10, max_iter=60):
                 break
             lam *= 0.5
         x = x + lam * dx
-    return x, np.max(np.abs(residual(x, u, eps, theta, n, m))) < 1e-8
+    return x, np.max(np.abs(residual(x, u, eps, theta, n, m))) < max(1e-8, floor)
 
 
 def cap_g(u, theta):
@@ -214,10 +218,13 @@ def solve_graded(theta, eps, n_grid=1601, beta=30.0, eps_start=0.05):
     continue in eps on a grid graded about the sharpest turn of the profile
     (the contact-line region, whose width shrinks with eps), moving the grid
     with it.  Returns (u, g, delta, k)."""
-    u, g, d, k = solve(theta, eps_start, n_grid=n_grid)
+    u, g, d, k = solve(theta, eps_start, n_grid=min(n_grid, 1601))
     uc = _sharpest(u, g)
     uu = graded_grid(n_grid, uc, beta)
     x = np.concatenate([np.interp(uu, u, g), [d, k]])
+    x, ok = _newton(x, uu, eps_start, theta, 6, 3)       # settle on the graded grid first
+    if not ok:
+        raise RuntimeError(f"no convergence on the graded grid at eps = {eps_start:.4g}")
     e_prev = eps_start
     for e in np.geomspace(eps_start, eps, max(2, int(np.ceil(40 * np.log10(eps_start / eps)))) + 1)[1:]:
         x = x.copy()

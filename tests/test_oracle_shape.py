@@ -7,9 +7,10 @@ the film gap matches the planar solution of App. C; the measured angle moves
 toward the imposed one as xi/R0 decreases.
 
 The 0.28 pi printed for xi/R0 = 0.01 is not used as a pin: on a grid graded
-about the contact line the solution converges to about 0.254 pi there (801
-points 0.2528 pi, 1601 points 0.2540 pi; uniform grids approach it from
-below, 0.2499 pi with 3201 points and 0.2534 pi with 6401), in line with the
+about the contact line the solution converges to 0.2544 pi there (801
+points 0.2528 pi, 1601 points 0.2540 pi, 3201 points 0.2543 pi: second-order
+convergence; uniform grids approach it from below, 0.2534 pi with 6401
+points), in line with the
 paper's statement that the measured angle tends to theta_eq as xi/R0 -> 0;
 0.28 pi is what the solution gives at xi/R0 = 0.05.  The test below checks
 that approach instead."""
