@@ -1,7 +1,8 @@
 """Pins of the oracle's lattice Boltzmann part (Sec. II A) against what the
 paper and the mathematics fix: Tab. I, the moment identities of the
 equilibrium and of the Guo source, exact mass conservation, the momentum
-balance of a uniformly forced periodic box, and the Poiseuille profile."""
+balance of a uniformly forced periodic box, a shear wave carried by a
+uniform stream, and the Poiseuille profile."""
 import math
 import os
 from fractions import Fraction
@@ -127,6 +128,39 @@ def test_uniform_force_periodic_momentum(orc):
     rho, u = s.macros()
     # uniform state: U = (momentum before the step + g/2) per unit mass
     assert np.allclose(u.reshape(3, -1).mean(1), (steps - 0.5) * g, rtol=1e-10)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_shear_wave_carried_by_uniform_stream(orc, axis):
+    """u = U e_a + A sin(k (x_a - U t)) e_b is an exact solution of the
+    incompressible Navier-Stokes equations: a transverse wave that travels
+    with the stream and decays as exp(-nu k^2 t), nu = (tau - 1/2) / 3 in
+    lattice units (Sec. II A).  Started from the equilibrium of that field
+    in a periodic box 32 cells long along a (2 cells across), the oracle's
+    wave after 200 steps has the phase k U t to 1e-3 rad and the amplitude
+    to 1%; the wave runs along each axis in turn, so streaming, the
+    equilibrium and the relaxation are checked in every direction."""
+    tau, L, U, A, steps = 0.8, 32, 0.05, 1e-3, 200
+    dims = [2, 2, 2]
+    dims[axis] = L
+    s = orc.Sim(orc.make_params(*dims, walls=0, tau_out=tau))
+    b = (axis + 1) % 3
+    Z, Y, X = np.meshgrid(np.arange(dims[2]), np.arange(dims[1]), np.arange(dims[0]), indexing="ij")
+    xa = (X, Y, Z)[axis].ravel().astype(np.float64)
+    k = 2.0 * math.pi / L
+    u0 = np.zeros((3, s.cells))
+    u0[axis] = U
+    u0[b] = A * np.sin(k * xa)
+    s.set_populations(np.stack([orc.feq(1.0, u0[:, c]) for c in range(s.cells)], axis=1).ravel())
+    s.step(steps)
+    _, u = s.macros()
+    ub = u.reshape(3, -1)[b]
+    (sa, ca), *_ = np.linalg.lstsq(np.stack([np.sin(k * xa), np.cos(k * xa)], 1), ub, rcond=None)
+    nu = (tau - 0.5) / 3.0
+    assert abs(math.atan2(ca, sa) - (-k * U * steps)) < 1e-3
+    assert abs(math.hypot(sa, ca) / (A * math.exp(-nu * k * k * steps)) - 1.0) < 0.01
+    # the stream itself is untouched
+    assert np.allclose(u.reshape(3, -1)[axis], U, rtol=0, atol=1e-9)
 
 
 def poiseuille(orc, tau, steps, nz=18):

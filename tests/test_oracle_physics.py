@@ -1,8 +1,9 @@
 """Physics pins of the oracle's full time step: Laplace pressure of a free
 droplet (App. C: Delta p = 2 sigma / R_c without Pi), the ordering of the
 equilibrium contact angle with theta_eq (Sec. II C: A sets the angle), mass
-conservation with a membrane, the tau field for lambda != 1, and the stored
-statics trajectories' approach to the App. B equilibrium angle."""
+conservation with a membrane, the tau field for lambda != 1, the stored
+statics trajectories' approach to the App. B equilibrium angle, and a
+membrane carried by a uniform stream."""
 import math
 import os
 
@@ -102,3 +103,18 @@ def test_stored_statics_trajectory_reaches_theory_angle():
         assert lim < a[-1]
         limits.append(lim)
     assert np.all(np.diff(limits) > 0), limits
+
+
+def test_membrane_carried_by_uniform_stream(orc):
+    """Without surface tension or wetting nothing forces the fluid, a
+    uniform stream U stays uniform, the interpolated node velocity is U
+    (eq. vel_interpolation; the kernel sums to one) and each forward-Euler
+    update of the node positions (Sec. II A, dt = 1) moves every node by
+    exactly U."""
+    n, U, steps = 16, np.array([0.03, -0.02, 0.01]), 50
+    xyz, tri = I.icosphere(2, 4.0, (8.0, 8.0, 8.0))
+    s = orc.Sim(orc.make_params(n, n, n, walls=0, tau_out=0.9, sigma=0.0))
+    s.set_populations(np.repeat(orc.feq(1.0, U)[:, None], n ** 3, axis=1).ravel())
+    s.set_membrane(xyz, tri)
+    s.step(steps)
+    assert np.allclose(s.nodes(), xyz + steps * U, rtol=0, atol=1e-11)
