@@ -3,7 +3,7 @@
 Argument marshalling only: every step of the IB-LB time step runs in the
 CUDA library.  Functions take numpy arrays (host) or integer device pointers
 where the C ABI takes device pointers, and raise IblbError on a non-zero
-status.  Importing this module loads libiblb.so and fails loudly if it is
+status.  The first call loads libiblb.so and raises OSError if it is
 missing: there is no CPU fallback.
 """
 from __future__ import annotations
