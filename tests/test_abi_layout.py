@@ -4,7 +4,8 @@ header and prints the size of each descriptor struct and the offset of each
 field, and every integer constant the header defines; the ctypes structures
 and the constants of paper_2503_20605_gb300/iblb.py must agree with them.
 A field added to a header struct without its binding (or in another order)
-would otherwise shift every later field silently."""
+would otherwise shift every later field silently.  The oracle's binding of
+oracle/oracle.h is checked the same way."""
 import ctypes as C
 import os
 import re
@@ -94,3 +95,30 @@ def test_constants_match_header(c_layout):
         assert hasattr(iblb, name), name
         assert getattr(iblb, name) == v, (name, getattr(iblb, name), v)
     assert set(iblb.CODE_NAMES) == {v for k, v in const.items() if k == "IBLB_OK" or k.startswith("IBLB_E_")}
+
+
+def test_oracle_binding_matches_its_header(tmp_path):
+    """The same check for the oracle's ctypes view of oracle/oracle.h: the
+    parameter struct's layout and the order of the observables array."""
+    import oracle.oracle as O
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "oracle.h"', "int main(void) {",
+             '    printf("size %zu\\n", sizeof(orc_params));']
+    for f, _ in O.Params._fields_:
+        lines.append(f'    printf("off {f} %zu\\n", offsetof(orc_params, {f}));')
+    for k, name in enumerate(O.OBS_NAMES):
+        lines.append(f'    printf("obs {name} %d\\n", (int)ORC_OBS_{name.upper()});')
+    lines.append('    printf("nobs %d\\n", (int)ORC_OBS_N);')
+    lines += ["    return 0;", "}"]
+    src, exe = tmp_path / "orc_abi.c", tmp_path / "orc_abi"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "oracle"), "-o", str(exe),
+                    str(src)], check=True, capture_output=True)
+    out = [ln.split() for ln in subprocess.run([str(exe)], check=True, capture_output=True,
+                                               text=True).stdout.splitlines()]
+    got = {(r[0], r[1]) if len(r) == 3 else (r[0],): int(r[-1]) for r in out}
+    assert C.sizeof(O.Params) == got[("size",)]
+    for f, _ in O.Params._fields_:
+        assert getattr(O.Params, f).offset == got[("off", f)], f
+    for k, name in enumerate(O.OBS_NAMES):
+        assert got[("obs", name)] == k, name
+    assert got[("nobs",)] == len(O.OBS_NAMES)
