@@ -224,6 +224,17 @@ int iblb_info(const iblb_ctx *ctx, int k, int *n_drops, int64_t *cells, int *n_n
 int iblb_set_membrane(iblb_ctx *ctx, int k, const double *xyz, int n_nodes, const int32_t *tri,
                       int n_tri);
 
+/* Host-only check of a membrane mesh, the one iblb_set_membrane applies
+ * (Sec. II A: the droplet is a closed triangular mesh; the in/out test and
+ * the volume need it closed and consistently oriented).  No context and no
+ * GPU needed.  xyz: host, 3*n_nodes doubles; tri: host, 3*n_tri int32.
+ * Returns IBLB_OK and writes the enclosed volume to *volume (if not NULL),
+ * IBLB_E_MESH with the reason in iblb_last_error(NULL) when the mesh is not
+ * closed, orientable, of Euler characteristic 2, with every node used,
+ * finite and of positive volume (faces counter-clockwise seen from
+ * outside), and IBLB_E_ARG for NULL arrays. */
+int iblb_check_mesh(const double *xyz, int n_nodes, const int32_t *tri, int n_tri, double *volume);
+
 /* Overwrite / read the node positions of droplet k (host, 3*n_nodes doubles). */
 int iblb_set_nodes(iblb_ctx *ctx, int k, const double *xyz);
 int iblb_get_nodes(iblb_ctx *ctx, int k, double *xyz);

@@ -257,6 +257,11 @@ int validate_mesh(const double *xyz, int n, const int32_t *tri, int nt, std::str
         why = "Euler characteristic is not 2";
         return 0;
     }
+    for (int k = 0; k < 3 * n; ++k)
+        if (!std::isfinite(xyz[k])) {
+            why = "non-finite node position";
+            return 0;
+        }
     double vol = 0.0;
     for (int t = 0; t < nt; ++t) {
         const double *a = xyz + 3 * tri[3 * t], *b = xyz + 3 * tri[3 * t + 1], *cc = xyz + 3 * tri[3 * t + 2];
@@ -268,11 +273,6 @@ int validate_mesh(const double *xyz, int n, const int32_t *tri, int nt, std::str
         why = "mesh volume not positive (faces must be counter-clockwise seen from outside)";
         return 0;
     }
-    for (int k = 0; k < 3 * n; ++k)
-        if (!std::isfinite(xyz[k])) {
-            why = "non-finite node position";
-            return 0;
-        }
     *V = vol;
     return 1;
 }
@@ -919,6 +919,19 @@ int iblb_info(const iblb_ctx *ctx, int k, int *n_drops, int64_t *cells, int *n_n
         *n_nodes = c->mem[k].set ? (int)(c->mem[k].xyz.size() / 3) : 0;
     if (n_tri)
         *n_tri = c->mem[k].set ? (int)(c->mem[k].tri.size() / 3) : 0;
+    return IBLB_OK;
+}
+
+int iblb_check_mesh(const double *xyz, int n_nodes, const int32_t *tri, int n_tri, double *volume)
+{
+    if (!xyz || !tri)
+        return fail(nullptr, IBLB_E_ARG, "iblb_check_mesh: null mesh arrays");
+    std::string why;
+    double V = 0.0;
+    if (!validate_mesh(xyz, n_nodes, tri, n_tri, why, &V))
+        return fail(nullptr, IBLB_E_MESH, why);
+    if (volume)
+        *volume = V;
     return IBLB_OK;
 }
 

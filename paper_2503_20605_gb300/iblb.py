@@ -81,6 +81,7 @@ _SIGS = {
     "iblb_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int),
                             C.POINTER(C.c_int)]),
     "iblb_set_membrane": (C.c_int, [_P, C.c_int, _D, C.c_int, _I32, C.c_int]),
+    "iblb_check_mesh": (C.c_int, [_D, C.c_int, _I32, C.c_int, _D]),
     "iblb_set_nodes": (C.c_int, [_P, C.c_int, _D]),
     "iblb_get_nodes": (C.c_int, [_P, C.c_int, _D]),
     "iblb_set_populations": (C.c_int, [_P, C.c_int, _D]),
@@ -220,6 +221,16 @@ def iblb_set_membrane(ctx, k, xyz, tri):
     xyz = _f64(xyz)
     tri = np.ascontiguousarray(tri, dtype=np.int32)
     _check(ctx, lib().iblb_set_membrane(ctx, k, _d(xyz), xyz.size // 3, tri.ctypes.data_as(_I32), tri.size // 3))
+
+
+def iblb_check_mesh(xyz, tri):
+    """Host-only mesh check (no GPU); returns the enclosed volume."""
+    xyz = _f64(xyz)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    V = C.c_double()
+    _check(None, lib().iblb_check_mesh(_d(xyz), xyz.size // 3, tri.ctypes.data_as(_I32), tri.size // 3,
+                                       C.byref(V)))
+    return V.value
 
 
 def iblb_set_nodes(ctx, k, xyz):
