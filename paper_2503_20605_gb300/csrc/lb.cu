@@ -62,6 +62,13 @@ __constant__ int kCz[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1
 __constant__ int kOpp[Q] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
 
 constexpr float W0 = 1.0f / 3.0f, W1 = 1.0f / 18.0f, W2 = 1.0f / 36.0f;
+// Coefficients 3 w of the first-order (odd) part, chosen so that the
+// lattice isotropy sum 2 K1 + 8 K2 = sum_i 3 w_i c_ix^2 is exactly 1 in FP32
+// arithmetic: K2 = fl(1/12), K1 = (1 - 8 K2) / 2 (both exact).  With
+// fl(3 w) for each class the sum is 1 + 2^-25, and every collision would
+// scale the momentum by 1 + omega 2^-25: in a uniform stream every cell
+// rounds alike and that gain adds up step after step.
+constexpr float K2 = 1.0f / 12.0f, K1 = (1.0f - 8.0f * K2) * 0.5f;
 
 // stage layout: [19][R][P] populations | [3][R][P] force | band flag
 template <typename S>
@@ -325,9 +332,11 @@ __device__ __forceinline__ void collide_group(const Arrays &a, const DropC &c, c
         const float jz = ((m5 + m11) - (m13 - m15)) - m17;
         const float rho = rho0 + drho;
         const float irho = __fdividef(1.0f, rho);
-        const float ux = (FORCE ? fmaf(0.5f, Fx, jx) : jx) * irho;
-        const float uy = (FORCE ? fmaf(0.5f, Fy, jy) : jy) * irho;
-        const float uz = (FORCE ? fmaf(0.5f, Fz, jz) : jz) * irho;
+        // J = rho U = j + F/2 (eq. hydro_var2)
+        const float Jx = FORCE ? fmaf(0.5f, Fx, jx) : jx;
+        const float Jy = FORCE ? fmaf(0.5f, Fy, jy) : jy;
+        const float Jz = FORCE ? fmaf(0.5f, Fz, jz) : jz;
+        const float ux = Jx * irho, uy = Jy * irho, uz = Jz * irho;
         const int64_t cell = (int64_t)P * (y + (int64_t)ny * z) + x;
         if (FORCE && band) {
             const int64_t gi = pcell0 + cell;
@@ -341,35 +350,38 @@ __device__ __forceinline__ void collide_group(const Arrays &a, const DropC &c, c
             X = fmaf(-3.0f * k, fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz)), X);
         S *o = outb + P * y + x;
         st(o, fmaf(om1, s0, W0 * X));
-        // per weight class: b = w X, ea = 9/2 w omega rho, ec = 3 w omega rho,
-        // kf = 9 w k, kd = 3 w k
-        const float b1 = W1 * X, ea1 = (4.5f * W1) * er, ec1 = (3.0f * W1) * er;
-        const float b2 = W2 * X, ea2 = (4.5f * W2) * er, ec2 = (3.0f * W2) * er;
-        const float kf1 = (9.0f * W1) * k, kd1 = (3.0f * W1) * k, kf2 = (9.0f * W2) * k, kd2 = (3.0f * W2) * k;
-#define PAIR(i, j, b, ea, ec, kf, kd, cu_e, cF_e, si, sj)                                                 \
+        // per weight class: b = w X, ea = 9/2 w omega rho, kf = 9 w k for the
+        // even part; the odd part takes 3 w omega rho (c.U) + 3 w k (c.F) as
+        // ec (c.J) + kd (c.F) with ec = K omega, kd = K k, J = rho U, so that
+        // the collision adds exactly (1 - omega/2) F to the momentum and
+        // leaves the rest unchanged, up to the rounding of each result
+        const float b1 = W1 * X, ea1 = (4.5f * W1) * er, ec1 = K1 * omega;
+        const float b2 = W2 * X, ea2 = (4.5f * W2) * er, ec2 = K2 * omega;
+        const float kf1 = (9.0f * W1) * k, kd1 = K1 * k, kf2 = (9.0f * W2) * k, kd2 = K2 * k;
+#define PAIR(i, j, b, ea, ec, kf, kd, cu_e, cJ_e, cF_e, si, sj)                                           \
         {                                                                                                \
-            const float cu_ = (cu_e);                                                                    \
+            const float cu_ = (cu_e), cJ_ = (cJ_e);                                                      \
             float Pp, Mm;                                                                                \
             if (FORCE) {                                                                                 \
                 const float cF_ = (cF_e);                                                                \
-                Mm = fmaf(ec, cu_, kd * cF_);                                                            \
+                Mm = fmaf(ec, cJ_, kd * cF_);                                                            \
                 Pp = fmaf(fmaf(ea, cu_, kf * cF_), cu_, b);                                              \
             } else { /* unfused products: the same roundings as with F = 0 above */                    \
-                Mm = __fmul_rn(ec, cu_);                                                                 \
+                Mm = __fmul_rn(ec, cJ_);                                                                 \
                 Pp = fmaf(__fmul_rn(ea, cu_), cu_, b);                                                   \
             }                                                                                            \
             st(o + (i) * PC, fmaf(om1, (si), Pp + Mm));                                                  \
             st(o + (j) * PC, fmaf(om1, (sj), Pp - Mm));                                                  \
         }
-        PAIR(1, 2, b1, ea1, ec1, kf1, kd1, ux, Fx, s1, s2);
-        PAIR(3, 4, b1, ea1, ec1, kf1, kd1, uy, Fy, s3, s4);
-        PAIR(5, 6, b1, ea1, ec1, kf1, kd1, uz, Fz, s5, s6);
-        PAIR(7, 8, b2, ea2, ec2, kf2, kd2, ux + uy, Fx + Fy, s7, s8);
-        PAIR(9, 10, b2, ea2, ec2, kf2, kd2, ux - uy, Fx - Fy, s9, s10);
-        PAIR(11, 12, b2, ea2, ec2, kf2, kd2, uy + uz, Fy + Fz, s11, s12);
-        PAIR(13, 14, b2, ea2, ec2, kf2, kd2, uy - uz, Fy - Fz, s13, s14);
-        PAIR(15, 16, b2, ea2, ec2, kf2, kd2, ux + uz, Fx + Fz, s15, s16);
-        PAIR(17, 18, b2, ea2, ec2, kf2, kd2, ux - uz, Fx - Fz, s17, s18);
+        PAIR(1, 2, b1, ea1, ec1, kf1, kd1, ux, Jx, Fx, s1, s2);
+        PAIR(3, 4, b1, ea1, ec1, kf1, kd1, uy, Jy, Fy, s3, s4);
+        PAIR(5, 6, b1, ea1, ec1, kf1, kd1, uz, Jz, Fz, s5, s6);
+        PAIR(7, 8, b2, ea2, ec2, kf2, kd2, ux + uy, Jx + Jy, Fx + Fy, s7, s8);
+        PAIR(9, 10, b2, ea2, ec2, kf2, kd2, ux - uy, Jx - Jy, Fx - Fy, s9, s10);
+        PAIR(11, 12, b2, ea2, ec2, kf2, kd2, uy + uz, Jy + Jz, Fy + Fz, s11, s12);
+        PAIR(13, 14, b2, ea2, ec2, kf2, kd2, uy - uz, Jy - Jz, Fy - Fz, s13, s14);
+        PAIR(15, 16, b2, ea2, ec2, kf2, kd2, ux + uz, Jx + Jz, Fx + Fz, s15, s16);
+        PAIR(17, 18, b2, ea2, ec2, kf2, kd2, ux - uz, Jx - Jz, Fx - Fz, s17, s18);
 #undef PAIR
     }
 }

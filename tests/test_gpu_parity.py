@@ -82,12 +82,14 @@ def test_shear_wave_gpu(axis):
     exp(-nu k^2 t) to 1% after 200 steps.
 
     Against the FP64 oracle the bar comes from the FP32 arithmetic: in a
-    uniform stream every cell rounds alike, so the collision's momentum
-    round-off adds up coherently over the steps instead of averaging out
-    (at rest, as in the 500-step parity case, it does average out).  Each
-    step can move a cell's velocity by at most the rounding of its 19
-    stored offsets, 19 half-ulps of the largest one; the GPU velocity must
-    stay within that many steps of it."""
+    uniform stream every cell rounds alike, so any bias of the collision's
+    momentum round-off adds up over the steps instead of averaging out (at
+    rest, as in the 500-step parity case, it does average out).  The
+    collision's first-order coefficients sum to exactly one in FP32 and its
+    odd part is taken from J = rho U itself, so what is left is the rounding
+    of the stored results; the velocity may move by one ulp of the largest
+    stored offset per step.  (With the coefficients fl(3 w), which sum to
+    1 + 2^-25, the stream gained 3.1e-9 per step, 3.4 times this bar.)"""
     tau, L, U, A, steps = 0.8, 32, 0.05, 1e-3, 200
     dims = [8, 8, 8]
     dims[axis] = L
@@ -114,7 +116,7 @@ def test_shear_wave_gpu(axis):
         iblb.iblb_destroy(g)
     u_g, u_o = u_g.reshape(3, -1), u_o.reshape(3, -1)
     off = np.abs(f0 - np.repeat(W, cells)).max()
-    bound = steps * 19 * 0.5 * float(np.spacing(np.float32(off)))
+    bound = steps * float(np.spacing(np.float32(off)))
     ub = u_g[b]
     (sa, ca), *_ = np.linalg.lstsq(np.stack([np.sin(k * xa), np.cos(k * xa)], 1), ub, rcond=None)
     nu = (tau - 0.5) / 3.0
