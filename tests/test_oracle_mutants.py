@@ -155,8 +155,8 @@ def _scratch_tree(dst):
         shutil.copy2(os.path.join(ROOT, pkg, f), os.path.join(dst, pkg, f))
     os.makedirs(os.path.join(dst, "tests"))
     for f in os.listdir(os.path.join(ROOT, "tests")):
-        if f == "conftest.py" or f.startswith("test_oracle_") and f != os.path.basename(__file__) \
-                or f == WSG:
+        pin_file = f.startswith("test_oracle_") and f != os.path.basename(__file__)
+        if f in ("conftest.py", WSG) or pin_file:
             shutil.copy2(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(dst, "tests", "golden"))
 
