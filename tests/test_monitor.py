@@ -68,3 +68,23 @@ def test_fields_exist_in_the_library_observation():
     assert set(monitor.FIELDS) <= set(d)
     r = monitor.record(0, 0, d, 0.0)
     assert r["volume_ratio"] is None and r["ell"] == 0.0
+
+
+@pytest.mark.gpu
+def test_log_of_a_real_context(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_20605_gb300 import inputs as I
+    w = I.workload_parity_32()
+    ctx = iblb.iblb_create(iblb.lattice_desc(w.nx, w.ny, w.nz, tau_out=w.tau),
+                           iblb.physics_desc(sigma=w.sigma, theta_eq_deg=w.theta_deg, xi=w.xi),
+                           torch.cuda.current_stream().cuda_stream)
+    try:
+        iblb.iblb_set_membrane(ctx, 0, *w.mesh())
+        recs = monitor.run_logged(ctx, 20, 10, str(tmp_path / "p.jsonl"))
+    finally:
+        iblb.iblb_destroy(ctx)
+    assert [r["step"] for r in recs] == [0, 10, 20]
+    assert all(r["status"] == 0 for r in recs)
+    assert abs(recs[-1]["volume_ratio"] - 1.0) < 1e-2 and recs[-1]["theta_RV_deg"] < 180.0 + 1e-9
