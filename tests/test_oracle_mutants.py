@@ -109,6 +109,10 @@ MUTANTS = [
      "sqrt((px - cx) * (px - cx) + (py - cy) * (py - cy))", "sqrt(px * px + py * py)", [OBS]),
     ("tau_inside_outside_swapped", "oracle.c", "static void one_step(",
      "in[c] ? p->tau_in : p->tau_out", "in[c] ? p->tau_out : p->tau_in", [PHY]),
+    ("volume_correction_about_origin", "oracle.c", "static void one_step(",
+     "s->q[3 * j + a] = c[a] + (s->q[3 * j + a] - c[a]) * k;", "s->q[3 * j + a] = s->q[3 * j + a] * k;", [OBS]),
+    ("volume_correction_square_root", "oracle.c", "static void one_step(",
+     "double k = cbrt(s->V0 / V);", "double k = sqrt(s->V0 / V);", [OBS]),
     ("advection_half_step", "oracle.c", "static void one_step(",
      "s->q[k] += s->qdot[k];", "s->q[k] += 0.5 * s->qdot[k];", [PHY]),
     ("mlp_tanh_derivative", "mlp.py", "def grad(",
@@ -134,6 +138,10 @@ MUTANTS = [
      "(u * gd + 3 * g)", "(u * gd + 2 * g)", [SHP]),
     ("wall_term_sign_of_cos", "shape.py", "def wall_term(",
      "(1.0 + np.cos(theta))", "(1.0 - np.cos(theta))", [SHP]),
+    ("wall_term_prefactor", "shape.py", "def wall_term(",
+     "(m - 1) * (n - 1) / ((n - m) * eps)", "(m - 1) * n / ((n - m) * eps)", [SHP]),
+    ("curvature_second_term_dropped_u", "shape.py", "def curvature(",
+     "(u * gd + 3 * g) / (g * Q)", "(3 * g) / (g * Q)", [SHP]),
     ("centroid_half_not_three_quarters", "shape.py", "def centroid_height(",
      "0.75 * np.trapezoid", "0.5 * np.trapezoid", [SHP]),
     ("shape_angleh_drops_factor_three", "shape.py", "def angle_from_height(",

@@ -78,3 +78,57 @@ def test_volume_correction_holds_volume(orc):
     s0.set_membrane(xyz, tri)
     s0.step(20)
     assert not np.allclose(s0.nodes(), s.nodes(), atol=1e-12)
+
+
+def _vc_pair(orc, shift):
+    """One step from the same state, with and without the volume correction.
+    The state is a droplet that has run 20 steps (so V != V0), placed
+    `shift` cells along x and y in the periodic box."""
+    sp = I.workload_parity_32()
+    xyz, tri = sp.mesh()
+    A = orc.wetting_A(sp.sigma, math.radians(60.0), sp.xi)
+    kw = dict(tau_out=1.0, sigma=sp.sigma, wetting=1, A=A, xi=sp.xi)
+    s = orc.Sim(orc.make_params(32, 32, 32, **kw))
+    s.set_membrane(xyz, tri)
+    s.step(20)
+    f = s.populations().reshape(19, 30, 32, 32)      # [i][z][y][x], fluid layers only
+    f = np.roll(f, (shift, shift), axis=(2, 3)).ravel()
+    q = s.nodes() + [shift, shift, 0.0]
+    out = []
+    for vc in (0, 1):
+        t = orc.Sim(orc.make_params(32, 32, 32, volume_correction=vc, **kw))
+        t.set_membrane(xyz + [shift, shift, 0.0], tri)   # V0: the volume of the mesh as set
+        t.set_populations(f)
+        t.set_nodes(q)
+        t.step(1)
+        out.append(t.nodes())
+    return out, orc.mesh_volume(xyz, tri), tri
+
+
+def test_volume_correction_keeps_node_centroid(orc):
+    """The correction rescales the mesh about its node centroid (a uniform
+    dilation about c leaves c in place): one corrected step and one
+    uncorrected step from the same state end with the same node centroid,
+    to round-off, while the corrected mesh has the initial volume and the
+    uncorrected one does not.  A dilation about another point (the origin,
+    say) moves the centroid by (k - 1) times its distance from that point."""
+    (q_off, q_on), V0, tri = _vc_pair(orc, 0)
+    assert abs(orc.mesh_volume(q_off, tri) / V0 - 1.0) > 1e-7
+    assert math.isclose(orc.mesh_volume(q_on, tri), V0, rel_tol=1e-13)
+    assert np.abs(q_on.mean(axis=0) - q_off.mean(axis=0)).max() < 1e-12
+    # the correction is a dilation: every node moves along its ray from c
+    c = q_off.mean(axis=0)
+    d_off, d_on = q_off - c, q_on - c
+    k = (d_on * d_off).sum() / (d_off * d_off).sum()
+    assert np.abs(d_on - k * d_off).max() < 1e-12
+    assert abs(k ** 3 - V0 / orc.mesh_volume(q_off, tri)) < 1e-12
+
+
+def test_volume_correction_commutes_with_translation(orc):
+    """The step is translation invariant in the periodic directions, and so
+    is a correction about the node centroid: the droplet moved by whole
+    cells along x and y ends moved by the same amount, with the same shape,
+    to round-off."""
+    (_, q0), _, _ = _vc_pair(orc, 0)
+    (_, q7), _, _ = _vc_pair(orc, 7)
+    assert np.abs(q7 - [7.0, 7.0, 0.0] - q0).max() < 1e-11

@@ -13,7 +13,14 @@ convergence; uniform grids approach it from below, 0.2534 pi with 6401
 points), in line with the
 paper's statement that the measured angle tends to theta_eq as xi/R0 -> 0;
 0.28 pi is what the solution gives at xi/R0 = 0.05.  The test below checks
-that approach instead."""
+that approach instead, and App. C's own structure arbitrates between the two
+values: at xi/R0 = 0.01 the solution must be the cap of eq. gcap away from
+the wall and the plane of eq. gplanar near u = -1, with c = 2/k from its own
+pressure jump and the angle it measures by eq. angleh.  It is, to a few
+parts in a thousand with the measured 0.253 pi; with 0.28 pi both forms miss
+it by about a tenth of R0.  A cap of volume 4 pi/3 whose pressure jump is the
+solution's (k = 0.779) meets the wall at 0.252 pi; 0.28 pi would need k =
+0.885."""
 import os
 
 import numpy as np
@@ -102,3 +109,41 @@ def test_graded_grid_agrees_and_angle_approaches_imposed():
     assert np.pi / 4 < th01 < th05 < th10
     assert th01 - np.pi / 4 < 0.2 * (th10 - np.pi / 4)
 
+
+
+@pytest.fixture(scope="module")
+def sol_001():
+    return S.solve_graded(np.pi / 4, 0.01, n_grid=801)
+
+
+def _gcap(u, c, th):
+    C2 = np.cos(th / 2) ** 2
+    return c * (-C2 * u + np.sqrt(1.0 - C2 * C2 * (1.0 - u * u)))
+
+
+def _gplanar(u, c, th):
+    return -c * np.sin(th / 2) ** 2 / u
+
+
+def test_app_c_structure_at_eps_001(sol_001):
+    """App. C at theta_eq = pi/4, xi/R0 = 0.01 (Fig. 9).  Away from the wall
+    the solution of eq. YL is the spherical cap eq. gcap of radius c = 2/k
+    (its Laplace pressure) meeting the wall at the angle measured by eq.
+    angleh; near u = -1 it is the plane eq. gplanar, z = -c sin^2(theta/2);
+    the film under it has the planar gap of App. C.  The cap radius is tied
+    to the pressure jump k and the angle to the half-height, so the check
+    involves the wall term (through k and the gap) and the curvature (through
+    the cap) independently of the solver."""
+    u, g, delta, k = sol_001
+    c = 2.0 / k
+    th = S.angle_from_height(g)
+    cap, flat = u >= 0.0, u <= -0.95
+    assert np.abs(g[cap] - _gcap(u[cap], c, th)).max() < 1e-2
+    assert np.abs(g[flat] - _gplanar(u[flat], c, th)).max() < 5e-3
+    # the cap radius from the half-height (eq. ell) against 2/k: O(eps)
+    assert abs(g[-1] / np.sin(th / 2) ** 2 / c - 1.0) < 0.015
+    assert abs(delta / S.film_thickness(0.01, k, np.pi / 4) - 1.0) < 1e-5
+    # the printed 0.28 pi does not fit the same structure
+    th_p = 0.28 * np.pi
+    assert np.abs(g[cap] - _gcap(u[cap], c, th_p)).max() > 0.1
+    assert np.abs(g[flat] - _gplanar(u[flat], c, th_p)).max() > 0.05
