@@ -181,6 +181,11 @@ typedef struct {
                                  (whole rows: max(1, round(cells / nx)) rows, at most ny),
                                  in place of IBLB_OPT_LB_ROW_MULT (1..16384; 0 = use the
                                  multiplier; default 768)                                */
+#define IBLB_OPT_GRAPH_CHUNK 11 /* steps per replayed CUDA graph (1..64; default 1): with
+                                 K > 1, iblb_step runs whole chunks of K steps as one
+                                 captured graph each and the rest one step per graph,
+                                 so the host launches once per K steps.  Not used while
+                                 IBLB_OPT_PROFILE is on.  Results are bit-identical.    */
 
 typedef struct iblb_ctx iblb_ctx;
 
@@ -324,9 +329,14 @@ int iblb_mesh_observe_dev(const double *d_xyz, int n_nodes, const int32_t *d_tri
  *   Limit: n_tri <= 1,048,576 and n_nodes <= 524,288; larger meshes return
  *   IBLB_E_ARG without touching the device.
  *   Nothing needs to be zeroed beforehand.
- *   The first call on a device (with that device current) looks up the
- *   array's address with cudaGetSymbolAddress and caches it; make that first
- *   call before capturing any stream.  Any CUDA error returns IBLB_E_CUDA.
+ *   Set-up: the first call in a CUDA context (with that device current)
+ *   loads the library's array and observation kernels into the context
+ *   (CUDA loads modules lazily, and loading allocates device memory) and
+ *   looks up the array's address with cudaGetSymbolAddress.  Only that first
+ *   call may allocate, so make it early, while device memory is still free,
+ *   and before capturing any stream.  The address is kept with the identity
+ *   of its context; a new context on the device (after cudaDeviceReset, say)
+ *   gets the set-up again.  Any CUDA error returns IBLB_E_CUDA.
  *   Not reentrant: calls in flight at the same time on the same device (other
  *   host threads, other streams) share the array and race.  Each call
  *   synchronises `stream` before it returns. */

@@ -7,7 +7,9 @@
  * (Bellantoni et al., arXiv 2503.20605), cited in its comment; where the
  * paper is silent the reading taken is stated in the comment ("Reading").
  *
- * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared oracle.c -lm
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -fPIC -shared oracle.c -lm
+ * (-fopenmp is optional: it only shares the independent cells of the
+ *  stream-collide loop among threads; the results are the same bits.)
  * (-ffp-contract=off keeps every product and sum individually rounded, so that
  *  the decisions taken in floating point -- in/out of a cell -- are those of
  *  plain IEEE arithmetic.)
@@ -20,6 +22,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------- */
 /* D3Q19 velocity set, Tab. I.  Group order as in the table (rest; 6 axis     */
@@ -738,6 +743,10 @@ static void one_step(orc_sim *s)
             s->tau[c] = p->tau_out;
     }
 
+    /* every cell reads the previous populations and writes only its own
+       results, so the z planes are independent: with OpenMP they are shared
+       among threads, with bitwise the same results as one thread */
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < nzf; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -785,6 +794,25 @@ static void one_step(orc_sim *s)
                     s->q[3 * j + a] = c[a] + (s->q[3 * j + a] - c[a]) * k;
         }
     }
+}
+
+/* Threads of the stream-collide loop (1 without OpenMP). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 void orc_step(orc_sim *s, int nsteps)

@@ -90,6 +90,8 @@ void   orc_get_nodes(const orc_sim *s, double *xyz);
 void   orc_set_populations(orc_sim *s, const double *f);
 void   orc_get_populations(const orc_sim *s, double *f);
 void   orc_step(orc_sim *s, int nsteps);
+void   orc_set_threads(int n);   /* threads of the stream-collide loop (OpenMP builds) */
+int    orc_get_threads(void);
 void   orc_get_macros(const orc_sim *s, double *rho, double *u);
 void   orc_get_force_density(const orc_sim *s, double *F);
 void   orc_get_node_forces(const orc_sim *s, double *phi);

@@ -25,8 +25,11 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
             os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "oracle.h"))):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off",
-                               "-fPIC", "-shared", "-o", tmp, SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC", "-shared"]
+        # OpenMP shares the independent cells of the stream-collide loop among
+        # threads (same bits as one thread); plain build where it is missing
+        if subprocess.run(base + ["-fopenmp", "-o", tmp, SRC, "-lm"], capture_output=True).returncode:
+            subprocess.check_call(base + ["-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -47,6 +50,8 @@ def lib():
     global _lib
     if _lib is None:
         L = C.CDLL(build())
+        # one thread unless asked otherwise (set_threads, or ORACLE_THREADS)
+        L.orc_set_threads(int(os.environ.get("ORACLE_THREADS", "1")))
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int)
         pp = C.POINTER(Params)
@@ -76,6 +81,8 @@ def lib():
             "orc_set_populations": (None, [C.c_void_p, dp]),
             "orc_get_populations": (None, [C.c_void_p, dp]),
             "orc_step": (None, [C.c_void_p, C.c_int]),
+            "orc_set_threads": (None, [C.c_int]),
+            "orc_get_threads": (C.c_int, []),
             "orc_get_macros": (None, [C.c_void_p, dp, dp]),
             "orc_get_force_density": (None, [C.c_void_p, dp]),
             "orc_get_node_forces": (None, [C.c_void_p, dp]),
@@ -291,3 +298,12 @@ class Sim:
 
     def clamped(self):
         return lib().orc_clamped_nodes(self.h)
+
+
+def set_threads(n: int) -> None:
+    """Threads of the stream-collide loop (1 when built without OpenMP)."""
+    lib().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return lib().orc_get_threads()

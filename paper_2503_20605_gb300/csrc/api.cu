@@ -78,6 +78,8 @@ struct iblb_ctx {
     int profile = 0;               // 0 off, 1 every phase, 2 whole step only
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     bool gvalid[2] = {false, false};
+    int graph_chunk = 1;           // steps per replayed graph (K-step graphs when > 1)
+    cudaGraphExec_t gchunk[2] = {nullptr, nullptr};   // K steps from buffer parity 0 / 1
     double ph_ms[IBLB_NPHASE] = {};
     double step_ms = 0.0;
     int64_t prof_steps = 0;
@@ -145,6 +147,17 @@ void leave(iblb_ctx *c)
     cudaStreamWaitEvent(c->user, c->ev_out, 0);
 }
 
+// enter() on construction, leave() on every way out of the scope, early
+// error returns included, so that the caller's stream is always ordered
+// after whatever the call managed to queue
+struct Entered {
+    iblb_ctx *c;
+    explicit Entered(iblb_ctx *ctx) : c(ctx) { enter(c); }
+    ~Entered() { leave(c); }
+    Entered(const Entered &) = delete;
+    Entered &operator=(const Entered &) = delete;
+};
+
 void invalidate_graphs(iblb_ctx *c)
 {
     for (int p = 0; p < 2; ++p) {
@@ -152,6 +165,9 @@ void invalidate_graphs(iblb_ctx *c)
             cudaGraphExecDestroy(c->gexec[p]);
         c->gexec[p] = nullptr;
         c->gvalid[p] = false;
+        if (c->gchunk[p])
+            cudaGraphExecDestroy(c->gchunk[p]);
+        c->gchunk[p] = nullptr;
     }
 }
 
@@ -638,11 +654,15 @@ int enqueue_step(iblb_ctx *c, int par, bool forces_only)
     return IBLB_OK;
 }
 
-int capture_step(iblb_ctx *c, int par)
+// Capture `nsteps` consecutive steps, the first from buffer parity `par`,
+// as one graph.
+int capture_steps(iblb_ctx *c, int par, int nsteps, cudaGraphExec_t *out)
 {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    int r = enqueue_step(c, par, false);
+    int r = IBLB_OK;
+    for (int i = 0; i < nsteps && r == IBLB_OK; ++i)
+        r = enqueue_step(c, par ^ (i & 1), false);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (r != IBLB_OK) {
         if (g)
@@ -651,12 +671,21 @@ int capture_step(iblb_ctx *c, int par)
     }
     if (e != cudaSuccess)
         return fail(c, IBLB_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&c->gexec[par], g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess)
+    if (e != cudaSuccess) {
+        *out = nullptr;
         return fail(c, IBLB_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    c->gvalid[par] = true;
+    }
     return IBLB_OK;
+}
+
+int capture_step(iblb_ctx *c, int par)
+{
+    int r = capture_steps(c, par, 1, &c->gexec[par]);
+    if (r == IBLB_OK)
+        c->gvalid[par] = true;
+    return r;
 }
 
 int accumulate_profile(iblb_ctx *c)
@@ -973,13 +1002,12 @@ int iblb_set_nodes(iblb_ctx *c, int k, const double *xyz)
         y[j] = xyz[3 * j + 1];
         z[j] = xyz[3 * j + 2];
     }
-    enter(c);
+    Entered entered_(c);
     CK(cudaMemcpyAsync(c->A.qx + D.node0, x.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->A.qy + D.node0, y.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->A.qz + D.node0, z.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->A.split_ok, 0, sizeof(int), c->stream));   // the previous band says nothing now
     CK(cudaStreamSynchronize(c->stream));   // the host vectors die here
-    leave(c);
     return IBLB_OK;
 }
 
@@ -992,12 +1020,11 @@ int iblb_get_nodes(iblb_ctx *c, int k, double *xyz)
     if (!D.nnodes)
         return fail(c, IBLB_E_STATE, "droplet has no membrane");
     std::vector<double> x(D.nnodes), y(D.nnodes), z(D.nnodes);
-    enter(c);
+    Entered entered_(c);
     CK(cudaMemcpyAsync(x.data(), c->A.qx + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(y.data(), c->A.qy + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(z.data(), c->A.qz + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    leave(c);
     for (int j = 0; j < D.nnodes; ++j) {
         xyz[3 * j] = x[j];
         xyz[3 * j + 1] = y[j];
@@ -1020,11 +1047,10 @@ int iblb_set_populations(iblb_ctx *c, int k, const double *f)
     const Drop &D = c->drops[k];
     Tmp t;
     CK(cudaMalloc(&t.p, sizeof(double) * Q * D.cells));
-    enter(c);
+    Entered entered_(c);
     CK(cudaMemcpyAsync(t.p, f, sizeof(double) * Q * D.cells, cudaMemcpyHostToDevice, c->stream));
     CK(launch_import_populations(c->A, k, c->storage, c->fbuf[c->cur], (const double *)t.p, D.cells, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    leave(c);
     return IBLB_OK;
 }
 
@@ -1036,11 +1062,10 @@ int iblb_get_populations(iblb_ctx *c, int k, double *f)
     const Drop &D = c->drops[k];
     Tmp t;
     CK(cudaMalloc(&t.p, sizeof(double) * Q * D.cells));
-    enter(c);
+    Entered entered_(c);
     CK(launch_export_populations(c->A, k, c->storage, c->fbuf[c->cur], (double *)t.p, D.cells, c->stream));
     CK(cudaMemcpyAsync(f, t.p, sizeof(double) * Q * D.cells, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    leave(c);
     return IBLB_OK;
 }
 
@@ -1053,12 +1078,11 @@ int iblb_get_macros(iblb_ctx *c, int k, double *rho, double *u)
     Tmp t;
     CK(cudaMalloc(&t.p, sizeof(double) * 4 * D.cells));
     double *dr = (double *)t.p, *du = dr + D.cells;
-    enter(c);
+    Entered entered_(c);
     CK(launch_export_macros(c->A, k, c->storage, c->fbuf[c->cur], dr, du, D.cells, c->stream));
     CK(cudaMemcpyAsync(rho, dr, sizeof(double) * D.cells, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(u, du, sizeof(double) * 3 * D.cells, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    leave(c);
     return IBLB_OK;
 }
 
@@ -1071,13 +1095,12 @@ int iblb_compute_forces(iblb_ctx *c)
         return r;
     const int prof = c->profile;
     c->profile = 0;
-    enter(c);
+    Entered entered_(c);
     r = enqueue_step(c, c->cur, true);
     c->profile = prof;
     if (r)
         return r;
     CK(cudaStreamSynchronize(c->stream));
-    leave(c);
     int flags = 0;
     if ((r = read_status(c, false, &flags)))
         return r;
@@ -1095,10 +1118,9 @@ int iblb_get_node_forces(iblb_ctx *c, int k, double *phi)
     if (!D.nnodes)
         return fail(c, IBLB_E_STATE, "droplet has no membrane");
     std::vector<NodeRec> rec(D.nnodes);
-    enter(c);
+    Entered entered_(c);
     CK(cudaMemcpyAsync(rec.data(), c->A.rec + D.node0, sizeof(NodeRec) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    leave(c);
     for (int j = 0; j < D.nnodes; ++j)
         for (int e = 0; e < 3; ++e)
             phi[3 * j + e] = rec[j].phi[e];
@@ -1113,11 +1135,10 @@ int iblb_get_force_density(iblb_ctx *c, int k, double *F)
     const Drop &D = c->drops[k];
     Tmp t;
     CK(cudaMalloc(&t.p, sizeof(double) * 3 * D.cells));
-    enter(c);
+    Entered entered_(c);
     CK(launch_export_force(c->A, k, (double *)t.p, D.cells, c->stream));
     CK(cudaMemcpyAsync(F, t.p, sizeof(double) * 3 * D.cells, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    leave(c);
     return IBLB_OK;
 }
 
@@ -1129,11 +1150,10 @@ int iblb_get_inside(iblb_ctx *c, int k, uint8_t *inside)
     const Drop &D = c->drops[k];
     Tmp t;
     CK(cudaMalloc(&t.p, D.cells));
-    enter(c);
+    Entered entered_(c);
     CK(launch_export_inside(c->A, k, (uint8_t *)t.p, D.cells, c->stream));
     CK(cudaMemcpyAsync(inside, t.p, D.cells, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    leave(c);
     return IBLB_OK;
 }
 
@@ -1147,7 +1167,19 @@ int iblb_step(iblb_ctx *c, int nsteps)
     int r = ensure_ready(c);
     if (r)
         return r;
-    enter(c);
+    Entered entered_(c);
+    // whole chunks of K steps as one graph each (not while profiling, which
+    // times every step from the host)
+    const int K = c->graph_chunk;
+    while (c->graphs && !c->profile && K > 1 && nsteps >= K) {
+        const int par = c->cur;
+        if (!c->gchunk[par] && (r = capture_steps(c, par, K, &c->gchunk[par])))
+            return r;
+        CK(cudaGraphLaunch(c->gchunk[par], c->stream));
+        c->cur ^= K & 1;
+        c->step_count += K;
+        nsteps -= K;
+    }
     for (int i = 0; i < nsteps; ++i) {
         const int par = c->cur;
         if (c->graphs) {
@@ -1162,7 +1194,6 @@ int iblb_step(iblb_ctx *c, int nsteps)
         if (c->profile && (r = accumulate_profile(c)))
             return r;
     }
-    leave(c);
     return IBLB_OK;
 }
 
@@ -1232,7 +1263,7 @@ int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs
     if (!out)
         return fail(c, IBLB_E_ARG, "null output");
     memset(out, 0, sizeof(*out));
-    enter(c);
+    Entered entered_(c);
     CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
     CK(cudaMemcpyAsync(&out->mass, c->d_mass + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     int flags = 0;
@@ -1240,7 +1271,6 @@ int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs
         return r;
     if ((r = observe_mesh(c, k, zcut_frac, eps_flat, out)))
         return r;
-    leave(c);
     return IBLB_OK;
 }
 
@@ -1255,7 +1285,7 @@ int iblb_observe_all(iblb_ctx *c, double zcut_frac, double eps_flat, iblb_obs *o
         return fail(c, IBLB_E_ARG, "null output");
     memset(out, 0, sizeof(*out) * (size_t)c->ndrops);
     std::vector<double> mass(c->ndrops);
-    enter(c);
+    Entered entered_(c);
     CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
     CK(cudaMemcpyAsync(mass.data(), c->d_mass, sizeof(double) * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
     int flags = 0;
@@ -1266,7 +1296,6 @@ int iblb_observe_all(iblb_ctx *c, double zcut_frac, double eps_flat, iblb_obs *o
         if ((r = observe_mesh(c, k, zcut_frac, eps_flat, &out[k])))
             return r;
     }
-    leave(c);
     return IBLB_OK;
 }
 
@@ -1319,6 +1348,13 @@ int iblb_set_option(iblb_ctx *c, int option, int value)
     case IBLB_OPT_FUSED_IB:
         c->fused_ib = value != 0;
         invalidate_graphs(c);
+        return IBLB_OK;
+    case IBLB_OPT_GRAPH_CHUNK:
+        if (value < 1 || value > 64)
+            return fail(c, IBLB_E_ARG, "steps per graph must be in [1, 64]");
+        if (c->graph_chunk != value)
+            invalidate_graphs(c);
+        c->graph_chunk = value;
         return IBLB_OK;
     case IBLB_OPT_PDL:
         c->pdl = value != 0;
@@ -1415,10 +1451,19 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
     int dev = 0, smem_max = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    enter(c);
+    struct Events {   // destroyed on every way out
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events()
+        {
+            for (cudaEvent_t x : e)
+                if (x)
+                    cudaEventDestroy(x);
+        }
+    } ev;
+    CK(cudaEventCreate(&ev.e[0]));
+    CK(cudaEventCreate(&ev.e[1]));
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
+    Entered entered_(c);
     int bs = c->cfg.lb_stages;
     // group sizes of 256 .. 1024 cells in steps of 128 (whole rows), with
     // every pipeline depth and both residencies whose stages fit
@@ -1450,9 +1495,6 @@ int iblb_autotune(iblb_ctx *c, const char *cache_path)
                     bs = ns;
                 }
             }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    leave(c);
     c->cfg.lb_blocks_per_sm = bb;
     c->cfg.lb_row_mult = bm;
     c->cfg.lb_group_cells = bcells;
@@ -1579,10 +1621,22 @@ int iblb_mesh_observe_dev(const double *d_xyz, int n_nodes, const int32_t *d_tri
 // instance) has claimed all free device memory, where any further allocation
 // fails with out-of-memory; or a handler that runs because an allocation just
 // failed and wants to record the droplet's state before giving up.  This
-// variant runs the same kernels on a statically sized __device__ array, so it
-// makes no allocation of any kind.  The array holds the scratch of meshes up
-// to kNoAllocMaxChunks reduction chunks (each RED_FACES faces and RED_NODES
-// nodes): 1,048,576 faces and 524,288 nodes, 53.6 KB of doubles.
+// variant runs the same kernels on a statically sized __device__ array.  The
+// array holds the scratch of meshes up to kNoAllocMaxChunks reduction chunks
+// (each RED_FACES faces and RED_NODES nodes): 1,048,576 faces and 524,288
+// nodes, 53.6 KB of doubles.
+//
+// Set-up.  The first call made in a CUDA context (normally a device's primary
+// context) loads the library's code for that context, looks up the array's
+// device address with cudaGetSymbolAddress and checks the result.  Module
+// loading is lazy by default and a load allocates device memory, so the
+// set-up loads the array's module and the observation kernels at once; after
+// it, calls on that context allocate nothing.  The address is kept per device
+// together with the identity of the context it was taken in: if the context
+// changes (after cudaDeviceReset, or with another context made current), the
+// set-up runs again instead of reusing an address of a context that is gone.
+// So make one call per device early, while memory is still free, and before
+// any stream capture.
 //
 // Nothing in the array needs to start at zero: every element the kernels read
 // is written earlier in the same call.  The array is one per device and the
@@ -1595,11 +1649,75 @@ constexpr int kNoAllocMaxFaces = kNoAllocMaxChunks * RED_FACES;
 constexpr int kNoAllocMaxNodes = kNoAllocMaxChunks * RED_NODES;
 constexpr int64_t kNoAllocScratch = (int64_t)NRED * kNoAllocMaxChunks + 32 + 5 * (int64_t)kNoAllocMaxChunks + 8;
 constexpr int kNoAllocMaxDevices = 256;
+struct NoAllocSlot {
+    unsigned long long ctx_id = 0;   // 0: no set-up yet (context ids start at 1)
+    double *ptr = nullptr;
+};
 std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+NoAllocSlot g_noalloc[kNoAllocMaxDevices];
+
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// the unique id of the calling thread's current context (0 if none), through
+// the driver entry points that the runtime hands out
+cudaError_t current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    *id = 0;
+    if (!get_current || !get_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess)
+            return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorSymbolNotFound;
+        get_current = (CtxGetCurrentFn)f1;
+        get_id = (CtxGetIdFn)f2;
+    }
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0)
+        return cudaErrorDeviceUninitialized;
+    if (ctx && get_id(ctx, id) != 0)
+        return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 }  // namespace
 
 static __device__ __align__(256) double g_observe_scratch[kNoAllocScratch];
+
+namespace {
+// the set-up described above, for the current device and context
+cudaError_t noalloc_scratch(int dev, double **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e != cudaSuccess)
+        return e;
+    NoAllocSlot &slot = g_noalloc[dev];
+    if (id == 0 || slot.ctx_id != id) {
+        double *p = nullptr;
+        e = cudaGetSymbolAddress((void **)&p, g_observe_scratch);   // makes the primary context current if none is
+        if (e != cudaSuccess)
+            return e;
+        if ((e = preload_observe_kernels()) != cudaSuccess)
+            return e;
+        if ((e = current_context_id(&id)) != cudaSuccess)
+            return e;
+        if (id == 0)
+            return cudaErrorDeviceUninitialized;
+        slot.ctx_id = id;
+        slot.ptr = p;
+    }
+    *out = slot.ptr;
+    return cudaSuccess;
+}
+}  // namespace
 
 extern "C" {
 
@@ -1620,14 +1738,7 @@ int iblb_mesh_observe_dev_noalloc(const double *d_xyz, int n_nodes, const int32_
     if (dev < 0 || dev >= kNoAllocMaxDevices)
         return fail(nullptr, IBLB_E_ARG, "iblb_mesh_observe_dev_noalloc: device ordinal out of range");
     double *scr = nullptr;
-    {
-        // The address of the array on this device is looked up once, on the
-        // first call made with the device current, and cached.
-        std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev])
-            CK(cudaGetSymbolAddress((void **)&g_noalloc_ptr[dev], g_observe_scratch));
-        scr = g_noalloc_ptr[dev];
-    }
+    CK(noalloc_scratch(dev, &scr));
     cudaStream_t s = (cudaStream_t)stream;
     CK(launch_observe_view(d_xyz, d_xyz + 1, d_xyz + 2, 3, d_tri, n_tri, 0, n_nodes, R0, zcut_frac, eps_flat, scr,
                            out, s));

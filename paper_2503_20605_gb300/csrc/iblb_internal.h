@@ -203,6 +203,9 @@ int64_t observe_scratch_doubles(int n_nodes, int n_tri);
 cudaError_t launch_observe_view(const double *qx, const double *qy, const double *qz, int stride,
                                 const int *tri, int ntri, int node0, int nnodes, double R0, double zcut_frac,
                                 double eps_flat, double *scratch, double *h_out, cudaStream_t s);
+// Bring the code of the observation kernels onto the current device now
+// (module loading is lazy by default, and a load allocates device memory).
+cudaError_t preload_observe_kernels();
 
 // Conversions of droplet d (device pointers; `cells` = that droplet's cells).
 cudaError_t launch_export_populations(const Arrays &a, int d, int storage, const void *f, double *out,

@@ -32,8 +32,14 @@ namespace iblb {
 
 namespace {
 
-constexpr int LB_THREADS = 256;                   // consumer threads per block
-constexpr int LB_BLOCK = LB_THREADS + 32;         // + one producer warp
+constexpr int LB_THREADS = 256;                   // consumer threads per block (FP32 storage)
+// 16-bit storage takes two cells per work item and needs more registers per
+// thread: 7 consumer warps (+ the producer) keep two blocks of 8 warps on an
+// SM at up to 128 registers, where two blocks of 9 warps allow 96
+template <typename S>
+constexpr int cons_threads() { return sizeof(S) == 2 ? 224 : LB_THREADS; }
+template <typename S>
+constexpr int lb_block() { return cons_threads<S>() + 32; }   // + one producer warp
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: bounded mbarrier wait
 constexpr int LB_MAX_STAGES = 8;
 
@@ -56,6 +62,7 @@ __device__ __forceinline__ int find_drop_group(const Drop *D, int n, int g)
     }
     return lo;
 }
+
 
 __constant__ int kCy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1, 0, 0, 0, 0};
 __constant__ int kCz[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
@@ -98,10 +105,11 @@ __device__ __forceinline__ void group_rows(const Drop &D, int g, int &y0, int &z
 // is the common case), with the thread's first cell (r0, x0) of a group.
 struct DropC {
     int d, nx, ny, P, R, PC, nzf, walls, vartau, gpp, block0, step_r, step_x, r0, x0;
+    int npr, pstep_r, pstep_x, pr0, px0;   // the same walk over cell pairs (x, x + 1), x even
     float inv_gpp, bfx, bfy, bfz, rho0, omega_out, omega_in;
     bool has_bf;
     int64_t pcell0, col0;
-    __device__ __forceinline__ void load(const Drop &D, int dd)
+    __device__ __forceinline__ void load(const Drop &D, int dd, int nt)
     {
         d = dd;
         nx = D.nx;
@@ -114,10 +122,15 @@ struct DropC {
         vartau = D.vartau;
         gpp = D.lb_gpp;
         block0 = D.lb_block0;
-        step_r = LB_THREADS / nx;
-        step_x = LB_THREADS - step_r * nx;
+        step_r = nt / nx;
+        step_x = nt - step_r * nx;
         r0 = threadIdx.x / nx;
         x0 = threadIdx.x - r0 * nx;
+        npr = (nx + 1) >> 1;
+        pstep_r = nt / npr;
+        pstep_x = nt - pstep_r * npr;
+        pr0 = threadIdx.x / npr;
+        px0 = threadIdx.x - pr0 * npr;
         inv_gpp = 1.0f / (float)gpp;
         bfx = D.bf[0];
         bfy = D.bf[1];
@@ -386,8 +399,248 @@ __device__ __forceinline__ void collide_group(const Arrays &a, const DropC &c, c
     }
 }
 
+// Two adjacent cells (x, x + 1), x even, per work item: for 16-bit storage
+// the pair shares one 32-bit shared-memory load per population (the x shift
+// of population i is taken from the pair at x for one cell and from one
+// 16-bit load for the other), one packed conversion and one 32-bit store per
+// population.  Each cell's arithmetic is exactly collide_group's.
+template <typename S>
+struct PairOf;
+template <>
+struct PairOf<__half> {
+    using T = __half2;
+    static __device__ __forceinline__ float lo(T v) { return __low2float(v); }
+    static __device__ __forceinline__ float hi(T v) { return __high2float(v); }
+    static __device__ __forceinline__ T pack(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <>
+struct PairOf<__nv_bfloat16> {
+    using T = __nv_bfloat162;
+    static __device__ __forceinline__ float lo(T v) { return __low2float(v); }
+    static __device__ __forceinline__ float hi(T v) { return __high2float(v); }
+    static __device__ __forceinline__ T pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+
+// BGK + Guo of one cell from its 19 pulled offsets s (the arithmetic of
+// collide_group, for the pair path): post-collision offsets into o, the
+// velocity into u.
+template <bool FORCE>
+__device__ __forceinline__ void bgk_guo_cell(const float (&s)[Q], float Fx, float Fy, float Fz, float omega,
+                                             float rho0, float (&o)[Q], float &ux, float &uy, float &uz)
+{
+    const float p1 = s[1] + s[2], m1 = s[1] - s[2], p3 = s[3] + s[4], m3 = s[3] - s[4], p5 = s[5] + s[6],
+                m5 = s[5] - s[6];
+    const float p7 = s[7] + s[8], m7 = s[7] - s[8], p9 = s[9] + s[10], m9 = s[9] - s[10];
+    const float p11 = s[11] + s[12], m11 = s[11] - s[12], p13 = s[13] + s[14], m13 = s[13] - s[14];
+    const float p15 = s[15] + s[16], m15 = s[15] - s[16], p17 = s[17] + s[18], m17 = s[17] - s[18];
+    const float drho = ((s[0] + p1) + (p3 + p5)) + ((p7 + p9) + (p11 + p13)) + (p15 + p17);
+    const float jx = ((m1 + m7) + (m9 + m15)) + m17;
+    const float jy = ((m3 + m7) - (m9 - m11)) + m13;
+    const float jz = ((m5 + m11) - (m13 - m15)) - m17;
+    const float rho = rho0 + drho;
+    const float irho = __fdividef(1.0f, rho);
+    const float Jx = FORCE ? fmaf(0.5f, Fx, jx) : jx;
+    const float Jy = FORCE ? fmaf(0.5f, Fy, jy) : jy;
+    const float Jz = FORCE ? fmaf(0.5f, Fz, jz) : jz;
+    ux = Jx * irho;
+    uy = Jy * irho;
+    uz = Jz * irho;
+    const float om1 = 1.0f - omega, k = fmaf(-0.5f, omega, 1.0f), er = omega * rho;
+    float X = omega * fmaf(-1.5f * rho, fmaf(ux, ux, fmaf(uy, uy, uz * uz)), drho);
+    if (FORCE)
+        X = fmaf(-3.0f * k, fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz)), X);
+    o[0] = fmaf(om1, s[0], W0 * X);
+    const float b1 = W1 * X, ea1 = (4.5f * W1) * er, ec1 = K1 * omega;
+    const float b2 = W2 * X, ea2 = (4.5f * W2) * er, ec2 = K2 * omega;
+    const float kf1 = (9.0f * W1) * k, kd1 = K1 * k, kf2 = (9.0f * W2) * k, kd2 = K2 * k;
+#define PAIR(i, j, b, ea, ec, kf, kd, cu_e, cJ_e, cF_e)                                                    \
+    {                                                                                                    \
+        const float cu_ = (cu_e), cJ_ = (cJ_e);                                                          \
+        float Pp, Mm;                                                                                    \
+        if (FORCE) {                                                                                     \
+            const float cF_ = (cF_e);                                                                    \
+            Mm = fmaf(ec, cJ_, kd * cF_);                                                                \
+            Pp = fmaf(fmaf(ea, cu_, kf * cF_), cu_, b);                                                  \
+        } else {                                                                                         \
+            Mm = __fmul_rn(ec, cJ_);                                                                     \
+            Pp = fmaf(__fmul_rn(ea, cu_), cu_, b);                                                       \
+        }                                                                                                \
+        o[i] = fmaf(om1, s[i], Pp + Mm);                                                                 \
+        o[j] = fmaf(om1, s[j], Pp - Mm);                                                                 \
+    }
+    PAIR(1, 2, b1, ea1, ec1, kf1, kd1, ux, Jx, Fx);
+    PAIR(3, 4, b1, ea1, ec1, kf1, kd1, uy, Jy, Fy);
+    PAIR(5, 6, b1, ea1, ec1, kf1, kd1, uz, Jz, Fz);
+    PAIR(7, 8, b2, ea2, ec2, kf2, kd2, ux + uy, Jx + Jy, Fx + Fy);
+    PAIR(9, 10, b2, ea2, ec2, kf2, kd2, ux - uy, Jx - Jy, Fx - Fy);
+    PAIR(11, 12, b2, ea2, ec2, kf2, kd2, uy + uz, Jy + Jz, Fy + Fz);
+    PAIR(13, 14, b2, ea2, ec2, kf2, kd2, uy - uz, Jy - Jz, Fy - Fz);
+    PAIR(15, 16, b2, ea2, ec2, kf2, kd2, ux + uz, Jx + Jz, Fx + Fz);
+    PAIR(17, 18, b2, ea2, ec2, kf2, kd2, ux - uz, Jx - Jz, Fx - Fz);
+#undef PAIR
+}
+
+// omega of cell (x, y, z) of a droplet with variable tau: tau_in iff an odd
+// number of the column's ray crossings lie below the cell (the in/out test)
+template <bool VARTAU>
+__device__ __forceinline__ float cell_omega(const Arrays &a, const DropC &c, int x, int y, int z)
+{
+    float omega = c.omega_out;
+    if (VARTAU && c.vartau) {
+        const int64_t col = c.col0 + x + (int64_t)c.nx * y;
+        const int cnt = min(a.col_cnt[col], MAXC);
+        const double Z = (double)(z + c.walls);
+        int par = 0;
+        for (int q = 0; q < cnt; ++q)
+            par ^= a.col_z[col * MAXC + q] < Z;
+        if (par)
+            omega = c.omega_in;
+    }
+    return omega;
+}
+
+// kk: the block's count of groups so far.  When the group's pairs do not
+// divide evenly among the consumer threads, the threads that take one pair
+// more change from group to group (a rotation by kk times the remainder),
+// so that no warp is always the last to release a stage.
+template <typename S, bool VARTAU, bool FORCE>
+__device__ __forceinline__ void collide_pairs(const Arrays &a, const DropC &c, const Stage<S> &stg, int y0, int z,
+                                              int nr, bool band, S *__restrict__ dst, int kk)
+{
+    using PT = typename PairOf<S>::T;
+    using PO = PairOf<S>;
+    const int nx = c.nx, ny = c.ny, P = c.P, R = c.R;
+    const int PC = c.PC;
+    const int64_t pcell0 = c.pcell0;
+    const bool bbm = c.walls && z == 0;            // rows pulled from z-1 bounced at the bottom
+    const bool bbp = c.walls && z == c.nzf - 1;    // rows pulled from z+1 bounced at the top
+    const int RP = R * P;
+    S *outb = dst + (int64_t)Q * pcell0 + (int64_t)P * ny * z;
+    const int64_t TP = a.total_pcells;
+    float *U = a.U;
+    const int npr = c.npr, step_r = c.pstep_r, step_x = c.pstep_x;
+    int r = c.pr0, px = c.px0;
+    constexpr int NT = cons_threads<S>();
+    const int extra = (nr * npr) % NT;
+    if (extra) {
+        int e0 = threadIdx.x + (int)(((int64_t)kk * extra) % NT);
+        if (e0 >= NT)
+            e0 -= NT;
+        r = e0 / npr;
+        px = e0 - r * npr;
+    }
+    for (; r < nr; r += step_r, px += step_x) {
+        if (px >= npr) {
+            px -= npr;
+            ++r;
+            if (r >= nr)
+                break;
+        }
+        const int x = 2 * px, y = y0 + r;
+        const bool hasB = x + 1 < nx;              // an odd row ends on a single cell
+        const int xm = x ? x - 1 : nx - 1;         // source of the +x populations of cell x
+        const int xp2 = x + 2 < nx ? x + 2 : x + 2 - nx;   // source of the -x populations of cell x + 1
+        const S *Rr = stg.pop + r * P;
+        PT pv[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            pv[i] = *reinterpret_cast<const PT *>(Rr + i * RP + x);
+#define SC(i, xx) cvt(Rr[(i) * RP + (xx)])
+        float FAx = 0.f, FAy = 0.f, FAz = 0.f, FBx = 0.f, FBy = 0.f, FBz = 0.f;
+        if (FORCE) {
+            FAx = FBx = c.bfx;
+            FAy = FBy = c.bfy;
+            FAz = FBz = c.bfz;
+            if (band) {     // F vanishes outside band tiles
+                const float *Fr = stg.F + r * P + x;
+                const float2 f0 = *reinterpret_cast<const float2 *>(Fr);
+                const float2 f1 = *reinterpret_cast<const float2 *>(Fr + RP);
+                const float2 f2 = *reinterpret_cast<const float2 *>(Fr + 2 * RP);
+                FAx += f0.x;
+                FBx += f0.y;
+                FAy += f1.x;
+                FBy += f1.y;
+                FAz += f2.x;
+                FBz += f2.y;
+            }
+        }
+        const int64_t cell = (int64_t)P * (y + (int64_t)ny * z) + x;
+        S *o = outb + P * y + x;
+        float oa[Q];
+        {   // cell x: c_x = 0 from the pair's low half, +x from x - 1, -x from the pair's high half
+            float sa[Q];
+            sa[0] = PO::lo(pv[0]);
+            sa[3] = PO::lo(pv[3]);
+            sa[4] = PO::lo(pv[4]);
+            sa[5] = PO::lo(pv[5]);
+            sa[6] = PO::lo(pv[6]);
+            sa[11] = PO::lo(pv[11]);
+            sa[12] = PO::lo(pv[12]);
+            sa[13] = PO::lo(pv[13]);
+            sa[14] = PO::lo(pv[14]);
+            sa[1] = SC(1, xm);
+            sa[7] = SC(7, xm);
+            sa[9] = SC(9, xm);
+            sa[15] = bbm ? PO::lo(pv[15]) : SC(15, xm);
+            sa[17] = bbp ? PO::lo(pv[17]) : SC(17, xm);
+            // (the -x populations of the last cell of an odd row wrap to x = 0)
+            sa[2] = hasB ? PO::hi(pv[2]) : SC(2, 0);
+            sa[8] = hasB ? PO::hi(pv[8]) : SC(8, 0);
+            sa[10] = hasB ? PO::hi(pv[10]) : SC(10, 0);
+            sa[16] = bbp ? PO::lo(pv[16]) : (hasB ? PO::hi(pv[16]) : SC(16, 0));
+            sa[18] = bbm ? PO::lo(pv[18]) : (hasB ? PO::hi(pv[18]) : SC(18, 0));
+            float ux, uy, uz;
+            bgk_guo_cell<FORCE>(sa, FAx, FAy, FAz, cell_omega<VARTAU>(a, c, x, y, z), c.rho0, oa, ux, uy, uz);
+            if (FORCE && band) {
+                const int64_t gi = pcell0 + cell;
+                U[gi] = ux;
+                U[TP + gi] = uy;
+                U[2 * TP + gi] = uz;
+            }
+        }
+        if (hasB) {  // cell x + 1: c_x = 0 from the high half, +x from the low half, -x from x + 2
+            float sb[Q], ob[Q];
+            sb[0] = PO::hi(pv[0]);
+            sb[3] = PO::hi(pv[3]);
+            sb[4] = PO::hi(pv[4]);
+            sb[5] = PO::hi(pv[5]);
+            sb[6] = PO::hi(pv[6]);
+            sb[11] = PO::hi(pv[11]);
+            sb[12] = PO::hi(pv[12]);
+            sb[13] = PO::hi(pv[13]);
+            sb[14] = PO::hi(pv[14]);
+            sb[1] = PO::lo(pv[1]);
+            sb[7] = PO::lo(pv[7]);
+            sb[9] = PO::lo(pv[9]);
+            sb[15] = bbm ? PO::hi(pv[15]) : PO::lo(pv[15]);
+            sb[17] = bbp ? PO::hi(pv[17]) : PO::lo(pv[17]);
+            sb[2] = SC(2, xp2);
+            sb[8] = SC(8, xp2);
+            sb[10] = SC(10, xp2);
+            sb[16] = bbp ? PO::hi(pv[16]) : SC(16, xp2);
+            sb[18] = bbm ? PO::hi(pv[18]) : SC(18, xp2);
+            float ux, uy, uz;
+            bgk_guo_cell<FORCE>(sb, FBx, FBy, FBz, cell_omega<VARTAU>(a, c, x + 1, y, z), c.rho0, ob, ux, uy, uz);
+            if (FORCE && band) {
+                const int64_t gi = pcell0 + cell + 1;
+                U[gi] = ux;
+                U[TP + gi] = uy;
+                U[2 * TP + gi] = uz;
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                *reinterpret_cast<PT *>(o + (int64_t)i * PC) = PO::pack(oa[i], ob[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                st(o + (int64_t)i * PC, oa[i]);
+        }
+#undef SC
+    }
+}
+
 template <typename S, bool VARTAU>
-__global__ void __launch_bounds__(LB_BLOCK, 2)
+__global__ void __launch_bounds__(lb_block<S>(), 2)
     lb_kernel(Arrays a, const S *__restrict__ src, S *__restrict__ dst, int ns, const int *__restrict__ list,
               const int *__restrict__ count, int no_force)
 {
@@ -402,7 +655,7 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
     if (threadIdx.x == 0) {
         for (int i = 0; i < ns; ++i) {
             mbar_init(&full[i], 32);
-            mbar_init(&empty[i], LB_THREADS);
+            mbar_init(&empty[i], cons_threads<S>());
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -413,7 +666,7 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
     // groups are in flight; each consumer warp moves on to the next group as
     // soon as its data landed, without waiting for the other warps.
     bool failed = false;
-    if (threadIdx.x >= LB_THREADS) {
+    if (threadIdx.x >= cons_threads<S>()) {
         int st_i = 0;
         uint32_t use = 0, bits = 0;
         DropC c;
@@ -433,7 +686,7 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
             const int g = list ? list[ig] : ig;
             const int d = find_drop_group(a.drops, a.ndrops, g);
             if (d != c.d)
-                c.load(a.drops[d], d);
+                c.load(a.drops[d], d, cons_threads<S>());
             int y0, z, nr;
             c.rows(g, y0, z, nr);
             produce<S>(a, c, src, y0, z, nr, smem_raw + st_i * a.lb_stage_bytes, &full[st_i],
@@ -444,15 +697,15 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
             }
         }
     } else {
-        int st_i = 0;
+        int st_i = 0, kk = 0;
         uint32_t phase = 0;
         DropC c;
         c.d = -1;
-        for (int ig = blockIdx.x; ig < total; ig += gridDim.x) {
+        for (int ig = blockIdx.x; ig < total; ig += gridDim.x, ++kk) {
             const int g = list ? list[ig] : ig;
             const int d = find_drop_group(a.drops, a.ndrops, g);
             if (d != c.d)
-                c.load(a.drops[d], d);
+                c.load(a.drops[d], d, cons_threads<S>());
             int y0, z, nr;
             c.rows(g, y0, z, nr);
             if (!mbar_wait_bounded(&full[st_i], phase, WAIT_CYCLES)) {
@@ -461,10 +714,17 @@ __global__ void __launch_bounds__(LB_BLOCK, 2)
             }
             const Stage<S> stg(smem_raw + st_i * a.lb_stage_bytes, c.R, c.P);
             const bool band = *stg.flag != 0;
-            if (band || c.has_bf)
-                collide_group<S, VARTAU, true>(a, c, stg, y0, z, nr, band, dst);
-            else
-                collide_group<S, VARTAU, false>(a, c, stg, y0, z, nr, false, dst);
+            if constexpr (sizeof(S) == 2) {      // 16-bit storage: two cells per work item
+                if (band || c.has_bf)
+                    collide_pairs<S, VARTAU, true>(a, c, stg, y0, z, nr, band, dst, kk);
+                else
+                    collide_pairs<S, VARTAU, false>(a, c, stg, y0, z, nr, false, dst, kk);
+            } else {
+                if (band || c.has_bf)
+                    collide_group<S, VARTAU, true>(a, c, stg, y0, z, nr, band, dst);
+                else
+                    collide_group<S, VARTAU, false>(a, c, stg, y0, z, nr, false, dst);
+            }
             mbar_arrive(&empty[st_i]);
             if (++st_i == ns) {
                 st_i = 0;
@@ -491,7 +751,7 @@ cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, c
     if (e != cudaSuccess)
         return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LB_BLOCK, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, lb_block<S>(), smem);
     if (e != cudaSuccess)
         return e;
     if (per_sm < 1)
@@ -503,9 +763,9 @@ cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, c
     grid = grid < total ? grid : total;
     const int nf = no_force ? 1 : 0;
     if (vartau)
-        return launch_k(lb_kernel<S, true>, dim3(grid), dim3(LB_BLOCK), smem, s, a.pdl != 0, a, (const S *)src,
+        return launch_k(lb_kernel<S, true>, dim3(grid), dim3(lb_block<S>()), smem, s, a.pdl != 0, a, (const S *)src,
                         (S *)dst, ns, list, count, nf);
-    return launch_k(lb_kernel<S, false>, dim3(grid), dim3(LB_BLOCK), smem, s, a.pdl != 0, a, (const S *)src, (S *)dst,
+    return launch_k(lb_kernel<S, false>, dim3(grid), dim3(lb_block<S>()), smem, s, a.pdl != 0, a, (const S *)src, (S *)dst,
                     ns, list, count, nf);
 }
 

@@ -327,6 +327,22 @@ cudaError_t launch_observe_view(const double *qx, const double *qy, const double
     return observe_view(m, R0, zcut_frac, eps_flat, scratch, h_out, s);
 }
 
+cudaError_t preload_observe_kernels()
+{
+    // under lazy module loading a kernel's code reaches the device at its
+    // first launch or at the first query of its attributes
+    cudaFuncAttributes fa;
+    const void *k[] = {(const void *)pass1_view_kernel, (const void *)fold_view_kernel,
+                       (const void *)pass2_view_kernel, (const void *)fold_sums_kernel,
+                       (const void *)pass3_view_kernel};
+    for (const void *f : k) {
+        cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_mass(const Arrays &a, int storage, const void *f, double *d_out, int mass_blocks,
                         cudaStream_t s)
 {

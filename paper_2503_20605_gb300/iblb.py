@@ -27,7 +27,7 @@ IBLB_NPHASE = 6
 PHASE_NAMES = ["forces", "spread", "inout", "lb", "advect", "reduce"]
 IBLB_OPT_GRAPHS, IBLB_OPT_PROFILE, IBLB_OPT_LB_BLOCKS_PER_SM, IBLB_OPT_LB_ROW_MULT, IBLB_OPT_LB_STAGES = 0, 1, 2, 3, 4
 IBLB_OPT_FUSED_IB, IBLB_OPT_IB_BLOCKS_PER_SM, IBLB_OPT_SPLIT_LB, IBLB_OPT_LB_FAR_BLOCKS_PER_SM = 5, 6, 7, 8
-IBLB_OPT_PDL, IBLB_OPT_LB_GROUP_CELLS = 9, 10
+IBLB_OPT_PDL, IBLB_OPT_LB_GROUP_CELLS, IBLB_OPT_GRAPH_CHUNK = 9, 10, 11
 
 CODE_NAMES = {0: "IBLB_OK", -1: "IBLB_E_ARG", -2: "IBLB_E_MESH", -3: "IBLB_E_NOMEM", -4: "IBLB_E_CUDA",
               -5: "IBLB_E_UNSTABLE", -6: "IBLB_E_TIMEOUT", -7: "IBLB_E_STATE", -8: "IBLB_E_IO",

@@ -2,10 +2,10 @@
 half-scale statics case (64^3 box, tau = 1, L4 icosphere of R = 12,
 sigma = 0.005, xi = 2, wetting from theta_eq by Eq. A_choice, wall plane at
 z = 0.5 per Sec. III, no volume correction) for theta_eq in {30, 60, 90,
-120, 150} degrees, observed every 1000 steps up to 10000.  The contact
-angle follows Eq. angleh with the initial radius R0 and with the current
-volume-equivalent radius.  Only oracle/ and the seeded input module are
-used; the five runs go to five processes (spawned) and take about 20 min.
+120, 150} degrees, observed every 1000 steps up to 20000 (the step count
+of the 128^3 statics sweep).  The contact angle follows Eq. angleh with
+the initial radius R0 and with the current volume-equivalent radius.  Only oracle/ and the seeded input module are
+used; the five runs go to five processes (spawned) and take about 40 min.
 
     python tests/golden/make_statics64.py
 """
@@ -18,7 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 ANGLES = (30.0, 60.0, 90.0, 120.0, 150.0)
-STEPS, EVERY = 10000, 1000
+STEPS, EVERY = 20000, 1000
 COLS = ("volume", "area", "zmin", "zmax", "theta_R0", "theta_RV", "rc_cut", "rc_flat", "mass")
 
 

@@ -327,11 +327,17 @@ def test_bitwise_determinism_graph_and_eager():
     sp = I.workload_parity_32()
     xyz, tri = sp.mesh()
     outs = []
-    for graphs in (1, 1, 0):
+    # one graph per step (twice), eager launches, and K-step graphs: 60 steps
+    # as 7 chunks of 8 plus 4 single steps, as 8 chunks of 7 (odd: each
+    # chunk ends on the other buffer) plus 4, and in calls of 13 steps
+    for graphs, chunk, calls in ((1, 1, [60]), (1, 1, [60]), (0, 1, [60]), (1, 8, [60]), (1, 7, [60]),
+                                 (1, 4, [13, 13, 13, 13, 8])):
         g = gpu_ctx(32, 32, 32, sigma=sp.sigma, theta=sp.theta_deg, xi=sp.xi, mesh=(xyz, tri))
         try:
             iblb.iblb_set_option(g, iblb.IBLB_OPT_GRAPHS, graphs)
-            iblb.iblb_step(g, 60)
+            iblb.iblb_set_option(g, iblb.IBLB_OPT_GRAPH_CHUNK, chunk)
+            for n in calls:
+                iblb.iblb_step(g, n)
             iblb.iblb_sync(g)
             outs.append((iblb.iblb_get_populations(g, 0), iblb.iblb_get_nodes(g, 0)))
         finally:

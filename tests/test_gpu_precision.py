@@ -73,6 +73,53 @@ def test_offset_codec_roundtrip(storage):
         iblb.iblb_destroy(ctx)
 
 
+def storage_ulp(s, storage):
+    """One unit in the last place of the stored offsets s: FP16 keeps 11
+    significant bits (subnormal spacing 2^-24), BF16 8."""
+    mant, tiny = (10, 2.0 ** -24) if storage == "f16" else (7, 2.0 ** -133)
+    e = np.floor(np.log2(np.maximum(np.abs(s), 1e-30)))
+    return np.maximum(2.0 ** (e - mant), tiny)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("shape,walls,bf", [((16, 12, 10), 1, (2e-6, -1e-6, 5e-7)),
+                                            ((13, 10, 11), 1, (2e-6, -1e-6, 5e-7)),
+                                            ((21, 9, 9), 1, (0.0, 0.0, 0.0)),
+                                            ((12, 9, 8), 0, (1e-6, 0.0, -2e-6)),
+                                            ((9, 8, 8), 0, (0.0, 0.0, 0.0))])
+def test_lb_step_16bit_elementwise(storage, shape, walls, bf):
+    """One stream-collide step on 16-bit offsets, cell by cell and
+    population by population against the FP64 oracle run from the same
+    decoded populations: the kernel computes in FP32 and rounds once to the
+    storage type, so every stored offset is within one unit in its last
+    place of the oracle's.  Odd row lengths (the last cell of a row without
+    a partner), both walls, periodic z, with and without a body force.  A
+    population pulled from a wrong cell or direction is off by the
+    perturbation itself, orders of magnitude more."""
+    import oracle.oracle as O
+    nx, ny, nz = shape
+    lat = iblb.lattice_desc(nx, ny, nz, tau_out=0.8, storage=storage, walls=walls, body_force=bf)
+    ctx = iblb.iblb_create(lat, iblb.physics_desc(), stream())
+    try:
+        cells = iblb.iblb_info(ctx, 0)["cells"]
+        iblb.iblb_set_populations(ctx, 0, I.perturbed_populations(cells, W, seed=23, amp=2e-2))
+        f0 = iblb.iblb_get_populations(ctx, 0)          # exactly what the kernel reads
+        iblb.iblb_step(ctx, 1)
+        iblb.iblb_sync(ctx)
+        f1 = iblb.iblb_get_populations(ctx, 0)
+    finally:
+        iblb.iblb_destroy(ctx)
+    s = O.Sim(O.make_params(nx, ny, nz, walls=walls, tau_out=0.8, body_force=bf))
+    s.set_populations(f0)
+    s.step(1)
+    fo = s.populations()
+    off = np.repeat(W, cells)
+    err = np.abs(f1 - fo)
+    tol = storage_ulp(fo - off, storage) + 1e-12
+    bad = np.flatnonzero(err > tol)
+    assert bad.size == 0, (bad[:10], err[bad[:10]], tol[bad[:10]])
+
+
 def load_golden():
     rows = np.loadtxt(GOLDEN)
     cols = ["theta_eq", "step", "volume", "area", "zmin", "zmax", "theta_R0", "theta_RV", "rc_cut", "rc_flat",

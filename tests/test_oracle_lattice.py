@@ -188,3 +188,25 @@ def test_poiseuille_tau1(orc):
     ux, exact = poiseuille(orc, 1.0, 8000)
     err = np.max(np.abs(ux - exact)) / exact.max()
     assert err < 5e-3, err
+
+
+def test_threaded_stream_collide_is_bitwise_serial(orc):
+    """The oracle's stream-collide loop shared among threads (an OpenMP
+    build) gives the same bits as one thread: every cell is independent."""
+    from paper_2503_20605_gb300 import inputs as I
+    sp = I.workload_parity_32()
+    xyz, tri = sp.mesh()
+    A = orc.wetting_A(sp.sigma, math.radians(sp.theta_deg), sp.xi)
+    out = []
+    n0 = orc.threads()
+    try:
+        for nt in (1, 4):
+            orc.set_threads(nt)
+            s = orc.Sim(orc.make_params(32, 32, 32, tau_out=0.9, tau_in=2.0, sigma=sp.sigma, wetting=1, A=A,
+                                        xi=sp.xi, body_force=(1e-6, 0.0, 0.0), volume_correction=1))
+            s.set_membrane(xyz, tri)
+            s.step(10)
+            out.append((s.populations(), s.nodes()))
+    finally:
+        orc.set_threads(n0)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])

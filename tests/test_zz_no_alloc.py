@@ -70,3 +70,33 @@ def test_noalloc_rejects_meshes_beyond_its_scratch(env):
     # the call still works after a rejected one
     ref, a, _ = _both(torch, iblb, (d_xyz, d_tri, n, nt), 4.0)
     np.testing.assert_allclose(a, ref, rtol=RTOL, atol=RTOL * np.abs(ref).max())
+
+
+def test_noalloc_with_device_memory_exhausted(env):
+    """The use the call exists for: a caching allocator (torch's, here) holds
+    every free byte of device memory, so that any further allocation fails.
+    After one earlier call in this context (which did the set-up), the call
+    still works and gives the same bits as before memory ran out."""
+    torch, iblb = env
+    m = _mesh(torch, 4, 12.0, 6)
+    d_xyz, d_tri, n, nt = m
+    ref, a, _ = _both(torch, iblb, m, 12.0)        # the warm-up call is among these
+    s = torch.cuda.current_stream().cuda_stream
+    hog, got = [], []
+    try:
+        chunk = 1 << 32
+        while chunk >= 1 << 20:
+            try:
+                hog.append(torch.empty(chunk, dtype=torch.uint8, device="cuda"))
+            except torch.cuda.OutOfMemoryError:
+                chunk //= 2
+        with pytest.raises(torch.cuda.OutOfMemoryError):
+            torch.empty(2 << 20, dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            got.append(iblb.iblb_mesh_observe_dev_noalloc(d_xyz.data_ptr(), n, d_tri.data_ptr(), nt, 12.0,
+                                                          0.05, 0.1, s))
+    finally:
+        del hog
+        torch.cuda.empty_cache()
+    for g in got:
+        np.testing.assert_allclose(g, ref, rtol=RTOL, atol=RTOL * np.abs(ref).max())
