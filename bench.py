@@ -150,11 +150,11 @@ def make_ctx(iblb, spec, storage, stream):
 
 def launches_per_step(spec):
     specs = spec if isinstance(spec, list) else [spec]
-    n = 1 + 3 + 1 + 1                # forces (opens the step); scan, fill, spread; stream-collide; advect
+    n = 1 + 1 + 1 + 1                # forces and tile lists; spread; stream-collide; interpolation + advection
     if any(w.lam != 1.0 for w in specs):
         n += 3                       # column reset, face crossings, column sort
     if any(w.volume_correction for w in specs):
-        n += 2                       # FP64 volume/centroid reduction, rescale
+        n += 1                       # FP64 volume and centroid, rescale (one cooperative launch)
     return n
 
 

@@ -302,7 +302,8 @@ int iblb_reset_profile(iblb_ctx *ctx);
 int iblb_autotune(iblb_ctx *ctx, const char *cache_path);
 
 /* Checkpoint: write / read the complete dynamic state (populations, nodes,
- * V0, step counter) of every droplet to / from a binary file.  Loading needs
+ * V0, the volume correction computed in the last step, step counter) of
+ * every droplet to / from a binary file.  Loading needs
  * a context created with the same descriptors and membranes.  A resumed run
  * is bitwise identical to an uninterrupted one. */
 int iblb_save(iblb_ctx *ctx, const char *path);

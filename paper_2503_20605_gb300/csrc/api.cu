@@ -39,7 +39,8 @@ const double kWh[Q] = {1.0 / 3.0,  1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.
 size_t storage_bytes(int storage) { return storage == IBLB_STORE_F32 ? 4 : 2; }
 
 struct Membrane {
-    std::vector<double> xyz;   // current positions (host copy, refreshed on rebuild)
+    std::vector<double> xyz;   // positions as stored on the device (host copy, refreshed on rebuild)
+    double corr[NRED] = {1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // its row of red_out (pending correction)
     std::vector<double> ref;   // the elastic reference: the mesh as given to iblb_set_membrane
     std::vector<int> tri;      // local node indices
     bool set = false;
@@ -411,9 +412,13 @@ int download_nodes(iblb_ctx *c)
     CK(cudaMemcpyAsync(x.data(), c->A.qx, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(y.data(), c->A.qy, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(z.data(), c->A.qz, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<double> ro((size_t)NRED * c->ndrops);
+    CK(cudaMemcpyAsync(ro.data(), c->A.red_out, sizeof(double) * ro.size(), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     for (int d = 0; d < c->ndrops; ++d) {
         const Drop &D = c->drops[d];
+        if (D.nnodes)
+            memcpy(c->mem[d].corr, &ro[(size_t)NRED * d], sizeof(double) * NRED);
         for (int j = 0; j < D.nnodes; ++j) {
             c->mem[d].xyz[3 * j] = x[D.node0 + j];
             c->mem[d].xyz[3 * j + 1] = y[D.node0 + j];
@@ -428,6 +433,10 @@ void free_membrane_arrays(iblb_ctx *c)
     dfree(c->A.qx);
     dfree(c->A.qy);
     dfree(c->A.qz);
+    dfree(c->A.px);
+    dfree(c->A.py);
+    dfree(c->A.pz);
+    c->A.px = c->A.py = c->A.pz = nullptr;
     dfree(c->A.node_drop);
     dfree(c->d_tri);
     dfree(c->A.face_drop);
@@ -514,6 +523,9 @@ int rebuild_membranes(iblb_ctx *c)
     CK(dalloc(&c->A.qx, N));
     CK(dalloc(&c->A.qy, N));
     CK(dalloc(&c->A.qz, N));
+    CK(dalloc(&c->A.px, N));
+    CK(dalloc(&c->A.py, N));
+    CK(dalloc(&c->A.pz, N));
     CK(dalloc(&c->A.node_drop, N));
     CK(dalloc(&c->d_tri, 3 * (size_t)NT));
     CK(dalloc(&c->A.face_drop, NT));
@@ -571,6 +583,12 @@ int rebuild_membranes(iblb_ctx *c)
     CK(up(c->d_adj, adj.data(), sizeof(int) * adj.size()));
     if (elastic)
         CK(up(c->d_fref, fref.data(), sizeof(float4) * fref.size()));
+    {   // each droplet's pending volume correction (none for a new membrane)
+        std::vector<double> ro((size_t)NRED * c->ndrops);
+        for (int d = 0; d < c->ndrops; ++d)
+            memcpy(&ro[(size_t)NRED * d], c->mem[d].corr, sizeof(double) * NRED);
+        CK(up(c->A.red_out, ro.data(), sizeof(double) * ro.size()));
+    }
     c->A.fref = c->d_fref;
     CK(cudaMemsetAsync(c->A.bin_cnt, 0, sizeof(int) * c->A.total_tiles, c->stream));
     CK(cudaMemsetAsync(c->A.split_ok, 0, sizeof(int), c->stream));   // no previous band for these nodes
@@ -606,8 +624,10 @@ int enqueue_step(iblb_ctx *c, int par, bool forces_only)
     const bool split = nodes && c->split_lb && !forces_only;
     if (split) {
         CK(launch_classify(a, s));
-        if (c->any_vartau)
+        if (c->any_vartau) {
+            CK(launch_corrected_positions(a, s));     // the force kernel has not written them yet
             CK(launch_inout(a, s));
+        }
         CK(cudaEventRecord(c->ev_fork, s));
         CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
         CK(launch_lb(a, c->storage, c->fbuf[par], c->fbuf[par ^ 1], c->any_vartau, c->cfg, c->side,
@@ -643,10 +663,8 @@ int enqueue_step(iblb_ctx *c, int par, bool forces_only)
         if (nodes)
             CK(launch_interp_advect(a, s));
         CK(mark(5));
-        if (nodes && c->any_volcorr) {
-            CK(launch_mesh_reduce(a, c->n_red_chunks, s));
-            CK(launch_volume_correct(a, s));
-        }
+        if (nodes && c->any_volcorr)
+            CK(launch_volume_correction(a, c->n_red_chunks, s));
     }
     if (split)
         CK(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -984,6 +1002,8 @@ int iblb_set_membrane(iblb_ctx *c, int k, const double *xyz, int n_nodes, const 
     M.tri.assign(tri, tri + 3 * (size_t)n_tri);
     M.set = true;
     M.V0 = V;
+    std::fill(M.corr, M.corr + NRED, 0.0);   // no volume correction pending
+    M.corr[0] = 1.0;
     c->mem_dirty = true;
     return rebuild_membranes(c);
 }
@@ -1006,6 +1026,11 @@ int iblb_set_nodes(iblb_ctx *c, int k, const double *xyz)
     CK(cudaMemcpyAsync(c->A.qx + D.node0, x.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->A.qy + D.node0, y.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->A.qz + D.node0, z.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
+    // the given positions are final: no volume correction pending on them
+    const double none = 0.0;
+    CK(cudaMemcpyAsync(c->A.red_out + (int64_t)NRED * k + 5, &none, sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+    c->mem[k].corr[5] = 0.0;
     CK(cudaMemsetAsync(c->A.split_ok, 0, sizeof(int), c->stream));   // the previous band says nothing now
     CK(cudaStreamSynchronize(c->stream));   // the host vectors die here
     return IBLB_OK;
@@ -1021,9 +1046,10 @@ int iblb_get_nodes(iblb_ctx *c, int k, double *xyz)
         return fail(c, IBLB_E_STATE, "droplet has no membrane");
     std::vector<double> x(D.nnodes), y(D.nnodes), z(D.nnodes);
     Entered entered_(c);
-    CK(cudaMemcpyAsync(x.data(), c->A.qx + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(y.data(), c->A.qy + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(z.data(), c->A.qz + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
+    CK(launch_corrected_positions(c->A, c->stream));   // the positions with the pending volume correction
+    CK(cudaMemcpyAsync(x.data(), c->A.px + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(y.data(), c->A.py + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(z.data(), c->A.pz + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     for (int j = 0; j < D.nnodes; ++j) {
         xyz[3 * j] = x[j];
@@ -1212,7 +1238,8 @@ int iblb_sync(iblb_ctx *c)
 }
 
 // mesh observables and status of droplet k into out (the mass is filled by
-// the caller); the observation scratch is kept in the context
+// the caller; the corrected positions are in c->A.p*); the observation
+// scratch is kept in the context
 int observe_mesh(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs *out)
 {
     const Drop &D = c->drops[k];
@@ -1232,7 +1259,7 @@ int observe_mesh(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs
             c->obs_scr_n = need;
         }
         double h[13];
-        CK(launch_observe_view(c->A.qx, c->A.qy, c->A.qz, 1, c->A.tri + 3 * (int64_t)D.tri0, D.ntri, D.node0,
+        CK(launch_observe_view(c->A.px, c->A.py, c->A.pz, 1, c->A.tri + 3 * (int64_t)D.tri0, D.ntri, D.node0,
                                D.nnodes, D.R0, zcut_frac, eps_flat, c->obs_scr, h, c->stream));
         out->volume = h[0];
         out->area = h[1];
@@ -1267,6 +1294,7 @@ int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs
     CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
     CK(cudaMemcpyAsync(&out->mass, c->d_mass + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     int flags = 0;
+    CK(launch_corrected_positions(c->A, c->stream));
     if ((r = read_status(c, false, &flags)))   // synchronises the stream
         return r;
     if ((r = observe_mesh(c, k, zcut_frac, eps_flat, out)))
@@ -1289,6 +1317,7 @@ int iblb_observe_all(iblb_ctx *c, double zcut_frac, double eps_flat, iblb_obs *o
     CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
     CK(cudaMemcpyAsync(mass.data(), c->d_mass, sizeof(double) * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
     int flags = 0;
+    CK(launch_corrected_positions(c->A, c->stream));
     if ((r = read_status(c, false, &flags)))
         return r;
     for (int k = 0; k < c->ndrops; ++k) {
@@ -1526,7 +1555,7 @@ int iblb_save(iblb_ctx *c, const char *path)
     const size_t sb = storage_bytes(c->storage);
     std::vector<char> buf;
     bool ok = true;
-    const char magic[8] = {'I', 'B', 'L', 'B', 'C', 'K', '0', '1'};
+    const char magic[8] = {'I', 'B', 'L', 'B', 'C', 'K', '0', '2'};
     ok &= fwrite(magic, 8, 1, fp) == 1;
     const int64_t hdr[4] = {c->ndrops, c->storage, c->step_count, c->A.total_cells};
     ok &= fwrite(hdr, sizeof(hdr), 1, fp) == 1;
@@ -1541,6 +1570,7 @@ int iblb_save(iblb_ctx *c, const char *path)
         if (D.nnodes) {
             ok &= fwrite(c->mem[d].xyz.data(), sizeof(double) * 3 * D.nnodes, 1, fp) == 1;
             ok &= fwrite(&c->mem[d].V0, sizeof(double), 1, fp) == 1;
+            ok &= fwrite(c->mem[d].corr, sizeof(double) * NRED, 1, fp) == 1;
         }
     }
     ok &= fclose(fp) == 0;
@@ -1560,7 +1590,7 @@ int iblb_load(iblb_ctx *c, const char *path)
     const size_t sb = storage_bytes(c->storage);
     char magic[8];
     int64_t hdr[4];
-    bool ok = fread(magic, 8, 1, fp) == 1 && !memcmp(magic, "IBLBCK01", 8) && fread(hdr, sizeof(hdr), 1, fp) == 1 &&
+    bool ok = fread(magic, 8, 1, fp) == 1 && !memcmp(magic, "IBLBCK02", 8) && fread(hdr, sizeof(hdr), 1, fp) == 1 &&
               hdr[0] == c->ndrops && hdr[1] == c->storage && hdr[3] == c->A.total_cells;
     std::vector<char> buf;
     CK(cudaStreamSynchronize(c->stream));
@@ -1577,12 +1607,14 @@ int iblb_load(iblb_ctx *c, const char *path)
         CK(cudaMemcpy((char *)c->fbuf[c->cur] + sb * Q * D.pcell0, buf.data(), buf.size(), cudaMemcpyHostToDevice));
         if (D.nnodes) {
             std::vector<double> xyz(3 * (size_t)D.nnodes);
-            double V0 = 0.0;
-            ok &= fread(xyz.data(), sizeof(double) * xyz.size(), 1, fp) == 1 && fread(&V0, sizeof(double), 1, fp) == 1;
+            double V0 = 0.0, corr[NRED];
+            ok &= fread(xyz.data(), sizeof(double) * xyz.size(), 1, fp) == 1 && fread(&V0, sizeof(double), 1, fp) == 1 &&
+                  fread(corr, sizeof(double) * NRED, 1, fp) == 1;
             if (!ok)
                 break;
             c->mem[d].xyz = xyz;
             c->mem[d].V0 = V0;
+            memcpy(c->mem[d].corr, corr, sizeof(corr));
         }
     }
     fclose(fp);

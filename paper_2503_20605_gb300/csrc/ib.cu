@@ -31,7 +31,7 @@ namespace {
 constexpr int FL = 8;            // lanes per node in the force computation
 constexpr int IB_THREADS = 256;  // block size of every membrane kernel
 constexpr int SPREAD_PARTS = IB_THREADS / TILE_CELLS;   // threads per cell in the spread
-constexpr int VC_RB = 256;       // threads per volume-correction chunk (= VC_ITEMS)
+constexpr int VC_RB = VC_ITEMS;  // threads per volume-correction chunk
 constexpr long long BARRIER_CYCLES = 4000000000LL;      // ~2 s: bounded grid-barrier wait
 
 __device__ __forceinline__ float psi_near(float r)  // 0 <= r <= 1
@@ -88,6 +88,32 @@ __device__ __forceinline__ int support_tiles(int b, int n, bool periodic, int *o
     return cnt;
 }
 
+// The volume correction of a step (not in the paper) is kept pending: the
+// stored positions q are those after advection, and the correction
+// q' = c + (q - c) k computed from them is applied wherever positions are
+// read, until the next advection replaces q.  Every reader applies it with
+// the same three individually rounded FP64 operations, so a position reads
+// the same wherever it is read.
+struct Corr {
+    bool on;
+    double k, cx, cy, cz;
+};
+__device__ __forceinline__ Corr load_corr(const Arrays &a, int d)
+{
+    const double *r = a.red_out + (int64_t)NRED * d;
+    Corr c;
+    c.on = r[5] != 0.0;
+    c.k = r[0];
+    c.cx = r[1];
+    c.cy = r[2];
+    c.cz = r[3];
+    return c;
+}
+__device__ __forceinline__ double corr1(double q, double c, double k)
+{
+    return __dadd_rn(c, __dmul_rn(__dsub_rn(q, c), k));
+}
+
 // Force work item gid = FL * j + l: lane l of node j takes the node's
 // incident faces l, l + FL, ...  Lane 0 writes the node record; the lanes
 // then list the node in the tiles its kernel support touches: its slot in a
@@ -104,11 +130,16 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
     float ex = 0.f, ey = 0.f, ez = 0.f;     // elastic (Skalak) force, when the droplet has moduli
     if (valid) {
         float ks3 = 0.0f, ka3 = 0.0f;
+        const int dn = a.node_drop[j];
         if (EL) {
-            const Drop &Dn = a.drops[a.node_drop[j]];
+            const Drop &Dn = a.drops[dn];
             ks3 = Dn.ks * (1.0f / 3.0f);
             ka3 = Dn.ka * (1.0f / 3.0f);
         }
+        // a pending volume correction dilates every edge by k about the
+        // centroid: the face's edge vectors are scaled by k
+        const Corr cr = load_corr(a, dn);
+        const float kf = cr.on ? (float)cr.k : 1.0f;
         const bool elastic = EL && (ks3 != 0.0f || ka3 != 0.0f);
         const int e1 = a.adj_start[j + 1];
         for (int e = a.adj_start[j] + l; e < e1; e += FL) {
@@ -118,8 +149,12 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
             const double x0 = a.qx[v0], y0 = a.qy[v0], z0 = a.qz[v0];
             const double x1 = a.qx[v1], y1 = a.qy[v1], z1 = a.qz[v1];
             const double x2 = a.qx[v2], y2 = a.qy[v2], z2 = a.qz[v2];
-            const float e1x = (float)(x1 - x0), e1y = (float)(y1 - y0), e1z = (float)(z1 - z0);
-            const float e2x = (float)(x2 - x0), e2y = (float)(y2 - y0), e2z = (float)(z2 - z0);
+            float e1x = (float)(x1 - x0), e1y = (float)(y1 - y0), e1z = (float)(z1 - z0);
+            float e2x = (float)(x2 - x0), e2y = (float)(y2 - y0), e2z = (float)(z2 - z0);
+            if (cr.on) {
+                e1x *= kf; e1y *= kf; e1z *= kf;
+                e2x *= kf; e2y *= kf; e2z *= kf;
+            }
             const float Nx = e1y * e2z - e1z * e2y;
             const float Ny = e1z * e2x - e1x * e2z;
             const float Nz = e1x * e2y - e1y * e2x;
@@ -134,6 +169,9 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
                 dx = (float)(x0 - x2); dy = (float)(y0 - y2); dz = (float)(z0 - z2);
             } else {
                 dx = (float)(x1 - x0); dy = (float)(y1 - y0); dz = (float)(z1 - z0);
+            }
+            if (cr.on) {
+                dx *= kf; dy *= kf; dz *= kf;
             }
             const float ax = 0.5f * (hy * dz - hz * dy), ay = 0.5f * (hz * dx - hx * dz),
                         az = 0.5f * (hx * dy - hy * dx);
@@ -185,7 +223,20 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
         return;
     const int d = a.node_drop[j];
     const Drop &D = a.drops[d];
-    const double qx = a.qx[j], qy = a.qy[j], qz = a.qz[j];
+    double qx = a.qx[j], qy = a.qy[j], qz = a.qz[j];
+    {
+        const Corr cr = load_corr(a, d);
+        if (cr.on) {
+            qx = corr1(qx, cr.cx, cr.k);
+            qy = corr1(qy, cr.cy, cr.k);
+            qz = corr1(qz, cr.cz, cr.k);
+        }
+    }
+    if (l == 0) {       // the corrected position, for the in/out test and the advection of this step
+        a.px[j] = qx;
+        a.py[j] = qy;
+        a.pz[j] = qz;
+    }
     const bool sane = fabs(qx) < 1e8 && fabs(qy) < 1e8 && fabs(qz) < 1e8;
     int bx = 0, by = 0, bz = 0;
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -292,16 +343,29 @@ __device__ __forceinline__ int per_off(int X, int b, int n)
     return d;
 }
 
-// Shared memory of one spread block: the staged records of a tile's nodes.
+// Shared memory of one spread block: the keys (node indices) of a tile's
+// nodes and, in increasing node order, one 16-float record per node: its
+// kernel weights at the tile's four cells of each axis, x at 0..3, y at
+// 4..7, z at 8..11 (0 where the cell lies outside the node's support), and
+// its force at 12..14.
 struct SpreadSmem {
     __align__(16) int node[SPREAD_CAP];
-    short perm[SPREAD_CAP];
-    int b[3][SPREAD_CAP];
-    float w[12][SPREAD_CAP];
-    float phi[3][SPREAD_CAP];
+    __align__(16) float rec[SPREAD_CAP][16];
     float part[3][SPREAD_PARTS][TILE_CELLS];
     int last;
 };
+
+// Kernel weights of one axis at the four cells T0 .. T0+3 of a tile: w[d+1]
+// where the cell is at offset d in -1 .. 2 from the support base b (wrapped
+// on a periodic axis of n cells), else 0.
+__device__ __forceinline__ void tile_weights(int T0, int b, int n, bool periodic, const float *w, float *out)
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int d = periodic ? per_off(T0 + c, b, n) : T0 + c - b;
+        out[c] = (d >= -1 && d <= 2) ? w[d + 1] : 0.0f;
+    }
+}
 
 // Tiles of the previous band that are not in this step's band: zero their
 // force so that F vanishes outside the band (band tiles are rewritten).
@@ -348,54 +412,68 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
         const int X0 = 4 * (local % D.tx), Y0 = 4 * ((local / D.tx) % D.ty), Z0 = 4 * (local / (D.tx * D.ty));
         const int64_t e0 = T * TILE_CAP;
         const int cnt = min(a.bin_cnt[T], TILE_CAP);     // overflow was flagged by the force kernel
-        for (int e = tid; e < cnt; e += IB_THREADS) {
-            const int j = a.tile_list[e0 + e];
-            const NodeRec &r = a.rec[j];
-            sm.node[e] = j;
-            sm.b[0][e] = r.bx;
-            sm.b[1][e] = r.by;
-            sm.b[2][e] = r.bz;
-            for (int q = 0; q < 4; ++q) {
-                sm.w[q][e] = r.wx[q];
-                sm.w[4 + q][e] = r.wy[q];
-                sm.w[8 + q][e] = r.wz[q];
+        // stage: every listed node's tile-local weights and force, kept in
+        // registers (at most two nodes per thread: SPREAD_CAP = 2 IB_THREADS)
+        static_assert(SPREAD_CAP <= 2 * IB_THREADS, "two staged nodes per thread");
+        float4 v[2][4];
+        int key[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = tid + h * IB_THREADS;
+            key[h] = 0x7fffffff;
+            if (e < cnt) {
+                const int j = a.tile_list[e0 + e];
+                const NodeRec &r = a.rec[j];
+                key[h] = j;
+                sm.node[e] = j;
+                float wl[16];
+                tile_weights(X0, r.bx, D.nx, true, r.wx, wl);
+                tile_weights(Y0, r.by, D.ny, true, r.wy, wl + 4);
+                tile_weights(Z0, r.bz, D.nzf, !D.walls, r.wz, wl + 8);
+                wl[12] = r.phi[0];
+                wl[13] = r.phi[1];
+                wl[14] = r.phi[2];
+                wl[15] = 0.0f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    v[h][q] = make_float4(wl[4 * q], wl[4 * q + 1], wl[4 * q + 2], wl[4 * q + 3]);
             }
-            sm.phi[0][e] = r.phi[0];
-            sm.phi[1][e] = r.phi[1];
-            sm.phi[2][e] = r.phi[2];
         }
         if (tid < ((cnt + 3) & ~3) - cnt)
             sm.node[cnt + tid] = 0x7fffffff;             // pad the keys to a multiple of 4
         __syncthreads();
         if (tid == 0)
             a.bin_cnt[T] = 0;                            // empty for the next step
-        // rank sort by node index: contributions are added in increasing j
+        // rank sort by node index: each record goes to the slot of its rank,
+        // so that contributions are added in increasing j
         const int4 *keys4 = reinterpret_cast<const int4 *>(sm.node);
-        for (int e = tid; e < cnt; e += IB_THREADS) {
-            const int key = sm.node[e];
-            int rank = 0;
-            for (int k = 0; k < (cnt + 3) >> 2; ++k) {
-                const int4 v = keys4[k];
-                rank += (v.x < key) + (v.y < key) + (v.z < key) + (v.w < key);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (tid + h * IB_THREADS < cnt) {
+                int rank = 0;
+                for (int k = 0; k < (cnt + 3) >> 2; ++k) {
+                    const int4 kv = keys4[k];
+                    rank += (kv.x < key[h]) + (kv.y < key[h]) + (kv.z < key[h]) + (kv.w < key[h]);
+                }
+                float4 *dst = reinterpret_cast<float4 *>(sm.rec[rank]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    dst[q] = v[h][q];
             }
-            sm.perm[rank] = (short)e;
         }
         __syncthreads();
         const int cell = tid & (TILE_CELLS - 1), part = tid / TILE_CELLS;
-        const int X = X0 + (cell & 3), Y = Y0 + ((cell >> 2) & 3), Z = Z0 + (cell >> 4);
+        const int cx = cell & 3, cy = (cell >> 2) & 3, cz = cell >> 4;
+        const int X = X0 + cx, Y = Y0 + cy, Z = Z0 + cz;
         const int k0 = (int)(((int64_t)cnt * part) / SPREAD_PARTS), k1 = (int)(((int64_t)cnt * (part + 1)) / SPREAD_PARTS);
         float fx = 0.f, fy = 0.f, fz = 0.f;
         for (int k = k0; k < k1; ++k) {
-            const int e = sm.perm[k];
-            const int dx = per_off(X, sm.b[0][e], D.nx);
-            const int dy = per_off(Y, sm.b[1][e], D.ny);
-            const int dz = D.walls ? Z - sm.b[2][e] : per_off(Z, sm.b[2][e], D.nzf);
-            if (dx < -1 || dx > 2 || dy < -1 || dy > 2 || dz < -1 || dz > 2)
-                continue;
-            const float w = (sm.w[dx + 1][e] * sm.w[4 + dy + 1][e]) * sm.w[8 + dz + 1][e];
-            fx += sm.phi[0][e] * w;
-            fy += sm.phi[1][e] * w;
-            fz += sm.phi[2][e] * w;
+            const float *r = sm.rec[k];
+            const float w = (r[cx] * r[4 + cy]) * r[8 + cz];
+            const float4 ph = *reinterpret_cast<const float4 *>(r + 12);
+            fx += ph.x * w;
+            fy += ph.y * w;
+            fz += ph.z * w;
         }
         sm.part[0][part][cell] = fx;
         sm.part[1][part][cell] = fy;
@@ -445,10 +523,10 @@ __device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
     float ax = 0.f, ay = 0.f, az = 0.f;
     int d = 0;
     double qx = 0.0, qy = 0.0, qz = 0.0;
-    if (valid && l == 0) {      // the position, read early: it does not depend on the record
-        qx = a.qx[j];
-        qy = a.qy[j];
-        qz = a.qz[j];
+    if (valid && l == 0) {      // the (corrected) position, read early: it does not depend on the record
+        qx = a.px[j];
+        qy = a.py[j];
+        qz = a.pz[j];
     }
     if (valid) {
         d = a.node_drop[j];
@@ -510,9 +588,34 @@ __device__ __forceinline__ int find_drop_chunk(const Drop *D, int n, int c)
 // node-coordinate sums; the chunk that finishes its droplet last folds the
 // droplet's chunks in a fixed order and stores
 // red_out = {(V0/V)^(1/3), cx, cy, cz, V}.
+// Sums of NV values over the NT threads of a block, in a fixed order: the
+// values go to shared memory, lane l of warp 0 adds entries l, l + 32, ...
+// and the warp's lanes are combined by a shuffle tree.  Few FP64
+// instructions (a warp-wide FP64 instruction is slow on this GPU).  Result
+// in thread 0.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum(double *v)
+{
+    __shared__ double sh[NV][NT];
+    for (int k = 0; k < NV; ++k)
+        sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        for (int k = 0; k < NV; ++k) {
+            double x = sh[k][threadIdx.x];
+            for (int i = threadIdx.x + 32; i < NT; i += 32)
+                x += sh[k][i];
+            v[k] = warp_sum(x);
+        }
+    }
+    __syncthreads();
+}
+
+// NT: the block size (at least VC_RB; threads beyond the chunk add zeros).
+template <int NT>
 __device__ void vc_chunk(const Arrays &a, int c)
 {
-    const int KIND[4] = {0, 0, 0, 0};
+    static_assert(NT >= VC_RB, "a chunk needs VC_RB threads");
     __shared__ int s_last;
     const int d = find_drop_chunk(a.drops, a.ndrops, c);
     const Drop &D = a.drops[d];
@@ -520,8 +623,9 @@ __device__ void vc_chunk(const Arrays &a, int c)
         return;                                        // block-uniform
     const int k = c - D.red_chunk0;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool mine = threadIdx.x < VC_RB;
     const int t = k * VC_RB + threadIdx.x;
-    if (t < D.ntri) {
+    if (mine && t < D.ntri) {
         const int *f = a.tri + 3 * ((int64_t)D.tri0 + t);
         const int ia = f[0], ib = f[1], ic = f[2];
         const double ax = a.qx[ia], ay = a.qy[ia], az = a.qz[ia];
@@ -529,13 +633,13 @@ __device__ void vc_chunk(const Arrays &a, int c)
         const double cx = a.qx[ic], cy = a.qy[ic], cz = a.qz[ic];
         v[0] = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
     }
-    if (t < D.nnodes) {
+    if (mine && t < D.nnodes) {
         const int j = D.node0 + t;
         v[1] = a.qx[j];
         v[2] = a.qy[j];
         v[3] = a.qz[j];
     }
-    block_reduce<4, VC_RB>(v, KIND);
+    block_sum<4, NT>(v);
     double *part = a.red_part + (int64_t)NRED * c;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 4; ++i)
@@ -563,23 +667,11 @@ __device__ void vc_chunk(const Arrays &a, int c)
             o[2] = w[2] / D.nnodes;
             o[3] = w[3] / D.nnodes;
             o[4] = V;
+            o[5] = 1.0;         // applied wherever the positions are read next
             a.vc_done[d] = 0;
         }
     }
     __syncthreads();
-}
-
-// q <- c + (q - c) (V0/V)^(1/3) about the node centroid c
-__device__ __forceinline__ void vc_scale_node(const Arrays &a, int j)
-{
-    const int d = a.rec[j].spare;
-    if (!a.drops[d].volcorr)
-        return;
-    const double *r = a.red_out + (int64_t)NRED * d;
-    const double k = r[0];
-    a.qx[j] = r[1] + (a.qx[j] - r[1]) * k;
-    a.qy[j] = r[2] + (a.qy[j] - r[2]) * k;
-    a.qz[j] = r[3] + (a.qz[j] - r[3]) * k;
 }
 
 // ------------------------------------------------------------- grid barrier
@@ -642,18 +734,32 @@ __global__ void __launch_bounds__(IB_THREADS) interp_advect_kernel(Arrays a)
     interp_item(a, (int64_t)blockIdx.x * IB_THREADS + threadIdx.x);
 }
 
-__global__ void __launch_bounds__(VC_RB) vc_reduce_kernel(Arrays a)
+// The volume correction of every droplet: FP64 volume and centroid
+// partials of chunk blockIdx.x; the last chunk of a droplet folds them into
+// k = (V0/V)^(1/3) and the centroid, which the readers of the positions
+// apply from then on.
+__global__ void __launch_bounds__(VC_RB) volume_correction_kernel(Arrays a)
 {
     griddep_wait();
-    vc_chunk(a, blockIdx.x);
+    vc_chunk<VC_RB>(a, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(IB_THREADS) volume_correct_kernel(Arrays a)
+// a.p* = the positions as read (the pending correction applied)
+__global__ void __launch_bounds__(IB_THREADS) corrected_positions_kernel(Arrays a)
 {
-    griddep_wait();
     const int j = blockIdx.x * IB_THREADS + threadIdx.x;
-    if (j < a.total_nodes)
-        vc_scale_node(a, j);
+    if (j >= a.total_nodes)
+        return;
+    double x = a.qx[j], y = a.qy[j], z = a.qz[j];
+    const Corr cr = load_corr(a, a.node_drop[j]);
+    if (cr.on) {
+        x = corr1(x, cr.cx, cr.k);
+        y = corr1(y, cr.cy, cr.k);
+        z = corr1(z, cr.cz, cr.k);
+    }
+    a.px[j] = x;
+    a.py[j] = y;
+    a.pz[j] = z;
 }
 
 // Before the stream-collide kernel: forces and tile lists of every node,
@@ -678,7 +784,7 @@ __global__ void __launch_bounds__(IB_THREADS) ib_front_kernel(Arrays a)
 
 // After the stream-collide kernel: interpolation and advection of every
 // node; then, if some droplet corrects its volume, grid barrier, FP64 volume
-// and centroid of every droplet, grid barrier, rescale.
+// and centroid of every droplet (the correction stays pending).
 __global__ void __launch_bounds__(IB_THREADS) ib_back_kernel(Arrays a, int n_chunks, int volcorr)
 {
     unsigned sense = *(volatile unsigned *)a.bar_flag;
@@ -691,11 +797,7 @@ __global__ void __launch_bounds__(IB_THREADS) ib_back_kernel(Arrays a, int n_chu
     if (!grid_barrier(a, sense))
         return;
     for (int c = blockIdx.x; c < n_chunks; c += gridDim.x)
-        vc_chunk(a, c);
-    if (!grid_barrier(a, sense))
-        return;
-    for (int64_t j = (int64_t)blockIdx.x * IB_THREADS + threadIdx.x; j < a.total_nodes; j += stride)
-        vc_scale_node(a, (int)j);
+        vc_chunk<IB_THREADS>(a, c);
 }
 
 int g_sm_count = 0;
@@ -740,20 +842,6 @@ cudaError_t launch_interp_advect(const Arrays &a, cudaStream_t s)
                     dim3(IB_THREADS), 0, s, a.pdl != 0, a);
 }
 
-cudaError_t launch_mesh_reduce(const Arrays &a, int n_chunks_total, cudaStream_t s)
-{
-    if (a.total_nodes <= 0 || n_chunks_total <= 0)
-        return cudaSuccess;
-    return launch_k(vc_reduce_kernel, dim3(n_chunks_total), dim3(VC_RB), 0, s, a.pdl != 0, a);
-}
-
-cudaError_t launch_volume_correct(const Arrays &a, cudaStream_t s)
-{
-    if (a.total_nodes <= 0)
-        return cudaSuccess;
-    return launch_k(volume_correct_kernel, dim3((a.total_nodes + IB_THREADS - 1) / IB_THREADS), dim3(IB_THREADS), 0, s,
-                    a.pdl != 0, a);
-}
 
 // Cooperative launches: every block must be resident, so the grid is at
 // most the number of blocks that fit on the device at once; per_sm > 0 asks
@@ -790,6 +878,21 @@ cudaError_t launch_ib_front(const Arrays &a, int per_sm, cudaStream_t s)
     Arrays arg = a;
     void *args[] = {&arg};
     return cudaLaunchCooperativeKernel(fn, grid, IB_THREADS, args, 0, s);
+}
+
+cudaError_t launch_volume_correction(const Arrays &a, int n_chunks_total, cudaStream_t s)
+{
+    if (a.total_nodes <= 0 || n_chunks_total <= 0)
+        return cudaSuccess;
+    return launch_k(volume_correction_kernel, dim3(n_chunks_total), dim3(VC_RB), 0, s, a.pdl != 0, a);
+}
+
+cudaError_t launch_corrected_positions(const Arrays &a, cudaStream_t s)
+{
+    if (a.total_nodes <= 0)
+        return cudaSuccess;
+    corrected_positions_kernel<<<(a.total_nodes + IB_THREADS - 1) / IB_THREADS, IB_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ib_back(const Arrays &a, int n_chunks_total, bool volcorr, int per_sm, cudaStream_t s)

@@ -19,7 +19,7 @@ constexpr int TILE_CAP = 512;      // nodes whose kernel support may touch one t
 constexpr int SPREAD_CAP = TILE_CAP;  // nodes the spread kernel stages per tile
 constexpr int RED_FACES = 2048;    // faces per chunk of the observation reductions
 constexpr int RED_NODES = 1024;    // nodes per chunk of the observation reductions
-constexpr int VC_ITEMS = 256;      // faces (and nodes) per chunk of the volume correction
+constexpr int VC_ITEMS = 128;      // faces (and nodes) per chunk of the volume correction
 constexpr int NRED = 8;            // partial sums per chunk (see reduce.cu)
 
 // device status bits (Arrays::status[4 * d + 0])
@@ -107,7 +107,9 @@ struct Arrays {
     unsigned *bar_count;           // grid barrier of the cooperative kernels: arrivals
     unsigned *bar_flag;            // and release flag (flips at every barrier)
     // membrane
-    double *qx, *qy, *qz;          // node positions (FP64)
+    double *qx, *qy, *qz;          // node positions (FP64) as advected; the volume correction of the
+                                   // last step, when pending, is applied on reading (see red_out)
+    double *px, *py, *pz;          // corrected positions of the step, written by the force kernel
     int *node_drop;                // droplet of each node
     const int *tri;                // 3 * total_tri global node indices
     const int *adj_start;          // total_nodes + 1
@@ -123,7 +125,8 @@ struct Arrays {
                                    // and the reference area A0 (w); null when no droplet is elastic
     // reductions
     double *red_part;              // NRED * chunks (volume-correction partials)
-    double *red_out;               // NRED * ndrops: (V0/V)^(1/3), cx, cy, cz, V
+    double *red_out;               // NRED * ndrops: k = (V0/V)^(1/3), cx, cy, cz, V, pending (1: the
+                                   // positions q are to be read as c + (q - c) k), -, -
     int *vc_done;                  // per droplet: finished chunks (returns to 0)
     double *mass_part;
     int *status;                   // 4 ints per droplet: flags (ST_*), -, -, -
@@ -191,10 +194,14 @@ cudaError_t launch_interp_advect(const Arrays &a, cudaStream_t s);
 // (per_sm: resident blocks per SM of the cooperative grid, 0 = as many as fit)
 cudaError_t launch_ib_front(const Arrays &a, int per_sm, cudaStream_t s);
 cudaError_t launch_ib_back(const Arrays &a, int n_chunks_total, bool volcorr, int per_sm, cudaStream_t s);
-cudaError_t launch_mesh_reduce(const Arrays &a, int n_chunks_total, cudaStream_t s);
-cudaError_t launch_volume_correct(const Arrays &a, cudaStream_t s);
+// FP64 volume and centroid of every droplet with volume correction and the
+// rescale of its nodes (one cooperative launch)
+cudaError_t launch_volume_correction(const Arrays &a, int n_chunks_total, cudaStream_t s);
 cudaError_t launch_mass(const Arrays &a, int storage, const void *f, double *d_out, int mass_blocks,
                         cudaStream_t s);
+// Corrected positions of every node into a.px, a.py, a.pz (the pending
+// volume correction applied; a plain copy where none is pending).
+cudaError_t launch_corrected_positions(const Arrays &a, cudaStream_t s);
 // Observables of one mesh: node j at q*[j * stride]; tri holds node indices
 // into q*; nodes node0 .. node0 + nnodes - 1.  Writes 13 doubles to h_out
 // (volume, area, centroid[3], zmin, zmax, theta_R0, theta_RV, rc_cut,

@@ -21,7 +21,7 @@ namespace {
 __device__ __forceinline__ double orient_edge(const Arrays &a, int iu, int iv, double px, double py)
 {
     const int lo = iu < iv ? iu : iv, hi = iu < iv ? iv : iu;
-    const double ax = a.qx[lo], ay = a.qy[lo], bx = a.qx[hi], by = a.qy[hi];
+    const double ax = a.px[lo], ay = a.py[lo], bx = a.px[hi], by = a.py[hi];
     const double e = __dsub_rn(__dmul_rn(__dsub_rn(bx, ax), __dsub_rn(py, ay)),
                                __dmul_rn(__dsub_rn(by, ay), __dsub_rn(px, ax)));
     return iu < iv ? e : -e;
@@ -30,7 +30,7 @@ __device__ __forceinline__ double orient_edge(const Arrays &a, int iu, int iv, d
 __device__ __forceinline__ bool edge_keeps(const Arrays &a, int iu, int iv, bool up)
 {
     const int lo = iu < iv ? iu : iv, hi = iu < iv ? iv : iu;
-    double dx = __dsub_rn(a.qx[hi], a.qx[lo]), dy = __dsub_rn(a.qy[hi], a.qy[lo]);
+    double dx = __dsub_rn(a.px[hi], a.px[lo]), dy = __dsub_rn(a.py[hi], a.py[lo]);
     if ((iu < iv) != up) {
         dx = -dx;
         dy = -dy;
@@ -45,8 +45,8 @@ __device__ __forceinline__ double face_orient(const Arrays &a, int v0, int v1, i
     if (x > y) { t = x; x = y; y = t; even = !even; }
     if (y > z) { t = y; y = z; z = t; even = !even; }
     if (x > y) { t = x; x = y; y = t; even = !even; }
-    const double D = __dsub_rn(__dmul_rn(__dsub_rn(a.qx[y], a.qx[x]), __dsub_rn(a.qy[z], a.qy[x])),
-                               __dmul_rn(__dsub_rn(a.qy[y], a.qy[x]), __dsub_rn(a.qx[z], a.qx[x])));
+    const double D = __dsub_rn(__dmul_rn(__dsub_rn(a.px[y], a.px[x]), __dsub_rn(a.py[z], a.py[x])),
+                               __dmul_rn(__dsub_rn(a.py[y], a.py[x]), __dsub_rn(a.px[z], a.px[x])));
     return even ? D : -D;
 }
 
@@ -71,17 +71,17 @@ __global__ void face_cross_kernel(Arrays a)
     const int v0 = a.tri[3 * t], v1 = a.tri[3 * t + 1], v2 = a.tri[3 * t + 2];
     for (int k = 0; k < 3; ++k) {
         const int v = k == 0 ? v0 : (k == 1 ? v1 : v2);
-        if (!(fabs(a.qx[v]) < 1e8 && fabs(a.qy[v]) < 1e8 && fabs(a.qz[v]) < 1e8))
+        if (!(fabs(a.px[v]) < 1e8 && fabs(a.py[v]) < 1e8 && fabs(a.pz[v]) < 1e8))
             return;   // flagged by the force kernel
     }
     const double Dor = face_orient(a, v0, v1, v2);
     if (Dor == 0.0)
         return;
     const bool up = Dor > 0.0;
-    const double xmin = fmin(a.qx[v0], fmin(a.qx[v1], a.qx[v2]));
-    const double xmax = fmax(a.qx[v0], fmax(a.qx[v1], a.qx[v2]));
-    const double ymin = fmin(a.qy[v0], fmin(a.qy[v1], a.qy[v2]));
-    const double ymax = fmax(a.qy[v0], fmax(a.qy[v1], a.qy[v2]));
+    const double xmin = fmin(a.px[v0], fmin(a.px[v1], a.px[v2]));
+    const double xmax = fmax(a.px[v0], fmax(a.px[v1], a.px[v2]));
+    const double ymin = fmin(a.py[v0], fmin(a.py[v1], a.py[v2]));
+    const double ymax = fmax(a.py[v0], fmax(a.py[v1], a.py[v2]));
     const int PX0 = (int)ceil(xmin), PX1 = (int)floor(xmax);
     const int PY0 = (int)ceil(ymin), PY1 = (int)floor(ymax);
     if (PX1 - PX0 > D.nx || PY1 - PY0 > D.ny) {
@@ -100,8 +100,8 @@ __global__ void face_cross_kernel(Arrays a)
             const bool in2 = (up ? e2 > 0.0 : e2 < 0.0) || (e2 == 0.0 && edge_keeps(a, v0, v1, up));
             if (!(in0 && in1 && in2))
                 continue;
-            const double num = __dadd_rn(__dadd_rn(__dmul_rn(e0, a.qz[v0]), __dmul_rn(e1, a.qz[v1])),
-                                         __dmul_rn(e2, a.qz[v2]));
+            const double num = __dadd_rn(__dadd_rn(__dmul_rn(e0, a.pz[v0]), __dmul_rn(e1, a.pz[v1])),
+                                         __dmul_rn(e2, a.pz[v2]));
             const double den = __dadd_rn(__dadd_rn(e0, e1), e2);
             const double zc = __ddiv_rn(num, den);
             const int64_t col = D.col0 + wrapi(((PX % D.nx) + D.nx) % D.nx, D.nx) +

@@ -46,9 +46,11 @@ constexpr int LB_MAX_STAGES = 8;
 __device__ __forceinline__ float cvt(float v) { return v; }
 __device__ __forceinline__ float cvt(__half v) { return __half2float(v); }
 __device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
-__device__ __forceinline__ void st(float *p, float v) { *p = v; }
-__device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
-__device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+// population stores are streamed (evict-first in L2): they are read again
+// only in the next step
+__device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void st(__half *p, float v) { __stcs(p, __float2half_rn(v)); }
+__device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
 
 __device__ __forceinline__ int find_drop_group(const Drop *D, int n, int g)
 {
@@ -235,10 +237,11 @@ __device__ __forceinline__ void produce(const Arrays &a, const DropC &c, const S
     if (lane < Q) {
         const S *plane = src + (int64_t)Q * c.pcell0 + (int64_t)src_pop * c.PC + (int64_t)P * ny * src_z;
         S *dst = stg.pop + (int64_t)lane * R * P;
+        const uint64_t pol = l2_evict_first();
         if (n_a > 0)
-            bulk_g2s(dst, plane + (int64_t)P * y_a, rowb * n_a, bar);
+            bulk_g2s_hint(dst, plane + (int64_t)P * y_a, rowb * n_a, bar, pol);
         if (n_b > 0)
-            bulk_g2s(dst + (int64_t)d_b * P, plane + (int64_t)P * y_b, rowb * n_b, bar);
+            bulk_g2s_hint(dst + (int64_t)d_b * P, plane + (int64_t)P * y_b, rowb * n_b, bar, pol);
     } else if (band && lane < Q + 3) {
         const int k = lane - Q;
         bulk_g2s(stg.F + (int64_t)k * R * P, a.F + k * a.total_pcells + c.pcell0 + (int64_t)P * (plane_row0 + y0),
@@ -629,7 +632,7 @@ __device__ __forceinline__ void collide_pairs(const Arrays &a, const DropC &c, c
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                *reinterpret_cast<PT *>(o + (int64_t)i * PC) = PO::pack(oa[i], ob[i]);
+                __stcs(reinterpret_cast<PT *>(o + (int64_t)i * PC), PO::pack(oa[i], ob[i]));
         } else {
 #pragma unroll
             for (int i = 0; i < Q; ++i)
