@@ -11,7 +11,7 @@ in FP16 or BF16, arithmetic in FP32) through the C ABI.
   tests/golden/statics64_oracle.txt (written by make_statics64.py from the
   oracle alone): contact angle (Eq. angleh, with R0 and with the
   volume-equivalent radius) within 1 degree, droplet volume and height within
-  0.5% at every observation up to 10000 steps (angles below 175 degrees,
+  0.5% at every observation up to 20000 steps (angles below 175 degrees,
   where Eq. angleh is well conditioned).  FP32 storage is held to 0.05
   degree and 0.05%."""
 import os
