@@ -22,6 +22,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -158,6 +159,52 @@ def launches_per_step(spec):
     return n
 
 
+GOLDEN64 = os.path.join(ROOT, "tests", "golden", "statics64_oracle.txt")
+
+
+def run_accuracy_vs_oracle(I, iblb, torch):
+    """FP32, FP16 and BF16 storage against the FP64 oracle's stored
+    trajectories of the half-scale statics case (64^3, R = 12, L4 mesh,
+    xi = 2, volume correction off, theta_eq in {30, 60, 90, 120, 150} deg,
+    observed every 1000 steps up to 20000; written from the oracle alone):
+    the largest contact-angle difference (eq. angleh with R0 and with the
+    volume-equivalent radius, angles below 175 deg) and relative volume
+    difference over every observation, all five angles in one batched
+    context per storage."""
+    stream = torch.cuda.current_stream().cuda_stream
+    g = np.loadtxt(GOLDEN64)
+    angles = sorted(set(g[:, 0]))
+    stops = sorted(set(g[:, 1]))
+    out = {"reference": "FP64 oracle, 64^3 half-scale statics, volume correction off", "steps": int(stops[-1]),
+           "theta_eq_deg": angles}
+    for storage in ("f32", "f16", "bf16"):
+        specs = [I.workload_statics_64(th, storage) for th in angles]
+        lats = [iblb.lattice_desc(w.nx, w.ny, w.nz, tau_out=w.tau, lam=w.lam, storage=storage) for w in specs]
+        phys = [iblb.physics_desc(sigma=w.sigma, theta_eq_deg=w.theta_deg, xi=w.xi, volume_correction=0)
+                for w in specs]
+        ctx = iblb.iblb_batch_create(lats, phys, stream)
+        dth, dv = 0.0, 0.0
+        try:
+            for k, w in enumerate(specs):
+                iblb.iblb_set_membrane(ctx, k, *w.mesh())
+            done = 0
+            for st in stops:
+                iblb.iblb_step(ctx, int(st) - done)
+                done = int(st)
+                for k, th in enumerate(angles):
+                    o = iblb.iblb_observe(ctx, k, 0.05, 0.1)
+                    row = g[(g[:, 0] == th) & (g[:, 1] == st)][0]
+                    for col, key in ((6, "theta_R0_deg"), (7, "theta_RV_deg")):
+                        if row[col] < 175.0:
+                            dth = max(dth, abs(o[key] - row[col]))
+                    dv = max(dv, abs(o["volume"] / row[2] - 1.0))
+        finally:
+            iblb.iblb_destroy(ctx)
+        out[f"max_abs_dtheta_{storage}_deg"] = dth
+        out[f"max_rel_dvolume_{storage}"] = dv
+    return out
+
+
 def run_accuracy(I, iblb, torch, steps, angles=(30.0, 60.0, 90.0, 120.0, 150.0)):
     """Contact angle after `steps` steps of the 128^3 statics droplet for each
     theta_eq, all angles in one batched context per storage; reduced storage
@@ -217,6 +264,8 @@ def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_SPLIT_LB, IB_SHAPE["split"])
         if "far_bps" in IB_SHAPE:
             iblb.iblb_set_option(ctx, iblb.IBLB_OPT_LB_FAR_BLOCKS_PER_SM, IB_SHAPE["far_bps"])
+        if "graphs" in IB_SHAPE:
+            iblb.iblb_set_option(ctx, iblb.IBLB_OPT_GRAPHS, IB_SHAPE["graphs"])
         if autotune and not LB_SHAPE:
             iblb.iblb_autotune(ctx, os.path.join(ROOT, "paper_2503_20605_gb300", "_build", "autotune.txt"))
         def timed(mode, n):
@@ -234,17 +283,19 @@ def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
             torch.cuda.synchronize()
             return iblb.iblb_get_profile(ctx)
 
-        # the whole step between two events (the value), then every phase
-        # between events (the breakdown and the stream-collide roofline)
+        # the whole step between two events (the value), every phase between
+        # events (the breakdown), and the stream-collide kernel alone between
+        # two events (the roofline)
         _, step_ms, n = timed(2, steps)
         phases, phase_step_ms, n_ph = timed(1, steps)
+        lb_only, _, n_lb = timed(3, steps)
         obs = iblb.iblb_observe(ctx, 0)
         nd = iblb.iblb_info(ctx, 0)["n_drops"]
         infos = [iblb.iblb_info(ctx, k) for k in range(nd)]
     finally:
         iblb.iblb_destroy(ctx)
     return dict(phases=phases, step_ms=step_ms, n=n, n_ph=n_ph, obs=obs, cells=sum(i["cells"] for i in infos),
-                nodes=sum(i["n_nodes"] for i in infos), drops=nd)
+                nodes=sum(i["n_nodes"] for i in infos), drops=nd, lb_kernel_ms=lb_only["lb"] / n_lb)
 
 
 def extra_workload(name, specs, storage, steps, warmup, torch, iblb, flush, autotune):
@@ -258,7 +309,7 @@ def extra_workload(name, specs, storage, steps, warmup, torch, iblb, flush, auto
             "value": r["cells"] * r["n"] / (r["step_ms"] * 1e-3) / 1e6, "unit": "MLUPS",
             "ms_per_step": r["step_ms"] / r["n"], "phase_ms_per_step": ph,
             "ib_nodes_per_s": r["nodes"] / (ib * 1e-3),
-            "lb_kernel_gbs": r["cells"] * bpc / (ph["lb"] * 1e-3) / 1e9,
+            "lb_kernel_gbs": r["cells"] * bpc / (r["lb_kernel_ms"] * 1e-3) / 1e9,
             "gpu_launches_per_step": launches_per_step(specs)}
 
 
@@ -333,11 +384,28 @@ def peaks_bf16():
     return 1700.0
 
 
-def cpu_oracle(spec, budget_s, steps_cap):
+def host_description():
+    """Core count and CPU model of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine()}
+
+
+def cpu_oracle(spec, budget_s, steps_cap, threads=1):
     """The FP64 oracle on the host cores: full steps of the same workload
-    until the time budget is used (at least one)."""
+    until the time budget is used (at least one), its stream-collide loop
+    on `threads` threads."""
     import oracle.oracle as O
     O.build()
+    O.set_threads(threads)
     xyz, tri = spec.mesh()
     A = O.wetting_A(spec.sigma, math.radians(spec.theta_deg), spec.xi)
     s = O.Sim(O.make_params(spec.nx, spec.ny, spec.nz, tau_out=spec.tau, tau_in=spec.tau_in, sigma=spec.sigma,
@@ -369,6 +437,7 @@ def main():
     ap.add_argument("--fused-ib", type=int, default=-1, help="1/0: cooperative or separate membrane kernels")
     ap.add_argument("--split-lb", type=int, default=-1, help="1/0: far stream-collide groups on a second stream")
     ap.add_argument("--pdl", type=int, default=-1, help="1/0: programmatic dependent launch in the step")
+    ap.add_argument("--graphs", type=int, default=-1, help="1/0: replay captured graphs or launch eagerly")
     ap.add_argument("--lb-far-blocks-per-sm", type=int, default=-1, help="blocks per SM of the far groups")
     ap.add_argument("--ib-blocks-per-sm", type=int, default=-1, help="blocks per SM of the cooperative kernels")
     ap.add_argument("--lb-group-cells", type=int, default=0,
@@ -400,6 +469,8 @@ def main():
         IB_SHAPE["pdl"] = args.pdl
     if args.split_lb >= 0:
         IB_SHAPE["split"] = args.split_lb
+    if args.graphs >= 0:
+        IB_SHAPE["graphs"] = args.graphs
     if args.lb_far_blocks_per_sm >= 0:
         IB_SHAPE["far_bps"] = args.lb_far_blocks_per_sm
     spec = I.workload_statics_128(90.0, args.storage)
@@ -410,15 +481,18 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        n, dt, cells, nodes = cpu_oracle(spec, budget_s=120.0, steps_cap=max(1, args.steps + args.warmup))
-        cores = 1
+        cores = os.cpu_count() or 1
+        n, dt, cells, nodes = cpu_oracle(spec, budget_s=120.0, steps_cap=max(1, args.steps + args.warmup),
+                                         threads=cores)
         v = cells * n / dt / 1e6
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / n * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": workload, "storage": "f64 (oracle)", "cells": cells, "nodes": nodes},
                 "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                                 "sample": f"{n} full oracle steps of the workload (time budget 120 s)"},
+                                 "sample": f"{n} full oracle steps of the workload (time budget 120 s), "
+                                           f"stream-collide loop on {cores} threads",
+                                 "host": host_description()},
                 "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -456,7 +530,7 @@ def main():
     ph = main_run["phases"]
     KP = main_run["n_ph"]
     ib_ms = (ph["forces"] + ph["spread"] + ph["inout"] + ph["advect"] + ph["reduce"]) / KP   # per step
-    lb_ms = ph["lb"] / KP
+    lb_ms = main_run["lb_kernel_ms"]          # the stream-collide kernel between two events of its own
     peak, src = peaks()
     bpc = BYTES_PER_CELL[args.storage]
     achieved = cells * bpc / (lb_ms * 1e-3) / 1e9
@@ -466,7 +540,7 @@ def main():
         ph32 = run32["phases"]
         KP32 = run32["n_ph"]
         ib32 = (ph32["forces"] + ph32["spread"] + ph32["inout"] + ph32["advect"] + ph32["reduce"]) / KP32
-        lb32 = ph32["lb"] / KP32
+        lb32 = run32["lb_kernel_ms"]
         fp32 = {"value": cells * run32["n"] / (run32["step_ms"] * 1e-3) / 1e6, "unit": "MLUPS",
                 "ms_per_step": run32["step_ms"] / run32["n"],
                 "phase_ms_per_step": {k: v / KP32 for k, v in ph32.items()},
@@ -490,13 +564,21 @@ def main():
 
     accuracy = None
     if rank == 0 and not args.only_main and args.accuracy_steps > 0:
-        accuracy = run_accuracy(I, iblb, torch, args.accuracy_steps)
+        accuracy = {"vs_oracle_64": run_accuracy_vs_oracle(I, iblb, torch),
+                    "vs_f32_128": run_accuracy(I, iblb, torch, args.accuracy_steps)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        n, dt, c_cells, _ = cpu_oracle(spec, args.cpu_budget, 1000)
-        cpu = {"value": c_cells * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"{n} full FP64 oracle steps of the same 128^3 workload on one host core"}
+        host = host_description()
+        allc = host["nproc"] or 1
+        n1, dt1, c_cells, c_nodes = cpu_oracle(spec, args.cpu_budget / 2, 1000, threads=1)
+        na, dta, _, _ = cpu_oracle(spec, args.cpu_budget / 2, 1000, threads=allc)
+        cpu = {"value": c_cells * na / dta / 1e6, "unit": "MLUPS", "cores": allc, "kind": "oracle",
+               "sample": f"{na} full FP64 oracle steps of the same 128^3 workload with the stream-collide loop "
+                         f"on {allc} threads; {n1} steps on one thread",
+               "one_core": {"value": c_cells * n1 / dt1 / 1e6, "unit": "MLUPS",
+                            "ib_nodes_per_s": c_nodes * n1 / dt1},
+               "all_cores_ib_nodes_per_s": c_nodes * na / dta, "host": host}
 
     if rank == 0:
         line = {
@@ -507,6 +589,12 @@ def main():
                        "grid": [spec.nx, spec.ny, spec.nz], "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "ib_nodes_per_s": world * nodes / (ib_ms * 1e-3),
+            # its fraction of an HBM bound: 64 stencil cells x 24 B (a read
+            # of U and a write of F, 3 x FP32 each) per node at the measured
+            # copy bandwidth
+            "ib_roofline": {"bound_nodes_per_s": peak * 1e9 / (64 * 24),
+                            "frac": world * nodes / (ib_ms * 1e-3) / (peak * 1e9 / (64 * 24)),
+                            "peak_gbs": peak, "peak_source": src},
             "phase_ms_per_step": {k: v / KP for k, v in ph.items()},
             "fp32": fp32,
             "roofline": {"bound": "hbm", "kernel": "lb_kernel (fused stream-collide)", "achieved": achieved,

@@ -142,10 +142,15 @@ typedef struct {
 #define IBLB_NPHASE 6
 
 /* Options for iblb_set_option. */
-#define IBLB_OPT_GRAPHS 0     /* 1 (default): replay captured CUDA graphs of one step    */
+#define IBLB_OPT_GRAPHS 0     /* 1: replay captured CUDA graphs of one step (or of
+                                 IBLB_OPT_GRAPH_CHUNK steps); 0 (default): launch the
+                                 kernels of each step directly, which with
+                                 IBLB_OPT_PDL measured faster on GB300 (81 against 84 us
+                                 per step at 128^3); results are bit-identical           */
 #define IBLB_OPT_PROFILE 1    /* 1: record CUDA events around each phase; 2: around the
-                                 whole step only; both add a host sync per step;
-                                 0 (default): off                                        */
+                                 whole step only; 3: around the stream-collide kernel
+                                 only (its time is reported as the IBLB_PH_LB phase);
+                                 each adds a host sync per step; 0 (default): off       */
 #define IBLB_OPT_LB_BLOCKS_PER_SM 2 /* resident blocks per SM of the persistent
                                  stream-collide kernel (0..8; 0 = as many as fit)       */
 #define IBLB_OPT_LB_ROW_MULT 3 /* cell rows per stream-collide group, in units of
@@ -172,8 +177,7 @@ typedef struct {
 #define IBLB_OPT_PDL 9         /* 1: the kernels of a step are launched with programmatic
                                  dependent launch (each may start while the previous one
                                  finishes, and waits for it before reading its results);
-                                 0 (default): plain stream order.  Bit-identical; on
-                                 GB300 it gains nothing measurable.                     */
+                                 1 (default); 0: plain stream order.  Bit-identical.     */
 #define IBLB_OPT_LB_FAR_BLOCKS_PER_SM 8 /* resident blocks per SM of those far groups
                                  (0..8; 0 = as many as fit; default 1, which leaves room
                                  for the membrane kernels)                               */

@@ -1,10 +1,10 @@
 // ib.cu -- the membrane side of the IB-LB step:
 //   * nodal forces: surface tension phi_sigma,j = -sigma dA/dq_j (Sec. II B)
 //     plus the wall interaction phi_Pi,j = -(chi_j/3) Pi(h_j) n_j (Sec. II C);
-//     8 lanes per node share its incident faces, partial sums meet in a fixed
-//     shuffle tree; every node is listed in the 4^3 tiles its 4x4x4 kernel
-//     support touches (at most 8, or 27 across a partial periodic tile), and
-//     the tiles with a node form the band;
+//     one thread per node sums over its incident faces in a fixed order;
+//     every node is listed in the 4^3 tiles its 4x4x4 kernel support touches
+//     (at most 8, or 27 across a partial periodic tile), and the tiles with a
+//     node form the band;
 //   * force spreading F(x) = sum_j phi_j Delta(q_j - x) (eq. force_spread) as
 //     a deterministic gather: every band tile orders its nodes by index and
 //     each cell adds their contributions in that order, so the result depends
@@ -28,20 +28,10 @@ namespace iblb {
 
 namespace {
 
-constexpr int FL = 8;            // lanes per node in the force computation
 constexpr int IB_THREADS = 256;  // block size of every membrane kernel
 constexpr int SPREAD_PARTS = IB_THREADS / TILE_CELLS;   // threads per cell in the spread
 constexpr int VC_RB = VC_ITEMS;  // threads per volume-correction chunk
 constexpr long long BARRIER_CYCLES = 4000000000LL;      // ~2 s: bounded grid-barrier wait
-
-__device__ __forceinline__ float psi_near(float r)  // 0 <= r <= 1
-{
-    return 0.375f - 0.25f * r + 0.25f * sqrtf(r - r * r + 0.25f);
-}
-__device__ __forceinline__ float psi_far(float r)   // 1 <= r <= 2
-{
-    return 0.625f - 0.25f * r - 0.25f * sqrtf(3.0f * r - r * r - 1.75f);
-}
 
 __device__ __forceinline__ float ipow(float r, int k)
 {
@@ -114,129 +104,157 @@ __device__ __forceinline__ double corr1(double q, double c, double k)
     return __dadd_rn(c, __dmul_rn(__dsub_rn(q, c), k));
 }
 
-// Force work item gid = FL * j + l: lane l of node j takes the node's
-// incident faces l, l + FL, ...  Lane 0 writes the node record; the lanes
-// then list the node in the tiles its kernel support touches: its slot in a
-// tile's list (TILE_CAP slots per tile) comes from the tile's counter, and
-// the node that takes slot 0 stamps the tile with the step's generation gen
-// and appends it to the band list.  All 32 lanes of a warp must take part
-// (the partial sums are combined with warp shuffles).
-template <bool EL>     // EL: some droplet of the launch has an elastic membrane (a.fref set)
-__device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_t gen)
+// Forces of node j (one thread per node).  Its incident faces are listed as
+// (a, b, t << 2 | k): the face's other two corners in counter-clockwise
+// order about the outward normal -- the face is (j, a, b) -- and the face
+// and the corner j takes in it.  With r_a = q_a - q_j and r_b = q_b - q_j
+// (FP64 differences rounded once to FP32, and dilated by k when a volume
+// correction is pending), the face normal is r_a x r_b, its area half its
+// length, and dA/dq_j = 1/2 n x (r_b - r_a).  The node's record is written
+// and the node is listed in the 4^3 tiles its kernel support touches: its
+// slot in a tile's list (TILE_CAP slots per tile) comes from the tile's
+// counter, and the node that takes slot 0 stamps the tile with the step's
+// generation gen and appends it to the band list.
+// One incident face (j, a, b) of a node: relative corner vectors r_a, r_b
+// (already dilated by a pending volume correction), accumulated into the
+// node's area gradient g, normal sum n, area sum chi and elastic force e.
+template <bool EL>
+__device__ __forceinline__ void face_terms(const Arrays &a, int4 en, float rax, float ray, float raz, float rbx,
+                                           float rby, float rbz, bool elastic, float ks3, float ka3, float &gx,
+                                           float &gy, float &gz, float &nx, float &ny, float &nz, float &chi,
+                                           float &ex, float &ey, float &ez)
 {
-    const int j = (int)(gid / FL), l = (int)(gid % FL);
-    const bool valid = j < a.total_nodes;
-    float gx = 0.f, gy = 0.f, gz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, chi = 0.f;
-    float ex = 0.f, ey = 0.f, ez = 0.f;     // elastic (Skalak) force, when the droplet has moduli
-    if (valid) {
-        float ks3 = 0.0f, ka3 = 0.0f;
-        const int dn = a.node_drop[j];
-        if (EL) {
-            const Drop &Dn = a.drops[dn];
-            ks3 = Dn.ks * (1.0f / 3.0f);
-            ka3 = Dn.ka * (1.0f / 3.0f);
+    const float Nx = ray * rbz - raz * rby;
+    const float Ny = raz * rbx - rax * rbz;
+    const float Nz = rax * rby - ray * rbx;
+    const float len = sqrtf(Nx * Nx + Ny * Ny + Nz * Nz);
+    const float il = 1.0f / len;
+    const float hx = Nx * il, hy = Ny * il, hz = Nz * il;
+    // dA/dq_j = 1/2 n x (q_prev - q_next), (prev, j, next) = (b, j, a)
+    const float dx = rbx - rax, dy = rby - ray, dz = rbz - raz;
+    const float ax = 0.5f * (hy * dz - hz * dy), ay = 0.5f * (hz * dx - hx * dz), az = 0.5f * (hx * dy - hy * dx);
+    gx += ax;
+    gy += ay;
+    gz += az;
+    if (EL && elastic) {
+        // Skalak energy against the reference triangle (Sec. II B's
+        // framework): with S = H^-1 and A0 from the reference,
+        // b = (S11 e1.e1 + 2 S12 e1.e2 + S22 e2.e2) / 2 - 1, r = A / A0,
+        // phi_k = -(A0 w_a / A) dA/dq_k - A0 w_b (1/2) dtr/dq_k, with the
+        // face's edges e1 = q1 - q0, e2 = q2 - q0 in its own corner order
+        // (j is corner k: (j, a, b) rotated)
+        const int t = en.z >> 2, k = en.z & 3;
+        float e1x, e1y, e1z, e2x, e2y, e2z;
+        if (k == 0) {
+            e1x = rax; e1y = ray; e1z = raz;
+            e2x = rbx; e2y = rby; e2z = rbz;
+        } else if (k == 1) {
+            e1x = -rbx; e1y = -rby; e1z = -rbz;
+            e2x = rax - rbx; e2y = ray - rby; e2z = raz - rbz;
+        } else {
+            e1x = rbx - rax; e1y = rby - ray; e1z = rbz - raz;
+            e2x = -rax; e2y = -ray; e2z = -raz;
         }
-        // a pending volume correction dilates every edge by k about the
-        // centroid: the face's edge vectors are scaled by k
-        const Corr cr = load_corr(a, dn);
-        const float kf = cr.on ? (float)cr.k : 1.0f;
-        const bool elastic = EL && (ks3 != 0.0f || ka3 != 0.0f);
-        const int e1 = a.adj_start[j + 1];
-        for (int e = a.adj_start[j] + l; e < e1; e += FL) {
-            const int code = a.adj[e];
-            const int t = code >> 2, k = code & 3;
-            const int v0 = a.tri[3 * t], v1 = a.tri[3 * t + 1], v2 = a.tri[3 * t + 2];
-            const double x0 = a.qx[v0], y0 = a.qy[v0], z0 = a.qz[v0];
-            const double x1 = a.qx[v1], y1 = a.qy[v1], z1 = a.qz[v1];
-            const double x2 = a.qx[v2], y2 = a.qy[v2], z2 = a.qz[v2];
-            float e1x = (float)(x1 - x0), e1y = (float)(y1 - y0), e1z = (float)(z1 - z0);
-            float e2x = (float)(x2 - x0), e2y = (float)(y2 - y0), e2z = (float)(z2 - z0);
-            if (cr.on) {
-                e1x *= kf; e1y *= kf; e1z *= kf;
-                e2x *= kf; e2y *= kf; e2z *= kf;
-            }
-            const float Nx = e1y * e2z - e1z * e2y;
-            const float Ny = e1z * e2x - e1x * e2z;
-            const float Nz = e1x * e2y - e1y * e2x;
-            const float len = sqrtf(Nx * Nx + Ny * Ny + Nz * Nz);
-            const float il = 1.0f / len;
-            const float hx = Nx * il, hy = Ny * il, hz = Nz * il;
-            // dA/dq_k = 1/2 n x (q_prev - q_next), corners in CCW order
-            float dx, dy, dz;
-            if (k == 0) {
-                dx = (float)(x2 - x1); dy = (float)(y2 - y1); dz = (float)(z2 - z1);
-            } else if (k == 1) {
-                dx = (float)(x0 - x2); dy = (float)(y0 - y2); dz = (float)(z0 - z2);
-            } else {
-                dx = (float)(x1 - x0); dy = (float)(y1 - y0); dz = (float)(z1 - z0);
-            }
-            if (cr.on) {
-                dx *= kf; dy *= kf; dz *= kf;
-            }
-            const float ax = 0.5f * (hy * dz - hz * dy), ay = 0.5f * (hz * dx - hx * dz),
-                        az = 0.5f * (hx * dy - hy * dx);
-            gx += ax;
-            gy += ay;
-            gz += az;
-            if (elastic) {
-                // Skalak energy against the reference triangle (Sec. II B's
-                // framework): with S = H^-1 and A0 from the reference,
-                // b = (S11 e1.e1 + 2 S12 e1.e2 + S22 e2.e2) / 2 - 1, r = A / A0,
-                // phi_k = -(A0 w_a / A) dA/dq_k - A0 w_b (1/2) dtr/dq_k
-                const float4 R = a.fref[t];
-                const float g11 = e1x * e1x + e1y * e1y + e1z * e1z, g12 = e1x * e2x + e1y * e2y + e1z * e2z;
-                const float g22 = e2x * e2x + e2y * e2y + e2z * e2z;
-                const float b = 0.5f * (R.x * g11 + 2.0f * R.y * g12 + R.z * g22) - 1.0f;
-                const float r = 0.5f * len / R.w;
-                const float cA = r * (ka3 * (r * r - 1.0f) - ks3), cB = R.w * ks3 * (2.0f * b + 1.0f);
-                const float h1x = R.x * e1x + R.y * e2x, h1y = R.x * e1y + R.y * e2y, h1z = R.x * e1z + R.y * e2z;
-                const float h2x = R.y * e1x + R.z * e2x, h2y = R.y * e1y + R.z * e2y, h2z = R.y * e1z + R.z * e2z;
-                const float tx = k == 0 ? -(h1x + h2x) : (k == 1 ? h1x : h2x);
-                const float ty = k == 0 ? -(h1y + h2y) : (k == 1 ? h1y : h2y);
-                const float tz = k == 0 ? -(h1z + h2z) : (k == 1 ? h1z : h2z);
-                ex -= cA * ax + cB * tx;
-                ey -= cA * ay + cB * ty;
-                ez -= cA * az + cB * tz;
-            }
-            nx += hx;
-            ny += hy;
-            nz += hz;
-            chi += 0.5f * len;
-        }
+        const float4 R = a.fref[t];
+        const float g11 = e1x * e1x + e1y * e1y + e1z * e1z, g12 = e1x * e2x + e1y * e2y + e1z * e2z;
+        const float g22 = e2x * e2x + e2y * e2y + e2z * e2z;
+        const float b = 0.5f * (R.x * g11 + 2.0f * R.y * g12 + R.z * g22) - 1.0f;
+        const float r = 0.5f * len / R.w;
+        const float cA = r * (ka3 * (r * r - 1.0f) - ks3), cB = R.w * ks3 * (2.0f * b + 1.0f);
+        const float h1x = R.x * e1x + R.y * e2x, h1y = R.x * e1y + R.y * e2y, h1z = R.x * e1z + R.y * e2z;
+        const float h2x = R.y * e1x + R.z * e2x, h2y = R.y * e1y + R.z * e2y, h2z = R.y * e1z + R.z * e2z;
+        const float tx = k == 0 ? -(h1x + h2x) : (k == 1 ? h1x : h2x);
+        const float ty = k == 0 ? -(h1y + h2y) : (k == 1 ? h1y : h2y);
+        const float tz = k == 0 ? -(h1z + h2z) : (k == 1 ? h1z : h2z);
+        ex -= cA * ax + cB * tx;
+        ey -= cA * ay + cB * ty;
+        ez -= cA * az + cB * tz;
     }
-    for (int o = FL / 2; o >= 1; o >>= 1) {
-        gx += __shfl_xor_sync(0xffffffffu, gx, o);
-        gy += __shfl_xor_sync(0xffffffffu, gy, o);
-        gz += __shfl_xor_sync(0xffffffffu, gz, o);
-        nx += __shfl_xor_sync(0xffffffffu, nx, o);
-        ny += __shfl_xor_sync(0xffffffffu, ny, o);
-        nz += __shfl_xor_sync(0xffffffffu, nz, o);
-        chi += __shfl_xor_sync(0xffffffffu, chi, o);
-    }
-    if (EL)
-        for (int o = FL / 2; o >= 1; o >>= 1) {
-            ex += __shfl_xor_sync(0xffffffffu, ex, o);
-            ey += __shfl_xor_sync(0xffffffffu, ey, o);
-            ez += __shfl_xor_sync(0xffffffffu, ez, o);
-        }
-    if (!valid)
-        return;
+    nx += hx;
+    ny += hy;
+    nz += hz;
+    chi += 0.5f * len;
+}
+
+// The four weights of the 4-point kernel at the support cells base-1 ..
+// base+2 of one axis, for the node's offset f in [0, 1) from the base: with
+// s = sqrt(1/4 + f - f^2), Psi(1 + f) = 3/8 - f/4 - s/4, Psi(f) = 3/8 - f/4
+// + s/4, Psi(1 - f) = 1/8 + f/4 + s/4 and Psi(2 - f) = 1/8 + f/4 - s/4 (both
+// branches of Psi, Sec. II A, evaluated at these four distances share s).
+__device__ __forceinline__ void psi4(float f, float *w)
+{
+    const float s = 0.25f * sqrtf(0.25f + f - f * f);
+    const float p = 0.375f - 0.25f * f, q = 0.125f + 0.25f * f;
+    w[0] = p - s;
+    w[1] = p + s;
+    w[2] = q + s;
+    w[3] = q - s;
+}
+
+// Forces of node j (one thread per node).  Its incident faces are listed as
+// (a, b, t << 2 | k): the face's other two corners in counter-clockwise
+// order about the outward normal -- the face is (j, a, b) -- and the face
+// and the corner j takes in it.  With r_a = q_a - q_j and r_b = q_b - q_j
+// (FP64 differences rounded once to FP32, and dilated by k when a volume
+// correction is pending), the face normal is r_a x r_b, its area half its
+// length, and dA/dq_j = 1/2 n x (r_b - r_a).  The faces are taken in batches
+// of FB whose loads are all issued before any arithmetic.  The node's record
+// is written and the node is listed in the 4^3 tiles its kernel support
+// touches: its slot in a tile's list (TILE_CAP slots per tile) comes from
+// the tile's counter, and the node that takes slot 0 stamps the tile with
+// the step's generation gen and appends it to the band list.
+template <bool EL>     // EL: some droplet of the launch has an elastic membrane (a.fref set)
+__device__ __forceinline__ void node_forces(const Arrays &a, int j, uint32_t gen)
+{
+    constexpr int FB = 8;
     const int d = a.node_drop[j];
     const Drop &D = a.drops[d];
-    double qx = a.qx[j], qy = a.qy[j], qz = a.qz[j];
-    {
-        const Corr cr = load_corr(a, d);
-        if (cr.on) {
-            qx = corr1(qx, cr.cx, cr.k);
-            qy = corr1(qy, cr.cy, cr.k);
-            qz = corr1(qz, cr.cz, cr.k);
-        }
+    const Corr cr = load_corr(a, d);
+    const float kf = cr.on ? (float)cr.k : 1.0f;
+    const double qx0 = a.qx[j], qy0 = a.qy[j], qz0 = a.qz[j];
+    float ks3 = 0.0f, ka3 = 0.0f;
+    if (EL) {
+        ks3 = D.ks * (1.0f / 3.0f);
+        ka3 = D.ka * (1.0f / 3.0f);
     }
-    if (l == 0) {       // the corrected position, for the in/out test and the advection of this step
-        a.px[j] = qx;
-        a.py[j] = qy;
-        a.pz[j] = qz;
+    const bool elastic = EL && (ks3 != 0.0f || ka3 != 0.0f);
+    float gx = 0.f, gy = 0.f, gz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, chi = 0.f;
+    float ex = 0.f, ey = 0.f, ez = 0.f;     // elastic (Skalak) force, when the droplet has moduli
+    const int e0 = a.adj_start[j], e1 = a.adj_start[j + 1];
+    for (int eb = e0; eb < e1; eb += FB) {
+        int4 en[FB];
+        double qa[FB][3], qb[FB][3];
+#pragma unroll
+        for (int i = 0; i < FB; ++i)
+            if (eb + i < e1)
+                en[i] = a.ring[eb + i];
+#pragma unroll
+        for (int i = 0; i < FB; ++i)
+            if (eb + i < e1) {
+                qa[i][0] = a.qx[en[i].x];
+                qa[i][1] = a.qy[en[i].x];
+                qa[i][2] = a.qz[en[i].x];
+                qb[i][0] = a.qx[en[i].y];
+                qb[i][1] = a.qy[en[i].y];
+                qb[i][2] = a.qz[en[i].y];
+            }
+#pragma unroll
+        for (int i = 0; i < FB; ++i)
+            if (eb + i < e1)
+                face_terms<EL>(a, en[i], (float)(qa[i][0] - qx0) * kf, (float)(qa[i][1] - qy0) * kf,
+                               (float)(qa[i][2] - qz0) * kf, (float)(qb[i][0] - qx0) * kf,
+                               (float)(qb[i][1] - qy0) * kf, (float)(qb[i][2] - qz0) * kf, elastic, ks3, ka3, gx, gy,
+                               gz, nx, ny, nz, chi, ex, ey, ez);
     }
+    double qx = qx0, qy = qy0, qz = qz0;
+    if (cr.on) {
+        qx = corr1(qx, cr.cx, cr.k);
+        qy = corr1(qy, cr.cy, cr.k);
+        qz = corr1(qz, cr.cz, cr.k);
+    }
+    a.px[j] = qx;       // the corrected position, for the in/out test and the advection of this step
+    a.py[j] = qy;
+    a.pz[j] = qz;
     const bool sane = fabs(qx) < 1e8 && fabs(qy) < 1e8 && fabs(qz) < 1e8;
     int bx = 0, by = 0, bz = 0;
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -261,73 +279,91 @@ __device__ __forceinline__ void force_item(const Arrays &a, int64_t gid, uint32_
         ntz = support_tiles(bz, D.nzf, !D.walls, tzs);
     }
     const int ncombo = ntx * nty * ntz;
-    if (l == 0) {
-        NodeRec r;
-        r.bx = bx;
-        r.by = by;
-        r.bz = bz;
-        r.key = ncombo;
-        r.spare = d;
-        uint8_t clamped = 0;
-        if (!sane) {
-            atomicOr(&a.status[4 * d], ST_NAN);
-            for (int k = 0; k < 4; ++k)
-                r.wx[k] = r.wy[k] = r.wz[k] = 0.0f;
-            r.phi[0] = r.phi[1] = r.phi[2] = 0.0f;
-        } else {
-            float px = -D.sigma * gx, py = -D.sigma * gy, pz = -D.sigma * gz;
-            if (EL) {
-                px += ex;
-                py += ey;
-                pz += ez;
-            }
-            if (D.wetting) {
-                float h = (float)(qz - 0.5);
-                if (h < D.hmin) {
-                    h = D.hmin;
-                    clamped = 1;
-                }
-                const float r0 = D.xi / h;
-                const float Pi = D.A * (ipow(r0, D.n) - ipow(r0, D.m));
-                const float inl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
-                const float s = -(chi * (1.0f / 3.0f)) * Pi * inl;
-                px += s * nx;
-                py += s * ny;
-                pz += s * nz;
-            }
-            r.wx[0] = psi_far(1.0f + fx); r.wx[1] = psi_near(fx); r.wx[2] = psi_near(1.0f - fx); r.wx[3] = psi_far(2.0f - fx);
-            r.wy[0] = psi_far(1.0f + fy); r.wy[1] = psi_near(fy); r.wy[2] = psi_near(1.0f - fy); r.wy[3] = psi_far(2.0f - fy);
-            r.wz[0] = psi_far(1.0f + fz); r.wz[1] = psi_near(fz); r.wz[2] = psi_near(1.0f - fz); r.wz[3] = psi_far(2.0f - fz);
-            r.phi[0] = px;
-            r.phi[1] = py;
-            r.phi[2] = pz;
-            if (ncombo == 0)
-                atomicOr(&a.status[4 * d], ST_ESCAPE);
+    NodeRec rec;
+    rec.bx = bx;
+    rec.by = by;
+    rec.bz = bz;
+    rec.key = ncombo;
+    rec.spare = d;
+    uint8_t clamped = 0;
+    if (!sane) {
+        atomicOr(&a.status[4 * d], ST_NAN);
+        for (int k = 0; k < 4; ++k)
+            rec.wx[k] = rec.wy[k] = rec.wz[k] = 0.0f;
+        rec.phi[0] = rec.phi[1] = rec.phi[2] = 0.0f;
+    } else {
+        float px = -D.sigma * gx, py = -D.sigma * gy, pz = -D.sigma * gz;
+        if (EL) {
+            px += ex;
+            py += ey;
+            pz += ez;
         }
-        a.rec[j] = r;
-        a.clamped[j] = clamped;
+        if (D.wetting) {
+            float h = (float)(qz - 0.5);
+            if (h < D.hmin) {
+                h = D.hmin;
+                clamped = 1;
+            }
+            const float r0 = D.xi / h;
+            const float Pi = D.A * (ipow(r0, D.n) - ipow(r0, D.m));
+            const float inl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
+            const float sc = -(chi * (1.0f / 3.0f)) * Pi * inl;
+            px += sc * nx;
+            py += sc * ny;
+            pz += sc * nz;
+        }
+        psi4(fx, rec.wx);
+        psi4(fy, rec.wy);
+        psi4(fz, rec.wz);
+        rec.phi[0] = px;
+        rec.phi[1] = py;
+        rec.phi[2] = pz;
+        if (ncombo == 0)
+            atomicOr(&a.status[4 * d], ST_ESCAPE);
     }
+    a.rec[j] = rec;
+    a.clamped[j] = clamped;
+    // the node's tiles: every counter's atomic is issued before any result
+    // is used (at most 8 at once; a support across a partial periodic tile
+    // can touch up to 27)
     const int cur = (int)(gen & 1u);
-    for (int c = l; c < ncombo; c += FL) {
-        const int ix = c % ntx, iy = (c / ntx) % nty, iz = c / (ntx * nty);
-        const int64_t t = D.tile0 + txs[ix] + (int64_t)D.tx * (tys[iy] + (int64_t)D.ty * tzs[iz]);
-        const int rank = atomicAdd(&a.bin_cnt[t], 1);
-        if (rank == 0) {        // first node of the tile: the tile joins the band
-            a.tile_gen[t] = gen;
-            const int slot = atomicAdd(&a.n_active[cur], 1);
-            if (slot < a.active_cap)
-                a.active[(int64_t)cur * a.active_cap + slot] = (int)t;
-            // its tile row too; the stream-collide rows run before this step's
-            // band was known assumed that this row could not hold band tiles
-            const int64_t tr = D.trow0 + tys[iy] + (int64_t)D.ty * tzs[iz];
-            a.rowgen[tr] = gen;
-            if (a.grp_cnt[2] && !a.candrow[tr])
-                atomicOr(&a.status[4 * d], ST_BAND_MISS);
+    for (int c0 = 0; c0 < ncombo; c0 += 8) {
+        int64_t tl[8];
+        int64_t trw[8];
+        int rk[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int c = c0 + i;
+            if (c < ncombo) {
+                const int ix = c % ntx, iy = (c / ntx) % nty, iz = c / (ntx * nty);
+                tl[i] = D.tile0 + txs[ix] + (int64_t)D.tx * (tys[iy] + (int64_t)D.ty * tzs[iz]);
+                trw[i] = D.trow0 + tys[iy] + (int64_t)D.ty * tzs[iz];
+                rk[i] = atomicAdd(&a.bin_cnt[tl[i]], 1);
+            }
         }
-        if (rank < TILE_CAP)
-            a.tile_list[t * TILE_CAP + rank] = j;
-        else
-            atomicOr(&a.status[4 * d], ST_SPREAD_OVF);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (c0 + i >= ncombo)
+                continue;
+            const int64_t t = tl[i];
+            const int rank = rk[i];
+            if (rank == 0) {        // first node of the tile: the tile joins the band
+                a.tile_gen[t] = gen;
+                const int slot = atomicAdd(&a.n_active[cur], 1);
+                if (slot < a.active_cap)
+                    a.active[(int64_t)cur * a.active_cap + slot] = (int)t;
+                // its tile row too; the stream-collide rows run before this
+                // step's band was known assumed that this row could not hold
+                // band tiles
+                a.rowgen[trw[i]] = gen;
+                if (a.grp_cnt[2] && !a.candrow[trw[i]])
+                    atomicOr(&a.status[4 * d], ST_BAND_MISS);
+            }
+            if (rank < TILE_CAP)
+                a.tile_list[t * TILE_CAP + rank] = j;
+            else
+                atomicOr(&a.status[4 * d], ST_SPREAD_OVF);
+        }
     }
 }
 
@@ -709,12 +745,17 @@ __device__ bool grid_barrier(const Arrays &a, unsigned &sense)
 }
 
 // ------------------------------------------------------------------ kernels
+constexpr int NF_THREADS = 64;   // block size of the force kernel: one node per thread, small blocks
+                                 // so that a mesh of ten thousand nodes spreads over every SM
+
 template <bool EL>
-__global__ void __launch_bounds__(IB_THREADS) node_force_kernel(Arrays a)
+__global__ void __launch_bounds__(NF_THREADS) node_force_kernel(Arrays a)
 {
     griddep_wait();
     const uint32_t gen = *a.gen + 1u;                  // committed by the spread
-    force_item<EL>(a, (int64_t)blockIdx.x * IB_THREADS + threadIdx.x, gen);
+    const int j = blockIdx.x * NF_THREADS + threadIdx.x;
+    if (j < a.total_nodes)
+        node_forces<EL>(a, j, gen);
 }
 
 __global__ void __launch_bounds__(IB_THREADS) spread_kernel(Arrays a)
@@ -771,10 +812,9 @@ __global__ void __launch_bounds__(IB_THREADS) ib_front_kernel(Arrays a)
     unsigned sense = *(volatile unsigned *)a.bar_flag;
     const uint32_t gen = *a.gen + 1u;
     const int cur = (int)(gen & 1u);
-    const int64_t nf = ((int64_t)a.total_nodes * FL + 31) & ~(int64_t)31;   // whole warps
     const int64_t stride = (int64_t)gridDim.x * IB_THREADS;
-    for (int64_t gid = (int64_t)blockIdx.x * IB_THREADS + threadIdx.x; gid < nf; gid += stride)
-        force_item<EL>(a, gid, gen);
+    for (int64_t j = (int64_t)blockIdx.x * IB_THREADS + threadIdx.x; j < a.total_nodes; j += stride)
+        node_forces<EL>(a, (int)j, gen);
     if (!grid_barrier(a, sense))
         return;
     zero_left_tiles(a, gen, cur, blockIdx.x, gridDim.x);
@@ -819,11 +859,10 @@ cudaError_t launch_node_force(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    const int64_t threads = (int64_t)a.total_nodes * FL;
-    const dim3 grid((unsigned)((threads + IB_THREADS - 1) / IB_THREADS));
+    const dim3 grid((unsigned)((a.total_nodes + NF_THREADS - 1) / NF_THREADS));
     if (a.fref)
-        return launch_k(node_force_kernel<true>, grid, dim3(IB_THREADS), 0, s, a.pdl != 0, a);
-    return launch_k(node_force_kernel<false>, grid, dim3(IB_THREADS), 0, s, a.pdl != 0, a);
+        return launch_k(node_force_kernel<true>, grid, dim3(NF_THREADS), 0, s, a.pdl != 0, a);
+    return launch_k(node_force_kernel<false>, grid, dim3(NF_THREADS), 0, s, a.pdl != 0, a);
 }
 
 cudaError_t launch_spread(const Arrays &a, cudaStream_t s)
@@ -869,7 +908,7 @@ cudaError_t launch_ib_front(const Arrays &a, int per_sm, cudaStream_t s)
     if (a.total_nodes <= 0)
         return cudaSuccess;
     int grid = 0;
-    const int64_t want = ((int64_t)a.total_nodes * FL + IB_THREADS - 1) / IB_THREADS;
+    const int64_t want = ((int64_t)a.total_nodes + IB_THREADS - 1) / IB_THREADS;
     const bool el = a.fref != nullptr;
     const void *fn = el ? (const void *)ib_front_kernel<true> : (const void *)ib_front_kernel<false>;
     cudaError_t e = coop_grid(fn, std::max<int64_t>(want, (int64_t)sm_count()), per_sm, grid, g_front_blocks[el]);

@@ -114,6 +114,8 @@ struct Arrays {
     const int *tri;                // 3 * total_tri global node indices
     const int *adj_start;          // total_nodes + 1
     const int *adj;                // (face << 2) | corner, faces in increasing order
+    const int4 *ring;              // per entry of adj: the face's other corners (a, b), counter-
+                                   // clockwise after the node, and (face << 2) | corner
     NodeRec *rec;                  // total_nodes
     // in/out
     int *col_cnt;                  // crossings per column

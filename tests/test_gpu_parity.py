@@ -490,3 +490,36 @@ def test_elastic_capsule_returns_to_its_reference_shape():
         iblb.iblb_destroy(g)
     print(f"aspect ratio {a0:.3f} -> {a1:.3f}")
     assert a0 > 1.35 and abs(a1 - 1.0) < 0.3 * (a0 - 1.0), (a0, a1)
+
+
+def test_profiling_modes_time_and_leave_results_unchanged():
+    """Every profiling mode (per phase, whole step, stream-collide kernel
+    alone), with graph replay and with eager launches, reports positive
+    times for what it times and leaves the results bitwise unchanged."""
+    sp = I.workload_parity_32()
+    xyz, tri = sp.mesh()
+    ref = None
+    for graphs in (1, 0):
+        for mode in (0, 1, 2, 3):
+            g = gpu_ctx(32, 32, 32, sigma=sp.sigma, theta=sp.theta_deg, xi=sp.xi, mesh=(xyz, tri),
+                        volume_correction=1)
+            try:
+                iblb.iblb_set_option(g, iblb.IBLB_OPT_GRAPHS, graphs)
+                iblb.iblb_set_option(g, iblb.IBLB_OPT_PROFILE, mode)
+                iblb.iblb_step(g, 12)
+                iblb.iblb_sync(g)
+                ph, step_ms, n = iblb.iblb_get_profile(g)
+                out = (iblb.iblb_get_populations(g, 0), iblb.iblb_get_nodes(g, 0))
+            finally:
+                iblb.iblb_destroy(g)
+            if mode:
+                assert n == 12
+            if mode == 1:
+                assert all(ph[k] > 0 for k in ("forces", "spread", "lb", "advect", "reduce")) and step_ms > 0
+            elif mode == 2:
+                assert step_ms > 0
+            elif mode == 3:
+                assert ph["lb"] > 0 and ph["forces"] == 0
+            if ref is None:
+                ref = out
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
