@@ -389,8 +389,16 @@ int iblb_deform_mesh(const double *g, int nphi, double R0, const double *xyz, in
                      const int32_t *tri, int n_tri, double cx, double cy, double z_bottom,
                      double *xyz_out);
 
-/* Message of the last failed iblb_mesh_profile / iblb_deform_mesh call of
- * this thread. */
+/* The spherical-cap start of Sec. III B as a profile for iblb_deform_mesh:
+ * g[k] = G(phi_k) / R0, phi_k = (k + 1/2) pi / nphi, of the exact spherical
+ * cap with contact angle theta_eq_deg (0 < theta < 180) and the volume of
+ * the unit sphere (App. B normalisation), measured from the centroid of the
+ * cap's surface (curved part and base disc, weighted by area).  Host only.
+ * IBLB_E_ARG on bad arguments. */
+int iblb_cap_profile(double theta_eq_deg, int nphi, double *g);
+
+/* Message of the last failed iblb_mesh_profile / iblb_deform_mesh /
+ * iblb_cap_profile call of this thread. */
 const char *iblb_warmstart_last_error(void);
 
 /* The network: multilayer perceptron 3 -> 256 -> 256 -> 256 -> 64, tanh

@@ -201,4 +201,31 @@ int iblb_deform_mesh(const double *g, int nphi, double R0, const double *xyz, in
     return IBLB_OK;
 }
 
+int iblb_cap_profile(double theta_eq_deg, int nphi, double *g)
+{
+    if (!g || nphi < 2 || !(theta_eq_deg > 0.0) || !(theta_eq_deg < 180.0))
+        return wfail(IBLB_E_ARG, "iblb_cap_profile: bad arguments");
+    const double th = theta_eq_deg * M_PI / 180.0, c = cos(th);
+    const double rho = cbrt(4.0 / (2.0 - 3.0 * c + c * c * c));   // radius of the cap's sphere (unit volume sphere)
+    const double h = rho * (1.0 - c);                              // cap height above its base z = 0
+    const double base = rho * sin(th);
+    // surface centroid: the curved part (area 2 pi rho h, its height spread
+    // evenly in z, so its mean is h / 2) and the base disc at z = 0
+    const double z0 = (2.0 * M_PI * rho * h * 0.5 * h) / (2.0 * M_PI * rho * h + M_PI * base * base);
+    const double dz = z0 + rho * c;                                // the centroid above the sphere's centre
+    for (int k = 0; k < nphi; ++k) {
+        const double phi = (k + 0.5) * M_PI / nphi;
+        const double ur = sin(phi), uz = cos(phi);
+        (void)ur;
+        // from the centroid along (sin phi, cos phi): the sphere's far
+        // intersection if it lies on the cap, else the base plane z = 0
+        const double t_sph = -uz * dz + sqrt(uz * dz * uz * dz - (dz * dz - rho * rho));
+        if (z0 + uz * t_sph >= 0.0)
+            g[k] = t_sph;
+        else
+            g[k] = -z0 / uz;
+    }
+    return IBLB_OK;
+}
+
 }  // extern "C"

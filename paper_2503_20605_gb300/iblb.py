@@ -108,6 +108,7 @@ _SIGS = {
     "iblb_deform_mesh": (C.c_int, [_D, C.c_int, C.c_double, _D, C.c_int, _I32, C.c_int, C.c_double, C.c_double,
                                    C.c_double, _D]),
     "iblb_warmstart_last_error": (C.c_char_p, []),
+    "iblb_cap_profile": (C.c_int, [C.c_double, C.c_int, _D]),
     "iblb_mlp_param_count": (C.c_int64, []),
     "iblb_mlp_create": (C.c_int, [C.POINTER(C.c_float), C.c_int64, C.c_int, _P, C.POINTER(_P)]),
     "iblb_mlp_destroy": (None, [_P]),
@@ -384,6 +385,13 @@ def iblb_deform_mesh(g, R0, xyz, tri, cx, cy, z_bottom):
     out = np.empty_like(xyz)
     _wcheck(lib().iblb_deform_mesh(_d(g), g.size, R0, _d(xyz), xyz.size // 3, tri.ctypes.data_as(_I32),
                                    tri.size // 3, cx, cy, z_bottom, _d(out)))
+    return out
+
+
+def iblb_cap_profile(theta_eq_deg, nphi=None):
+    n = NPHI if nphi is None else int(nphi)
+    out = np.empty(n)
+    _wcheck(lib().iblb_cap_profile(float(theta_eq_deg), n, _d(out)))
     return out
 
 

@@ -59,28 +59,10 @@ def cap_extent(theta_deg, R):
 
 def cap_profile(theta_deg, nphi=iblb.NPHI):
     """Profile g(phi_k) = G / R0 of an exact spherical cap with contact
-    angle theta_deg and the volume of the unit sphere (the App. B
-    normalisation), about the centroid of its surface (the curved part and
-    the base disc, weighted by area), at phi_k = (k + 1/2) pi / nphi: the
-    spherical-cap start of Sec. III B, as a profile for the mesh deformation
-    of a warm start."""
-    th = math.radians(theta_deg)
-    c = math.cos(th)
-    rho = (4.0 / (2.0 - 3.0 * c + c ** 3)) ** (1.0 / 3.0)     # radius of the cap's sphere
-    h = rho * (1.0 - c)                                       # cap height above its base z = 0
-    base2 = (rho * math.sin(th)) ** 2                         # squared base radius
-    # the curved part has area 2 pi rho h spread evenly in z (Archimedes),
-    # so its mean height is h / 2; the base disc sits at z = 0
-    z0 = (2.0 * math.pi * rho * h * 0.5 * h) / (2.0 * math.pi * rho * h + math.pi * base2)
-    phi = (np.arange(nphi) + 0.5) * math.pi / nphi
-    ur, uz = np.sin(phi), np.cos(phi)
-    dz = z0 + rho * c                                         # centroid height above the sphere's centre
-    # ray (ur t, z0 + uz t) against the sphere r^2 + (z + rho c)^2 = rho^2: far root
-    t_sph = -uz * dz + np.sqrt((uz * dz) ** 2 - (dz * dz - rho * rho))
-    on_sphere = z0 + uz * t_sph >= 0.0
-    with np.errstate(divide="ignore"):
-        t_base = np.where(uz < 0.0, -z0 / np.where(uz < 0.0, uz, -1.0), np.inf)
-    return np.where(on_sphere, t_sph, t_base)
+    angle theta_deg and the volume of the unit sphere, about the centroid of
+    its surface, at phi_k = (k + 1/2) pi / nphi: the spherical-cap start of
+    Sec. III B (computed by the library, iblb_cap_profile)."""
+    return iblb.iblb_cap_profile(theta_deg, nphi)
 
 
 def case_box(theta_deg, R, xi):
