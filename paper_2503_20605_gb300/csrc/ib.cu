@@ -1,7 +1,8 @@
 // ib.cu -- the membrane side of the IB-LB step:
 //   * nodal forces: surface tension phi_sigma,j = -sigma dA/dq_j (Sec. II B)
 //     plus the wall interaction phi_Pi,j = -(chi_j/3) Pi(h_j) n_j (Sec. II C);
-//     one thread per node sums over its incident faces in a fixed order;
+//     four lanes per node share its incident faces, partial sums meet in a
+//     fixed shuffle tree, one lane per axis takes the kernel support;
 //     every node is listed in the 4^3 tiles its 4x4x4 kernel support touches
 //     (at most 8, or 27 across a partial periodic tile), and the tiles with a
 //     node form the band;
@@ -54,30 +55,6 @@ __device__ __forceinline__ int find_drop_tile(const Drop *D, int n, int64_t t)
     return lo;
 }
 
-// Distinct tiles (in increasing cell order) holding the support cells
-// b-1 .. b+2 of one axis of n cells: wrapped on a periodic axis, clipped to
-// [0, n) otherwise.  At most 3 (a partial last tile of a periodic axis).
-__device__ __forceinline__ int support_tiles(int b, int n, bool periodic, int *out)
-{
-    int cnt = 0;
-    for (int k = -1; k <= 2; ++k) {
-        int c = b + k;
-        if (periodic)
-            c = wrapi(c, n);
-        else if (c < 0 || c >= n)
-            continue;
-        const int t = c >> 2;
-        if (cnt == 0 || out[cnt - 1] != t) {
-            bool dup = false;
-            for (int i = 0; i < cnt; ++i)
-                dup |= out[i] == t;
-            if (!dup)
-                out[cnt++] = t;
-        }
-    }
-    return cnt;
-}
-
 // The volume correction of a step (not in the paper) is kept pending: the
 // stored positions q are those after advection, and the correction
 // q' = c + (q - c) k computed from them is applied wherever positions are
@@ -104,17 +81,6 @@ __device__ __forceinline__ double corr1(double q, double c, double k)
     return __dadd_rn(c, __dmul_rn(__dsub_rn(q, c), k));
 }
 
-// Forces of node j (one thread per node).  Its incident faces are listed as
-// (a, b, t << 2 | k): the face's other two corners in counter-clockwise
-// order about the outward normal -- the face is (j, a, b) -- and the face
-// and the corner j takes in it.  With r_a = q_a - q_j and r_b = q_b - q_j
-// (FP64 differences rounded once to FP32, and dilated by k when a volume
-// correction is pending), the face normal is r_a x r_b, its area half its
-// length, and dA/dq_j = 1/2 n x (r_b - r_a).  The node's record is written
-// and the node is listed in the 4^3 tiles its kernel support touches: its
-// slot in a tile's list (TILE_CAP slots per tile) comes from the tile's
-// counter, and the node that takes slot 0 stamps the tile with the step's
-// generation gen and appends it to the band list.
 // One incident face (j, a, b) of a node: relative corner vectors r_a, r_b
 // (already dilated by a pending volume correction), accumulated into the
 // node's area gradient g, normal sum n, area sum chi and elastic force e.
@@ -191,159 +157,217 @@ __device__ __forceinline__ void psi4(float f, float *w)
     w[3] = q - s;
 }
 
-// Forces of node j (one thread per node).  Its incident faces are listed as
-// (a, b, t << 2 | k): the face's other two corners in counter-clockwise
-// order about the outward normal -- the face is (j, a, b) -- and the face
-// and the corner j takes in it.  With r_a = q_a - q_j and r_b = q_b - q_j
-// (FP64 differences rounded once to FP32, and dilated by k when a volume
-// correction is pending), the face normal is r_a x r_b, its area half its
-// length, and dA/dq_j = 1/2 n x (r_b - r_a).  The faces are taken in batches
-// of FB whose loads are all issued before any arithmetic.  The node's record
-// is written and the node is listed in the 4^3 tiles its kernel support
-// touches: its slot in a tile's list (TILE_CAP slots per tile) comes from
-// the tile's counter, and the node that takes slot 0 stamps the tile with
-// the step's generation gen and appends it to the band list.
-template <bool EL>     // EL: some droplet of the launch has an elastic membrane (a.fref set)
-__device__ __forceinline__ void node_forces(const Arrays &a, int j, uint32_t gen)
+// The distinct tiles (in increasing cell order) holding the support cells
+// b-1 .. b+2 of one axis of n cells: wrapped on a periodic axis, clipped to
+// [0, n) otherwise; at most 3 (a partial last tile of a periodic axis).
+__device__ __forceinline__ int support_tiles3(int b, int n, bool periodic, int &t0, int &t1, int &t2)
 {
-    constexpr int FB = 8;
-    const int d = a.node_drop[j];
-    const Drop &D = a.drops[d];
-    const Corr cr = load_corr(a, d);
-    const float kf = cr.on ? (float)cr.k : 1.0f;
-    const double qx0 = a.qx[j], qy0 = a.qy[j], qz0 = a.qz[j];
-    float ks3 = 0.0f, ka3 = 0.0f;
-    if (EL) {
-        ks3 = D.ks * (1.0f / 3.0f);
-        ka3 = D.ka * (1.0f / 3.0f);
+    int cnt = 0;
+    t0 = t1 = t2 = -1;
+#pragma unroll
+    for (int k = -1; k <= 2; ++k) {
+        int c = b + k;
+        if (periodic)
+            c = wrapi(c, n);
+        else if (c < 0 || c >= n)
+            continue;
+        const int t = c >> 2;
+        if (t == t0 || t == t1 || t == t2)
+            continue;
+        if (cnt == 0)
+            t0 = t;
+        else if (cnt == 1)
+            t1 = t;
+        else
+            t2 = t;
+        ++cnt;
     }
-    const bool elastic = EL && (ks3 != 0.0f || ka3 != 0.0f);
+    return cnt;
+}
+
+// Forces of node j, NL = 4 lanes per node.  The node's incident faces are
+// listed as (a, b, t << 2 | k): the face's other two corners in
+// counter-clockwise order about the outward normal -- the face is (j, a, b)
+// -- and the face and the corner j takes in it.  Lane l takes the faces l,
+// l + 4, ...; with r_a = q_a - q_j and r_b = q_b - q_j (FP64 differences
+// rounded once to FP32, dilated by k when a volume correction is pending) a
+// face's normal is r_a x r_b, its area half its length, and dA/dq_j =
+// 1/2 n x (r_b - r_a).  The lanes' sums meet in a fixed shuffle tree.  Lane
+// c < 3 then takes axis c of the node (its corrected coordinate, kernel
+// support and weights) and lane 3 the nodal force; the record is written and
+// the node is listed in the 4^3 tiles its kernel support touches, the
+// lanes sharing the tiles: its slot in a tile's list (TILE_CAP slots per
+// tile) comes from the tile's counter, and the node that takes slot 0 stamps
+// the tile with the step's generation gen and appends it to the band list.
+// Every lane of the warp takes part (the shuffles span whole quads).
+constexpr int NL = 4;
+template <bool EL>     // EL: some droplet of the launch has an elastic membrane (a.fref set)
+__device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32_t gen)
+{
+    const int j = (int)(gid >> 2), l = (int)(gid & 3);
+    const bool valid = j < a.total_nodes;
     float gx = 0.f, gy = 0.f, gz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, chi = 0.f;
     float ex = 0.f, ey = 0.f, ez = 0.f;     // elastic (Skalak) force, when the droplet has moduli
-    const int e0 = a.adj_start[j], e1 = a.adj_start[j + 1];
-    for (int eb = e0; eb < e1; eb += FB) {
-        int4 en[FB];
-        double qa[FB][3], qb[FB][3];
-#pragma unroll
-        for (int i = 0; i < FB; ++i)
-            if (eb + i < e1)
-                en[i] = a.ring[eb + i];
-#pragma unroll
-        for (int i = 0; i < FB; ++i)
-            if (eb + i < e1) {
-                qa[i][0] = a.qx[en[i].x];
-                qa[i][1] = a.qy[en[i].x];
-                qa[i][2] = a.qz[en[i].x];
-                qb[i][0] = a.qx[en[i].y];
-                qb[i][1] = a.qy[en[i].y];
-                qb[i][2] = a.qz[en[i].y];
-            }
-#pragma unroll
-        for (int i = 0; i < FB; ++i)
-            if (eb + i < e1)
-                face_terms<EL>(a, en[i], (float)(qa[i][0] - qx0) * kf, (float)(qa[i][1] - qy0) * kf,
-                               (float)(qa[i][2] - qz0) * kf, (float)(qb[i][0] - qx0) * kf,
-                               (float)(qb[i][1] - qy0) * kf, (float)(qb[i][2] - qz0) * kf, elastic, ks3, ka3, gx, gy,
-                               gz, nx, ny, nz, chi, ex, ey, ez);
-    }
-    double qx = qx0, qy = qy0, qz = qz0;
-    if (cr.on) {
-        qx = corr1(qx, cr.cx, cr.k);
-        qy = corr1(qy, cr.cy, cr.k);
-        qz = corr1(qz, cr.cz, cr.k);
-    }
-    a.px[j] = qx;       // the corrected position, for the in/out test and the advection of this step
-    a.py[j] = qy;
-    a.pz[j] = qz;
-    const bool sane = fabs(qx) < 1e8 && fabs(qy) < 1e8 && fabs(qz) < 1e8;
-    int bx = 0, by = 0, bz = 0;
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    if (sane) {
-        // support of the 4-point kernel: base-1 .. base+2 on each axis
-        const double fbx = floor(qx), fby = floor(qy), fbz = floor(qz);
-        fx = (float)(qx - fbx);
-        fy = (float)(qy - fby);
-        fz = (float)(qz - fbz);
-        bx = wrapi((int)fbx % D.nx, D.nx);
-        by = wrapi((int)fby % D.ny, D.ny);
-        bz = (int)fbz - D.walls;
-        if (!D.walls)
-            bz = wrapi(bz % D.nz, D.nz);
-    }
-    // tiles touched by the support (fluid cells only)
-    int txs[3], tys[3], tzs[3];
-    int ntx = 0, nty = 0, ntz = 0;
-    if (sane) {
-        ntx = support_tiles(bx, D.nx, true, txs);
-        nty = support_tiles(by, D.ny, true, tys);
-        ntz = support_tiles(bz, D.nzf, !D.walls, tzs);
-    }
-    const int ncombo = ntx * nty * ntz;
-    NodeRec rec;
-    rec.bx = bx;
-    rec.by = by;
-    rec.bz = bz;
-    rec.key = ncombo;
-    rec.spare = d;
-    uint8_t clamped = 0;
-    if (!sane) {
-        atomicOr(&a.status[4 * d], ST_NAN);
-        for (int k = 0; k < 4; ++k)
-            rec.wx[k] = rec.wy[k] = rec.wz[k] = 0.0f;
-        rec.phi[0] = rec.phi[1] = rec.phi[2] = 0.0f;
-    } else {
-        float px = -D.sigma * gx, py = -D.sigma * gy, pz = -D.sigma * gz;
+    int d = 0;
+    Corr cr = {false, 1.0, 0.0, 0.0, 0.0};
+    double qx0 = 0.0, qy0 = 0.0, qz0 = 0.0;
+    if (valid) {
+        d = a.node_drop[j];
+        cr = load_corr(a, d);
+        qx0 = a.qx[j];
+        qy0 = a.qy[j];
+        qz0 = a.qz[j];
+        const float kf = cr.on ? (float)cr.k : 1.0f;
+        float ks3 = 0.0f, ka3 = 0.0f;
         if (EL) {
-            px += ex;
-            py += ey;
-            pz += ez;
+            ks3 = a.drops[d].ks * (1.0f / 3.0f);
+            ka3 = a.drops[d].ka * (1.0f / 3.0f);
         }
-        if (D.wetting) {
-            float h = (float)(qz - 0.5);
-            if (h < D.hmin) {
-                h = D.hmin;
-                clamped = 1;
+        const bool elastic = EL && (ks3 != 0.0f || ka3 != 0.0f);
+        const int e0 = a.adj_start[j], e1 = a.adj_start[j + 1];
+        for (int eb = e0 + l; eb < e1; eb += 2 * NL) {
+            // two faces per pass, every load issued before the arithmetic
+            const bool two = eb + NL < e1;
+            const int4 en0 = a.ring[eb];
+            const int4 en1 = two ? a.ring[eb + NL] : en0;
+            const double a0x = a.qx[en0.x], a0y = a.qy[en0.x], a0z = a.qz[en0.x];
+            const double b0x = a.qx[en0.y], b0y = a.qy[en0.y], b0z = a.qz[en0.y];
+            const double a1x = a.qx[en1.x], a1y = a.qy[en1.x], a1z = a.qz[en1.x];
+            const double b1x = a.qx[en1.y], b1y = a.qy[en1.y], b1z = a.qz[en1.y];
+            face_terms<EL>(a, en0, (float)(a0x - qx0) * kf, (float)(a0y - qy0) * kf, (float)(a0z - qz0) * kf,
+                           (float)(b0x - qx0) * kf, (float)(b0y - qy0) * kf, (float)(b0z - qz0) * kf, elastic, ks3,
+                           ka3, gx, gy, gz, nx, ny, nz, chi, ex, ey, ez);
+            if (two)
+                face_terms<EL>(a, en1, (float)(a1x - qx0) * kf, (float)(a1y - qy0) * kf, (float)(a1z - qz0) * kf,
+                               (float)(b1x - qx0) * kf, (float)(b1y - qy0) * kf, (float)(b1z - qz0) * kf, elastic,
+                               ks3, ka3, gx, gy, gz, nx, ny, nz, chi, ex, ey, ez);
+        }
+    }
+    for (int o = NL / 2; o >= 1; o >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        nx += __shfl_xor_sync(0xffffffffu, nx, o);
+        ny += __shfl_xor_sync(0xffffffffu, ny, o);
+        nz += __shfl_xor_sync(0xffffffffu, nz, o);
+        chi += __shfl_xor_sync(0xffffffffu, chi, o);
+    }
+    if (EL)
+        for (int o = NL / 2; o >= 1; o >>= 1) {
+            ex += __shfl_xor_sync(0xffffffffu, ex, o);
+            ey += __shfl_xor_sync(0xffffffffu, ey, o);
+            ez += __shfl_xor_sync(0xffffffffu, ez, o);
+        }
+    // axis c = l of the node (lanes 0 .. 2): corrected coordinate, kernel
+    // support and weights
+    const Drop &D = a.drops[d];
+    const int ax = l < 3 ? l : 2;
+    double q = ax == 0 ? qx0 : (ax == 1 ? qy0 : qz0);
+    if (cr.on)
+        q = corr1(q, ax == 0 ? cr.cx : (ax == 1 ? cr.cy : cr.cz), cr.k);
+    const int qb = threadIdx.x & 28;      // the quad's first lane
+    const int sane_l = fabs(q) < 1e8 ? 1 : 0;
+    const bool sane = __shfl_sync(0xffffffffu, sane_l, qb | 0) && __shfl_sync(0xffffffffu, sane_l, qb | 1) &&
+                      __shfl_sync(0xffffffffu, sane_l, qb | 2);
+    int b = 0, nt = 0, t0 = -1, t1 = -1, t2 = -1;
+    float w[4] = {0.f, 0.f, 0.f, 0.f};
+    if (valid && l < 3 && sane) {
+        const double fb = floor(q);
+        const float f = (float)(q - fb);
+        const int n = ax == 0 ? D.nx : (ax == 1 ? D.ny : D.nzf);
+        if (ax < 2) {
+            b = wrapi((int)fb % n, n);
+            nt = support_tiles3(b, n, true, t0, t1, t2);
+        } else {
+            b = (int)fb - D.walls;
+            if (!D.walls)
+                b = wrapi(b % D.nz, D.nz);
+            nt = support_tiles3(b, n, !D.walls, t0, t1, t2);
+        }
+        psi4(f, w);
+    }
+    // the z coordinate (lane 2) for the wall interaction; the tile counts
+    // and tiles of every axis for the listing
+    const double qz = __shfl_sync(0xffffffffu, q, qb | 2);
+    const int ntx = __shfl_sync(0xffffffffu, nt, qb | 0), nty = __shfl_sync(0xffffffffu, nt, qb | 1),
+              ntz = __shfl_sync(0xffffffffu, nt, qb | 2);
+    const int tx0 = __shfl_sync(0xffffffffu, t0, qb | 0), tx1 = __shfl_sync(0xffffffffu, t1, qb | 0),
+              tx2 = __shfl_sync(0xffffffffu, t2, qb | 0);
+    const int ty0 = __shfl_sync(0xffffffffu, t0, qb | 1), ty1 = __shfl_sync(0xffffffffu, t1, qb | 1),
+              ty2 = __shfl_sync(0xffffffffu, t2, qb | 1);
+    const int tz0 = __shfl_sync(0xffffffffu, t0, qb | 2), tz1 = __shfl_sync(0xffffffffu, t1, qb | 2),
+              tz2 = __shfl_sync(0xffffffffu, t2, qb | 2);
+    if (!valid)
+        return;
+    const int ncombo = ntx * nty * ntz;
+    NodeRec &rec = a.rec[j];
+    if (l < 3) {
+        // the corrected coordinate, for the in/out test and the advection of this step
+        (ax == 0 ? a.px : (ax == 1 ? a.py : a.pz))[j] = q;
+        (&rec.bx)[ax] = b;
+        float *rw = ax == 0 ? rec.wx : (ax == 1 ? rec.wy : rec.wz);
+        *reinterpret_cast<float4 *>(rw) = make_float4(w[0], w[1], w[2], w[3]);
+    } else {
+        rec.key = ncombo;
+        rec.spare = d;
+        uint8_t clamped = 0;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        if (!sane) {
+            atomicOr(&a.status[4 * d], ST_NAN);
+        } else {
+            px = -D.sigma * gx;
+            py = -D.sigma * gy;
+            pz = -D.sigma * gz;
+            if (EL) {
+                px += ex;
+                py += ey;
+                pz += ez;
             }
-            const float r0 = D.xi / h;
-            const float Pi = D.A * (ipow(r0, D.n) - ipow(r0, D.m));
-            const float inl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
-            const float sc = -(chi * (1.0f / 3.0f)) * Pi * inl;
-            px += sc * nx;
-            py += sc * ny;
-            pz += sc * nz;
+            if (D.wetting) {
+                float h = (float)(qz - 0.5);
+                if (h < D.hmin) {
+                    h = D.hmin;
+                    clamped = 1;
+                }
+                const float r0 = D.xi / h;
+                const float Pi = D.A * (ipow(r0, D.n) - ipow(r0, D.m));
+                const float inl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
+                const float sc = -(chi * (1.0f / 3.0f)) * Pi * inl;
+                px += sc * nx;
+                py += sc * ny;
+                pz += sc * nz;
+            }
+            if (ncombo == 0)
+                atomicOr(&a.status[4 * d], ST_ESCAPE);
         }
-        psi4(fx, rec.wx);
-        psi4(fy, rec.wy);
-        psi4(fz, rec.wz);
         rec.phi[0] = px;
         rec.phi[1] = py;
         rec.phi[2] = pz;
-        if (ncombo == 0)
-            atomicOr(&a.status[4 * d], ST_ESCAPE);
+        a.clamped[j] = clamped;
     }
-    a.rec[j] = rec;
-    a.clamped[j] = clamped;
-    // the node's tiles: every counter's atomic is issued before any result
-    // is used (at most 8 at once; a support across a partial periodic tile
-    // can touch up to 27)
+    // the node's tiles, shared by the four lanes: every counter's atomic is
+    // issued before any result is used (a support across a partial periodic
+    // tile can touch up to 27 tiles)
     const int cur = (int)(gen & 1u);
-    for (int c0 = 0; c0 < ncombo; c0 += 8) {
-        int64_t tl[8];
-        int64_t trw[8];
-        int rk[8];
+    for (int c0 = l; c0 < ncombo; c0 += 2 * NL) {
+        int64_t tl[2], trw[2];
+        int rk[2];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int c = c0 + i;
+        for (int i = 0; i < 2; ++i) {
+            const int c = c0 + i * NL;
             if (c < ncombo) {
                 const int ix = c % ntx, iy = (c / ntx) % nty, iz = c / (ntx * nty);
-                tl[i] = D.tile0 + txs[ix] + (int64_t)D.tx * (tys[iy] + (int64_t)D.ty * tzs[iz]);
-                trw[i] = D.trow0 + tys[iy] + (int64_t)D.ty * tzs[iz];
+                const int tx = ix == 0 ? tx0 : (ix == 1 ? tx1 : tx2);
+                const int ty = iy == 0 ? ty0 : (iy == 1 ? ty1 : ty2);
+                const int tz = iz == 0 ? tz0 : (iz == 1 ? tz1 : tz2);
+                tl[i] = D.tile0 + tx + (int64_t)D.tx * (ty + (int64_t)D.ty * tz);
+                trw[i] = D.trow0 + ty + (int64_t)D.ty * tz;
                 rk[i] = atomicAdd(&a.bin_cnt[tl[i]], 1);
             }
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (c0 + i >= ncombo)
+        for (int i = 0; i < 2; ++i) {
+            if (c0 + i * NL >= ncombo)
                 continue;
             const int64_t t = tl[i];
             const int rank = rk[i];
@@ -558,12 +582,14 @@ __device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
     const bool valid = j < a.total_nodes;
     float ax = 0.f, ay = 0.f, az = 0.f;
     int d = 0;
-    double qx = 0.0, qy = 0.0, qz = 0.0;
-    if (valid && l == 0) {      // the (corrected) position, read early: it does not depend on the record
-        qx = a.px[j];
-        qy = a.py[j];
-        qz = a.pz[j];
-    }
+    // lane c < 3 advects coordinate c (one FP64 operation per lane, all
+    // three at once); its (corrected) position is read early: it does not
+    // depend on the record
+    const double *pc = l == 0 ? a.px : (l == 1 ? a.py : a.pz);
+    double *qc = l == 0 ? a.qx : (l == 1 ? a.qy : a.qz);
+    double q = 0.0;
+    if (valid && l < 3)
+        q = pc[j];
     if (valid) {
         d = a.node_drop[j];
         const NodeRec &r = a.rec[j];
@@ -600,10 +626,9 @@ __device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
             atomicOr(&a.status[4 * d], ST_NAN);
         else if (ax * ax + ay * ay + az * az > 0.25f)
             atomicOr(&a.status[4 * d], ST_JUMP);
-        a.qx[j] = qx + (double)ax;
-        a.qy[j] = qy + (double)ay;
-        a.qz[j] = qz + (double)az;
     }
+    if (valid && l < 3)
+        qc[j] = q + (double)(l == 0 ? ax : (l == 1 ? ay : az));
 }
 
 __device__ __forceinline__ int find_drop_chunk(const Drop *D, int n, int c)
@@ -745,17 +770,15 @@ __device__ bool grid_barrier(const Arrays &a, unsigned &sense)
 }
 
 // ------------------------------------------------------------------ kernels
-constexpr int NF_THREADS = 64;   // block size of the force kernel: one node per thread, small blocks
-                                 // so that a mesh of ten thousand nodes spreads over every SM
+constexpr int NF_THREADS = 128;  // block size of the force kernel (32 nodes): small blocks, so that a
+                                 // mesh of ten thousand nodes spreads over every SM
 
 template <bool EL>
 __global__ void __launch_bounds__(NF_THREADS) node_force_kernel(Arrays a)
 {
     griddep_wait();
     const uint32_t gen = *a.gen + 1u;                  // committed by the spread
-    const int j = blockIdx.x * NF_THREADS + threadIdx.x;
-    if (j < a.total_nodes)
-        node_forces<EL>(a, j, gen);
+    node_forces<EL>(a, (int64_t)blockIdx.x * NF_THREADS + threadIdx.x, gen);
 }
 
 __global__ void __launch_bounds__(IB_THREADS) spread_kernel(Arrays a)
@@ -812,9 +835,10 @@ __global__ void __launch_bounds__(IB_THREADS) ib_front_kernel(Arrays a)
     unsigned sense = *(volatile unsigned *)a.bar_flag;
     const uint32_t gen = *a.gen + 1u;
     const int cur = (int)(gen & 1u);
+    const int64_t nf = ((int64_t)a.total_nodes * NL + 31) & ~(int64_t)31;   // whole warps
     const int64_t stride = (int64_t)gridDim.x * IB_THREADS;
-    for (int64_t j = (int64_t)blockIdx.x * IB_THREADS + threadIdx.x; j < a.total_nodes; j += stride)
-        node_forces<EL>(a, (int)j, gen);
+    for (int64_t gid = (int64_t)blockIdx.x * IB_THREADS + threadIdx.x; gid < nf; gid += stride)
+        node_forces<EL>(a, gid, gen);
     if (!grid_barrier(a, sense))
         return;
     zero_left_tiles(a, gen, cur, blockIdx.x, gridDim.x);
@@ -859,7 +883,7 @@ cudaError_t launch_node_force(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    const dim3 grid((unsigned)((a.total_nodes + NF_THREADS - 1) / NF_THREADS));
+    const dim3 grid((unsigned)(((int64_t)a.total_nodes * NL + NF_THREADS - 1) / NF_THREADS));
     if (a.fref)
         return launch_k(node_force_kernel<true>, grid, dim3(NF_THREADS), 0, s, a.pdl != 0, a);
     return launch_k(node_force_kernel<false>, grid, dim3(NF_THREADS), 0, s, a.pdl != 0, a);
@@ -908,7 +932,7 @@ cudaError_t launch_ib_front(const Arrays &a, int per_sm, cudaStream_t s)
     if (a.total_nodes <= 0)
         return cudaSuccess;
     int grid = 0;
-    const int64_t want = ((int64_t)a.total_nodes + IB_THREADS - 1) / IB_THREADS;
+    const int64_t want = ((int64_t)a.total_nodes * NL + IB_THREADS - 1) / IB_THREADS;
     const bool el = a.fref != nullptr;
     const void *fn = el ? (const void *)ib_front_kernel<true> : (const void *)ib_front_kernel<false>;
     cudaError_t e = coop_grid(fn, std::max<int64_t>(want, (int64_t)sm_count()), per_sm, grid, g_front_blocks[el]);
