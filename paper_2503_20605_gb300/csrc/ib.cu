@@ -30,7 +30,9 @@ namespace iblb {
 namespace {
 
 constexpr int IB_THREADS = 256;  // block size of every membrane kernel
-constexpr int SPREAD_PARTS = IB_THREADS / TILE_CELLS;   // threads per cell in the spread
+constexpr int SPREAD_PARTS = 4;  // parts of a tile's sorted node list, summed separately per cell
+constexpr int SP_THREADS = 256;  // block size of the separate spread kernel and its blocks per SM
+constexpr int SP_PER_SM = 4;     // (128-thread blocks, six per SM, measured slower: 15.2 against 13.0 us)
 constexpr int VC_RB = VC_ITEMS;  // threads per volume-correction chunk
 constexpr long long BARRIER_CYCLES = 4000000000LL;      // ~2 s: bounded grid-barrier wait
 
@@ -212,7 +214,7 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
     Corr cr = {false, 1.0, 0.0, 0.0, 0.0};
     double qx0 = 0.0, qy0 = 0.0, qz0 = 0.0;
     if (valid) {
-        d = a.node_drop[j];
+        d = a.ndrops == 1 ? 0 : a.node_drop[j];   // (one droplet: no lookup on the critical path)
         cr = load_corr(a, d);
         qx0 = a.qx[j];
         qy0 = a.qy[j];
@@ -429,13 +431,15 @@ __device__ __forceinline__ void tile_weights(int T0, int b, int n, bool periodic
 
 // Tiles of the previous band that are not in this step's band: zero their
 // force so that F vanishes outside the band (band tiles are rewritten).
-// Block bid of nb takes SPREAD_PARTS tiles per pass, 64 threads each.
+// Block bid of nb (NT threads) takes NT / 64 tiles per pass, 64 threads each.
+template <int NT>
 __device__ void zero_left_tiles(const Arrays &a, uint32_t gen, int cur, int bid, int nb)
 {
+    constexpr int TPB = NT / TILE_CELLS;
     const int tid = threadIdx.x;
     const int nprev = min(a.n_active[cur ^ 1], a.active_cap);
     const int *plist = a.active + (int64_t)(cur ^ 1) * a.active_cap;
-    for (int it = bid * SPREAD_PARTS + tid / TILE_CELLS; it < nprev; it += nb * SPREAD_PARTS) {
+    for (int it = bid * TPB + tid / TILE_CELLS; it < nprev; it += nb * TPB) {
         const int64_t T = plist[it];
         if (a.tile_gen[T] == gen)
             continue;
@@ -455,12 +459,16 @@ __device__ void zero_left_tiles(const Arrays &a, uint32_t gen, int cur, int bid,
 }
 
 // Band tiles bid, bid + nb, ...: the tile's nodes are staged in parallel and
-// sorted by node index; SPREAD_PARTS threads per cell add consecutive parts
-// of the sorted list and the parts are summed in a fixed order, so every
-// cell's force is the same for any launch shape.  The tile's counter returns
+// sorted by node index; every cell adds SPREAD_PARTS consecutive parts of the
+// sorted list separately (NT / 64 threads per cell, each taking one or more
+// parts) and the parts are summed in a fixed order, so every cell's force is
+// the same for any launch shape and block size.  The tile's counter returns
 // to zero for the next step.
+template <int NT>
 __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, int nb, SpreadSmem &sm)
 {
+    constexpr int TPC = NT / TILE_CELLS;           // threads per cell
+    constexpr int H = SPREAD_CAP / NT;             // staged nodes per thread, at most
     const int tid = threadIdx.x;
     const int nact = min(a.n_active[cur], a.active_cap);
     const int *list = a.active + (int64_t)cur * a.active_cap;
@@ -473,13 +481,13 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
         const int64_t e0 = T * TILE_CAP;
         const int cnt = min(a.bin_cnt[T], TILE_CAP);     // overflow was flagged by the force kernel
         // stage: every listed node's tile-local weights and force, kept in
-        // registers (at most two nodes per thread: SPREAD_CAP = 2 IB_THREADS)
-        static_assert(SPREAD_CAP <= 2 * IB_THREADS, "two staged nodes per thread");
-        float4 v[2][4];
-        int key[2];
+        // registers (at most H nodes per thread)
+        static_assert(SPREAD_CAP == H * NT, "whole staging passes");
+        float4 v[H][4];
+        int key[H];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int e = tid + h * IB_THREADS;
+        for (int h = 0; h < H; ++h) {
+            const int e = tid + h * NT;
             key[h] = 0x7fffffff;
             if (e < cnt) {
                 const int j = a.tile_list[e0 + e];
@@ -508,8 +516,8 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
         // so that contributions are added in increasing j
         const int4 *keys4 = reinterpret_cast<const int4 *>(sm.node);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (tid + h * IB_THREADS < cnt) {
+        for (int h = 0; h < H; ++h) {
+            if (tid + h * NT < cnt) {
                 int rank = 0;
                 for (int k = 0; k < (cnt + 3) >> 2; ++k) {
                     const int4 kv = keys4[k];
@@ -522,24 +530,28 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
             }
         }
         __syncthreads();
-        const int cell = tid & (TILE_CELLS - 1), part = tid / TILE_CELLS;
+        const int cell = tid & (TILE_CELLS - 1), lane_part = tid / TILE_CELLS;
         const int cx = cell & 3, cy = (cell >> 2) & 3, cz = cell >> 4;
         const int X = X0 + cx, Y = Y0 + cy, Z = Z0 + cz;
-        const int k0 = (int)(((int64_t)cnt * part) / SPREAD_PARTS), k1 = (int)(((int64_t)cnt * (part + 1)) / SPREAD_PARTS);
-        float fx = 0.f, fy = 0.f, fz = 0.f;
-        for (int k = k0; k < k1; ++k) {
-            const float *r = sm.rec[k];
-            const float w = (r[cx] * r[4 + cy]) * r[8 + cz];
-            const float4 ph = *reinterpret_cast<const float4 *>(r + 12);
-            fx += ph.x * w;
-            fy += ph.y * w;
-            fz += ph.z * w;
+#pragma unroll
+        for (int part = lane_part; part < SPREAD_PARTS; part += TPC) {
+            const int k0 = (int)(((int64_t)cnt * part) / SPREAD_PARTS);
+            const int k1 = (int)(((int64_t)cnt * (part + 1)) / SPREAD_PARTS);
+            float fx = 0.f, fy = 0.f, fz = 0.f;
+            for (int k = k0; k < k1; ++k) {
+                const float *r = sm.rec[k];
+                const float w = (r[cx] * r[4 + cy]) * r[8 + cz];
+                const float4 ph = *reinterpret_cast<const float4 *>(r + 12);
+                fx += ph.x * w;
+                fy += ph.y * w;
+                fz += ph.z * w;
+            }
+            sm.part[0][part][cell] = fx;
+            sm.part[1][part][cell] = fy;
+            sm.part[2][part][cell] = fz;
         }
-        sm.part[0][part][cell] = fx;
-        sm.part[1][part][cell] = fy;
-        sm.part[2][part][cell] = fz;
         __syncthreads();
-        if (part == 0 && X < D.nx && Y < D.ny && Z < D.nzf) {
+        if (lane_part == 0 && X < D.nx && Y < D.ny && Z < D.nzf) {
             float sx = sm.part[0][0][cell], sy = sm.part[1][0][cell], sz = sm.part[2][0][cell];
             for (int p = 1; p < SPREAD_PARTS; ++p) {
                 sx += sm.part[0][p][cell];
@@ -591,7 +603,7 @@ __device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
     if (valid && l < 3)
         q = pc[j];
     if (valid) {
-        d = a.node_drop[j];
+        d = a.ndrops == 1 ? 0 : a.node_drop[j];
         const NodeRec &r = a.rec[j];
         const Drop &D = a.drops[d];
         if (r.key > 0) {
@@ -657,19 +669,24 @@ __device__ __forceinline__ int find_drop_chunk(const Drop *D, int n, int c)
 template <int NV, int NT>
 __device__ __forceinline__ void block_sum(double *v)
 {
+    static_assert(NV * 32 <= NT, "one warp per value");
     __shared__ double sh[NV][NT];
+    __shared__ double res[NV];
     for (int k = 0; k < NV; ++k)
         sh[k][threadIdx.x] = v[k];
     __syncthreads();
-    if (threadIdx.x < 32) {
-        for (int k = 0; k < NV; ++k) {
-            double x = sh[k][threadIdx.x];
-            for (int i = threadIdx.x + 32; i < NT; i += 32)
-                x += sh[k][i];
-            v[k] = warp_sum(x);
-        }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < NV) {           // warp w sums value w
+        double x = sh[w][lane];
+        for (int i = lane + 32; i < NT; i += 32)
+            x += sh[w][i];
+        x = warp_sum(x);
+        if (lane == 0)
+            res[w] = x;
     }
     __syncthreads();
+    for (int k = 0; k < NV; ++k)
+        v[k] = res[k];
 }
 
 // NT: the block size (at least VC_RB; threads beyond the chunk add zeros).
@@ -709,28 +726,28 @@ __device__ void vc_chunk(const Arrays &a, int c)
         s_last = atomicAdd(&a.vc_done[d], 1) == D.red_nchunks - 1;
     }
     __syncthreads();
-    if (s_last && threadIdx.x < 32) {
+    __shared__ double fold[4];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (s_last && w < 4) {  // warp q folds value q of every chunk of the droplet
         __threadfence();
-        const int lane = threadIdx.x;
-        double w[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int i = lane; i < D.red_nchunks; i += 32) {
-            const volatile double *p = a.red_part + (int64_t)NRED * (D.red_chunk0 + i);
-            for (int q = 0; q < 4; ++q)
-                w[q] += p[q];
-        }
-        for (int q = 0; q < 4; ++q)
-            w[q] = warp_sum(w[q]);
-        if (lane == 0) {
-            const double V = w[0] / 6.0;
-            double *o = a.red_out + (int64_t)NRED * d;
-            o[0] = cbrt(D.V0 / V);
-            o[1] = w[1] / D.nnodes;
-            o[2] = w[2] / D.nnodes;
-            o[3] = w[3] / D.nnodes;
-            o[4] = V;
-            o[5] = 1.0;         // applied wherever the positions are read next
-            a.vc_done[d] = 0;
-        }
+        double x = 0.0;
+        for (int i = lane; i < D.red_nchunks; i += 32)
+            x += ((const volatile double *)(a.red_part + (int64_t)NRED * (D.red_chunk0 + i)))[w];
+        x = warp_sum(x);
+        if (lane == 0)
+            fold[w] = x;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        const double V = fold[0] / 6.0;
+        double *o = a.red_out + (int64_t)NRED * d;
+        o[0] = cbrt(D.V0 / V);
+        o[1] = fold[1] / D.nnodes;
+        o[2] = fold[2] / D.nnodes;
+        o[3] = fold[3] / D.nnodes;
+        o[4] = V;
+        o[5] = 1.0;         // applied wherever the positions are read next
+        a.vc_done[d] = 0;
     }
     __syncthreads();
 }
@@ -781,14 +798,14 @@ __global__ void __launch_bounds__(NF_THREADS) node_force_kernel(Arrays a)
     node_forces<EL>(a, (int64_t)blockIdx.x * NF_THREADS + threadIdx.x, gen);
 }
 
-__global__ void __launch_bounds__(IB_THREADS) spread_kernel(Arrays a)
+__global__ void __launch_bounds__(SP_THREADS, SP_PER_SM) spread_kernel(Arrays a)
 {
     griddep_wait();
     __shared__ SpreadSmem sm;
     const uint32_t gen = *a.gen + 1u;
     const int cur = (int)(gen & 1u);
-    zero_left_tiles(a, gen, cur, blockIdx.x, gridDim.x);
-    spread_tiles(a, gen, cur, blockIdx.x, gridDim.x, sm);
+    zero_left_tiles<SP_THREADS>(a, gen, cur, blockIdx.x, gridDim.x);
+    spread_tiles<SP_THREADS>(a, gen, cur, blockIdx.x, gridDim.x, sm);
     spread_finish(a, gen, cur, sm);
 }
 
@@ -841,8 +858,8 @@ __global__ void __launch_bounds__(IB_THREADS) ib_front_kernel(Arrays a)
         node_forces<EL>(a, gid, gen);
     if (!grid_barrier(a, sense))
         return;
-    zero_left_tiles(a, gen, cur, blockIdx.x, gridDim.x);
-    spread_tiles(a, gen, cur, blockIdx.x, gridDim.x, sm);
+    zero_left_tiles<IB_THREADS>(a, gen, cur, blockIdx.x, gridDim.x);
+    spread_tiles<IB_THREADS>(a, gen, cur, blockIdx.x, gridDim.x, sm);
     spread_finish(a, gen, cur, sm);
 }
 
@@ -893,7 +910,7 @@ cudaError_t launch_spread(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    return launch_k(spread_kernel, dim3(sm_count() * 4), dim3(IB_THREADS), 0, s, a.pdl != 0, a);
+    return launch_k(spread_kernel, dim3(sm_count() * SP_PER_SM), dim3(SP_THREADS), 0, s, a.pdl != 0, a);
 }
 
 cudaError_t launch_interp_advect(const Arrays &a, cudaStream_t s)
