@@ -875,7 +875,7 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
     if ((e = cudaMalloc(&c->fbuf[0], sb * Q * A.total_pcells)) != cudaSuccess ||
         (e = cudaMalloc(&c->fbuf[1], sb * Q * A.total_pcells)) != cudaSuccess ||
         (e = dalloc(&A.F, 3 * (size_t)A.total_pcells)) != cudaSuccess ||
-        (e = dalloc(&A.U, 3 * (size_t)A.total_pcells)) != cudaSuccess ||
+        (e = dalloc(&A.U, (size_t)A.total_pcells)) != cudaSuccess ||
         (e = dalloc(&A.tile_gen, (size_t)T)) != cudaSuccess || (e = dalloc(&A.gen, 1)) != cudaSuccess ||
         (e = dalloc(&A.n_active, 2)) != cudaSuccess || (e = dalloc(&A.active, 2 * (size_t)T)) != cudaSuccess ||
         (e = dalloc(&A.bin_cnt, (size_t)T)) != cudaSuccess ||
@@ -911,7 +911,7 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
         (e = cudaMemsetAsync(A.col_cnt, 0, sizeof(int) * A.total_cols, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.status, 0, sizeof(int) * 4 * n, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(A.F, 0, sizeof(float) * 3 * A.total_pcells, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(A.U, 0, sizeof(float) * 3 * A.total_pcells, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A.U, 0, sizeof(float4) * A.total_pcells, s)) != cudaSuccess ||
         (e = launch_init_populations(A, c->storage, c->fbuf[0], s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(c->d_drops, c->drops.data(), sizeof(Drop) * n, cudaMemcpyHostToDevice, s)) !=
             cudaSuccess ||

@@ -432,16 +432,38 @@ __device__ __forceinline__ void tile_weights(int T0, int b, int n, bool periodic
 // Tiles of the previous band that are not in this step's band: zero their
 // force so that F vanishes outside the band (band tiles are rewritten).
 // Block bid of nb (NT threads) takes NT / 64 tiles per pass, 64 threads each.
+// The first tile of a thread's pass is looked up by zero_left_first (its
+// loads can be issued when the kernel starts) and zeroed at the end with the
+// others: the spread writes only tiles of this step's band, so the order
+// does not matter.
+struct LeftTile {
+    int64_t T = -1;
+    uint32_t g = 0;
+};
 template <int NT>
-__device__ void zero_left_tiles(const Arrays &a, uint32_t gen, int cur, int bid, int nb)
+__device__ __forceinline__ LeftTile zero_left_first(const Arrays &a, int cur, int bid)
+{
+    constexpr int TPB = NT / TILE_CELLS;
+    LeftTile lt;
+    const int it = bid * TPB + threadIdx.x / TILE_CELLS;
+    if (it < min(a.n_active[cur ^ 1], a.active_cap)) {
+        lt.T = a.active[(int64_t)(cur ^ 1) * a.active_cap + it];
+        lt.g = a.tile_gen[lt.T];
+    }
+    return lt;
+}
+
+template <int NT>
+__device__ void zero_left_tiles(const Arrays &a, uint32_t gen, int cur, int bid, int nb, LeftTile first)
 {
     constexpr int TPB = NT / TILE_CELLS;
     const int tid = threadIdx.x;
     const int nprev = min(a.n_active[cur ^ 1], a.active_cap);
     const int *plist = a.active + (int64_t)(cur ^ 1) * a.active_cap;
     for (int it = bid * TPB + tid / TILE_CELLS; it < nprev; it += nb * TPB) {
-        const int64_t T = plist[it];
-        if (a.tile_gen[T] == gen)
+        const bool pre = it == bid * TPB + tid / TILE_CELLS && first.T >= 0;
+        const int64_t T = pre ? first.T : plist[it];
+        if ((pre ? first.g : a.tile_gen[T]) == gen)
             continue;
         const int d = find_drop_tile(a.drops, a.ndrops, T);
         const Drop &D = a.drops[d];
@@ -621,9 +643,10 @@ __device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
                 for (int dx = 0; dx < 4; ++dx) {
                     const int64_t g = row + wrapi(r.bx - 1 + dx, D.nx);
                     const float w = r.wx[dx] * wyz;
-                    ax += a.U[g] * w;
-                    ay += a.U[a.total_pcells + g] * w;
-                    az += a.U[2 * a.total_pcells + g] * w;
+                    const float4 u = a.U[g];
+                    ax += u.x * w;
+                    ay += u.y * w;
+                    az += u.z * w;
                 }
             }
         }
@@ -804,8 +827,9 @@ __global__ void __launch_bounds__(SP_THREADS, SP_PER_SM) spread_kernel(Arrays a)
     __shared__ SpreadSmem sm;
     const uint32_t gen = *a.gen + 1u;
     const int cur = (int)(gen & 1u);
-    zero_left_tiles<SP_THREADS>(a, gen, cur, blockIdx.x, gridDim.x);
+    const LeftTile first = zero_left_first<SP_THREADS>(a, cur, blockIdx.x);
     spread_tiles<SP_THREADS>(a, gen, cur, blockIdx.x, gridDim.x, sm);
+    zero_left_tiles<SP_THREADS>(a, gen, cur, blockIdx.x, gridDim.x, first);
     spread_finish(a, gen, cur, sm);
 }
 
@@ -858,8 +882,9 @@ __global__ void __launch_bounds__(IB_THREADS) ib_front_kernel(Arrays a)
         node_forces<EL>(a, gid, gen);
     if (!grid_barrier(a, sense))
         return;
-    zero_left_tiles<IB_THREADS>(a, gen, cur, blockIdx.x, gridDim.x);
+    const LeftTile first = zero_left_first<IB_THREADS>(a, cur, blockIdx.x);
     spread_tiles<IB_THREADS>(a, gen, cur, blockIdx.x, gridDim.x, sm);
+    zero_left_tiles<IB_THREADS>(a, gen, cur, blockIdx.x, gridDim.x, first);
     spread_finish(a, gen, cur, sm);
 }
 

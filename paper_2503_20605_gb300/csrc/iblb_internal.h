@@ -86,7 +86,9 @@ struct Arrays {
     int64_t total_rows;            // sum of ny * nzf
     // lattice
     float *F;                      // 3 * total_pcells, force density: exactly 0 outside band tiles
-    float *U;                      // 3 * total_pcells, velocity (valid on band rows only)
+    float4 *U;                     // total_pcells, velocity (ux, uy, uz, 0) per cell, interleaved so
+                                   // that the interpolation reads a cell in one load (valid on band
+                                   // rows only)
     uint32_t *tile_gen;            // tile is in the band of this step iff == *gen
     uint32_t *gen;                 // step generation counter (device)
     int *n_active;                 // 2: band tiles of this step / of the previous step

@@ -277,8 +277,7 @@ __device__ __forceinline__ void collide_group(const Arrays &a, const DropC &c, c
     const bool bbp = walls && z == c.nzf - 1;      // rows pulled from z+1 bounced at the top
     const int RP = R * P;
     S *outb = dst + (int64_t)Q * pcell0 + (int64_t)P * ny * z;
-    const int64_t TP = a.total_pcells;
-    float *U = a.U;
+    float4 *U = a.U;
     // cell e = r * nx + x of the group, walked without divisions
     const int step_r = c.step_r, step_x = c.step_x;
     int r = c.r0, x = c.x0;
@@ -356,9 +355,7 @@ __device__ __forceinline__ void collide_group(const Arrays &a, const DropC &c, c
         const int64_t cell = (int64_t)P * (y + (int64_t)ny * z) + x;
         if (FORCE && band) {
             const int64_t gi = pcell0 + cell;
-            U[gi] = ux;
-            U[TP + gi] = uy;
-            U[2 * TP + gi] = uz;
+            U[gi] = make_float4(ux, uy, uz, 0.0f);
         }
         const float om1 = 1.0f - omega, k = fmaf(-0.5f, omega, 1.0f), er = omega * rho;
         float X = omega * fmaf(-1.5f * rho, fmaf(ux, ux, fmaf(uy, uy, uz * uz)), drho);
@@ -519,8 +516,7 @@ __device__ __forceinline__ void collide_pairs(const Arrays &a, const DropC &c, c
     const bool bbp = c.walls && z == c.nzf - 1;    // rows pulled from z+1 bounced at the top
     const int RP = R * P;
     S *outb = dst + (int64_t)Q * pcell0 + (int64_t)P * ny * z;
-    const int64_t TP = a.total_pcells;
-    float *U = a.U;
+    float4 *U = a.U;
     const int npr = c.npr, step_r = c.pstep_r, step_x = c.pstep_x;
     int r = c.pr0, px = c.px0;
     constexpr int NT = cons_threads<S>();
@@ -596,9 +592,7 @@ __device__ __forceinline__ void collide_pairs(const Arrays &a, const DropC &c, c
             bgk_guo_cell<FORCE>(sa, FAx, FAy, FAz, cell_omega<VARTAU>(a, c, x, y, z), c.rho0, oa, ux, uy, uz);
             if (FORCE && band) {
                 const int64_t gi = pcell0 + cell;
-                U[gi] = ux;
-                U[TP + gi] = uy;
-                U[2 * TP + gi] = uz;
+                U[gi] = make_float4(ux, uy, uz, 0.0f);
             }
         }
         if (hasB) {  // cell x + 1: c_x = 0 from the high half, +x from the low half, -x from x + 2
@@ -626,9 +620,7 @@ __device__ __forceinline__ void collide_pairs(const Arrays &a, const DropC &c, c
             bgk_guo_cell<FORCE>(sb, FBx, FBy, FBz, cell_omega<VARTAU>(a, c, x + 1, y, z), c.rho0, ob, ux, uy, uz);
             if (FORCE && band) {
                 const int64_t gi = pcell0 + cell + 1;
-                U[gi] = ux;
-                U[TP + gi] = uy;
-                U[2 * TP + gi] = uz;
+                U[gi] = make_float4(ux, uy, uz, 0.0f);
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i)
