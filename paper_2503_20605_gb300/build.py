@@ -32,6 +32,14 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def file_flags(src):
+    """The membrane kernels (ib.cu) are compiled without implicit fused
+    multiply-adds: their device functions are inlined into the separate and
+    the cooperative kernels, and only explicit fmaf calls may fuse, so that
+    both give the same bits whatever the optimiser does around them."""
+    return ["-fmad=false"] if os.path.basename(src) == "ib.cu" else []
+
+
 def _deps_mtime():
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h") or f.endswith(".cuh")]
     hdrs.append(os.path.join(os.path.dirname(HERE), "include", "iblb.h"))
@@ -47,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), dep):
-            jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
+            jobs.append([nvcc(), *ARCH, *FLAGS, *extra, *file_flags(s), "-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             futs = [ex.submit(subprocess.run, j, capture_output=True, text=True) for j in jobs]

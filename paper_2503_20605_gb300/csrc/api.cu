@@ -180,6 +180,10 @@ int check_desc(const iblb_lattice_desc &l, const iblb_physics_desc &p, std::stri
         why = "box sides must be >= 8";
         return 0;
     }
+    if (l.nx > 8188 || l.ny > 8188 || l.nz > 4094) {
+        why = "box sides must be at most 8188 (x, y) and 4094 (z) cells";
+        return 0;
+    }
     if ((int64_t)l.nx * l.ny * l.nz > ((int64_t)1 << 31) / 2) {
         why = "box too large (cells must stay below 2^30)";
         return 0;

@@ -20,6 +20,10 @@
 // the same device functions, the same arithmetic, bit-identical results.
 // Node positions are FP64 so that edge vectors and kernel offsets are exact
 // before they are rounded to FP32 for the force and kernel arithmetic.
+// This file is compiled without implicit fused multiply-adds (-fmad=false):
+// its device functions are inlined into both the separate and the
+// cooperative kernels, and only the explicit fmaf calls fuse, so that both
+// give the same bits.
 #include <algorithm>
 
 #include "iblb_internal.h"
@@ -353,7 +357,7 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
     const int cur = (int)(gen & 1u);
     for (int c0 = l; c0 < ncombo; c0 += 2 * NL) {
         int64_t tl[2], trw[2];
-        int rk[2];
+        int rk[2], tc[2];
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int c = c0 + i * NL;
@@ -364,6 +368,7 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
                 const int tz = iz == 0 ? tz0 : (iz == 1 ? tz1 : tz2);
                 tl[i] = D.tile0 + tx + (int64_t)D.tx * (ty + (int64_t)D.ty * tz);
                 trw[i] = D.trow0 + ty + (int64_t)D.ty * tz;
+                tc[i] = tile_coords(tx, ty, tz);
                 rk[i] = atomicAdd(&a.bin_cnt[tl[i]], 1);
             }
         }
@@ -377,7 +382,7 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
                 a.tile_gen[t] = gen;
                 const int slot = atomicAdd(&a.n_active[cur], 1);
                 if (slot < a.active_cap)
-                    a.active[(int64_t)cur * a.active_cap + slot] = (int)t;
+                    a.active[(int64_t)cur * a.active_cap + slot] = make_int2((int)t, tc[i]);
                 // its tile row too; the stream-collide rows run before this
                 // step's band was known assumed that this row could not hold
                 // band tiles
@@ -438,6 +443,7 @@ __device__ __forceinline__ void tile_weights(int T0, int b, int n, bool periodic
 // does not matter.
 struct LeftTile {
     int64_t T = -1;
+    int coords = 0;
     uint32_t g = 0;
 };
 template <int NT>
@@ -447,7 +453,9 @@ __device__ __forceinline__ LeftTile zero_left_first(const Arrays &a, int cur, in
     LeftTile lt;
     const int it = bid * TPB + threadIdx.x / TILE_CELLS;
     if (it < min(a.n_active[cur ^ 1], a.active_cap)) {
-        lt.T = a.active[(int64_t)(cur ^ 1) * a.active_cap + it];
+        const int2 e = a.active[(int64_t)(cur ^ 1) * a.active_cap + it];
+        lt.T = e.x;
+        lt.coords = e.y;
         lt.g = a.tile_gen[lt.T];
     }
     return lt;
@@ -459,18 +467,19 @@ __device__ void zero_left_tiles(const Arrays &a, uint32_t gen, int cur, int bid,
     constexpr int TPB = NT / TILE_CELLS;
     const int tid = threadIdx.x;
     const int nprev = min(a.n_active[cur ^ 1], a.active_cap);
-    const int *plist = a.active + (int64_t)(cur ^ 1) * a.active_cap;
+    const int2 *plist = a.active + (int64_t)(cur ^ 1) * a.active_cap;
     for (int it = bid * TPB + tid / TILE_CELLS; it < nprev; it += nb * TPB) {
         const bool pre = it == bid * TPB + tid / TILE_CELLS && first.T >= 0;
-        const int64_t T = pre ? first.T : plist[it];
+        const int2 e = pre ? make_int2((int)first.T, first.coords) : plist[it];
+        const int64_t T = e.x;
         if ((pre ? first.g : a.tile_gen[T]) == gen)
             continue;
-        const int d = find_drop_tile(a.drops, a.ndrops, T);
+        const int d = a.ndrops == 1 ? 0 : find_drop_tile(a.drops, a.ndrops, T);
         const Drop &D = a.drops[d];
-        const int local = (int)(T - D.tile0), cell = tid & (TILE_CELLS - 1);
-        const int X = 4 * (local % D.tx) + (cell & 3);
-        const int Y = 4 * ((local / D.tx) % D.ty) + ((cell >> 2) & 3);
-        const int Z = 4 * (local / (D.tx * D.ty)) + (cell >> 4);
+        const int cell = tid & (TILE_CELLS - 1);
+        const int X = 4 * (e.y & 2047) + (cell & 3);
+        const int Y = 4 * ((e.y >> 11) & 2047) + ((cell >> 2) & 3);
+        const int Z = 4 * (e.y >> 22) + (cell >> 4);
         if (X < D.nx && Y < D.ny && Z < D.nzf) {
             const int64_t g = D.pcell0 + X + (int64_t)D.pitch * (Y + (int64_t)D.ny * Z);
             a.F[g] = 0.0f;
@@ -493,13 +502,13 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
     constexpr int H = SPREAD_CAP / NT;             // staged nodes per thread, at most
     const int tid = threadIdx.x;
     const int nact = min(a.n_active[cur], a.active_cap);
-    const int *list = a.active + (int64_t)cur * a.active_cap;
+    const int2 *list = a.active + (int64_t)cur * a.active_cap;
     for (int it = bid; it < nact; it += nb) {
-        const int64_t T = list[it];
-        const int d = find_drop_tile(a.drops, a.ndrops, T);
+        const int2 te = list[it];
+        const int64_t T = te.x;
+        const int d = a.ndrops == 1 ? 0 : find_drop_tile(a.drops, a.ndrops, T);
         const Drop &D = a.drops[d];
-        const int local = (int)(T - D.tile0);
-        const int X0 = 4 * (local % D.tx), Y0 = 4 * ((local / D.tx) % D.ty), Z0 = 4 * (local / (D.tx * D.ty));
+        const int X0 = 4 * (te.y & 2047), Y0 = 4 * ((te.y >> 11) & 2047), Z0 = 4 * (te.y >> 22);
         const int64_t e0 = T * TILE_CAP;
         const int cnt = min(a.bin_cnt[T], TILE_CAP);     // overflow was flagged by the force kernel
         // stage: every listed node's tile-local weights and force, kept in
@@ -564,9 +573,9 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
                 const float *r = sm.rec[k];
                 const float w = (r[cx] * r[4 + cy]) * r[8 + cz];
                 const float4 ph = *reinterpret_cast<const float4 *>(r + 12);
-                fx += ph.x * w;
-                fy += ph.y * w;
-                fz += ph.z * w;
+                fx = fmaf(ph.x, w, fx);
+                fy = fmaf(ph.y, w, fy);
+                fz = fmaf(ph.z, w, fz);
             }
             sm.part[0][part][cell] = fx;
             sm.part[1][part][cell] = fy;
@@ -644,9 +653,9 @@ __device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
                     const int64_t g = row + wrapi(r.bx - 1 + dx, D.nx);
                     const float w = r.wx[dx] * wyz;
                     const float4 u = a.U[g];
-                    ax += u.x * w;
-                    ay += u.y * w;
-                    az += u.z * w;
+                    ax = fmaf(u.x, w, ax);
+                    ay = fmaf(u.y, w, ay);
+                    az = fmaf(u.z, w, az);
                 }
             }
         }

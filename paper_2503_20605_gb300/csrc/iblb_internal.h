@@ -68,6 +68,7 @@ struct __align__(16) NodeRec {
     float phi[3];
     int spare;
 };
+static_assert(sizeof(NodeRec) == 80, "the spread reads a record as five 16-byte words");
 
 // Every device array of a context.  Lattice fields are pooled over droplets
 // in the padded row layout of the populations: cell (x, row = y + ny z) of
@@ -92,7 +93,9 @@ struct Arrays {
     uint32_t *tile_gen;            // tile is in the band of this step iff == *gen
     uint32_t *gen;                 // step generation counter (device)
     int *n_active;                 // 2: band tiles of this step / of the previous step
-    int *active;                   // 2 * active_cap: band tiles, indexed by generation parity
+    int2 *active;                  // 2 * active_cap: band tiles, indexed by generation parity: the
+                                   // pooled tile index and the tile's coordinates in its droplet
+                                   // (tile_coords), so that readers need no divisions
     int active_cap;
     // per-tile node lists
     int *bin_cnt;                  // total_tiles: nodes listed in this step (returns to 0 in the spread)
@@ -161,6 +164,9 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
 }
+
+// tile coordinates (tx < 2048, ty < 2048, tz < 1024) packed in one int
+__host__ __device__ inline int tile_coords(int tx, int ty, int tz) { return tx | (ty << 11) | (tz << 22); }
 
 __host__ __device__ inline int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
