@@ -108,6 +108,8 @@ __device__ __forceinline__ void group_rows(const Drop &D, int g, int &y0, int &z
 struct DropC {
     int d, nx, ny, P, R, PC, nzf, walls, vartau, gpp, block0, step_r, step_x, r0, x0;
     int npr, pstep_r, pstep_x, pr0, px0;   // the same walk over cell pairs (x, x + 1), x even
+    int tx, ty;                            // tiles per row and per plane of tile rows
+    int64_t tile0;
     float inv_gpp, bfx, bfy, bfz, rho0, omega_out, omega_in;
     bool has_bf;
     int64_t pcell0, col0;
@@ -128,6 +130,9 @@ struct DropC {
         step_x = nt - step_r * nx;
         r0 = threadIdx.x / nx;
         x0 = threadIdx.x - r0 * nx;
+        tx = D.tx;
+        ty = D.ty;
+        tile0 = D.tile0;
         npr = (nx + 1) >> 1;
         pstep_r = nt / npr;
         pstep_x = nt - pstep_r * npr;
@@ -262,9 +267,16 @@ __device__ __forceinline__ void produce(const Arrays &a, const DropC &c, const S
 // is the case F = 0 (a group outside the band without a body force), where
 // every F term drops out; it rounds exactly as the FORCE path does with
 // F = 0, so a cell's result does not depend on which group shape holds it.
+// the cell's tile is in this step's band: its velocity is read by the
+// interpolation (every node's kernel support lies in band tiles)
+__device__ __forceinline__ bool in_band_tile(const Arrays &a, const DropC &c, int x, int y, int z, uint32_t gen)
+{
+    return a.tile_gen[c.tile0 + (x >> 2) + (int64_t)c.tx * ((y >> 2) + (int64_t)c.ty * (z >> 2))] == gen;
+}
+
 template <typename S, bool VARTAU, bool FORCE>
 __device__ __forceinline__ void collide_group(const Arrays &a, const DropC &c, const Stage<S> &stg, int y0, int z,
-                                              int nr, bool band, S *__restrict__ dst)
+                                              int nr, bool band, S *__restrict__ dst, uint32_t gen)
 {
     const int nx = c.nx, ny = c.ny, P = c.P, R = c.R;
     const int PC = c.PC;
@@ -353,7 +365,7 @@ __device__ __forceinline__ void collide_group(const Arrays &a, const DropC &c, c
         const float Jz = FORCE ? fmaf(0.5f, Fz, jz) : jz;
         const float ux = Jx * irho, uy = Jy * irho, uz = Jz * irho;
         const int64_t cell = (int64_t)P * (y + (int64_t)ny * z) + x;
-        if (FORCE && band) {
+        if (FORCE && band && in_band_tile(a, c, x, y, z, gen)) {
             const int64_t gi = pcell0 + cell;
             U[gi] = make_float4(ux, uy, uz, 0.0f);
         }
@@ -505,7 +517,7 @@ __device__ __forceinline__ float cell_omega(const Arrays &a, const DropC &c, int
 // so that no warp is always the last to release a stage.
 template <typename S, bool VARTAU, bool FORCE>
 __device__ __forceinline__ void collide_pairs(const Arrays &a, const DropC &c, const Stage<S> &stg, int y0, int z,
-                                              int nr, bool band, S *__restrict__ dst, int kk)
+                                              int nr, bool band, S *__restrict__ dst, int kk, uint32_t gen)
 {
     using PT = typename PairOf<S>::T;
     using PO = PairOf<S>;
@@ -565,6 +577,7 @@ __device__ __forceinline__ void collide_pairs(const Arrays &a, const DropC &c, c
         }
         const int64_t cell = (int64_t)P * (y + (int64_t)ny * z) + x;
         S *o = outb + P * y + x;
+        const bool ub = FORCE && band && in_band_tile(a, c, x, y, z, gen);   // both cells share the tile
         float oa[Q];
         {   // cell x: c_x = 0 from the pair's low half, +x from x - 1, -x from the pair's high half
             float sa[Q];
@@ -590,7 +603,7 @@ __device__ __forceinline__ void collide_pairs(const Arrays &a, const DropC &c, c
             sa[18] = bbm ? PO::lo(pv[18]) : (hasB ? PO::hi(pv[18]) : SC(18, 0));
             float ux, uy, uz;
             bgk_guo_cell<FORCE>(sa, FAx, FAy, FAz, cell_omega<VARTAU>(a, c, x, y, z), c.rho0, oa, ux, uy, uz);
-            if (FORCE && band) {
+            if (FORCE && ub) {
                 const int64_t gi = pcell0 + cell;
                 U[gi] = make_float4(ux, uy, uz, 0.0f);
             }
@@ -618,7 +631,7 @@ __device__ __forceinline__ void collide_pairs(const Arrays &a, const DropC &c, c
             sb[18] = bbm ? PO::hi(pv[18]) : SC(18, xp2);
             float ux, uy, uz;
             bgk_guo_cell<FORCE>(sb, FBx, FBy, FBz, cell_omega<VARTAU>(a, c, x + 1, y, z), c.rho0, ob, ux, uy, uz);
-            if (FORCE && band) {
+            if (FORCE && ub) {
                 const int64_t gi = pcell0 + cell + 1;
                 U[gi] = make_float4(ux, uy, uz, 0.0f);
             }
@@ -711,14 +724,14 @@ __global__ void __launch_bounds__(lb_block<S>(), 2)
             const bool band = *stg.flag != 0;
             if constexpr (sizeof(S) == 2) {      // 16-bit storage: two cells per work item
                 if (band || c.has_bf)
-                    collide_pairs<S, VARTAU, true>(a, c, stg, y0, z, nr, band, dst, kk);
+                    collide_pairs<S, VARTAU, true>(a, c, stg, y0, z, nr, band, dst, kk, gen);
                 else
-                    collide_pairs<S, VARTAU, false>(a, c, stg, y0, z, nr, false, dst, kk);
+                    collide_pairs<S, VARTAU, false>(a, c, stg, y0, z, nr, false, dst, kk, gen);
             } else {
                 if (band || c.has_bf)
-                    collide_group<S, VARTAU, true>(a, c, stg, y0, z, nr, band, dst);
+                    collide_group<S, VARTAU, true>(a, c, stg, y0, z, nr, band, dst, gen);
                 else
-                    collide_group<S, VARTAU, false>(a, c, stg, y0, z, nr, false, dst);
+                    collide_group<S, VARTAU, false>(a, c, stg, y0, z, nr, false, dst, gen);
             }
             mbar_arrive(&empty[st_i]);
             if (++st_i == ns) {
