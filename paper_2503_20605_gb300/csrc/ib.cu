@@ -26,6 +26,8 @@
 // give the same bits.
 #include <algorithm>
 
+#include <cuda/atomic>
+
 #include "iblb_internal.h"
 #include "reduce_util.cuh"
 
@@ -604,8 +606,8 @@ __device__ void spread_finish(const Arrays &a, uint32_t gen, int cur, SpreadSmem
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        sm.last = atomicAdd(a.spread_done, 1) == (int)gridDim.x - 1;
+        sm.last = cuda::atomic_ref<int, cuda::thread_scope_device>(*a.spread_done).fetch_add(
+                      1, cuda::memory_order_acq_rel) == (int)gridDim.x - 1;
     }
     __syncthreads();
     if (sm.last && threadIdx.x == 0) {
@@ -754,14 +756,14 @@ __device__ void vc_chunk(const Arrays &a, int c)
     if (threadIdx.x == 0) {
         for (int i = 0; i < 4; ++i)
             part[i] = v[i];
-        __threadfence();
-        s_last = atomicAdd(&a.vc_done[d], 1) == D.red_nchunks - 1;
+        // release: the partials above are visible to whoever sees the count
+        s_last = cuda::atomic_ref<int, cuda::thread_scope_device>(a.vc_done[d]).fetch_add(
+                     1, cuda::memory_order_acq_rel) == D.red_nchunks - 1;
     }
     __syncthreads();
     __shared__ double fold[4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (s_last && w < 4) {  // warp q folds value q of every chunk of the droplet
-        __threadfence();
         double x = 0.0;
         for (int i = lane; i < D.red_nchunks; i += 32)
             x += ((const volatile double *)(a.red_part + (int64_t)NRED * (D.red_chunk0 + i)))[w];
