@@ -63,7 +63,7 @@ struct iblb_ctx {
     void *fbuf[2] = {nullptr, nullptr};
     int cur = 0;
     int *d_tri = nullptr, *d_adj_start = nullptr, *d_adj = nullptr;
-    int4 *d_ring = nullptr;
+    int4 *d_ring = nullptr, *d_ring8 = nullptr;
     float4 *d_fref = nullptr;
     int n_red_chunks = 0, mass_blocks = 0;
     double *d_mass = nullptr;
@@ -449,8 +449,9 @@ void free_membrane_arrays(iblb_ctx *c)
     dfree(c->d_adj_start);
     dfree(c->d_adj);
     dfree(c->d_ring);
-    c->d_ring = nullptr;
-    c->A.ring = nullptr;
+    dfree(c->d_ring8);
+    c->d_ring = c->d_ring8 = nullptr;
+    c->A.ring = c->A.ring8 = nullptr;
     dfree(c->d_fref);
     c->d_fref = nullptr;
     c->A.fref = nullptr;
@@ -521,7 +522,7 @@ int rebuild_membranes(iblb_ctx *c)
     for (int j = 0; j < N; ++j)
         start[j + 1] += start[j];
     adj.resize(start[N] > 0 ? start[N] : 1);
-    std::vector<int4> ring(adj.size());
+    std::vector<int4> ring(adj.size()), ring8((size_t)RING8 * std::max(N, 1), make_int4(-1, -1, 0, 0));
     {
         std::vector<int> pos(start.begin(), start.end() - 1);
         for (int t = 0; t < NT; ++t)       // faces in increasing order per node
@@ -531,6 +532,14 @@ int rebuild_membranes(iblb_ctx *c)
                 // the other corners in counter-clockwise order after this one
                 ring[e] = make_int4(tri[3 * (size_t)t + (k + 1) % 3], tri[3 * (size_t)t + (k + 2) % 3], (t << 2) | k, 0);
             }
+        for (int j = 0; j < N; ++j) {
+            const int v = start[j + 1] - start[j];
+            for (int q = 0; q < RING8; ++q) {
+                int4 en = q < v ? ring[start[j] + q] : make_int4(-1, -1, 0, 0);
+                en.w = v;
+                ring8[(size_t)RING8 * j + q] = en;
+            }
+        }
     }
     if (NT >= (1 << 29))
         return fail(c, IBLB_E_ARG, "too many faces");
@@ -575,6 +584,7 @@ int rebuild_membranes(iblb_ctx *c)
     CK(dalloc(&c->d_adj_start, N + 1));
     CK(dalloc(&c->d_adj, adj.size()));
     CK(dalloc(&c->d_ring, ring.size()));
+    CK(dalloc(&c->d_ring8, ring8.size()));
     CK(dalloc(&c->A.rec, N));
     CK(dalloc(&c->A.clamped, N));
     CK(cudaMemsetAsync(c->A.clamped, 0, N, c->stream));
@@ -586,6 +596,7 @@ int rebuild_membranes(iblb_ctx *c)
     c->A.adj_start = c->d_adj_start;
     c->A.adj = c->d_adj;
     c->A.ring = c->d_ring;
+    c->A.ring8 = c->d_ring8;
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream) : cudaSuccess;
     };
@@ -598,6 +609,7 @@ int rebuild_membranes(iblb_ctx *c)
     CK(up(c->d_adj_start, start.data(), sizeof(int) * (N + 1)));
     CK(up(c->d_adj, adj.data(), sizeof(int) * adj.size()));
     CK(up(c->d_ring, ring.data(), sizeof(int4) * ring.size()));
+    CK(up(c->d_ring8, ring8.data(), sizeof(int4) * ring8.size()));
     if (elastic)
         CK(up(c->d_fref, fref.data(), sizeof(float4) * fref.size()));
     {   // each droplet's pending volume correction (none for a new membrane)

@@ -232,12 +232,16 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
             ka3 = a.drops[d].ka * (1.0f / 3.0f);
         }
         const bool elastic = EL && (ks3 != 0.0f || ka3 != 0.0f);
-        const int e0 = a.adj_start[j], e1 = a.adj_start[j + 1];
-        for (int eb = e0 + l; eb < e1; eb += 2 * NL) {
+        // the node's first RING8 faces at a fixed stride (lane l: entries l
+        // and l + 4), further ones (a face count above RING8) from the list
+        const int4 f0 = a.ring8[(int64_t)RING8 * j + l], f1 = a.ring8[(int64_t)RING8 * j + l + NL];
+        const int nfaces = f0.w;
+        const int e0 = nfaces > RING8 ? a.adj_start[j] : 0;
+        for (int eb = l; eb < nfaces; eb += 2 * NL) {
             // two faces per pass, every load issued before the arithmetic
-            const bool two = eb + NL < e1;
-            const int4 en0 = a.ring[eb];
-            const int4 en1 = two ? a.ring[eb + NL] : en0;
+            const bool two = eb + NL < nfaces;
+            const int4 en0 = eb < RING8 ? f0 : a.ring[e0 + eb];
+            const int4 en1 = eb + NL < RING8 ? f1 : (two ? a.ring[e0 + eb + NL] : en0);
             const double a0x = a.qx[en0.x], a0y = a.qy[en0.x], a0z = a.qz[en0.x];
             const double b0x = a.qx[en0.y], b0y = a.qy[en0.y], b0z = a.qz[en0.y];
             const double a1x = a.qx[en1.x], a1y = a.qy[en1.x], a1z = a.qz[en1.x];

@@ -21,6 +21,7 @@ constexpr int RED_FACES = 2048;    // faces per chunk of the observation reducti
 constexpr int RED_NODES = 1024;    // nodes per chunk of the observation reductions
 constexpr int VC_ITEMS = 128;      // faces (and nodes) per chunk of the volume correction
 constexpr int NRED = 8;            // partial sums per chunk (see reduce.cu)
+constexpr int RING8 = 8;           // face entries per node kept at a fixed stride
 
 // device status bits (Arrays::status[4 * d + 0])
 constexpr int ST_NAN = 1;          // NaN / Inf in a node velocity or position
@@ -121,6 +122,9 @@ struct Arrays {
     const int *adj;                // (face << 2) | corner, faces in increasing order
     const int4 *ring;              // per entry of adj: the face's other corners (a, b), counter-
                                    // clockwise after the node, and (face << 2) | corner
+    const int4 *ring8;             // RING8 entries per node: its first RING8 entries of ring, with
+                                   // the node's face count in w (unused entries a = -1), so that
+                                   // the force kernel needs no adj_start lookup first
     NodeRec *rec;                  // total_nodes
     // in/out
     int *col_cnt;                  // crossings per column

@@ -151,6 +151,37 @@ def test_forces_and_spread_parity(theta, lam):
     assert np.all(F_g[F_o == 0] == 0)
 
 
+def _bipyramid(n, R, h, center):
+    """Closed mesh: an n-gon equator of radius R and two apexes at +-h; each
+    apex belongs to n faces (faces counter-clockwise seen from outside)."""
+    ang = 2 * np.pi * np.arange(n) / n
+    eq = np.stack([R * np.cos(ang), R * np.sin(ang), np.zeros(n)], axis=1)
+    xyz = np.vstack([eq, [[0.0, 0.0, h]], [[0.0, 0.0, -h]]]) + np.asarray(center)
+    top, bot = n, n + 1
+    tri = [[i, (i + 1) % n, top] for i in range(n)] + [[(i + 1) % n, i, bot] for i in range(n)]
+    return xyz, np.asarray(tri, np.int32)
+
+
+def test_forces_parity_high_valence_nodes():
+    """Nodes with more incident faces than the force kernel keeps at a fixed
+    stride (12 > 8 at each apex of a 12-gon bipyramid) take the rest from the
+    node's face list: forces and spread as the oracle's."""
+    xyz, tri = _bipyramid(12, 5.0, 4.0, (16.2, 15.7, 0.5 + 4.0 + 2.3))
+    xyz = I.jitter_nodes(xyz, 4, 0.1)
+    kw = dict(nx=32, ny=30, nz=24, tau=0.9, sigma=0.02, theta=70.0, xi=2.0, mesh=(xyz, tri))
+    g, s = pair(**kw)
+    try:
+        iblb.iblb_compute_forces(g)
+        phi_g = iblb.iblb_get_node_forces(g, 0)
+        F_g = iblb.iblb_get_force_density(g, 0)
+    finally:
+        iblb.iblb_destroy(g)
+    phi_o, _, _, _ = O.membrane_forces(s.p, xyz, tri)
+    F_o = O.spread(s.p, xyz, phi_o)
+    assert rel_l2(phi_g, phi_o) < 2e-6
+    assert rel_l2(F_g, F_o) < 2e-6
+
+
 # ------------------------------------- elastic membrane (Skalak, Sec. II B framework)
 def test_elastic_membrane_forces_parity():
     # the reference is the mesh given at set-up; the nodes are then moved to a
