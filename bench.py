@@ -23,7 +23,6 @@ import json
 import math
 import os
 import platform
-import re
 import statistics
 import subprocess
 import sys
@@ -78,16 +77,15 @@ def lb_source_sha():
 
 def ncu_traffic(storage):
     """DRAM bytes per launch of the stream-collide kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", f"lb_kernel_{storage}_statics128.md")
+    ncu capture (profiles/traffic.json), if it was taken on the current
+    kernel source; None otherwise."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    txt = open(p).read()
-    m = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
-    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != lb_source_sha():
+    e = json.load(open(p)).get("lb_kernel", {}).get(storage)
+    if not e or e.get("source_sha") != lb_source_sha():
         return None
-    return float(t.group(1))
+    return float(e["traffic_bytes_per_launch"])
 
 
 class Clocks:

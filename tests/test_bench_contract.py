@@ -26,3 +26,20 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_traffic_file_is_read_only_for_the_current_kernel_source():
+    """profiles/traffic.json holds read + write bytes per captured launch;
+    bench.py reports them only while the stream-collide source still hashes
+    to the capture's source_sha."""
+    sys.path.insert(0, ROOT)
+    import bench
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for st, e in d["lb_kernel"].items():
+        assert e["traffic_bytes_per_launch"] == e["read_bytes"] + e["write_bytes"]
+        got = bench.ncu_traffic(st)
+        if e["source_sha"] == bench.lb_source_sha():
+            assert got == e["traffic_bytes_per_launch"]
+        else:
+            assert got is None
+    assert bench.ncu_traffic("no-such-storage") is None
