@@ -493,6 +493,8 @@ int rebuild_membranes(iblb_ctx *c)
         D.red_nchunks = nc;
         D.V0 = M.V0;
         D.R0 = cbrt(3.0 * M.V0 / (4.0 * M_PI));
+        D.inv_n = D.nnodes ? 1.0 / D.nnodes : 0.0;
+        D.inv6V0 = M.V0 > 0.0 ? 1.0 / (6.0 * M.V0) : 0.0;
         N += D.nnodes;
         NT += D.ntri;
         chunks += nc;

@@ -727,29 +727,63 @@ __device__ __forceinline__ void block_sum(double *v)
         v[k] = res[k];
 }
 
+// (V/V0)^(-1/3) for s = V/V0 given as e = s - 1: the binomial series
+// 1 - e/3 + 2e^2/9 - 14e^3/81 + 35e^4/243 - 91e^5/729 when |e| <= 2^-10
+// (the first omitted term is below 1e-19, so the sum is within about one
+// unit in the last place of the cube root), else cbrt(V0/V).  A step's
+// volume drift is many orders below 2^-10; the series costs six dependent
+// FP64 operations where the division and cube root cost about fifteen
+// times as long on this GPU.
+__device__ __forceinline__ double inv_cbrt_ratio(double e, double V0, double V)
+{
+    if (fabs(e) > 0x1p-10)
+        return cbrt(V0 / V);
+    double p = -91.0 / 729.0;
+    p = fma(p, e, 35.0 / 243.0);
+    p = fma(p, e, -14.0 / 81.0);
+    p = fma(p, e, 2.0 / 9.0);
+    p = fma(p, e, -1.0 / 3.0);
+    return fma(p, e, 1.0);
+}
+
 // NT: the block size (at least VC_RB; threads beyond the chunk add zeros).
-template <int NT>
+// WAIT: the launch follows the advection with programmatic dependent
+// launch; the droplet lookup and the face corners (topology, which no step
+// writes) are read before waiting for it, the positions after.
+template <int NT, bool WAIT>
 __device__ void vc_chunk(const Arrays &a, int c)
 {
     static_assert(NT >= VC_RB, "a chunk needs VC_RB threads");
     __shared__ int s_last;
     const int d = find_drop_chunk(a.drops, a.ndrops, c);
     const Drop &D = a.drops[d];
-    if (D.nnodes == 0 || !D.volcorr)
-        return;                                        // block-uniform
+    if (D.nnodes == 0 || !D.volcorr) {                 // block-uniform
+        if (WAIT)
+            griddep_wait();    // every block waits: the next launch may then read the advected positions
+        return;
+    }
     const int k = c - D.red_chunk0;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
     const bool mine = threadIdx.x < VC_RB;
     const int t = k * VC_RB + threadIdx.x;
-    if (mine && t < D.ntri) {
+    const bool face = mine && t < D.ntri, node = mine && t < D.nnodes;
+    int ia = 0, ib = 0, ic = 0;
+    if (face) {
         const int *f = a.tri + 3 * ((int64_t)D.tri0 + t);
-        const int ia = f[0], ib = f[1], ic = f[2];
+        ia = f[0];
+        ib = f[1];
+        ic = f[2];
+    }
+    if (WAIT)
+        griddep_wait();
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (face) {   // 6 x the signed volume of the tetrahedron (0, q_a, q_b, q_c): q_a . (q_b x q_c)
         const double ax = a.qx[ia], ay = a.qy[ia], az = a.qz[ia];
         const double bx = a.qx[ib], by = a.qy[ib], bz = a.qz[ib];
         const double cx = a.qx[ic], cy = a.qy[ic], cz = a.qz[ic];
-        v[0] = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
+        const double x = fma(by, cz, -(bz * cy)), y = fma(bz, cx, -(bx * cz)), z = fma(bx, cy, -(by * cx));
+        v[0] = fma(ax, x, fma(ay, y, az * z));
     }
-    if (mine && t < D.nnodes) {
+    if (node) {
         const int j = D.node0 + t;
         v[1] = a.qx[j];
         v[2] = a.qy[j];
@@ -776,16 +810,19 @@ __device__ void vc_chunk(const Arrays &a, int c)
             fold[w] = x;
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        const double V = fold[0] / 6.0;
+    if (s_last && threadIdx.x < 4) {
+        // lane 0: V = fold0 / 6 and k = (V0/V)^(1/3); lanes 1-3: the centroid
         double *o = a.red_out + (int64_t)NRED * d;
-        o[0] = cbrt(D.V0 / V);
-        o[1] = fold[1] / D.nnodes;
-        o[2] = fold[2] / D.nnodes;
-        o[3] = fold[3] / D.nnodes;
-        o[4] = V;
-        o[5] = 1.0;         // applied wherever the positions are read next
-        a.vc_done[d] = 0;
+        const double f = fold[threadIdx.x];
+        if (threadIdx.x == 0) {
+            const double V = f * (1.0 / 6.0);
+            o[0] = inv_cbrt_ratio(fma(f, D.inv6V0, -1.0), D.V0, V);
+            o[4] = V;
+            o[5] = 1.0;     // applied wherever the positions are read next
+            a.vc_done[d] = 0;
+        } else {
+            o[threadIdx.x] = f * D.inv_n;
+        }
     }
     __syncthreads();
 }
@@ -860,8 +897,7 @@ __global__ void __launch_bounds__(IB_THREADS) interp_advect_kernel(Arrays a)
 // apply from then on.
 __global__ void __launch_bounds__(VC_RB) volume_correction_kernel(Arrays a)
 {
-    griddep_wait();
-    vc_chunk<VC_RB>(a, blockIdx.x);
+    vc_chunk<VC_RB, true>(a, blockIdx.x);
 }
 
 // a.p* = the positions as read (the pending correction applied)
@@ -918,7 +954,7 @@ __global__ void __launch_bounds__(IB_THREADS) ib_back_kernel(Arrays a, int n_chu
     if (!grid_barrier(a, sense))
         return;
     for (int c = blockIdx.x; c < n_chunks; c += gridDim.x)
-        vc_chunk<IB_THREADS>(a, c);
+        vc_chunk<IB_THREADS, false>(a, c);
 }
 
 int g_sm_count = 0;

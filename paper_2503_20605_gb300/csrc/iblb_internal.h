@@ -56,6 +56,7 @@ struct Drop {
     float ks, ka;                  // Skalak moduli of an elastic membrane (0, 0: a droplet)
     int n, m, wetting, vartau, volcorr;
     double V0, R0;
+    double inv_n, inv6V0;          // 1 / nnodes and 1 / (6 V0): the volume correction's fold multiplies
 };
 
 // Record written per node by the force kernel and read by the spread and
