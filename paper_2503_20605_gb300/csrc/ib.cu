@@ -801,10 +801,25 @@ __device__ void vc_chunk(const Arrays &a, int c)
     __syncthreads();
     __shared__ double fold[4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (s_last && w < 4) {  // warp q folds value q of every chunk of the droplet
+    if (s_last && w < 4) {
+        // warp q folds value q of every chunk of the droplet: lane l adds
+        // chunks l, l + 32, ... in that order.  Thread 0's acquire and the
+        // block barrier order these loads after every chunk's release; they
+        // read L2 (not the non-coherent L1), all of a pass issued at once.
+        constexpr int U = 8;
+        const double *pp = a.red_part + (int64_t)NRED * D.red_chunk0 + w;
         double x = 0.0;
-        for (int i = lane; i < D.red_nchunks; i += 32)
-            x += ((const volatile double *)(a.red_part + (int64_t)NRED * (D.red_chunk0 + i)))[w];
+        for (int i0 = lane; i0 < D.red_nchunks; i0 += 32 * U) {
+            double t[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + 32 * u;
+                t[u] = i < D.red_nchunks ? __ldcg(pp + (int64_t)NRED * i) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                x += t[u];
+        }
         x = warp_sum(x);
         if (lane == 0)
             fold[w] = x;
