@@ -434,6 +434,18 @@ int download_nodes(iblb_ctx *c)
     return IBLB_OK;
 }
 
+// Node positions as FP32 pairs: hi = q rounded to FP32, lo = q - hi (exact
+// in FP64) rounded to FP32; the advection writes the same split on the
+// device.
+void split_positions(const double *x, const double *y, const double *z, int64_t n, float4 *hi, float4 *lo)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        const float hx = (float)x[j], hy = (float)y[j], hz = (float)z[j];
+        hi[j] = make_float4(hx, hy, hz, 0.0f);
+        lo[j] = make_float4((float)(x[j] - (double)hx), (float)(y[j] - (double)hy), (float)(z[j] - (double)hz), 0.0f);
+    }
+}
+
 void free_membrane_arrays(iblb_ctx *c)
 {
     dfree(c->A.qx);
@@ -443,6 +455,9 @@ void free_membrane_arrays(iblb_ctx *c)
     dfree(c->A.py);
     dfree(c->A.pz);
     c->A.px = c->A.py = c->A.pz = nullptr;
+    dfree(c->A.qh);
+    dfree(c->A.ql);
+    c->A.qh = c->A.ql = nullptr;
     dfree(c->A.node_drop);
     dfree(c->d_tri);
     dfree(c->A.face_drop);
@@ -551,6 +566,8 @@ int rebuild_membranes(iblb_ctx *c)
     CK(dalloc(&c->A.px, N));
     CK(dalloc(&c->A.py, N));
     CK(dalloc(&c->A.pz, N));
+    CK(dalloc(&c->A.qh, N));
+    CK(dalloc(&c->A.ql, N));
     CK(dalloc(&c->A.node_drop, N));
     CK(dalloc(&c->d_tri, 3 * (size_t)NT));
     CK(dalloc(&c->A.face_drop, NT));
@@ -605,6 +622,10 @@ int rebuild_membranes(iblb_ctx *c)
     CK(up(c->A.qx, x.data(), sizeof(double) * N));
     CK(up(c->A.qy, y.data(), sizeof(double) * N));
     CK(up(c->A.qz, z.data(), sizeof(double) * N));
+    std::vector<float4> qh(N), ql(N);
+    split_positions(x.data(), y.data(), z.data(), N, qh.data(), ql.data());
+    CK(up(c->A.qh, qh.data(), sizeof(float4) * N));
+    CK(up(c->A.ql, ql.data(), sizeof(float4) * N));
     CK(up(c->A.node_drop, nd.data(), sizeof(int) * N));
     CK(up(c->d_tri, tri.data(), sizeof(int) * tri.size()));
     CK(up(c->A.face_drop, fd.data(), sizeof(int) * NT));
@@ -1072,6 +1093,10 @@ int iblb_set_nodes(iblb_ctx *c, int k, const double *xyz)
     CK(cudaMemcpyAsync(c->A.qx + D.node0, x.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->A.qy + D.node0, y.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->A.qz + D.node0, z.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
+    std::vector<float4> qh(D.nnodes), ql(D.nnodes);
+    split_positions(x.data(), y.data(), z.data(), D.nnodes, qh.data(), ql.data());
+    CK(cudaMemcpyAsync(c->A.qh + D.node0, qh.data(), sizeof(float4) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->A.ql + D.node0, ql.data(), sizeof(float4) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
     // the given positions are final: no volume correction pending on them
     const double none = 0.0;
     CK(cudaMemcpyAsync(c->A.red_out + (int64_t)NRED * k + 5, &none, sizeof(double), cudaMemcpyHostToDevice,

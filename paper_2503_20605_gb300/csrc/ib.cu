@@ -89,6 +89,34 @@ __device__ __forceinline__ double corr1(double q, double c, double k)
     return __dadd_rn(c, __dmul_rn(__dsub_rn(q, c), k));
 }
 
+// x rounded to nearest (ties to even) FP32 by integer operations on its
+// bits: equal to the FP64 -> FP32 conversion for |x| in FP32's normal range,
+// zero, infinities and NaN; smaller magnitudes give a signed zero.  The
+// conversion instruction costs about as much issue as two FP64 additions on
+// this GPU, the integer operations a small fraction of one.
+__device__ __forceinline__ float dtof_rn(double x)
+{
+    const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+    const unsigned s = h & 0x80000000u;
+    const int e = (int)((h >> 20) & 0x7ffu) - 896;          // FP32 biased exponent
+    const unsigned m = ((h & 0xfffffu) << 3) | (l >> 29);    // the top 23 fraction bits
+    const unsigned r = l & 0x1fffffffu;                      // the 29 bits below them
+    unsigned b = ((unsigned)e << 23) + m;
+    b += (r > 0x10000000u || (r == 0x10000000u && (m & 1u))) ? 1u : 0u;   // a carry moves into the exponent
+    if (e <= 0)
+        b = 0u;
+    if (e >= 255)
+        b = ((h & 0x7ff00000u) == 0x7ff00000u && ((h & 0xfffffu) | l)) ? 0x7fc00000u : 0x7f800000u;
+    return __uint_as_float(s | b);
+}
+
+// One coordinate of q_a - q_j from the FP32 pairs of the two positions: the
+// hi parts of nearby positions differ exactly, the lo parts carry the rest.
+__device__ __forceinline__ float rel_coord(float ah, float al, float jh, float jl)
+{
+    return __fadd_rn(__fsub_rn(ah, jh), __fsub_rn(al, jl));
+}
+
 // One incident face (j, a, b) of a node: relative corner vectors r_a, r_b
 // (already dilated by a pending volume correction), accumulated into the
 // node's area gradient g, normal sum n, area sum chi and elastic force e.
@@ -225,7 +253,8 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
         qx0 = a.qx[j];
         qy0 = a.qy[j];
         qz0 = a.qz[j];
-        const float kf = cr.on ? (float)cr.k : 1.0f;
+        const float4 jh = a.qh[j], jl = a.ql[j];
+        const float kf = cr.on ? dtof_rn(cr.k) : 1.0f;
         float ks3 = 0.0f, ka3 = 0.0f;
         if (EL) {
             ks3 = a.drops[d].ks * (1.0f / 3.0f);
@@ -242,17 +271,18 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
             const bool two = eb + NL < nfaces;
             const int4 en0 = eb < RING8 ? f0 : a.ring[e0 + eb];
             const int4 en1 = eb + NL < RING8 ? f1 : (two ? a.ring[e0 + eb + NL] : en0);
-            const double a0x = a.qx[en0.x], a0y = a.qy[en0.x], a0z = a.qz[en0.x];
-            const double b0x = a.qx[en0.y], b0y = a.qy[en0.y], b0z = a.qz[en0.y];
-            const double a1x = a.qx[en1.x], a1y = a.qy[en1.x], a1z = a.qz[en1.x];
-            const double b1x = a.qx[en1.y], b1y = a.qy[en1.y], b1z = a.qz[en1.y];
-            face_terms<EL>(a, en0, (float)(a0x - qx0) * kf, (float)(a0y - qy0) * kf, (float)(a0z - qz0) * kf,
-                           (float)(b0x - qx0) * kf, (float)(b0y - qy0) * kf, (float)(b0z - qz0) * kf, elastic, ks3,
-                           ka3, gx, gy, gz, nx, ny, nz, chi, ex, ey, ez);
+            const float4 a0h = a.qh[en0.x], a0l = a.ql[en0.x], b0h = a.qh[en0.y], b0l = a.ql[en0.y];
+            const float4 a1h = a.qh[en1.x], a1l = a.ql[en1.x], b1h = a.qh[en1.y], b1l = a.ql[en1.y];
+            face_terms<EL>(a, en0, rel_coord(a0h.x, a0l.x, jh.x, jl.x) * kf, rel_coord(a0h.y, a0l.y, jh.y, jl.y) * kf,
+                           rel_coord(a0h.z, a0l.z, jh.z, jl.z) * kf, rel_coord(b0h.x, b0l.x, jh.x, jl.x) * kf,
+                           rel_coord(b0h.y, b0l.y, jh.y, jl.y) * kf, rel_coord(b0h.z, b0l.z, jh.z, jl.z) * kf,
+                           elastic, ks3, ka3, gx, gy, gz, nx, ny, nz, chi, ex, ey, ez);
             if (two)
-                face_terms<EL>(a, en1, (float)(a1x - qx0) * kf, (float)(a1y - qy0) * kf, (float)(a1z - qz0) * kf,
-                               (float)(b1x - qx0) * kf, (float)(b1y - qy0) * kf, (float)(b1z - qz0) * kf, elastic,
-                               ks3, ka3, gx, gy, gz, nx, ny, nz, chi, ex, ey, ez);
+                face_terms<EL>(a, en1, rel_coord(a1h.x, a1l.x, jh.x, jl.x) * kf,
+                               rel_coord(a1h.y, a1l.y, jh.y, jl.y) * kf, rel_coord(a1h.z, a1l.z, jh.z, jl.z) * kf,
+                               rel_coord(b1h.x, b1l.x, jh.x, jl.x) * kf, rel_coord(b1h.y, b1l.y, jh.y, jl.y) * kf,
+                               rel_coord(b1h.z, b1l.z, jh.z, jl.z) * kf, elastic, ks3, ka3, gx, gy, gz, nx, ny, nz,
+                               chi, ex, ey, ez);
         }
     }
     for (int o = NL / 2; o >= 1; o >>= 1) {
@@ -285,7 +315,7 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
     float w[4] = {0.f, 0.f, 0.f, 0.f};
     if (valid && l < 3 && sane) {
         const double fb = floor(q);
-        const float f = (float)(q - fb);
+        const float f = dtof_rn(q - fb);
         const int n = ax == 0 ? D.nx : (ax == 1 ? D.ny : D.nzf);
         if (ax < 2) {
             b = wrapi((int)fb % n, n);
@@ -336,7 +366,7 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
                 pz += ez;
             }
             if (D.wetting) {
-                float h = (float)(qz - 0.5);
+                float h = dtof_rn(qz - 0.5);
                 if (h < D.hmin) {
                     h = D.hmin;
                     clamped = 1;
@@ -677,8 +707,13 @@ __device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
         else if (ax * ax + ay * ay + az * az > 0.25f)
             atomicOr(&a.status[4 * d], ST_JUMP);
     }
-    if (valid && l < 3)
-        qc[j] = q + (double)(l == 0 ? ax : (l == 1 ? ay : az));
+    if (valid && l < 3) {
+        const double qn = q + (double)(l == 0 ? ax : (l == 1 ? ay : az));
+        qc[j] = qn;
+        const float hi = dtof_rn(qn);
+        reinterpret_cast<float *>(a.qh + j)[l] = hi;
+        reinterpret_cast<float *>(a.ql + j)[l] = dtof_rn(qn - (double)hi);
+    }
 }
 
 __device__ __forceinline__ int find_drop_chunk(const Drop *D, int n, int c)

@@ -117,6 +117,9 @@ struct Arrays {
     double *qx, *qy, *qz;          // node positions (FP64) as advected; the volume correction of the
                                    // last step, when pending, is applied on reading (see red_out)
     double *px, *py, *pz;          // corrected positions of the step, written by the force kernel
+    float4 *qh, *ql;               // q split into FP32 pairs (x, y, z, 0): qh = q rounded to FP32,
+                                   // ql = q - qh rounded to FP32; written with q, read by the force
+                                   // kernel for its relative vectors
     int *node_drop;                // droplet of each node
     const int *tri;                // 3 * total_tri global node indices
     const int *adj_start;          // total_nodes + 1
