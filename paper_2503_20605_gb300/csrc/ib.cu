@@ -37,8 +37,10 @@ namespace {
 
 constexpr int IB_THREADS = 256;  // block size of every membrane kernel
 constexpr int SPREAD_PARTS = 4;  // parts of a tile's sorted node list, summed separately per cell
-constexpr int SP_THREADS = 256;  // block size of the separate spread kernel and its blocks per SM
-constexpr int SP_PER_SM = 4;     // (128-thread blocks, six per SM, measured slower: 15.2 against 13.0 us)
+constexpr int SP_THREADS = 128;  // block size of the separate spread kernel and its blocks per SM: 1216
+constexpr int SP_PER_SM = 8;     // blocks, so that a droplet's band (about 1200 tiles at R = 24) takes
+                                 // one round (256-thread blocks, four per SM, took two: 2.6 us more)
+constexpr int SPREAD_STAGE = 256;  // records of a tile staged in shared memory at a time
 constexpr int VC_RB = VC_ITEMS;  // threads per volume-correction chunk
 constexpr long long BARRIER_CYCLES = 4000000000LL;      // ~2 s: bounded grid-barrier wait
 
@@ -447,14 +449,15 @@ __device__ __forceinline__ int per_off(int X, int b, int n)
 }
 
 // Shared memory of one spread block: the keys (node indices) of a tile's
-// nodes and, in increasing node order, one 16-float record per node: its
-// kernel weights at the tile's four cells of each axis, x at 0..3, y at
-// 4..7, z at 8..11 (0 where the cell lies outside the node's support), and
-// its force at 12..14.
+// nodes in arrival order and, for a window of SPREAD_STAGE consecutive ranks
+// of the keys in increasing order, one 16-float record per node: its kernel
+// weights at the tile's four cells of each axis, x at 0..3, y at 4..7, z at
+// 8..11 (0 where the cell lies outside the node's support), and its force at
+// 12..14.
 struct SpreadSmem {
-    __align__(16) int node[SPREAD_CAP];
-    __align__(16) float rec[SPREAD_CAP][16];
-    float part[3][SPREAD_PARTS][TILE_CELLS];
+    __align__(16) int node[TILE_CAP];
+    __align__(16) float rec[SPREAD_STAGE][16];
+    __align__(16) float part[3][SPREAD_PARTS][TILE_CELLS];
     int last;
 };
 
@@ -525,17 +528,21 @@ __device__ void zero_left_tiles(const Arrays &a, uint32_t gen, int cur, int bid,
     }
 }
 
-// Band tiles bid, bid + nb, ...: the tile's nodes are staged in parallel and
-// sorted by node index; every cell adds SPREAD_PARTS consecutive parts of the
-// sorted list separately (NT / 64 threads per cell, each taking one or more
-// parts) and the parts are summed in a fixed order, so every cell's force is
-// the same for any launch shape and block size.  The tile's counter returns
-// to zero for the next step.
+// Band tiles bid, bid + nb, ...: the tile's node indices are staged and
+// ranked (rank = how many of the tile's nodes have a smaller index); the
+// records of ranks w0 .. w0 + SPREAD_STAGE - 1 are placed in shared memory
+// in rank order, one window after the other.  Every cell adds SPREAD_PARTS
+// consecutive parts of the sorted list separately (a thread per part and
+// x-row of four cells, its sums carried from window to window) and the parts
+// are summed in a fixed order, so every cell's force is the same for any
+// launch shape, block size and window size.  The tile's counter returns to
+// zero for the next step.
 template <int NT>
 __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, int nb, SpreadSmem &sm)
 {
-    constexpr int TPC = NT / TILE_CELLS;           // threads per cell
-    constexpr int H = SPREAD_CAP / NT;             // staged nodes per thread, at most
+    static_assert(NT >= 16 * SPREAD_PARTS && NT >= TILE_CELLS, "a thread per part and x-row, and per cell");
+    static_assert(TILE_CAP % NT == 0, "whole key passes");
+    constexpr int HK = TILE_CAP / NT;              // a tile's nodes per thread, at most
     const int tid = threadIdx.x;
     const int nact = min(a.n_active[cur], a.active_cap);
     const int2 *list = a.active + (int64_t)cur * a.active_cap;
@@ -547,31 +554,14 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
         const int X0 = 4 * (te.y & 2047), Y0 = 4 * ((te.y >> 11) & 2047), Z0 = 4 * (te.y >> 22);
         const int64_t e0 = T * TILE_CAP;
         const int cnt = min(a.bin_cnt[T], TILE_CAP);     // overflow was flagged by the force kernel
-        // stage: every listed node's tile-local weights and force, kept in
-        // registers (at most H nodes per thread)
-        static_assert(SPREAD_CAP == H * NT, "whole staging passes");
-        float4 v[H][4];
-        int key[H];
+        int key[HK];
 #pragma unroll
-        for (int h = 0; h < H; ++h) {
+        for (int h = 0; h < HK; ++h) {
             const int e = tid + h * NT;
             key[h] = 0x7fffffff;
             if (e < cnt) {
-                const int j = a.tile_list[e0 + e];
-                const NodeRec &r = a.rec[j];
-                key[h] = j;
-                sm.node[e] = j;
-                float wl[16];
-                tile_weights(X0, r.bx, D.nx, true, r.wx, wl);
-                tile_weights(Y0, r.by, D.ny, true, r.wy, wl + 4);
-                tile_weights(Z0, r.bz, D.nzf, !D.walls, r.wz, wl + 8);
-                wl[12] = r.phi[0];
-                wl[13] = r.phi[1];
-                wl[14] = r.phi[2];
-                wl[15] = 0.0f;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    v[h][q] = make_float4(wl[4 * q], wl[4 * q + 1], wl[4 * q + 2], wl[4 * q + 3]);
+                key[h] = a.tile_list[e0 + e];
+                sm.node[e] = key[h];
             }
         }
         if (tid < ((cnt + 3) & ~3) - cnt)
@@ -579,45 +569,75 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
         __syncthreads();
         if (tid == 0)
             a.bin_cnt[T] = 0;                            // empty for the next step
-        // rank sort by node index: each record goes to the slot of its rank,
-        // so that contributions are added in increasing j
+        int rank[HK];
         const int4 *keys4 = reinterpret_cast<const int4 *>(sm.node);
 #pragma unroll
-        for (int h = 0; h < H; ++h) {
+        for (int h = 0; h < HK; ++h) {
+            rank[h] = -1;
             if (tid + h * NT < cnt) {
-                int rank = 0;
+                int r = 0;
                 for (int k = 0; k < (cnt + 3) >> 2; ++k) {
                     const int4 kv = keys4[k];
-                    rank += (kv.x < key[h]) + (kv.y < key[h]) + (kv.z < key[h]) + (kv.w < key[h]);
+                    r += (kv.x < key[h]) + (kv.y < key[h]) + (kv.z < key[h]) + (kv.w < key[h]);
                 }
-                float4 *dst = reinterpret_cast<float4 *>(sm.rec[rank]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    dst[q] = v[h][q];
+                rank[h] = r;
             }
+        }
+        // part sums: thread t < 16 SPREAD_PARTS takes part t / 16 of the
+        // four cells of x-row t % 16 (y = row & 3, z = row >> 2 in the tile),
+        // one load of the x weights serving the four cells
+        const bool summer = tid < 16 * SPREAD_PARTS;
+        const int part = (tid >> 4) & (SPREAD_PARTS - 1), row = tid & 15, ry = row & 3, rz = row >> 2;
+        const int k0 = (int)(((int64_t)cnt * part) / SPREAD_PARTS);
+        const int k1 = (int)(((int64_t)cnt * (part + 1)) / SPREAD_PARTS);
+        float fx[4] = {0.f, 0.f, 0.f, 0.f}, fy[4] = {0.f, 0.f, 0.f, 0.f}, fz[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int w0 = 0; w0 < cnt; w0 += SPREAD_STAGE) {
+            if (w0 > 0)
+                __syncthreads();                         // the previous window's sums are done
+#pragma unroll
+            for (int h = 0; h < HK; ++h) {
+                if (rank[h] >= w0 && rank[h] < w0 + SPREAD_STAGE) {
+                    const NodeRec &r = a.rec[key[h]];
+                    float wl[16];
+                    tile_weights(X0, r.bx, D.nx, true, r.wx, wl);
+                    tile_weights(Y0, r.by, D.ny, true, r.wy, wl + 4);
+                    tile_weights(Z0, r.bz, D.nzf, !D.walls, r.wz, wl + 8);
+                    wl[12] = r.phi[0];
+                    wl[13] = r.phi[1];
+                    wl[14] = r.phi[2];
+                    wl[15] = 0.0f;
+                    float4 *dst = reinterpret_cast<float4 *>(sm.rec[rank[h] - w0]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        dst[q] = make_float4(wl[4 * q], wl[4 * q + 1], wl[4 * q + 2], wl[4 * q + 3]);
+                }
+            }
+            __syncthreads();
+            if (summer) {
+                const int ka = max(k0, w0), kb = min(k1, w0 + SPREAD_STAGE);
+                for (int k = ka; k < kb; ++k) {
+                    const float *r = sm.rec[k - w0];
+                    const float4 wx = *reinterpret_cast<const float4 *>(r);
+                    const float wy = r[4 + ry], wz = r[8 + rz];
+                    const float4 ph = *reinterpret_cast<const float4 *>(r + 12);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float w = ((&wx.x)[c] * wy) * wz;
+                        fx[c] = fmaf(ph.x, w, fx[c]);
+                        fy[c] = fmaf(ph.y, w, fy[c]);
+                        fz[c] = fmaf(ph.z, w, fz[c]);
+                    }
+                }
+            }
+        }
+        if (summer) {
+            *reinterpret_cast<float4 *>(&sm.part[0][part][4 * row]) = make_float4(fx[0], fx[1], fx[2], fx[3]);
+            *reinterpret_cast<float4 *>(&sm.part[1][part][4 * row]) = make_float4(fy[0], fy[1], fy[2], fy[3]);
+            *reinterpret_cast<float4 *>(&sm.part[2][part][4 * row]) = make_float4(fz[0], fz[1], fz[2], fz[3]);
         }
         __syncthreads();
         const int cell = tid & (TILE_CELLS - 1), lane_part = tid / TILE_CELLS;
-        const int cx = cell & 3, cy = (cell >> 2) & 3, cz = cell >> 4;
-        const int X = X0 + cx, Y = Y0 + cy, Z = Z0 + cz;
-#pragma unroll
-        for (int part = lane_part; part < SPREAD_PARTS; part += TPC) {
-            const int k0 = (int)(((int64_t)cnt * part) / SPREAD_PARTS);
-            const int k1 = (int)(((int64_t)cnt * (part + 1)) / SPREAD_PARTS);
-            float fx = 0.f, fy = 0.f, fz = 0.f;
-            for (int k = k0; k < k1; ++k) {
-                const float *r = sm.rec[k];
-                const float w = (r[cx] * r[4 + cy]) * r[8 + cz];
-                const float4 ph = *reinterpret_cast<const float4 *>(r + 12);
-                fx = fmaf(ph.x, w, fx);
-                fy = fmaf(ph.y, w, fy);
-                fz = fmaf(ph.z, w, fz);
-            }
-            sm.part[0][part][cell] = fx;
-            sm.part[1][part][cell] = fy;
-            sm.part[2][part][cell] = fz;
-        }
-        __syncthreads();
+        const int X = X0 + (cell & 3), Y = Y0 + ((cell >> 2) & 3), Z = Z0 + (cell >> 4);
         if (lane_part == 0 && X < D.nx && Y < D.ny && Z < D.nzf) {
             float sx = sm.part[0][0][cell], sy = sm.part[1][0][cell], sz = sm.part[2][0][cell];
             for (int p = 1; p < SPREAD_PARTS; ++p) {

@@ -16,7 +16,6 @@ constexpr int TILE = 4;            // band tiles are 4x4x4 fluid cells
 constexpr int TILE_CELLS = 64;
 constexpr int MAXC = 16;           // ray crossings kept per lattice column
 constexpr int TILE_CAP = 512;      // nodes whose kernel support may touch one tile
-constexpr int SPREAD_CAP = TILE_CAP;  // nodes the spread kernel stages per tile
 constexpr int RED_FACES = 2048;    // faces per chunk of the observation reductions
 constexpr int RED_NODES = 1024;    // nodes per chunk of the observation reductions
 constexpr int VC_ITEMS = 128;      // faces (and nodes) per chunk of the volume correction

@@ -151,6 +151,35 @@ def test_forces_and_spread_parity(theta, lam):
     assert np.all(F_g[F_o == 0] == 0)
 
 
+def test_spread_parity_dense_mesh_several_windows():
+    """An L4 icosphere of radius 6 (2562 nodes) puts up to about 435 nodes'
+    supports on one 4^3 tile, 27 tiles above 256: the spread stages such a
+    tile's records in two windows of sorted ranks and carries its part sums
+    across them.  Forces and force density agree with the oracle, and the
+    cooperative (256-thread) and separate (128-thread) spread kernels give
+    the same bits."""
+    xyz, tri = I.icosphere(4, 6.0, (16.3, 15.6, 0.5 + 6.0 + 1.1))
+    xyz = I.jitter_nodes(xyz, 4, 0.05)
+    kw = dict(nx=32, ny=30, nz=24, tau=0.9, sigma=0.02, theta=75.0, xi=2.0, mesh=(xyz, tri))
+    Fs = []
+    for fused in (0, 1):
+        g, s = pair(**kw)
+        try:
+            iblb.iblb_set_option(g, iblb.IBLB_OPT_FUSED_IB, fused)
+            iblb.iblb_compute_forces(g)
+            phi_g = iblb.iblb_get_node_forces(g, 0)
+            Fs.append(iblb.iblb_get_force_density(g, 0))
+            assert iblb.iblb_observe(g, 0)["status"] == 0
+        finally:
+            iblb.iblb_destroy(g)
+    phi_o, _, _, _ = O.membrane_forces(s.p, xyz, tri)
+    F_o = O.spread(s.p, xyz, phi_o)
+    assert rel_l2(phi_g, phi_o) < 2e-6
+    assert rel_l2(Fs[0], F_o) < 2e-6
+    assert np.all(Fs[0][F_o == 0] == 0)
+    assert np.array_equal(Fs[0], Fs[1])
+
+
 def _bipyramid(n, R, h, center):
     """Closed mesh: an n-gon equator of radius R and two apexes at +-h; each
     apex belongs to n faces (faces counter-clockwise seen from outside)."""
