@@ -673,22 +673,28 @@ __device__ void spread_finish(const Arrays &a, uint32_t gen, int cur, SpreadSmem
     }
 }
 
+// Interpolation and advection of the IB_THREADS / 16 nodes of one block
+// (base: the global index of its thread 0, a multiple of IB_THREADS).
 // 16 lanes per node: lane l covers support row (dy, dz) = (l & 3, l >> 2)
 // and the four cells of that row; partial sums meet in a fixed shuffle tree.
-__device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
+// The FP64 advection then runs on the block's first 3 IB_THREADS / 16
+// threads, one coordinate each, so that its FP64 operations fill whole
+// warps (on this GPU they issue at a small fraction of the FP32 rate); each
+// thread reads its (corrected) coordinate when the kernel starts.
+__device__ __forceinline__ void interp_block(const Arrays &a, int64_t base)
 {
+    constexpr int NPB = IB_THREADS / 16;
+    __shared__ float inc_s[3 * NPB];
+    const int64_t gid = base + threadIdx.x;
     const int j = (int)(gid >> 4), l = (int)(gid & 15);
     const bool valid = j < a.total_nodes;
+    const int jn = (int)(base >> 4) + (int)threadIdx.x / 3, an = (int)threadIdx.x % 3;
+    const bool adv = threadIdx.x < 3 * NPB && jn < a.total_nodes;
+    double q = 0.0;
+    if (adv)
+        q = (an == 0 ? a.px : (an == 1 ? a.py : a.pz))[jn];
     float ax = 0.f, ay = 0.f, az = 0.f;
     int d = 0;
-    // lane c < 3 advects coordinate c (one FP64 operation per lane, all
-    // three at once); its (corrected) position is read early: it does not
-    // depend on the record
-    const double *pc = l == 0 ? a.px : (l == 1 ? a.py : a.pz);
-    double *qc = l == 0 ? a.qx : (l == 1 ? a.qy : a.qz);
-    double q = 0.0;
-    if (valid && l < 3)
-        q = pc[j];
     if (valid) {
         d = a.ndrops == 1 ? 0 : a.node_drop[j];
         const NodeRec &r = a.rec[j];
@@ -726,13 +732,18 @@ __device__ __forceinline__ void interp_item(const Arrays &a, int64_t gid)
             atomicOr(&a.status[4 * d], ST_NAN);
         else if (ax * ax + ay * ay + az * az > 0.25f)
             atomicOr(&a.status[4 * d], ST_JUMP);
+        float *o = inc_s + 3 * (j - (int)(base >> 4));
+        o[0] = ax;
+        o[1] = ay;
+        o[2] = az;
     }
-    if (valid && l < 3) {
-        const double qn = q + (double)(l == 0 ? ax : (l == 1 ? ay : az));
-        qc[j] = qn;
+    __syncthreads();
+    if (adv) {
+        const double qn = q + (double)inc_s[threadIdx.x];
+        (an == 0 ? a.qx : (an == 1 ? a.qy : a.qz))[jn] = qn;
         const float hi = dtof_rn(qn);
-        reinterpret_cast<float *>(a.qh + j)[l] = hi;
-        reinterpret_cast<float *>(a.ql + j)[l] = dtof_rn(qn - (double)hi);
+        reinterpret_cast<float *>(a.qh + jn)[an] = hi;
+        reinterpret_cast<float *>(a.ql + jn)[an] = dtof_rn(qn - (double)hi);
     }
 }
 
@@ -810,6 +821,19 @@ __device__ void vc_chunk(const Arrays &a, int c)
 {
     static_assert(NT >= VC_RB, "a chunk needs VC_RB threads");
     __shared__ int s_last;
+    const bool mine = threadIdx.x < VC_RB, one = a.ndrops == 1;
+    int ia = 0, ib = 0, ic = 0;
+    bool face = false;
+    if (one) {      // one droplet: its faces and chunks start at 0, no droplet field is needed first
+        const int t = c * VC_RB + threadIdx.x;
+        face = mine && t < a.total_tri;
+        if (face) {
+            const int *f = a.tri + 3 * (int64_t)t;
+            ia = f[0];
+            ib = f[1];
+            ic = f[2];
+        }
+    }
     const int d = find_drop_chunk(a.drops, a.ndrops, c);
     const Drop &D = a.drops[d];
     if (D.nnodes == 0 || !D.volcorr) {                 // block-uniform
@@ -818,15 +842,16 @@ __device__ void vc_chunk(const Arrays &a, int c)
         return;
     }
     const int k = c - D.red_chunk0;
-    const bool mine = threadIdx.x < VC_RB;
     const int t = k * VC_RB + threadIdx.x;
-    const bool face = mine && t < D.ntri, node = mine && t < D.nnodes;
-    int ia = 0, ib = 0, ic = 0;
-    if (face) {
-        const int *f = a.tri + 3 * ((int64_t)D.tri0 + t);
-        ia = f[0];
-        ib = f[1];
-        ic = f[2];
+    const bool node = mine && t < D.nnodes;
+    if (!one) {
+        face = mine && t < D.ntri;
+        if (face) {
+            const int *f = a.tri + 3 * ((int64_t)D.tri0 + t);
+            ia = f[0];
+            ib = f[1];
+            ic = f[2];
+        }
     }
     if (WAIT)
         griddep_wait();
@@ -958,7 +983,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_PER_SM) spread_kernel(Arrays a)
 __global__ void __launch_bounds__(IB_THREADS) interp_advect_kernel(Arrays a)
 {
     griddep_wait();
-    interp_item(a, (int64_t)blockIdx.x * IB_THREADS + threadIdx.x);
+    interp_block(a, (int64_t)blockIdx.x * IB_THREADS);
 }
 
 // The volume correction of every droplet: FP64 volume and centroid
@@ -1015,10 +1040,12 @@ __global__ void __launch_bounds__(IB_THREADS) ib_front_kernel(Arrays a)
 __global__ void __launch_bounds__(IB_THREADS) ib_back_kernel(Arrays a, int n_chunks, int volcorr)
 {
     unsigned sense = *(volatile unsigned *)a.bar_flag;
-    const int64_t ni = ((int64_t)a.total_nodes * 16 + 31) & ~(int64_t)31;
+    const int64_t ni = (int64_t)a.total_nodes * 16;
     const int64_t stride = (int64_t)gridDim.x * IB_THREADS;
-    for (int64_t gid = (int64_t)blockIdx.x * IB_THREADS + threadIdx.x; gid < ni; gid += stride)
-        interp_item(a, gid);
+    for (int64_t base = (int64_t)blockIdx.x * IB_THREADS; base < ni; base += stride) {   // block-uniform
+        interp_block(a, base);
+        __syncthreads();    // the next pass rewrites inc_s
+    }
     if (!volcorr)
         return;
     if (!grid_barrier(a, sense))
