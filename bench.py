@@ -287,13 +287,38 @@ def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
         _, step_ms, n = timed(2, steps)
         phases, phase_step_ms, n_ph = timed(1, steps)
         lb_only, _, n_lb = timed(3, steps)
+        iblb.iblb_set_option(ctx, iblb.IBLB_OPT_PROFILE, 0)
+        traces = []
+        for _ in range(TRACE_STEPS):      # after the timed region: one traced step after each flush
+            flush.zero_()
+            traces.append(iblb.iblb_trace_step(ctx))
         obs = iblb.iblb_observe(ctx, 0)
         nd = iblb.iblb_info(ctx, 0)["n_drops"]
         infos = [iblb.iblb_info(ctx, k) for k in range(nd)]
     finally:
         iblb.iblb_destroy(ctx)
     return dict(phases=phases, step_ms=step_ms, n=n, n_ph=n_ph, obs=obs, cells=sum(i["cells"] for i in infos),
-                nodes=sum(i["n_nodes"] for i in infos), drops=nd, lb_kernel_ms=lb_only["lb"] / n_lb)
+                nodes=sum(i["n_nodes"] for i in infos), drops=nd, lb_kernel_ms=lb_only["lb"] / n_lb,
+                in_step=in_step(traces))
+
+
+TRACE_STEPS = 20
+
+
+def in_step(traces):
+    """Medians over traced steps: each kernel from its first warp past the
+    wait on the previous kernel to the next kernel's first start (which
+    follows its last exit), the span from the force kernel's start to the end
+    of the last kernel, and the membrane's share of it (span minus the
+    stream-collide kernel)."""
+    names = [k for k in traces[0] if traces[0][k] is not None]
+    med = lambda f: statistics.median(f(t) for t in traces)
+    out = {k: med(lambda t, k=k: t[k]["end_us"] - t[k]["first_start_us"]) for k in names}
+    span = lambda t: max(t[k]["end_us"] for k in names) - t["force"]["first_start_us"]
+    out["span"] = med(span)
+    out["membrane"] = med(lambda t: span(t) - (t["lb"]["end_us"] - t["lb"]["first_start_us"]))
+    out["steps"] = len(traces)
+    return out
 
 
 def extra_workload(name, specs, storage, steps, warmup, torch, iblb, flush, autotune):
@@ -308,6 +333,8 @@ def extra_workload(name, specs, storage, steps, warmup, torch, iblb, flush, auto
             "ms_per_step": r["step_ms"] / r["n"], "phase_ms_per_step": ph,
             "ib_nodes_per_s": r["nodes"] / (ib * 1e-3),
             "lb_kernel_gbs": r["cells"] * bpc / (r["lb_kernel_ms"] * 1e-3) / 1e9,
+            "in_step_us": r["in_step"],
+            "ib_nodes_per_s_in_step": r["nodes"] / (r["in_step"]["membrane"] * 1e-6),
             "gpu_launches_per_step": launches_per_step(specs)}
 
 
@@ -595,6 +622,17 @@ def main():
                             "peak_gbs": peak, "peak_source": src},
             "phase_ms_per_step": {k: v / KP for k, v in ph.items()},
             "fp32": fp32,
+            # per-warp %globaltimer stamps of steps traced after the timed
+            # region (iblb_trace_step, L2 flushed before each): every kernel
+            # from its first warp past the wait on the previous kernel to the
+            # next kernel's first start, as it runs inside the chained step
+            "in_step": {
+                "us": {k: v for k, v in main_run["in_step"].items() if k != "steps"},
+                "steps": main_run["in_step"]["steps"],
+                "ib_nodes_per_s": world * nodes / (main_run["in_step"]["membrane"] * 1e-6),
+                "lb_achieved_gbs": cells * bpc / (main_run["in_step"]["lb"] * 1e-6) / 1e9,
+                "lb_frac": cells * bpc / (main_run["in_step"]["lb"] * 1e-6) / 1e9 / peak,
+            },
             "roofline": {"bound": "hbm", "kernel": "lb_kernel (fused stream-collide)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
                          "algorithmic_bytes_per_cell": bpc, "traffic": traffic},

@@ -280,6 +280,32 @@ int iblb_step(iblb_ctx *ctx, int nsteps);
  * IBLB_E_UNSTABLE or IBLB_E_OVERFLOW) and clears it. */
 int iblb_sync(iblb_ctx *ctx);
 
+/* Run ONE time step (the same work as iblb_step(ctx, 1), launched eagerly)
+ * with tracing on: every warp of the step's kernels records the GPU's global
+ * timer once its wait on the previous kernel returned (programmatic dependent
+ * launch), and a one-warp marker kernel launched after the step does the
+ * same.  Synchronises the context's stream.  out (host, IBLB_TRACE_KERNELS x
+ * 5 doubles, kernel-major in the order of IBLB_TRACE_*) receives per kernel,
+ * in microseconds from the earliest stamp of the step: the first, median and
+ * last warp start, the kernel's end = the first start of the next kernel that
+ * ran (or of the marker), which comes after its last warp's exit, and the
+ * number of warps recorded (0, and NaN times, for a kernel that did not run,
+ * such as the volume correction with none requested).  The first call
+ * allocates a 1.5 MB stamp buffer, freed by iblb_destroy.  Only the
+ * one-kernel-per-stage path is traced (the cooperative kernels of
+ * IBLB_OPT_FUSED_IB record nothing), and with IBLB_OPT_SPLIT_LB the two
+ * stream-collide launches share their stamps.  The stamps are separate
+ * instantiations of the kernels, launched only by this call: iblb_step runs
+ * none of their code.  Not thread-safe: trace one context at a time.
+ * Returns IBLB_E_ARG for a null out; CUDA errors as elsewhere. */
+#define IBLB_TRACE_KERNELS 5
+#define IBLB_TRACE_FORCE 0    /* node forces and tile lists */
+#define IBLB_TRACE_SPREAD 1   /* deterministic spread */
+#define IBLB_TRACE_LB 2       /* fused stream-collide */
+#define IBLB_TRACE_INTERP 3   /* interpolation and advection */
+#define IBLB_TRACE_VC 4       /* volume correction */
+int iblb_trace_step(iblb_ctx *ctx, double *out);
+
 /* Observables of droplet k (synchronises).  zcut_frac: protocol (i) plane
  * height over R0 (the paper's optimum 0.05); eps_flat: protocol (ii)
  * flatness parameter (the paper's optimum 0.1). */

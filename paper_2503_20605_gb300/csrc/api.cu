@@ -91,6 +91,7 @@ struct iblb_ctx {
     int *h_status = nullptr;     // pinned, 4 per droplet
     double *obs_scr = nullptr;   // scratch of the mesh observation kernels
     int64_t obs_scr_n = 0;
+    unsigned long long *d_trace = nullptr;   // per-warp stamps of iblb_trace_step (allocated by its first call)
     std::string err;
 };
 
@@ -973,6 +974,7 @@ void iblb_destroy(iblb_ctx *c)
         cudaStreamSynchronize(c->stream);
     invalidate_graphs(c);
     free_membrane_arrays(c);
+    dfree(c->d_trace);
     Arrays &A = c->A;
     dfree(c->fbuf[0]);
     dfree(c->fbuf[1]);
@@ -1290,6 +1292,76 @@ int iblb_step(iblb_ctx *c, int nsteps)
         c->step_count++;
         if (c->profile && (r = accumulate_profile(c)))
             return r;
+    }
+    return IBLB_OK;
+}
+
+int iblb_trace_step(iblb_ctx *c, double *out)
+{
+    Trace trace_("iblb_trace_step");
+    if (!c)
+        return fail(nullptr, IBLB_E_ARG, "null context");
+    if (!out)
+        return fail(c, IBLB_E_ARG, "null output");
+    int r = ensure_ready(c);
+    if (r)
+        return r;
+    Entered entered_(c);
+    const size_t n = (size_t)(TRACE_KERNELS + 1) * TRACE_WARPS;
+    if (!c->d_trace)
+        CK(dalloc(&c->d_trace, n));
+    CK(cudaMemsetAsync(c->d_trace, 0, n * sizeof(unsigned long long), c->stream));
+    const int prof = c->profile;
+    c->profile = 0;
+    set_trace_ib(c->d_trace);
+    set_trace_lb(c->d_trace);
+    r = enqueue_step(c, c->cur, false);
+    const cudaError_t em = r ? cudaSuccess : launch_trace_marker(c->A, c->d_trace, c->stream);
+    set_trace_ib(nullptr);
+    set_trace_lb(nullptr);
+    c->profile = prof;
+    if (r)
+        return r;
+    CK(em);
+    c->cur ^= 1;
+    c->step_count++;
+    std::vector<unsigned long long> h(n);
+    CK(cudaMemcpyAsync(h.data(), c->d_trace, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    // per kernel (and the marker): first, median and last warp start
+    double first[TRACE_KERNELS + 1], med[TRACE_KERNELS + 1], last[TRACE_KERNELS + 1];
+    int warps[TRACE_KERNELS + 1];
+    unsigned long long t0 = ~0ull;
+    for (size_t i = 0; i < n; ++i)
+        if (h[i])
+            t0 = std::min(t0, h[i]);
+    for (int k = 0; k <= TRACE_KERNELS; ++k) {
+        std::vector<unsigned long long> v;
+        for (int w = 0; w < TRACE_WARPS; ++w)
+            if (h[(size_t)k * TRACE_WARPS + w])
+                v.push_back(h[(size_t)k * TRACE_WARPS + w]);
+        warps[k] = (int)v.size();
+        if (v.empty()) {
+            first[k] = med[k] = last[k] = NAN;
+            continue;
+        }
+        std::sort(v.begin(), v.end());
+        first[k] = (double)(v.front() - t0) * 1e-3;
+        med[k] = (double)(v[v.size() / 2] - t0) * 1e-3;
+        last[k] = (double)(v.back() - t0) * 1e-3;
+    }
+    for (int k = 0; k < TRACE_KERNELS; ++k) {
+        double *o = out + 5 * k;
+        o[0] = first[k];
+        o[1] = med[k];
+        o[2] = last[k];
+        o[3] = NAN;             // end: the first start of the next kernel that ran
+        for (int m = k + 1; m <= TRACE_KERNELS && warps[k]; ++m)
+            if (warps[m]) {
+                o[3] = first[m];
+                break;
+            }
+        o[4] = (double)warps[k];
     }
     return IBLB_OK;
 }

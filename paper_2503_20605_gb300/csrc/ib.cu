@@ -35,6 +35,8 @@ namespace iblb {
 
 namespace {
 
+unsigned long long *g_trace_ib = nullptr;   // host: stamp buffer of a traced step (see iblb_trace_step)
+
 constexpr int IB_THREADS = 256;  // block size of every membrane kernel
 constexpr int SPREAD_PARTS = 4;  // parts of a tile's sorted node list, summed separately per cell
 constexpr int SP_THREADS = 128;  // block size of the separate spread kernel and its blocks per SM: 1216
@@ -816,8 +818,8 @@ __device__ __forceinline__ double inv_cbrt_ratio(double e, double V0, double V)
 // WAIT: the launch follows the advection with programmatic dependent
 // launch; the droplet lookup and the face corners (topology, which no step
 // writes) are read before waiting for it, the positions after.
-template <int NT, bool WAIT>
-__device__ void vc_chunk(const Arrays &a, int c)
+template <int NT, bool WAIT, bool TR = false>
+__device__ void vc_chunk(const Arrays &a, int c, unsigned long long *tr = nullptr)
 {
     static_assert(NT >= VC_RB, "a chunk needs VC_RB threads");
     __shared__ int s_last;
@@ -853,8 +855,11 @@ __device__ void vc_chunk(const Arrays &a, int c)
             ic = f[2];
         }
     }
-    if (WAIT)
+    if (WAIT) {
         griddep_wait();
+        if constexpr (TR)
+            trace_start(tr, TR_VC);
+    }
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (face) {   // 6 x the signed volume of the tetrahedron (0, q_a, q_b, q_c): q_a . (q_b x q_c)
         const double ax = a.qx[ia], ay = a.qy[ia], az = a.qz[ia];
@@ -960,17 +965,22 @@ __device__ bool grid_barrier(const Arrays &a, unsigned &sense)
 constexpr int NF_THREADS = 128;  // block size of the force kernel (32 nodes): small blocks, so that a
                                  // mesh of ten thousand nodes spreads over every SM
 
-template <bool EL>
-__global__ void __launch_bounds__(NF_THREADS) node_force_kernel(Arrays a)
+template <bool EL, bool TR>
+__global__ void __launch_bounds__(NF_THREADS) node_force_kernel(Arrays a, unsigned long long *tr)
 {
     griddep_wait();
+    if constexpr (TR)
+        trace_start(tr, TR_FORCE);
     const uint32_t gen = *a.gen + 1u;                  // committed by the spread
     node_forces<EL>(a, (int64_t)blockIdx.x * NF_THREADS + threadIdx.x, gen);
 }
 
-__global__ void __launch_bounds__(SP_THREADS, SP_PER_SM) spread_kernel(Arrays a)
+template <bool TR>
+__global__ void __launch_bounds__(SP_THREADS, SP_PER_SM) spread_kernel(Arrays a, unsigned long long *tr)
 {
     griddep_wait();
+    if constexpr (TR)
+        trace_start(tr, TR_SPREAD);
     __shared__ SpreadSmem sm;
     const uint32_t gen = *a.gen + 1u;
     const int cur = (int)(gen & 1u);
@@ -980,9 +990,12 @@ __global__ void __launch_bounds__(SP_THREADS, SP_PER_SM) spread_kernel(Arrays a)
     spread_finish(a, gen, cur, sm);
 }
 
-__global__ void __launch_bounds__(IB_THREADS) interp_advect_kernel(Arrays a)
+template <bool TR>
+__global__ void __launch_bounds__(IB_THREADS) interp_advect_kernel(Arrays a, unsigned long long *tr)
 {
     griddep_wait();
+    if constexpr (TR)
+        trace_start(tr, TR_INTERP);
     interp_block(a, (int64_t)blockIdx.x * IB_THREADS);
 }
 
@@ -990,9 +1003,18 @@ __global__ void __launch_bounds__(IB_THREADS) interp_advect_kernel(Arrays a)
 // partials of chunk blockIdx.x; the last chunk of a droplet folds them into
 // k = (V0/V)^(1/3) and the centroid, which the readers of the positions
 // apply from then on.
-__global__ void __launch_bounds__(VC_RB) volume_correction_kernel(Arrays a)
+template <bool TR>
+__global__ void __launch_bounds__(VC_RB) volume_correction_kernel(Arrays a, unsigned long long *tr)
 {
-    vc_chunk<VC_RB, true>(a, blockIdx.x);
+    vc_chunk<VC_RB, true, TR>(a, blockIdx.x, tr);
+}
+
+// The trailing marker of a traced step: starts once the step's last kernel
+// has finished.
+__global__ void trace_marker_kernel(Arrays a, unsigned long long *tr)
+{
+    griddep_wait();
+    trace_start(tr, TR_END);
 }
 
 // a.p* = the positions as read (the pending correction applied)
@@ -1075,15 +1097,31 @@ cudaError_t launch_node_force(const Arrays &a, cudaStream_t s)
         return cudaSuccess;
     const dim3 grid((unsigned)(((int64_t)a.total_nodes * NL + NF_THREADS - 1) / NF_THREADS));
     if (a.fref)
-        return launch_k(node_force_kernel<true>, grid, dim3(NF_THREADS), 0, s, a.pdl != 0, a);
-    return launch_k(node_force_kernel<false>, grid, dim3(NF_THREADS), 0, s, a.pdl != 0, a);
+        return g_trace_ib ? launch_k(node_force_kernel<true, true>, grid, dim3(NF_THREADS), 0, s, a.pdl != 0, a,
+                                     g_trace_ib)
+                          : launch_k(node_force_kernel<true, false>, grid, dim3(NF_THREADS), 0, s, a.pdl != 0, a,
+                                     (unsigned long long *)nullptr);
+    return g_trace_ib ? launch_k(node_force_kernel<false, true>, grid, dim3(NF_THREADS), 0, s, a.pdl != 0, a,
+                                 g_trace_ib)
+                      : launch_k(node_force_kernel<false, false>, grid, dim3(NF_THREADS), 0, s, a.pdl != 0, a,
+                                 (unsigned long long *)nullptr);
 }
 
 cudaError_t launch_spread(const Arrays &a, cudaStream_t s)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    return launch_k(spread_kernel, dim3(sm_count() * SP_PER_SM), dim3(SP_THREADS), 0, s, a.pdl != 0, a);
+    const dim3 grid(sm_count() * SP_PER_SM);
+    return g_trace_ib ? launch_k(spread_kernel<true>, grid, dim3(SP_THREADS), 0, s, a.pdl != 0, a, g_trace_ib)
+                      : launch_k(spread_kernel<false>, grid, dim3(SP_THREADS), 0, s, a.pdl != 0, a,
+                                 (unsigned long long *)nullptr);
+}
+
+void set_trace_ib(unsigned long long *trace) { g_trace_ib = trace; }
+
+cudaError_t launch_trace_marker(const Arrays &a, unsigned long long *trace, cudaStream_t s)
+{
+    return launch_k(trace_marker_kernel, dim3(1), dim3(32), 0, s, a.pdl != 0, a, trace);
 }
 
 cudaError_t launch_interp_advect(const Arrays &a, cudaStream_t s)
@@ -1091,8 +1129,10 @@ cudaError_t launch_interp_advect(const Arrays &a, cudaStream_t s)
     if (a.total_nodes <= 0)
         return cudaSuccess;
     const int64_t threads = (int64_t)a.total_nodes * 16;
-    return launch_k(interp_advect_kernel, dim3((unsigned)((threads + IB_THREADS - 1) / IB_THREADS)),
-                    dim3(IB_THREADS), 0, s, a.pdl != 0, a);
+    const dim3 grid((unsigned)((threads + IB_THREADS - 1) / IB_THREADS));
+    return g_trace_ib ? launch_k(interp_advect_kernel<true>, grid, dim3(IB_THREADS), 0, s, a.pdl != 0, a, g_trace_ib)
+                      : launch_k(interp_advect_kernel<false>, grid, dim3(IB_THREADS), 0, s, a.pdl != 0, a,
+                                 (unsigned long long *)nullptr);
 }
 
 
@@ -1137,7 +1177,10 @@ cudaError_t launch_volume_correction(const Arrays &a, int n_chunks_total, cudaSt
 {
     if (a.total_nodes <= 0 || n_chunks_total <= 0)
         return cudaSuccess;
-    return launch_k(volume_correction_kernel, dim3(n_chunks_total), dim3(VC_RB), 0, s, a.pdl != 0, a);
+    return g_trace_ib ? launch_k(volume_correction_kernel<true>, dim3(n_chunks_total), dim3(VC_RB), 0, s,
+                                 a.pdl != 0, a, g_trace_ib)
+                      : launch_k(volume_correction_kernel<false>, dim3(n_chunks_total), dim3(VC_RB), 0, s,
+                                 a.pdl != 0, a, (unsigned long long *)nullptr);
 }
 
 cudaError_t launch_corrected_positions(const Arrays &a, cudaStream_t s)

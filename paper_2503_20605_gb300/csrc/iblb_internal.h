@@ -147,6 +147,38 @@ struct Arrays {
     uint8_t *clamped;              // per node: 1 if the near-wall guard clamped it in this step
 };
 
+// Tracing (iblb_trace_step): once its wait on the previous kernel returned,
+// every warp of the step's kernels writes %globaltimer (ns) into
+// trace[k * TRACE_WARPS + w] for kernel k (TraceKernel) and warp w of the
+// launch (blockIdx.x * warps per block + warp; warps from TRACE_WARPS on are
+// not recorded).  A kernel's end is read as the next kernel's first start
+// (TR_END: a marker kernel launched after the step), which programmatic
+// dependent launch places after its last exit.  The stamps live in separate
+// instantiations of the kernels (template flag TR, the buffer as a trailing
+// argument), launched only while a host-side buffer is set: the untraced
+// kernels carry no stamp code (a run-time check, an exit stamp or a kernel
+// parameter read each cost measurable time in the chained step).
+enum TraceKernel { TR_FORCE = 0, TR_SPREAD = 1, TR_LB = 2, TR_INTERP = 3, TR_VC = 4, TR_END = 5, TRACE_KERNELS = 5 };
+constexpr int TRACE_WARPS = 32768;
+__device__ __forceinline__ void trace_start(unsigned long long *trace, int k)
+{
+    if (trace == nullptr || (threadIdx.x & 31) != 0)
+        return;
+    const unsigned w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= (unsigned)TRACE_WARPS)
+        return;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    trace[(size_t)k * TRACE_WARPS + w] = t;
+}
+// Launch the traced instantiations with this stamp buffer from now on
+// (nullptr: the plain ones); host-side state of the membrane launches and of
+// the stream-collide launches.
+void set_trace_ib(unsigned long long *trace);
+void set_trace_lb(unsigned long long *trace);
+// The step's trailing marker (one warp): its start ends the last kernel.
+cudaError_t launch_trace_marker(const Arrays &a, unsigned long long *trace, cudaStream_t s);
+
 // Programmatic dependent launch: a kernel of the step may be launched while
 // the previous one finishes; griddep_wait() returns once the previous kernel
 // has completed and its writes are visible, and it is the first statement of

@@ -32,6 +32,11 @@ namespace iblb {
 
 namespace {
 
+unsigned long long *g_trace_lb = nullptr;   // host: stamp buffer of a traced step (see iblb_trace_step)
+// The traced kernel's stamp as a call: inlined, it costs the collision loop
+// a register spill, and the traced step would not time the plain kernel.
+__device__ __noinline__ void lb_trace_start(unsigned long long *tr) { trace_start(tr, TR_LB); }
+
 constexpr int LB_THREADS = 256;                   // consumer threads per block (FP32 storage)
 // 16-bit storage takes two cells per work item and needs more registers per
 // thread: 7 consumer warps (+ the producer) keep two blocks of 8 warps on an
@@ -647,16 +652,18 @@ __device__ __forceinline__ void collide_pairs(const Arrays &a, const DropC &c, c
     }
 }
 
-template <typename S, bool VARTAU>
+template <typename S, bool VARTAU, bool TR>
 __global__ void __launch_bounds__(lb_block<S>(), 2)
     lb_kernel(Arrays a, const S *__restrict__ src, S *__restrict__ dst, int ns, const int *__restrict__ list,
-              const int *__restrict__ count, int no_force)
+              const int *__restrict__ count, int no_force, unsigned long long *tr)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // full[s]: the stage's bulk copies landed (32 producer lanes arrive with
     // the byte count); empty[s]: every consumer thread is done reading it
     __shared__ __align__(8) uint64_t full[LB_MAX_STAGES], empty[LB_MAX_STAGES];
     griddep_wait();
+    if constexpr (TR)
+        lb_trace_start(tr);
     const uint32_t gen = *a.gen;
     // the groups of this launch: list[0 .. *count) or all of them
     const int total = list ? *count : a.lb_blocks_total;
@@ -754,7 +761,9 @@ cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, c
         return cudaSuccess;
     const int ns = cfg.lb_stages < 2 ? 2 : (cfg.lb_stages > LB_MAX_STAGES ? LB_MAX_STAGES : cfg.lb_stages);
     const size_t smem = (size_t)ns * a.lb_stage_bytes;
-    const void *fn = vartau ? (const void *)lb_kernel<S, true> : (const void *)lb_kernel<S, false>;
+    const bool traced = g_trace_lb != nullptr;
+    const void *fn = vartau ? (traced ? (const void *)lb_kernel<S, true, true> : (const void *)lb_kernel<S, true, false>)
+                            : (traced ? (const void *)lb_kernel<S, false, true> : (const void *)lb_kernel<S, false, false>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
@@ -770,11 +779,17 @@ cudaError_t launch_t(const Arrays &a, const void *src, void *dst, bool vartau, c
     int grid = cfg.sm_count * per_sm;
     grid = grid < total ? grid : total;
     const int nf = no_force ? 1 : 0;
+    unsigned long long *tr = g_trace_lb;
+    const dim3 g(grid), b(lb_block<S>());
     if (vartau)
-        return launch_k(lb_kernel<S, true>, dim3(grid), dim3(lb_block<S>()), smem, s, a.pdl != 0, a, (const S *)src,
-                        (S *)dst, ns, list, count, nf);
-    return launch_k(lb_kernel<S, false>, dim3(grid), dim3(lb_block<S>()), smem, s, a.pdl != 0, a, (const S *)src, (S *)dst,
-                    ns, list, count, nf);
+        return traced ? launch_k(lb_kernel<S, true, true>, g, b, smem, s, a.pdl != 0, a, (const S *)src, (S *)dst, ns,
+                                 list, count, nf, tr)
+                      : launch_k(lb_kernel<S, true, false>, g, b, smem, s, a.pdl != 0, a, (const S *)src, (S *)dst, ns,
+                                 list, count, nf, tr);
+    return traced ? launch_k(lb_kernel<S, false, true>, g, b, smem, s, a.pdl != 0, a, (const S *)src, (S *)dst, ns, list,
+                             count, nf, tr)
+                  : launch_k(lb_kernel<S, false, false>, g, b, smem, s, a.pdl != 0, a, (const S *)src, (S *)dst, ns,
+                             list, count, nf, tr);
 }
 
 }  // namespace
@@ -868,6 +883,8 @@ __global__ void __launch_bounds__(256) classify_kernel(Arrays a)
 }
 
 }  // namespace
+
+void set_trace_lb(unsigned long long *trace) { g_trace_lb = trace; }
 
 cudaError_t launch_classify(const Arrays &a, cudaStream_t s)
 {

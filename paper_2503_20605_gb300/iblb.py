@@ -24,6 +24,8 @@ STORAGE = {"f32": IBLB_STORE_F32, "f16": IBLB_STORE_F16, "bf16": IBLB_STORE_BF16
 IBLB_WET_OFF, IBLB_WET_THETA, IBLB_WET_RAW = 0, 1, 2
 IBLB_PH_FORCES, IBLB_PH_SPREAD, IBLB_PH_INOUT, IBLB_PH_LB, IBLB_PH_ADVECT, IBLB_PH_REDUCE = range(6)
 IBLB_NPHASE = 6
+IBLB_TRACE_FORCE, IBLB_TRACE_SPREAD, IBLB_TRACE_LB, IBLB_TRACE_INTERP, IBLB_TRACE_VC = range(5)
+IBLB_TRACE_KERNELS = 5
 PHASE_NAMES = ["forces", "spread", "inout", "lb", "advect", "reduce"]
 IBLB_OPT_GRAPHS, IBLB_OPT_PROFILE, IBLB_OPT_LB_BLOCKS_PER_SM, IBLB_OPT_LB_ROW_MULT, IBLB_OPT_LB_STAGES = 0, 1, 2, 3, 4
 IBLB_OPT_FUSED_IB, IBLB_OPT_IB_BLOCKS_PER_SM, IBLB_OPT_SPLIT_LB, IBLB_OPT_LB_FAR_BLOCKS_PER_SM = 5, 6, 7, 8
@@ -93,6 +95,7 @@ _SIGS = {
     "iblb_get_inside": (C.c_int, [_P, C.c_int, C.POINTER(C.c_uint8)]),
     "iblb_step": (C.c_int, [_P, C.c_int]),
     "iblb_sync": (C.c_int, [_P]),
+    "iblb_trace_step": (C.c_int, [_P, _D]),
     "iblb_observe": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.POINTER(Obs)]),
     "iblb_observe_all": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(Obs)]),
     "iblb_set_option": (C.c_int, [_P, C.c_int, C.c_int]),
@@ -297,6 +300,25 @@ def iblb_step(ctx, nsteps=1):
 
 def iblb_sync(ctx):
     _check(ctx, lib().iblb_sync(ctx))
+
+
+TRACE_KERNELS = ("force", "spread", "lb", "interp", "vc")
+
+
+def iblb_trace_step(ctx):
+    """One traced step: per kernel (force, spread, lb, interp, vc) a dict of
+    first_start_us, median_start_us, last_start_us (warps past their wait on
+    the previous kernel), end_us (the next kernel's first start, after this
+    one's last exit), all from the step's earliest stamp, and warps; None for
+    a kernel that did not run."""
+    out = (C.c_double * (IBLB_TRACE_KERNELS * 5))()
+    _check(ctx, lib().iblb_trace_step(ctx, out))
+    res = {}
+    for k, name in enumerate(TRACE_KERNELS):
+        o = list(out[5 * k:5 * k + 5])
+        res[name] = None if o[4] == 0 else {"first_start_us": o[0], "median_start_us": o[1],
+                                            "last_start_us": o[2], "end_us": o[3], "warps": int(o[4])}
+    return res
 
 
 def iblb_observe(ctx, k=0, zcut_frac=0.05, eps_flat=0.1):
