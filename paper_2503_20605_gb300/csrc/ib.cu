@@ -229,17 +229,19 @@ __device__ __forceinline__ int support_tiles3(int b, int n, bool periodic, int &
 // listed as (a, b, t << 2 | k): the face's other two corners in
 // counter-clockwise order about the outward normal -- the face is (j, a, b)
 // -- and the face and the corner j takes in it.  Lane l takes the faces l,
-// l + 4, ...; with r_a = q_a - q_j and r_b = q_b - q_j (FP64 differences
-// rounded once to FP32, dilated by k when a volume correction is pending) a
+// l + 4, ...; with r_a = q_a - q_j and r_b = q_b - q_j (from the FP32 pairs
+// of the positions, dilated by k when a volume correction is pending) a
 // face's normal is r_a x r_b, its area half its length, and dA/dq_j =
 // 1/2 n x (r_b - r_a).  The lanes' sums meet in a fixed shuffle tree.  Lane
-// c < 3 then takes axis c of the node (its corrected coordinate, kernel
-// support and weights) and lane 3 the nodal force; the record is written and
-// the node is listed in the 4^3 tiles its kernel support touches, the
-// lanes sharing the tiles: its slot in a tile's list (TILE_CAP slots per
-// tile) comes from the tile's counter, and the node that takes slot 0 stamps
-// the tile with the step's generation gen and appends it to the band list.
-// Every lane of the warp takes part (the shuffles span whole quads).
+// c < 3 takes axis c of the node (its corrected coordinate, kernel support
+// and weights) and lane 3 the nodal force; the node is listed in the 4^3
+// tiles its kernel support touches, the lanes sharing the tiles: its slot in
+// a tile's list (TILE_CAP slots per tile) comes from the tile's counter, and
+// the node that takes slot 0 stamps the tile with the step's generation gen
+// and appends it to the band list.  The axis work and the listing depend on
+// the node's own position only: they run while the first faces'
+// neighbour positions are in flight.  Every lane of the warp takes part
+// (the shuffles span whole quads).
 constexpr int NL = 4;
 template <bool EL>     // EL: some droplet of the launch has an elastic membrane (a.fref set)
 __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32_t gen)
@@ -251,59 +253,38 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
     int d = 0;
     Corr cr = {false, 1.0, 0.0, 0.0, 0.0};
     double qx0 = 0.0, qy0 = 0.0, qz0 = 0.0;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 jh = zero4, jl = zero4;
+    // the node's first RING8 faces at a fixed stride (lane l: entries l and
+    // l + 4, the first pass), further ones (a face count above RING8) from
+    // the list; the first pass's neighbour positions are loaded at once
+    int4 f0 = make_int4(-1, -1, 0, 0), f1 = f0;
+    int nfaces = 0;
+    float4 a0h = zero4, a0l = zero4, b0h = zero4, b0l = zero4, a1h = zero4, a1l = zero4, b1h = zero4, b1l = zero4;
     if (valid) {
         d = a.ndrops == 1 ? 0 : a.node_drop[j];   // (one droplet: no lookup on the critical path)
         cr = load_corr(a, d);
         qx0 = a.qx[j];
         qy0 = a.qy[j];
         qz0 = a.qz[j];
-        const float4 jh = a.qh[j], jl = a.ql[j];
-        const float kf = cr.on ? dtof_rn(cr.k) : 1.0f;
-        float ks3 = 0.0f, ka3 = 0.0f;
-        if (EL) {
-            ks3 = a.drops[d].ks * (1.0f / 3.0f);
-            ka3 = a.drops[d].ka * (1.0f / 3.0f);
+        jh = a.qh[j];
+        jl = a.ql[j];
+        f0 = a.ring8[(int64_t)RING8 * j + l];
+        f1 = a.ring8[(int64_t)RING8 * j + l + NL];
+        nfaces = f0.w;
+        if (l < nfaces) {
+            a0h = a.qh[f0.x];
+            a0l = a.ql[f0.x];
+            b0h = a.qh[f0.y];
+            b0l = a.ql[f0.y];
         }
-        const bool elastic = EL && (ks3 != 0.0f || ka3 != 0.0f);
-        // the node's first RING8 faces at a fixed stride (lane l: entries l
-        // and l + 4), further ones (a face count above RING8) from the list
-        const int4 f0 = a.ring8[(int64_t)RING8 * j + l], f1 = a.ring8[(int64_t)RING8 * j + l + NL];
-        const int nfaces = f0.w;
-        const int e0 = nfaces > RING8 ? a.adj_start[j] : 0;
-        for (int eb = l; eb < nfaces; eb += 2 * NL) {
-            // two faces per pass, every load issued before the arithmetic
-            const bool two = eb + NL < nfaces;
-            const int4 en0 = eb < RING8 ? f0 : a.ring[e0 + eb];
-            const int4 en1 = eb + NL < RING8 ? f1 : (two ? a.ring[e0 + eb + NL] : en0);
-            const float4 a0h = a.qh[en0.x], a0l = a.ql[en0.x], b0h = a.qh[en0.y], b0l = a.ql[en0.y];
-            const float4 a1h = a.qh[en1.x], a1l = a.ql[en1.x], b1h = a.qh[en1.y], b1l = a.ql[en1.y];
-            face_terms<EL>(a, en0, rel_coord(a0h.x, a0l.x, jh.x, jl.x) * kf, rel_coord(a0h.y, a0l.y, jh.y, jl.y) * kf,
-                           rel_coord(a0h.z, a0l.z, jh.z, jl.z) * kf, rel_coord(b0h.x, b0l.x, jh.x, jl.x) * kf,
-                           rel_coord(b0h.y, b0l.y, jh.y, jl.y) * kf, rel_coord(b0h.z, b0l.z, jh.z, jl.z) * kf,
-                           elastic, ks3, ka3, gx, gy, gz, nx, ny, nz, chi, ex, ey, ez);
-            if (two)
-                face_terms<EL>(a, en1, rel_coord(a1h.x, a1l.x, jh.x, jl.x) * kf,
-                               rel_coord(a1h.y, a1l.y, jh.y, jl.y) * kf, rel_coord(a1h.z, a1l.z, jh.z, jl.z) * kf,
-                               rel_coord(b1h.x, b1l.x, jh.x, jl.x) * kf, rel_coord(b1h.y, b1l.y, jh.y, jl.y) * kf,
-                               rel_coord(b1h.z, b1l.z, jh.z, jl.z) * kf, elastic, ks3, ka3, gx, gy, gz, nx, ny, nz,
-                               chi, ex, ey, ez);
+        if (l + NL < nfaces) {
+            a1h = a.qh[f1.x];
+            a1l = a.ql[f1.x];
+            b1h = a.qh[f1.y];
+            b1l = a.ql[f1.y];
         }
     }
-    for (int o = NL / 2; o >= 1; o >>= 1) {
-        gx += __shfl_xor_sync(0xffffffffu, gx, o);
-        gy += __shfl_xor_sync(0xffffffffu, gy, o);
-        gz += __shfl_xor_sync(0xffffffffu, gz, o);
-        nx += __shfl_xor_sync(0xffffffffu, nx, o);
-        ny += __shfl_xor_sync(0xffffffffu, ny, o);
-        nz += __shfl_xor_sync(0xffffffffu, nz, o);
-        chi += __shfl_xor_sync(0xffffffffu, chi, o);
-    }
-    if (EL)
-        for (int o = NL / 2; o >= 1; o >>= 1) {
-            ex += __shfl_xor_sync(0xffffffffu, ex, o);
-            ey += __shfl_xor_sync(0xffffffffu, ey, o);
-            ez += __shfl_xor_sync(0xffffffffu, ez, o);
-        }
     // axis c = l of the node (lanes 0 .. 2): corrected coordinate, kernel
     // support and weights
     const Drop &D = a.drops[d];
@@ -343,59 +324,20 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
               ty2 = __shfl_sync(0xffffffffu, t2, qb | 1);
     const int tz0 = __shfl_sync(0xffffffffu, t0, qb | 2), tz1 = __shfl_sync(0xffffffffu, t1, qb | 2),
               tz2 = __shfl_sync(0xffffffffu, t2, qb | 2);
-    if (!valid)
-        return;
     const int ncombo = ntx * nty * ntz;
-    NodeRec &rec = a.rec[j];
-    if (l < 3) {
+    NodeRec &rec = a.rec[valid ? j : 0];
+    if (valid && l < 3) {
         // the corrected coordinate, for the in/out test and the advection of this step
         (ax == 0 ? a.px : (ax == 1 ? a.py : a.pz))[j] = q;
         (&rec.bx)[ax] = b;
         float *rw = ax == 0 ? rec.wx : (ax == 1 ? rec.wy : rec.wz);
         *reinterpret_cast<float4 *>(rw) = make_float4(w[0], w[1], w[2], w[3]);
-    } else {
-        rec.key = ncombo;
-        rec.spare = d;
-        uint8_t clamped = 0;
-        float px = 0.f, py = 0.f, pz = 0.f;
-        if (!sane) {
-            atomicOr(&a.status[4 * d], ST_NAN);
-        } else {
-            px = -D.sigma * gx;
-            py = -D.sigma * gy;
-            pz = -D.sigma * gz;
-            if (EL) {
-                px += ex;
-                py += ey;
-                pz += ez;
-            }
-            if (D.wetting) {
-                float h = dtof_rn(qz - 0.5);
-                if (h < D.hmin) {
-                    h = D.hmin;
-                    clamped = 1;
-                }
-                const float r0 = D.xi / h;
-                const float Pi = D.A * (ipow(r0, D.n) - ipow(r0, D.m));
-                const float inl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
-                const float sc = -(chi * (1.0f / 3.0f)) * Pi * inl;
-                px += sc * nx;
-                py += sc * ny;
-                pz += sc * nz;
-            }
-            if (ncombo == 0)
-                atomicOr(&a.status[4 * d], ST_ESCAPE);
-        }
-        rec.phi[0] = px;
-        rec.phi[1] = py;
-        rec.phi[2] = pz;
-        a.clamped[j] = clamped;
     }
     // the node's tiles, shared by the four lanes: every counter's atomic is
     // issued before any result is used (a support across a partial periodic
     // tile can touch up to 27 tiles)
     const int cur = (int)(gen & 1u);
-    for (int c0 = l; c0 < ncombo; c0 += 2 * NL) {
+    for (int c0 = l; valid && c0 < ncombo; c0 += 2 * NL) {
         int64_t tl[2], trw[2];
         int rk[2], tc[2];
 #pragma unroll
@@ -435,6 +377,99 @@ __device__ __forceinline__ void node_forces(const Arrays &a, int64_t gid, uint32
             else
                 atomicOr(&a.status[4 * d], ST_SPREAD_OVF);
         }
+    }
+    // the faces: the first pass from the positions loaded above, then any
+    // further passes (nodes with more than RING8 faces)
+    if (valid) {
+        const float kf = cr.on ? dtof_rn(cr.k) : 1.0f;
+        float ks3 = 0.0f, ka3 = 0.0f;
+        if (EL) {
+            ks3 = a.drops[d].ks * (1.0f / 3.0f);
+            ka3 = a.drops[d].ka * (1.0f / 3.0f);
+        }
+        const bool elastic = EL && (ks3 != 0.0f || ka3 != 0.0f);
+        if (l < nfaces)
+            face_terms<EL>(a, f0, rel_coord(a0h.x, a0l.x, jh.x, jl.x) * kf, rel_coord(a0h.y, a0l.y, jh.y, jl.y) * kf,
+                           rel_coord(a0h.z, a0l.z, jh.z, jl.z) * kf, rel_coord(b0h.x, b0l.x, jh.x, jl.x) * kf,
+                           rel_coord(b0h.y, b0l.y, jh.y, jl.y) * kf, rel_coord(b0h.z, b0l.z, jh.z, jl.z) * kf,
+                           elastic, ks3, ka3, gx, gy, gz, nx, ny, nz, chi, ex, ey, ez);
+        if (l + NL < nfaces)
+            face_terms<EL>(a, f1, rel_coord(a1h.x, a1l.x, jh.x, jl.x) * kf, rel_coord(a1h.y, a1l.y, jh.y, jl.y) * kf,
+                           rel_coord(a1h.z, a1l.z, jh.z, jl.z) * kf, rel_coord(b1h.x, b1l.x, jh.x, jl.x) * kf,
+                           rel_coord(b1h.y, b1l.y, jh.y, jl.y) * kf, rel_coord(b1h.z, b1l.z, jh.z, jl.z) * kf,
+                           elastic, ks3, ka3, gx, gy, gz, nx, ny, nz, chi, ex, ey, ez);
+        const int e0 = nfaces > RING8 ? a.adj_start[j] : 0;
+        for (int eb = l + 2 * NL; eb < nfaces; eb += 2 * NL) {
+            // two faces per pass, every load issued before the arithmetic
+            const bool two = eb + NL < nfaces;
+            const int4 en0 = a.ring[e0 + eb];
+            const int4 en1 = two ? a.ring[e0 + eb + NL] : en0;
+            const float4 c0h = a.qh[en0.x], c0l = a.ql[en0.x], d0h = a.qh[en0.y], d0l = a.ql[en0.y];
+            const float4 c1h = a.qh[en1.x], c1l = a.ql[en1.x], d1h = a.qh[en1.y], d1l = a.ql[en1.y];
+            face_terms<EL>(a, en0, rel_coord(c0h.x, c0l.x, jh.x, jl.x) * kf, rel_coord(c0h.y, c0l.y, jh.y, jl.y) * kf,
+                           rel_coord(c0h.z, c0l.z, jh.z, jl.z) * kf, rel_coord(d0h.x, d0l.x, jh.x, jl.x) * kf,
+                           rel_coord(d0h.y, d0l.y, jh.y, jl.y) * kf, rel_coord(d0h.z, d0l.z, jh.z, jl.z) * kf,
+                           elastic, ks3, ka3, gx, gy, gz, nx, ny, nz, chi, ex, ey, ez);
+            if (two)
+                face_terms<EL>(a, en1, rel_coord(c1h.x, c1l.x, jh.x, jl.x) * kf,
+                               rel_coord(c1h.y, c1l.y, jh.y, jl.y) * kf, rel_coord(c1h.z, c1l.z, jh.z, jl.z) * kf,
+                               rel_coord(d1h.x, d1l.x, jh.x, jl.x) * kf, rel_coord(d1h.y, d1l.y, jh.y, jl.y) * kf,
+                               rel_coord(d1h.z, d1l.z, jh.z, jl.z) * kf, elastic, ks3, ka3, gx, gy, gz, nx, ny, nz,
+                               chi, ex, ey, ez);
+        }
+    }
+    for (int o = NL / 2; o >= 1; o >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        nx += __shfl_xor_sync(0xffffffffu, nx, o);
+        ny += __shfl_xor_sync(0xffffffffu, ny, o);
+        nz += __shfl_xor_sync(0xffffffffu, nz, o);
+        chi += __shfl_xor_sync(0xffffffffu, chi, o);
+    }
+    if (EL)
+        for (int o = NL / 2; o >= 1; o >>= 1) {
+            ex += __shfl_xor_sync(0xffffffffu, ex, o);
+            ey += __shfl_xor_sync(0xffffffffu, ey, o);
+            ez += __shfl_xor_sync(0xffffffffu, ez, o);
+        }
+    if (valid && l == 3) {
+        rec.key = ncombo;
+        rec.spare = d;
+        uint8_t clamped = 0;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        if (!sane) {
+            atomicOr(&a.status[4 * d], ST_NAN);
+        } else {
+            px = -D.sigma * gx;
+            py = -D.sigma * gy;
+            pz = -D.sigma * gz;
+            if (EL) {
+                px += ex;
+                py += ey;
+                pz += ez;
+            }
+            if (D.wetting) {
+                float h = dtof_rn(qz - 0.5);
+                if (h < D.hmin) {
+                    h = D.hmin;
+                    clamped = 1;
+                }
+                const float r0 = D.xi / h;
+                const float Pi = D.A * (ipow(r0, D.n) - ipow(r0, D.m));
+                const float inl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
+                const float sc = -(chi * (1.0f / 3.0f)) * Pi * inl;
+                px += sc * nx;
+                py += sc * ny;
+                pz += sc * nz;
+            }
+            if (ncombo == 0)
+                atomicOr(&a.status[4 * d], ST_ESCAPE);
+        }
+        rec.phi[0] = px;
+        rec.phi[1] = py;
+        rec.phi[2] = pz;
+        a.clamped[j] = clamped;
     }
 }
 
