@@ -692,13 +692,18 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
 }
 
 // The last block to finish the spread commits the generation and empties the
-// previous step's band list, which the next step fills.
+// previous step's band list, which the next step fills.  A relaxed count
+// suffices: the last block writes only these step-level words and reads
+// nothing another block wrote, every block has read the generation and the
+// previous band list before it counts, and the next kernel sees all the
+// spread's writes at the kernel boundary (a release here made each block
+// wait for its force-density stores first).
 __device__ void spread_finish(const Arrays &a, uint32_t gen, int cur, SpreadSmem &sm)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         sm.last = cuda::atomic_ref<int, cuda::thread_scope_device>(*a.spread_done).fetch_add(
-                      1, cuda::memory_order_acq_rel) == (int)gridDim.x - 1;
+                      1, cuda::memory_order_relaxed) == (int)gridDim.x - 1;
     }
     __syncthreads();
     if (sm.last && threadIdx.x == 0) {
