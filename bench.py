@@ -288,6 +288,16 @@ def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
         phases, phase_step_ms, n_ph = timed(1, steps)
         lb_only, _, n_lb = timed(3, steps)
         iblb.iblb_set_option(ctx, iblb.IBLB_OPT_PROFILE, 0)
+        # the same steps back to back in one call (no flush between them:
+        # each step streams the populations, larger than L2, through it)
+        iblb.iblb_step(ctx, warmup)
+        b2b = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        b2b[0].record()
+        iblb.iblb_step(ctx, steps)
+        b2b[1].record()
+        torch.cuda.synchronize()
+        b2b_ms = b2b[0].elapsed_time(b2b[1])
         traces = []
         for _ in range(TRACE_STEPS):      # after the timed region: one traced step after each flush
             flush.zero_()
@@ -299,7 +309,7 @@ def run_gpu(spec, storage, steps, warmup, torch, iblb, flush, autotune=True):
         iblb.iblb_destroy(ctx)
     return dict(phases=phases, step_ms=step_ms, n=n, n_ph=n_ph, obs=obs, cells=sum(i["cells"] for i in infos),
                 nodes=sum(i["n_nodes"] for i in infos), drops=nd, lb_kernel_ms=lb_only["lb"] / n_lb,
-                in_step=in_step(traces))
+                in_step=in_step(traces), b2b_ms=b2b_ms)
 
 
 TRACE_STEPS = 20
@@ -633,6 +643,11 @@ def main():
                 "lb_achieved_gbs": cells * bpc / (main_run["in_step"]["lb"] * 1e-6) / 1e9,
                 "lb_frac": cells * bpc / (main_run["in_step"]["lb"] * 1e-6) / 1e9 / peak,
             },
+            "back_to_back": {
+                "value": whole_job_mlups(cells, K, max_over_ranks(main_run["b2b_ms"], world, "cuda"), world),
+                "unit": "MLUPS", "ms_per_step": main_run["b2b_ms"] / K,
+                "l2": "not flushed: the K steps in one iblb_step call; every step streams the populations "
+                      "(larger than L2) through it"},
             "roofline": {"bound": "hbm", "kernel": "lb_kernel (fused stream-collide)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
                          "algorithmic_bytes_per_cell": bpc, "traffic": traffic},
