@@ -379,7 +379,7 @@ void layout(iblb_ctx *c)
         D.lb_block0 = lb0;
         D.lb_nblocks = D.lb_gpp * D.nzf;
         D.mass_block0 = mb0;
-        D.mass_nblocks = (int)((D.cells + 255) / 256);
+        D.mass_nblocks = (int)((D.cells + MASS_CELLS_PER_BLOCK - 1) / MASS_CELLS_PER_BLOCK);
         stage = std::max(stage, lb_stage_bytes(D.lb_rows, D.pitch, sb));
         cell0 += D.cells;
         pcell0 += D.pcells;
@@ -1797,9 +1797,10 @@ int iblb_mesh_observe_dev(const double *d_xyz, int n_nodes, const int32_t *d_tri
 // fails with out-of-memory; or a handler that runs because an allocation just
 // failed and wants to record the droplet's state before giving up.  This
 // variant runs the same kernels on a statically sized __device__ array.  The
-// array holds the scratch of meshes up to kNoAllocMaxChunks reduction chunks
-// (each RED_FACES faces and RED_NODES nodes): 1,048,576 faces and 524,288
-// nodes, 53.6 KB of doubles.
+// array holds the scratch of kNoAllocMaxChunks reduction chunks (53.6 KB of
+// doubles), the most any mesh uses; meshes are accepted up to 1,048,576
+// faces and 524,288 nodes (RED_FACES faces and RED_NODES nodes a chunk at
+// most).
 //
 // Set-up.  The first call made in a CUDA context (normally a device's primary
 // context) loads the library's code for that context, looks up the array's

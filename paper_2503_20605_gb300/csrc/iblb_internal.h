@@ -16,8 +16,9 @@ constexpr int TILE = 4;            // band tiles are 4x4x4 fluid cells
 constexpr int TILE_CELLS = 64;
 constexpr int MAXC = 16;           // ray crossings kept per lattice column
 constexpr int TILE_CAP = 512;      // nodes whose kernel support may touch one tile
-constexpr int RED_FACES = 2048;    // faces per chunk of the observation reductions
-constexpr int RED_NODES = 1024;    // nodes per chunk of the observation reductions
+constexpr int RED_FACES = 2048;    // at most this many faces and nodes per chunk of the observation
+constexpr int RED_NODES = 1024;    // reductions within the allocation-free call's limit (512 chunks)
+constexpr int MASS_CELLS_PER_BLOCK = 1024;   // cells per block of the lattice-mass reduction
 constexpr int VC_ITEMS = 128;      // faces (and nodes) per chunk of the volume correction
 constexpr int NRED = 8;            // partial sums per chunk (see reduce.cu)
 constexpr int RING8 = 8;           // face entries per node kept at a fixed stride

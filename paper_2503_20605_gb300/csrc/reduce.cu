@@ -4,11 +4,13 @@
 //   * contact-radius protocols (i) and (ii) of Sec. III B;
 //   * lattice mass sum_x sum_i f_i: each cell's 19 stored offsets are added
 //     in FP32 (a few rounding errors of the offsets' size, about 1e-3 of a
-//     cell's density) and the cells in FP64 with the fixed tree.
+//     cell's density) and the cells in FP64 in a fixed order and tree.
 // Every reduction uses a fixed assignment of items to threads and a fixed
 // shuffle tree, so results are bitwise reproducible and a droplet's values
 // do not depend on the other droplets of a batch.
 #include <math.h>
+
+#include <algorithm>
 
 #include "iblb_internal.h"
 #include "reduce_util.cuh"
@@ -21,20 +23,35 @@ struct MeshView {
     const int *tri;              // this droplet's faces (node indices into q*)
     int ntri;
     int node0, nnodes;           // this droplet's node range
+    int fpc, npc;                // faces and nodes per reduction chunk (mesh_chunks)
 };
 
 namespace {
 
 constexpr int RB = 256;          // threads per reduction block
 
-// chunk k of a mesh: faces [k*RED_FACES, ...) and nodes [k*RED_NODES, ...)
+// Chunks of a mesh for the observation passes: enough for every SM to
+// share the FP64 work (at least RED_MIN_FACES faces and RED_MIN_NODES nodes
+// a chunk), at most RED_MAX_CHUNKS (the allocation-free scratch's size);
+// the split depends on the mesh's size alone, so results are reproducible.
+constexpr int RED_MIN_FACES = 64, RED_MIN_NODES = 32, RED_MAX_CHUNKS = 512;
+int mesh_chunks(int nnodes, int ntri, int &fpc, int &npc)
+{
+    int nc = std::max((ntri + RED_MIN_FACES - 1) / RED_MIN_FACES, (nnodes + RED_MIN_NODES - 1) / RED_MIN_NODES);
+    nc = std::min(std::max(nc, 1), RED_MAX_CHUNKS);
+    fpc = std::max((ntri + nc - 1) / nc, 1);
+    npc = std::max((nnodes + nc - 1) / nc, 1);
+    return nc;
+}
+
+// chunk k of a mesh: faces [k*fpc, ...) and nodes [k*npc, ...)
 // -> 6V, area, sum x, sum y, sum z, z_min, z_max
 __device__ void pass1_chunk(const MeshView &m, int k, double *out)
 {
     const int KIND[7] = {0, 0, 0, 0, 0, 1, 2};
     double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};
-    const int f1 = min(m.ntri, (k + 1) * RED_FACES);
-    for (int t = k * RED_FACES + threadIdx.x; t < f1; t += RB) {
+    const int f1 = min(m.ntri, (k + 1) * m.fpc);
+    for (int t = k * m.fpc + threadIdx.x; t < f1; t += RB) {
         const int ia = m.tri[3 * t] * m.stride, ib = m.tri[3 * t + 1] * m.stride, ic = m.tri[3 * t + 2] * m.stride;
         const double ax = m.qx[ia], ay = m.qy[ia], az = m.qz[ia];
         const double bx = m.qx[ib], by = m.qy[ib], bz = m.qz[ib];
@@ -44,8 +61,8 @@ __device__ void pass1_chunk(const MeshView &m, int k, double *out)
         const double Nx = e1y * e2z - e1z * e2y, Ny = e1z * e2x - e1x * e2z, Nz = e1x * e2y - e1y * e2x;
         v[1] += 0.5 * sqrt(Nx * Nx + Ny * Ny + Nz * Nz);
     }
-    const int n1 = min(m.nnodes, (k + 1) * RED_NODES);
-    for (int j = k * RED_NODES + threadIdx.x; j < n1; j += RB) {
+    const int n1 = min(m.nnodes, (k + 1) * m.npc);
+    for (int j = k * m.npc + threadIdx.x; j < n1; j += RB) {
         const int ij = (m.node0 + j) * m.stride;
         v[2] += m.qx[ij];
         v[3] += m.qy[ij];
@@ -113,8 +130,8 @@ __global__ void __launch_bounds__(RB) pass2_view_kernel(MeshView m, const double
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const double zmid = 0.5 * (R[5] + R[6]);
     const int k = blockIdx.x;
-    const int f1 = min(m.ntri, (k + 1) * RED_FACES);
-    for (int t = k * RED_FACES + threadIdx.x; t < f1; t += RB) {
+    const int f1 = min(m.ntri, (k + 1) * m.fpc);
+    for (int t = k * m.fpc + threadIdx.x; t < f1; t += RB) {
         int idx[3] = {m.tri[3 * t], m.tri[3 * t + 1], m.tri[3 * t + 2]};
         double zz[3];
         for (int e = 0; e < 3; ++e)
@@ -156,8 +173,8 @@ __global__ void __launch_bounds__(RB) pass3_view_kernel(MeshView m, double zp, c
     double v[1] = {0.0};
     const double cx = C[0], cy = C[1];
     const int k = blockIdx.x;
-    const int f1 = min(m.ntri, (k + 1) * RED_FACES);
-    for (int t = k * RED_FACES + threadIdx.x; t < f1; t += RB)
+    const int f1 = min(m.ntri, (k + 1) * m.fpc);
+    for (int t = k * m.fpc + threadIdx.x; t < f1; t += RB)
         for (int e = 0; e < 3; ++e) {
             const int ia = m.tri[3 * t + e], ib = m.tri[3 * t + (e + 1) % 3];
             if (ia > ib)
@@ -215,50 +232,63 @@ __device__ __forceinline__ int find_drop_mass(const Drop *D, int n, int b)
     return lo;
 }
 
+// block b: cells [(b - mass_block0) MASS_CELLS_PER_BLOCK, ...) of its
+// droplet, MASS_CELLS_PER_BLOCK / RB per thread (added in FP64 in a fixed
+// order), then the fixed block tree: a quarter of the FP64 tree work per
+// cell of one cell per thread.
 template <typename S>
 __global__ void __launch_bounds__(RB) mass_kernel(Arrays a, const S *f)
 {
+    constexpr int CPT = MASS_CELLS_PER_BLOCK / RB;
+    static_assert(CPT * RB == MASS_CELLS_PER_BLOCK, "whole cells per thread");
     const int KIND[1] = {0};
     const int b = blockIdx.x;
     const int d = find_drop_mass(a.drops, a.ndrops, b);
     const Drop &D = a.drops[d];
-    const int64_t c = (int64_t)(b - D.mass_block0) * RB + threadIdx.x;
-    double v[1] = {0.0};
-    if (c < D.cells) {
-        const int64_t row = c / D.nx;
-        const S *p = f + (int64_t)Q * D.pcell0 + (c - row * D.nx) + (int64_t)D.pitch * row;
-        float cell = 0.0f;
-        for (int i = 0; i < Q; ++i)
-            cell += tof<S>(p[(int64_t)i * D.pcells]);
-        v[0] = (double)cell;
+    const int64_t cb = (int64_t)(b - D.mass_block0) * MASS_CELLS_PER_BLOCK + threadIdx.x;
+    float cell[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+        const int64_t c = cb + (int64_t)u * RB;
+        cell[u] = 0.0f;
+        if (c < D.cells) {
+            const int64_t row = c / D.nx;
+            const S *p = f + (int64_t)Q * D.pcell0 + (c - row * D.nx) + (int64_t)D.pitch * row;
+            for (int i = 0; i < Q; ++i)
+                cell[u] += tof<S>(p[(int64_t)i * D.pcells]);
+        }
     }
+    double v[1] = {0.0};
+#pragma unroll
+    for (int u = 0; u < CPT; ++u)
+        v[0] += (double)cell[u];
     block_reduce<1, RB>(v, KIND);
     if (threadIdx.x == 0)
         a.mass_part[b] = v[0];
 }
 
-__global__ void mass_fold_kernel(Arrays a, double *out)
+// one block of RB threads per droplet: thread t adds partials t, t + RB, ...,
+// then the fixed block tree
+__global__ void __launch_bounds__(RB) mass_fold_kernel(Arrays a, double *out)
 {
+    const int KIND[1] = {0};
     const Drop &D = a.drops[blockIdx.x];
-    double v = 0.0;
-    for (int i = threadIdx.x; i < D.mass_nblocks; i += 32)
-        v += a.mass_part[D.mass_block0 + i];
-    v = warp_sum(v);
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < D.mass_nblocks; i += RB)
+        v[0] += a.mass_part[D.mass_block0 + i];
+    block_reduce<1, RB>(v, KIND);
     if (threadIdx.x == 0)
-        out[blockIdx.x] = v + (double)D.rho0 * (double)D.cells;
+        out[blockIdx.x] = v[0] + (double)D.rho0 * (double)D.cells;
 }
 
 }  // namespace
 
 
 // scratch: at least NRED*nch + 32 + 4*nch + nch doubles
-static cudaError_t observe_view(const MeshView &m, double R0, double zcut_frac, double eps_flat,
-                                double *scr, double *h_out, cudaStream_t s)
+static cudaError_t observe_view(MeshView m, double R0, double zcut_frac, double eps_flat, double *scr,
+                                double *h_out, cudaStream_t s)
 {
-    const int nch = (m.ntri + RED_FACES - 1) / RED_FACES > (m.nnodes + RED_NODES - 1) / RED_NODES
-                        ? (m.ntri + RED_FACES - 1) / RED_FACES
-                        : (m.nnodes + RED_NODES - 1) / RED_NODES;
-    const int nc = nch > 0 ? nch : 1;
+    const int nc = mesh_chunks(m.nnodes, m.ntri, m.fpc, m.npc);
     double *part1 = scr;                    // NRED * nc
     double *R = scr + (int64_t)NRED * nc;  // 8 results
     double *S2 = R + 8;                     // 4 protocol sums
@@ -312,10 +342,8 @@ static cudaError_t observe_view(const MeshView &m, double R0, double zcut_frac, 
 
 int64_t observe_scratch_doubles(int n_nodes, int n_tri)
 {
-    int nch = (n_tri + RED_FACES - 1) / RED_FACES;
-    int nn = (n_nodes + RED_NODES - 1) / RED_NODES;
-    nch = nch > nn ? nch : nn;
-    nch = nch > 0 ? nch : 1;
+    int fpc = 0, npc = 0;
+    const int nch = mesh_chunks(n_nodes, n_tri, fpc, npc);
     return (int64_t)NRED * nch + 32 + 5 * (int64_t)nch + 8;
 }
 
@@ -323,7 +351,7 @@ cudaError_t launch_observe_view(const double *qx, const double *qy, const double
                                 const int *tri, int ntri, int node0, int nnodes, double R0, double zcut_frac,
                                 double eps_flat, double *scratch, double *h_out, cudaStream_t s)
 {
-    MeshView m{qx, qy, qz, stride, tri, ntri, node0, nnodes};
+    MeshView m{qx, qy, qz, stride, tri, ntri, node0, nnodes, 0, 0};
     return observe_view(m, R0, zcut_frac, eps_flat, scratch, h_out, s);
 }
 
@@ -352,7 +380,7 @@ cudaError_t launch_mass(const Arrays &a, int storage, const void *f, double *d_o
     case 2: mass_kernel<__nv_bfloat16><<<mass_blocks, RB, 0, s>>>(a, (const __nv_bfloat16 *)f); break;
     default: return cudaErrorInvalidValue;
     }
-    mass_fold_kernel<<<a.ndrops, 32, 0, s>>>(a, d_out);
+    mass_fold_kernel<<<a.ndrops, RB, 0, s>>>(a, d_out);
     return cudaGetLastError();
 }
 
