@@ -92,6 +92,10 @@ struct iblb_ctx {
     double *obs_scr = nullptr;   // scratch of the mesh observation kernels
     int64_t obs_scr_n = 0;
     unsigned long long *d_trace = nullptr;   // per-warp stamps of iblb_trace_step (allocated by its first call)
+    double *d_stage = nullptr;   // x, y, z per node of one droplet: node uploads and downloads
+    int64_t d_stage_n = 0;
+    double *h_obs = nullptr;     // pinned: 32 raw observation doubles, then one mass per droplet
+    cudaEvent_t ev_copy = nullptr;   // a node upload has left the caller's buffer
     std::string err;
 };
 
@@ -830,6 +834,19 @@ int read_status(iblb_ctx *c, bool clear, int *flags_or)
     return IBLB_OK;
 }
 
+// The staging array for one droplet's nodes (x, y, z per node), grown on demand.
+int ensure_stage(iblb_ctx *c, int64_t n)
+{
+    if (n > c->d_stage_n) {
+        dfree(c->d_stage);
+        c->d_stage = nullptr;
+        c->d_stage_n = 0;
+        CK(dalloc(&c->d_stage, (size_t)n));
+        c->d_stage_n = n;
+    }
+    return IBLB_OK;
+}
+
 int check_k(iblb_ctx *c, int k)
 {
     if (!c)
@@ -932,6 +949,9 @@ int iblb_batch_create(int n, const iblb_lattice_desc *lat, const iblb_physics_de
         (e = dalloc(&A.status, 4 * (size_t)n)) != cudaSuccess ||
         (e = dalloc(&c->d_mass, (size_t)n)) != cudaSuccess || (e = dalloc(&c->d_drops, (size_t)n)) != cudaSuccess)
         return bad(e, "cudaMalloc");
+    if ((e = cudaMallocHost(&c->h_obs, sizeof(double) * (32 + (size_t)n))) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming)) != cudaSuccess)
+        return bad(e, "cudaMallocHost");
     if ((e = cudaMallocHost(&c->h_status, sizeof(int) * 4 * n)) != cudaSuccess)
         return bad(e, "cudaMallocHost");
     A.drops = c->d_drops;
@@ -1003,6 +1023,11 @@ void iblb_destroy(iblb_ctx *c)
     dfree(c->obs_scr);
     if (c->h_status)
         cudaFreeHost(c->h_status);
+    if (c->h_obs)
+        cudaFreeHost(c->h_obs);
+    if (c->ev_copy)
+        cudaEventDestroy(c->ev_copy);
+    dfree(c->d_stage);
     for (int k = 0; k <= IBLB_NPHASE; ++k)
         if (c->ph[k])
             cudaEventDestroy(c->ph[k]);
@@ -1085,27 +1110,17 @@ int iblb_set_nodes(iblb_ctx *c, int k, const double *xyz)
     const Drop &D = c->drops[k];
     if (!D.nnodes)
         return fail(c, IBLB_E_STATE, "droplet has no membrane");
-    std::vector<double> x(D.nnodes), y(D.nnodes), z(D.nnodes);
-    for (int j = 0; j < D.nnodes; ++j) {
-        x[j] = xyz[3 * j];
-        y[j] = xyz[3 * j + 1];
-        z[j] = xyz[3 * j + 2];
-    }
     Entered entered_(c);
-    CK(cudaMemcpyAsync(c->A.qx + D.node0, x.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->A.qy + D.node0, y.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->A.qz + D.node0, z.data(), sizeof(double) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
-    std::vector<float4> qh(D.nnodes), ql(D.nnodes);
-    split_positions(x.data(), y.data(), z.data(), D.nnodes, qh.data(), ql.data());
-    CK(cudaMemcpyAsync(c->A.qh + D.node0, qh.data(), sizeof(float4) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->A.ql + D.node0, ql.data(), sizeof(float4) * D.nnodes, cudaMemcpyHostToDevice, c->stream));
+    if ((r = ensure_stage(c, 3 * (int64_t)D.nnodes)))
+        return r;
+    // one copy of the caller's x, y, z per node; the split into the position
+    // planes and their FP32 pairs runs on the device
+    CK(cudaMemcpyAsync(c->d_stage, xyz, sizeof(double) * 3 * D.nnodes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaEventRecord(c->ev_copy, c->stream));
+    CK(launch_set_nodes(c->A, c->d_stage, D.node0, D.nnodes, k, c->stream));
     // the given positions are final: no volume correction pending on them
-    const double none = 0.0;
-    CK(cudaMemcpyAsync(c->A.red_out + (int64_t)NRED * k + 5, &none, sizeof(double), cudaMemcpyHostToDevice,
-                       c->stream));
     c->mem[k].corr[5] = 0.0;
-    CK(cudaMemsetAsync(c->A.split_ok, 0, sizeof(int), c->stream));   // the previous band says nothing now
-    CK(cudaStreamSynchronize(c->stream));   // the host vectors die here
+    CK(cudaEventSynchronize(c->ev_copy));   // the caller may reuse xyz
     return IBLB_OK;
 }
 
@@ -1117,18 +1132,13 @@ int iblb_get_nodes(iblb_ctx *c, int k, double *xyz)
     const Drop &D = c->drops[k];
     if (!D.nnodes)
         return fail(c, IBLB_E_STATE, "droplet has no membrane");
-    std::vector<double> x(D.nnodes), y(D.nnodes), z(D.nnodes);
     Entered entered_(c);
-    CK(launch_corrected_positions(c->A, c->stream));   // the positions with the pending volume correction
-    CK(cudaMemcpyAsync(x.data(), c->A.px + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(y.data(), c->A.py + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(z.data(), c->A.pz + D.node0, sizeof(double) * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
+    if ((r = ensure_stage(c, 3 * (int64_t)D.nnodes)))
+        return r;
+    // the positions with the pending volume correction, interleaved on the device
+    CK(launch_corrected_positions(c->A, c->stream, c->d_stage, D.node0, D.nnodes));
+    CK(cudaMemcpyAsync(xyz, c->d_stage, sizeof(double) * 3 * D.nnodes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    for (int j = 0; j < D.nnodes; ++j) {
-        xyz[3 * j] = x[j];
-        xyz[3 * j + 1] = y[j];
-        xyz[3 * j + 2] = z[j];
-    }
     return IBLB_OK;
 }
 
@@ -1383,27 +1393,33 @@ int iblb_sync(iblb_ctx *c)
 // mesh observables and status of droplet k into out (the mass is filled by
 // the caller; the corrected positions are in c->A.p*); the observation
 // scratch is kept in the context
-int observe_mesh(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs *out)
+// Enqueue the mesh observation of droplet k (kernels and a copy of the raw
+// results to c->h_obs); observe_mesh_finish fills out once the stream has
+// passed them (and c->h_status was refreshed with them).
+int observe_mesh_enqueue(iblb_ctx *c, int k, double zcut_frac, double eps_flat)
+{
+    const Drop &D = c->drops[k];
+    if (!D.nnodes)
+        return IBLB_OK;
+    const int64_t need = observe_scratch_doubles(D.nnodes, D.ntri);
+    if (need > c->obs_scr_n) {
+        dfree(c->obs_scr);
+        c->obs_scr = nullptr;
+        c->obs_scr_n = 0;
+        CK(dalloc(&c->obs_scr, (size_t)need));
+        c->obs_scr_n = need;
+    }
+    CK(enqueue_observe(c->A.px, c->A.py, c->A.pz, c->A.clamped, c->A.tri + 3 * (int64_t)D.tri0, D.ntri, D.node0,
+                       D.nnodes, D.R0, zcut_frac, eps_flat, c->obs_scr, c->h_obs, c->stream));
+    return IBLB_OK;
+}
+
+void observe_mesh_finish(iblb_ctx *c, int k, iblb_obs *out)
 {
     const Drop &D = c->drops[k];
     if (D.nnodes) {
-        std::vector<uint8_t> cl(D.nnodes);
-        CK(cudaMemcpy(cl.data(), c->A.clamped + D.node0, D.nnodes, cudaMemcpyDeviceToHost));
-        int n = 0;
-        for (uint8_t v : cl)
-            n += v;
-        out->clamped = n;
-        const int64_t need = observe_scratch_doubles(D.nnodes, D.ntri);
-        if (need > c->obs_scr_n) {
-            dfree(c->obs_scr);
-            c->obs_scr = nullptr;
-            c->obs_scr_n = 0;
-            CK(dalloc(&c->obs_scr, (size_t)need));
-            c->obs_scr_n = need;
-        }
-        double h[13];
-        CK(launch_observe_view(c->A.px, c->A.py, c->A.pz, 1, c->A.tri + 3 * (int64_t)D.tri0, D.ntri, D.node0,
-                               D.nnodes, D.R0, zcut_frac, eps_flat, c->obs_scr, h, c->stream));
+        double h[14];
+        finish_observe(c->h_obs, D.R0, h);
         out->volume = h[0];
         out->area = h[1];
         out->centroid[0] = h[2];
@@ -1417,11 +1433,11 @@ int observe_mesh(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs
         out->rc_flat = h[10];
         out->n_cut = h[11];
         out->chi_flat = h[12];
+        out->clamped = (int)h[13];
     }
-    // this droplet's flags (c->h_status was refreshed by the caller); a
-    // bounded-wait timeout is recorded on droplet 0 and concerns every droplet
+    // this droplet's flags; a bounded-wait timeout is recorded on droplet 0
+    // and concerns every droplet
     out->status = status_code(c->h_status[4 * k] | (c->h_status[0] & ST_TIMEOUT));
-    return IBLB_OK;
 }
 
 int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs *out)
@@ -1434,14 +1450,18 @@ int iblb_observe(iblb_ctx *c, int k, double zcut_frac, double eps_flat, iblb_obs
         return fail(c, IBLB_E_ARG, "null output");
     memset(out, 0, sizeof(*out));
     Entered entered_(c);
+    // everything enqueued, one synchronisation: the mass, the corrected
+    // positions and the mesh passes, then the copies of their results and of
+    // the status words to pinned host memory
     CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
-    CK(cudaMemcpyAsync(&out->mass, c->d_mass + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    int flags = 0;
     CK(launch_corrected_positions(c->A, c->stream));
-    if ((r = read_status(c, false, &flags)))   // synchronises the stream
+    if ((r = observe_mesh_enqueue(c, k, zcut_frac, eps_flat)))
         return r;
-    if ((r = observe_mesh(c, k, zcut_frac, eps_flat, out)))
-        return r;
+    CK(cudaMemcpyAsync(c->h_obs + 32 + k, c->d_mass + k, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->h_status, c->A.status, sizeof(int) * 4 * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out->mass = c->h_obs[32 + k];
+    observe_mesh_finish(c, k, out);
     return IBLB_OK;
 }
 
@@ -1455,18 +1475,17 @@ int iblb_observe_all(iblb_ctx *c, double zcut_frac, double eps_flat, iblb_obs *o
     if (!out)
         return fail(c, IBLB_E_ARG, "null output");
     memset(out, 0, sizeof(*out) * (size_t)c->ndrops);
-    std::vector<double> mass(c->ndrops);
     Entered entered_(c);
     CK(launch_mass(c->A, c->storage, c->fbuf[c->cur], c->d_mass, c->mass_blocks, c->stream));
-    CK(cudaMemcpyAsync(mass.data(), c->d_mass, sizeof(double) * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
-    int flags = 0;
+    CK(cudaMemcpyAsync(c->h_obs + 32, c->d_mass, sizeof(double) * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->h_status, c->A.status, sizeof(int) * 4 * c->ndrops, cudaMemcpyDeviceToHost, c->stream));
     CK(launch_corrected_positions(c->A, c->stream));
-    if ((r = read_status(c, false, &flags)))
-        return r;
-    for (int k = 0; k < c->ndrops; ++k) {
-        out[k].mass = mass[k];
-        if ((r = observe_mesh(c, k, zcut_frac, eps_flat, &out[k])))
+    for (int k = 0; k < c->ndrops; ++k) {   // one droplet at a time through the shared scratch
+        if ((r = observe_mesh_enqueue(c, k, zcut_frac, eps_flat)))
             return r;
+        CK(cudaStreamSynchronize(c->stream));
+        out[k].mass = c->h_obs[32 + k];
+        observe_mesh_finish(c, k, &out[k]);
     }
     return IBLB_OK;
 }

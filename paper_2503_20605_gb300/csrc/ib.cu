@@ -1058,7 +1058,9 @@ __global__ void trace_marker_kernel(Arrays a, unsigned long long *tr)
 }
 
 // a.p* = the positions as read (the pending correction applied)
-__global__ void __launch_bounds__(IB_THREADS) corrected_positions_kernel(Arrays a)
+// and, for nodes node0 .. node0 + n - 1 when xyz is set, the same
+// positions interleaved (x, y, z per node) into xyz
+__global__ void __launch_bounds__(IB_THREADS) corrected_positions_kernel(Arrays a, double *xyz, int node0, int n)
 {
     const int j = blockIdx.x * IB_THREADS + threadIdx.x;
     if (j >= a.total_nodes)
@@ -1073,6 +1075,35 @@ __global__ void __launch_bounds__(IB_THREADS) corrected_positions_kernel(Arrays 
     a.px[j] = x;
     a.py[j] = y;
     a.pz[j] = z;
+    if (xyz && j >= node0 && j < node0 + n) {
+        double *o = xyz + 3 * (int64_t)(j - node0);
+        o[0] = x;
+        o[1] = y;
+        o[2] = z;
+    }
+}
+
+// Positions of droplet k's nodes node0 .. node0 + n - 1 from xyz (x, y, z
+// per node), final (no volume correction pending for the droplet), with
+// their FP32 pairs; the previous band no longer predicts this step's.
+__global__ void __launch_bounds__(IB_THREADS) set_nodes_kernel(Arrays a, const double *xyz, int node0, int n, int k)
+{
+    const int j = blockIdx.x * IB_THREADS + threadIdx.x;
+    if (j == 0) {
+        a.red_out[(int64_t)NRED * k + 5] = 0.0;
+        *a.split_ok = 0;
+    }
+    if (j >= n)
+        return;
+    const double *p = xyz + 3 * (int64_t)j;
+    const double x = p[0], y = p[1], z = p[2];
+    const int g = node0 + j;
+    a.qx[g] = x;
+    a.qy[g] = y;
+    a.qz[g] = z;
+    const float hx = dtof_rn(x), hy = dtof_rn(y), hz = dtof_rn(z);
+    a.qh[g] = make_float4(hx, hy, hz, 0.0f);
+    a.ql[g] = make_float4(dtof_rn(x - (double)hx), dtof_rn(y - (double)hy), dtof_rn(z - (double)hz), 0.0f);
 }
 
 // Before the stream-collide kernel: forces and tile lists of every node,
@@ -1223,11 +1254,18 @@ cudaError_t launch_volume_correction(const Arrays &a, int n_chunks_total, cudaSt
                                  a.pdl != 0, a, (unsigned long long *)nullptr);
 }
 
-cudaError_t launch_corrected_positions(const Arrays &a, cudaStream_t s)
+cudaError_t launch_corrected_positions(const Arrays &a, cudaStream_t s, double *xyz, int node0, int n)
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    corrected_positions_kernel<<<(a.total_nodes + IB_THREADS - 1) / IB_THREADS, IB_THREADS, 0, s>>>(a);
+    corrected_positions_kernel<<<(a.total_nodes + IB_THREADS - 1) / IB_THREADS, IB_THREADS, 0, s>>>(a, xyz, node0,
+                                                                                                  n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_nodes(const Arrays &a, const double *xyz, int node0, int n, int k, cudaStream_t s)
+{
+    set_nodes_kernel<<<(n + IB_THREADS - 1) / IB_THREADS, IB_THREADS, 0, s>>>(a, xyz, node0, n, k);
     return cudaGetLastError();
 }
 

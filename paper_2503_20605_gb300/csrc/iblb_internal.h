@@ -251,7 +251,11 @@ cudaError_t launch_mass(const Arrays &a, int storage, const void *f, double *d_o
                         cudaStream_t s);
 // Corrected positions of every node into a.px, a.py, a.pz (the pending
 // volume correction applied; a plain copy where none is pending).
-cudaError_t launch_corrected_positions(const Arrays &a, cudaStream_t s);
+cudaError_t launch_corrected_positions(const Arrays &a, cudaStream_t s, double *xyz = nullptr, int node0 = 0,
+                                       int n = 0);
+// Droplet k's nodes node0 .. node0 + n - 1 set from the device array xyz
+// (x, y, z per node), with no volume correction pending for the droplet.
+cudaError_t launch_set_nodes(const Arrays &a, const double *xyz, int node0, int n, int k, cudaStream_t s);
 // Observables of one mesh: node j at q*[j * stride]; tri holds node indices
 // into q*; nodes node0 .. node0 + nnodes - 1.  Writes 13 doubles to h_out
 // (volume, area, centroid[3], zmin, zmax, theta_R0, theta_RV, rc_cut,
@@ -260,6 +264,15 @@ int64_t observe_scratch_doubles(int n_nodes, int n_tri);
 cudaError_t launch_observe_view(const double *qx, const double *qy, const double *qz, int stride,
                                 const int *tri, int ntri, int node0, int nnodes, double R0, double zcut_frac,
                                 double eps_flat, double *scratch, double *h_out, cudaStream_t s);
+// The same for a context's droplet (positions with stride 1, and the
+// near-wall guard's per-node flags, counted as a fourteenth value) without
+// the synchronisation: the kernels and a copy of 32 raw doubles to hv (host,
+// pinned) are enqueued on s; once s has passed them, finish_observe turns hv
+// into the 14 values.
+cudaError_t enqueue_observe(const double *qx, const double *qy, const double *qz, const uint8_t *clamped,
+                            const int *tri, int ntri, int node0, int nnodes, double R0, double zcut_frac,
+                            double eps_flat, double *scratch, double *hv, cudaStream_t s);
+void finish_observe(const double *hv, double R0, double *h_out);
 // Bring the code of the observation kernels onto the current device now
 // (module loading is lazy by default, and a load allocates device memory).
 cudaError_t preload_observe_kernels();

@@ -24,6 +24,7 @@ struct MeshView {
     int ntri;
     int node0, nnodes;           // this droplet's node range
     int fpc, npc;                // faces and nodes per reduction chunk (mesh_chunks)
+    const uint8_t *clamped;      // per node (global index): clamped by the near-wall guard, or nullptr
 };
 
 namespace {
@@ -45,11 +46,11 @@ int mesh_chunks(int nnodes, int ntri, int &fpc, int &npc)
 }
 
 // chunk k of a mesh: faces [k*fpc, ...) and nodes [k*npc, ...)
-// -> 6V, area, sum x, sum y, sum z, z_min, z_max
+// -> 6V, area, sum x, sum y, sum z, z_min, z_max, clamped nodes
 __device__ void pass1_chunk(const MeshView &m, int k, double *out)
 {
-    const int KIND[7] = {0, 0, 0, 0, 0, 1, 2};
-    double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};
+    const int KIND[8] = {0, 0, 0, 0, 0, 1, 2, 0};
+    double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY, 0.0};
     const int f1 = min(m.ntri, (k + 1) * m.fpc);
     for (int t = k * m.fpc + threadIdx.x; t < f1; t += RB) {
         const int ia = m.tri[3 * t] * m.stride, ib = m.tri[3 * t + 1] * m.stride, ic = m.tri[3 * t + 2] * m.stride;
@@ -64,6 +65,8 @@ __device__ void pass1_chunk(const MeshView &m, int k, double *out)
     const int n1 = min(m.nnodes, (k + 1) * m.npc);
     for (int j = k * m.npc + threadIdx.x; j < n1; j += RB) {
         const int ij = (m.node0 + j) * m.stride;
+        if (m.clamped)
+            v[7] += (double)m.clamped[m.node0 + j];
         v[2] += m.qx[ij];
         v[3] += m.qy[ij];
         const double z = m.qz[ij];
@@ -71,30 +74,32 @@ __device__ void pass1_chunk(const MeshView &m, int k, double *out)
         v[5] = fmin(v[5], z);
         v[6] = fmax(v[6], z);
     }
-    block_reduce<7, RB>(v, KIND);
+    block_reduce<8, RB>(v, KIND);
     if (threadIdx.x == 0)
-        for (int i = 0; i < 7; ++i)
+        for (int i = 0; i < 8; ++i)
             out[i] = v[i];
 }
 
 // Fold the chunks of droplet blockIdx.x (one warp; chunk i goes to lane i % 32,
 // lanes add their chunks in order, then a fixed shuffle tree).  Writes
-// V, A, cx, cy, cz, zmin, zmax.
+// V, A, cx, cy, cz, zmin, zmax, clamped nodes.
 __device__ void fold_chunks(const double *part, int nch, int nnodes, double *out)
 {
     const int lane = threadIdx.x;
-    double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};
+    double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY, 0.0};
     for (int i = lane; i < nch; i += 32) {
         const double *p = part + (int64_t)NRED * i;
         for (int k = 0; k < 5; ++k)
             v[k] += p[k];
         v[5] = fmin(v[5], p[5]);
         v[6] = fmax(v[6], p[6]);
+        v[7] += p[7];
     }
     for (int k = 0; k < 5; ++k)
         v[k] = warp_sum(v[k]);
     v[5] = warp_min(v[5]);
     v[6] = warp_max(v[6]);
+    v[7] = warp_sum(v[7]);
     if (lane == 0) {
         out[0] = v[0] / 6.0;
         out[1] = v[1];
@@ -103,12 +108,13 @@ __device__ void fold_chunks(const double *part, int nch, int nnodes, double *out
         out[4] = v[4] / nnodes;
         out[5] = v[5];
         out[6] = v[6];
+        out[7] = v[7];
     }
 }
 
 // --- observation of one mesh (view), used by iblb_observe and the stateless
 //     entry point.  scratch layout (doubles): [0, NRED*nch) chunk partials,
-//     then 8 result slots R: V, A, cx, cy, cz, zmin, zmax, -, then protocol
+//     then 8 result slots R: V, A, cx, cy, cz, zmin, zmax, clamped, then protocol
 //     partials.
 
 __global__ void __launch_bounds__(RB) pass1_view_kernel(MeshView m, double *part)
@@ -285,8 +291,12 @@ __global__ void __launch_bounds__(RB) mass_fold_kernel(Arrays a, double *out)
 
 
 // scratch: at least NRED*nch + 32 + 4*nch + nch doubles
-static cudaError_t observe_view(MeshView m, double R0, double zcut_frac, double eps_flat, double *scr,
-                                double *h_out, cudaStream_t s)
+// Enqueue the observation of a mesh on s: the three passes and their folds,
+// then a copy of the 32 result doubles to hv (host; pinned for an
+// asynchronous copy).  observe_view_finish turns them into the observables
+// once s has reached that point.
+static cudaError_t observe_view_enqueue(MeshView m, double R0, double zcut_frac, double eps_flat, double *scr,
+                                        double *hv, cudaStream_t s)
 {
     const int nc = mesh_chunks(m.nnodes, m.ntri, m.fpc, m.npc);
     double *part1 = scr;                    // NRED * nc
@@ -307,14 +317,14 @@ static cudaError_t observe_view(MeshView m, double R0, double zcut_frac, double 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    double hv[32];
-    e = cudaMemcpyAsync(hv, R, sizeof(double) * 32, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess)
-        return e;
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess)
-        return e;
-    // hv: R[0..6], S2 at 8..11, Cc at 12..13, S3 at 14
+    return cudaMemcpyAsync(hv, R, sizeof(double) * 32, cudaMemcpyDeviceToHost, s);
+}
+
+// h_out: V, A, cx, cy, cz, zmin, zmax, theta(R0), theta(R_V), rc_cut,
+// rc_flat, n_cut, chi_flat, clamped nodes
+static void observe_view_finish(const double *hv, double R0, double *h_out)
+{
+    // hv: R[0..7], S2 at 8..11, Cc at 12..13, S3 at 14
     const double V = hv[0], A = hv[1], zmin = hv[5], zmax = hv[6];
     const double ell = 0.5 * (zmax - zmin);
     const double RV = cbrt(3.0 * V / (4.0 * M_PI));
@@ -337,7 +347,7 @@ static cudaError_t observe_view(MeshView m, double R0, double zcut_frac, double 
     h_out[10] = sqrt(hv[11] / M_PI);                  // rc_flat
     h_out[11] = hv[10];                               // n_cut
     h_out[12] = hv[11];                               // chi_flat
-    return cudaSuccess;
+    h_out[13] = hv[7];                                // clamped nodes
 }
 
 int64_t observe_scratch_doubles(int n_nodes, int n_tri)
@@ -351,9 +361,28 @@ cudaError_t launch_observe_view(const double *qx, const double *qy, const double
                                 const int *tri, int ntri, int node0, int nnodes, double R0, double zcut_frac,
                                 double eps_flat, double *scratch, double *h_out, cudaStream_t s)
 {
-    MeshView m{qx, qy, qz, stride, tri, ntri, node0, nnodes, 0, 0};
-    return observe_view(m, R0, zcut_frac, eps_flat, scratch, h_out, s);
+    MeshView m{qx, qy, qz, stride, tri, ntri, node0, nnodes, 0, 0, nullptr};
+    double hv[32], t[14];
+    cudaError_t e = observe_view_enqueue(m, R0, zcut_frac, eps_flat, scratch, hv, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return e;
+    observe_view_finish(hv, R0, t);
+    for (int i = 0; i < 13; ++i)   // the first 13 (no clamped count for a bare mesh)
+        h_out[i] = t[i];
+    return cudaSuccess;
 }
+
+cudaError_t enqueue_observe(const double *qx, const double *qy, const double *qz, const uint8_t *clamped,
+                            const int *tri, int ntri, int node0, int nnodes, double R0, double zcut_frac,
+                            double eps_flat, double *scratch, double *hv, cudaStream_t s)
+{
+    MeshView m{qx, qy, qz, 1, tri, ntri, node0, nnodes, 0, 0, clamped};
+    return observe_view_enqueue(m, R0, zcut_frac, eps_flat, scratch, hv, s);
+}
+
+void finish_observe(const double *hv, double R0, double *h_out) { observe_view_finish(hv, R0, h_out); }
 
 cudaError_t preload_observe_kernels()
 {
