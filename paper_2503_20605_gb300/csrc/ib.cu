@@ -1062,6 +1062,7 @@ __global__ void trace_marker_kernel(Arrays a, unsigned long long *tr)
 // positions interleaved (x, y, z per node) into xyz
 __global__ void __launch_bounds__(IB_THREADS) corrected_positions_kernel(Arrays a, double *xyz, int node0, int n)
 {
+    griddep_wait();
     const int j = blockIdx.x * IB_THREADS + threadIdx.x;
     if (j >= a.total_nodes)
         return;
@@ -1258,9 +1259,8 @@ cudaError_t launch_corrected_positions(const Arrays &a, cudaStream_t s, double *
 {
     if (a.total_nodes <= 0)
         return cudaSuccess;
-    corrected_positions_kernel<<<(a.total_nodes + IB_THREADS - 1) / IB_THREADS, IB_THREADS, 0, s>>>(a, xyz, node0,
-                                                                                                  n);
-    return cudaGetLastError();
+    return launch_k(corrected_positions_kernel, dim3((a.total_nodes + IB_THREADS - 1) / IB_THREADS),
+                    dim3(IB_THREADS), 0, s, a.pdl != 0, a, xyz, node0, n);
 }
 
 cudaError_t launch_set_nodes(const Arrays &a, const double *xyz, int node0, int n, int k, cudaStream_t s)

@@ -119,11 +119,13 @@ __device__ void fold_chunks(const double *part, int nch, int nnodes, double *out
 
 __global__ void __launch_bounds__(RB) pass1_view_kernel(MeshView m, double *part)
 {
+    griddep_wait();
     pass1_chunk(m, blockIdx.x, part + (int64_t)NRED * blockIdx.x);
 }
 
 __global__ void fold_view_kernel(MeshView m, const double *part, int nch, double *R)
 {
+    griddep_wait();
     fold_chunks(part, nch, m.nnodes, R);
 }
 
@@ -132,6 +134,7 @@ __global__ void fold_view_kernel(MeshView m, const double *part, int nch, double
 __global__ void __launch_bounds__(RB) pass2_view_kernel(MeshView m, const double *R, double zp, double flat,
                                                         double *part)
 {
+    griddep_wait();
     const int KIND[4] = {0, 0, 0, 0};
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const double zmid = 0.5 * (R[5] + R[6]);
@@ -175,6 +178,7 @@ __global__ void __launch_bounds__(RB) pass2_view_kernel(MeshView m, const double
 // protocol (i) second pass: sum of distances of the crossings from their centre
 __global__ void __launch_bounds__(RB) pass3_view_kernel(MeshView m, double zp, const double *C, double *part)
 {
+    griddep_wait();
     const int KIND[1] = {0};
     double v[1] = {0.0};
     const double cx = C[0], cy = C[1];
@@ -203,6 +207,7 @@ __global__ void __launch_bounds__(RB) pass3_view_kernel(MeshView m, double zp, c
 // with center != NULL also writes the crossing centre (sum x / count, sum y / count)
 __global__ void fold_sums_kernel(const double *part, int nch, int width, double *out, double *center)
 {
+    griddep_wait();
     const int lane = threadIdx.x;
     for (int k = 0; k < width; ++k) {
         double v = 0.0;
@@ -245,6 +250,7 @@ __device__ __forceinline__ int find_drop_mass(const Drop *D, int n, int b)
 template <typename S>
 __global__ void __launch_bounds__(RB) mass_kernel(Arrays a, const S *f)
 {
+    griddep_wait();
     constexpr int CPT = MASS_CELLS_PER_BLOCK / RB;
     static_assert(CPT * RB == MASS_CELLS_PER_BLOCK, "whole cells per thread");
     const int KIND[1] = {0};
@@ -277,6 +283,7 @@ __global__ void __launch_bounds__(RB) mass_kernel(Arrays a, const S *f)
 // then the fixed block tree
 __global__ void __launch_bounds__(RB) mass_fold_kernel(Arrays a, double *out)
 {
+    griddep_wait();
     const int KIND[1] = {0};
     const Drop &D = a.drops[blockIdx.x];
     double v[1] = {0.0};
@@ -308,14 +315,20 @@ static cudaError_t observe_view_enqueue(MeshView m, double R0, double zcut_frac,
     double *part3 = part2 + 4 * (int64_t)nc;  // nc
     const double zp = 0.5 + zcut_frac * R0;
     const double flat = eps_flat * R0;
-    pass1_view_kernel<<<nc, RB, 0, s>>>(m, part1);
-    fold_view_kernel<<<1, 32, 0, s>>>(m, part1, nc, R);
-    pass2_view_kernel<<<nc, RB, 0, s>>>(m, R, zp, flat, part2);
-    fold_sums_kernel<<<1, 32, 0, s>>>(part2, nc, 4, S2, Cc);
-    pass3_view_kernel<<<nc, RB, 0, s>>>(m, zp, Cc, part3);
-    fold_sums_kernel<<<1, 32, 0, s>>>(part3, nc, 1, S3, nullptr);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
+    // chained by programmatic dependent launch: each kernel waits for the
+    // previous one before reading its results
+    cudaError_t e;
+    if ((e = launch_k(pass1_view_kernel, dim3(nc), dim3(RB), 0, s, true, m, part1)) != cudaSuccess ||
+        (e = launch_k(fold_view_kernel, dim3(1), dim3(32), 0, s, true, m, (const double *)part1, nc, R)) !=
+            cudaSuccess ||
+        (e = launch_k(pass2_view_kernel, dim3(nc), dim3(RB), 0, s, true, m, (const double *)R, zp, flat, part2)) !=
+            cudaSuccess ||
+        (e = launch_k(fold_sums_kernel, dim3(1), dim3(32), 0, s, true, (const double *)part2, nc, 4, S2, Cc)) !=
+            cudaSuccess ||
+        (e = launch_k(pass3_view_kernel, dim3(nc), dim3(RB), 0, s, true, m, zp, (const double *)Cc, part3)) !=
+            cudaSuccess ||
+        (e = launch_k(fold_sums_kernel, dim3(1), dim3(32), 0, s, true, (const double *)part3, nc, 1, S3,
+                      (double *)nullptr)) != cudaSuccess)
         return e;
     return cudaMemcpyAsync(hv, R, sizeof(double) * 32, cudaMemcpyDeviceToHost, s);
 }
@@ -403,14 +416,19 @@ cudaError_t preload_observe_kernels()
 cudaError_t launch_mass(const Arrays &a, int storage, const void *f, double *d_out, int mass_blocks,
                         cudaStream_t s)
 {
+    cudaError_t e;
     switch (storage) {
-    case 0: mass_kernel<float><<<mass_blocks, RB, 0, s>>>(a, (const float *)f); break;
-    case 1: mass_kernel<__half><<<mass_blocks, RB, 0, s>>>(a, (const __half *)f); break;
-    case 2: mass_kernel<__nv_bfloat16><<<mass_blocks, RB, 0, s>>>(a, (const __nv_bfloat16 *)f); break;
+    case 0: e = launch_k(mass_kernel<float>, dim3(mass_blocks), dim3(RB), 0, s, true, a, (const float *)f); break;
+    case 1: e = launch_k(mass_kernel<__half>, dim3(mass_blocks), dim3(RB), 0, s, true, a, (const __half *)f); break;
+    case 2:
+        e = launch_k(mass_kernel<__nv_bfloat16>, dim3(mass_blocks), dim3(RB), 0, s, true, a,
+                     (const __nv_bfloat16 *)f);
+        break;
     default: return cudaErrorInvalidValue;
     }
-    mass_fold_kernel<<<a.ndrops, RB, 0, s>>>(a, d_out);
-    return cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    return launch_k(mass_fold_kernel, dim3(a.ndrops), dim3(RB), 0, s, true, a, d_out);
 }
 
 }  // namespace iblb
