@@ -244,7 +244,14 @@ int iblb_set_membrane(iblb_ctx *ctx, int k, const double *xyz, int n_nodes, cons
  * outside), and IBLB_E_ARG for NULL arrays. */
 int iblb_check_mesh(const double *xyz, int n_nodes, const int32_t *tri, int n_tri, double *volume);
 
-/* Overwrite / read the node positions of droplet k (host, 3*n_nodes doubles). */
+/* Overwrite / read the node positions of droplet k (host, 3*n_nodes doubles,
+ * x, y, z per node; pinned host memory makes the transfer asynchronous up to
+ * the call's return).  iblb_set_nodes makes the positions final (no volume
+ * correction pending) and returns once xyz has been copied, so the caller may
+ * reuse it; the device work it queued runs in stream order.  iblb_get_nodes
+ * returns the positions with any pending volume correction applied and
+ * synchronises the context's stream.  IBLB_E_STATE for a droplet without a
+ * membrane; CUDA errors as elsewhere. */
 int iblb_set_nodes(iblb_ctx *ctx, int k, const double *xyz);
 int iblb_get_nodes(iblb_ctx *ctx, int k, double *xyz);
 
