@@ -43,3 +43,33 @@ def test_traffic_file_is_read_only_for_the_current_kernel_source():
         else:
             assert got is None
     assert bench.ncu_traffic("no-such-storage") is None
+
+
+def test_in_step_reduction_of_traced_steps():
+    """bench.in_step: each kernel's time is its first start to its end (the
+    next kernel's first start), medians over steps; the membrane share is
+    the traced span minus the stream-collide kernel."""
+    sys.path.insert(0, ROOT)
+    import bench
+    names = ("force", "spread", "lb", "interp", "vc")
+
+    def step(starts, end):
+        ends = list(starts[1:]) + [end]
+        return {k: {"first_start_us": s, "median_start_us": s, "last_start_us": s, "end_us": e, "warps": 4}
+                for k, s, e in zip(names, starts, ends)}
+
+    tr = [step((0.0, 8.0, 16.0, 48.0, 54.0), 60.0), step((0.0, 9.0, 17.0, 50.0, 57.0), 64.0),
+          step((0.0, 8.5, 16.5, 49.0, 55.0), 61.0)]
+    out = bench.in_step(tr)
+    assert out["steps"] == 3
+    assert out["force"] == 8.5 and out["spread"] == 8.0 and out["lb"] == 32.5
+    assert out["interp"] == 6.0 and out["vc"] == 6.0
+    assert out["span"] == 61.0
+    assert out["membrane"] == 61.0 - 32.5
+
+
+def test_whole_job_rate_counts_every_rank():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.whole_job_mlups(2_000_000, 100, 100.0, 1) == 2000.0
+    assert bench.whole_job_mlups(2_000_000, 100, 100.0, 4) == 8000.0
