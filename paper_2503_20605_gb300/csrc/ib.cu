@@ -583,21 +583,30 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
     const int tid = threadIdx.x;
     const int nact = min(a.n_active[cur], a.active_cap);
     const int2 *list = a.active + (int64_t)cur * a.active_cap;
+    // a block's next tile is looked up while it works on the current one:
+    // its list entry at once, its count and first key once the entry is in
+    // (a thread's first key slot is loaded whatever the count: the tile's
+    // list has TILE_CAP slots, and slots beyond the count are not used)
+    int2 te_n = bid < nact ? list[bid] : make_int2(0, 0);
+    int cnt_n = -1, key0_n = 0x7fffffff;
     for (int it = bid; it < nact; it += nb) {
-        const int2 te = list[it];
+        const int2 te = te_n;
+        if (it + nb < nact)
+            te_n = list[it + nb];
         const int64_t T = te.x;
         const int d = a.ndrops == 1 ? 0 : find_drop_tile(a.drops, a.ndrops, T);
         const Drop &D = a.drops[d];
         const int X0 = 4 * (te.y & 2047), Y0 = 4 * ((te.y >> 11) & 2047), Z0 = 4 * (te.y >> 22);
         const int64_t e0 = T * TILE_CAP;
-        const int cnt = min(a.bin_cnt[T], TILE_CAP);     // overflow was flagged by the force kernel
+        // (overflow was flagged by the force kernel)
+        const int cnt = min(cnt_n >= 0 ? cnt_n : a.bin_cnt[T], TILE_CAP);
         int key[HK];
 #pragma unroll
         for (int h = 0; h < HK; ++h) {
             const int e = tid + h * NT;
             key[h] = 0x7fffffff;
             if (e < cnt) {
-                key[h] = a.tile_list[e0 + e];
+                key[h] = (h == 0 && cnt_n >= 0) ? key0_n : a.tile_list[e0 + e];
                 sm.node[e] = key[h];
             }
         }
@@ -619,6 +628,10 @@ __device__ void spread_tiles(const Arrays &a, uint32_t gen, int cur, int bid, in
                 }
                 rank[h] = r;
             }
+        }
+        if (it + nb < nact) {   // the next tile's count and first key
+            cnt_n = a.bin_cnt[te_n.x];
+            key0_n = a.tile_list[(int64_t)te_n.x * TILE_CAP + tid];
         }
         // part sums: thread t < 16 SPREAD_PARTS takes part t / 16 of the
         // four cells of x-row t % 16 (y = row & 3, z = row >> 2 in the tile),
